@@ -1,0 +1,421 @@
+"""CPU oracle for the quantized MLS-MPM step (ctypes wrapper over ``liboracle.so``).
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow, single-threaded FP64 C that restates what the
+hot path computes, written from the paper ("Automatic Quantization for Physics-Based
+Simulation", Liu et al. 2022): the fixed-point codec of Sec. 3.1 (Eq. 3), the dithered
+store of Sec. 5 (Eq. 11), the bit pack placement of Sec. 7, the quantized step of
+Eq. 1 on the MLS-MPM simulator of Sec. 8.1 and the bit-allocation solve of Sec. 4
+(Eq. 6-10, Algorithm 1).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference legs of ``bench.py`` may import it.  It shares no code with
+the CUDA library and never imports it.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+NEOHOOKEAN, COROTATED, FLUID = 0, 1, 2
+MATERIALS = {"neohookean": NEOHOOKEAN, "corotated": COROTATED, "fluid": FLUID}
+MAX_COMP = 24
+N_STATS = 13
+
+
+class Phys(ct.Structure):
+    _fields_ = [("dim", ct.c_int), ("material", ct.c_int), ("grid_log2", ct.c_int),
+                ("bound", ct.c_int), ("dt", ct.c_double), ("E", ct.c_double),
+                ("nu", ct.c_double), ("bulk", ct.c_double), ("p_vol", ct.c_double),
+                ("p_mass", ct.c_double), ("gravity", ct.c_double * 3)]
+
+
+class Codec(ct.Structure):
+    _fields_ = [("n_comp", ct.c_int), ("n_words", ct.c_int),
+                ("bits", ct.c_int * MAX_COMP), ("frac", ct.c_int * MAX_COMP),
+                ("offset", ct.c_int64 * MAX_COMP), ("bitpos", ct.c_int * MAX_COMP),
+                ("field", ct.c_int * MAX_COMP), ("seed", ct.c_uint64), ("dither", ct.c_int)]
+
+
+class SolveIn(ct.Structure):
+    _fields_ = [("H", ct.c_int), ("P", ct.c_double * 8), ("g", ct.c_double * 8),
+                ("lo", ct.c_double * 8), ("hi", ct.c_double * 8), ("kappa", ct.c_double),
+                ("z", ct.c_double), ("eps", ct.c_double), ("mode", ct.c_int),
+                ("rounding", ct.c_int)]
+
+
+class SolveOut(ct.Structure):
+    _fields_ = [("delta_cont", ct.c_double * 8), ("bits_paper", ct.c_int * 8),
+                ("bits", ct.c_int * 8), ("frac", ct.c_int * 8), ("offset", ct.c_int64 * 8),
+                ("pred_err", ct.c_double), ("total_bits", ct.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        P = ct.POINTER
+        d, i64, u32 = ct.c_double, ct.c_int64, ct.c_uint32
+        L.or_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+        L.or_dither_draw.argtypes = [ct.c_uint64, u32, u32, ct.c_int]
+        L.or_dither_draw.restype = u32
+        L.or_encode.argtypes = [d, ct.c_int, ct.c_int, i64, ct.c_int, u32, P(ct.c_int)]
+        L.or_encode.restype = u32
+        L.or_decode.argtypes = [u32, ct.c_int, i64]
+        L.or_decode.restype = d
+        L.or_n_comp.argtypes = [ct.c_int, ct.c_int]
+        L.or_layout.argtypes = [ct.c_int, ct.c_int, P(ct.c_int), P(ct.c_int), P(ct.c_int),
+                                P(ct.c_int)]
+        L.or_pack.argtypes = [ct.c_int, P(ct.c_int), P(ct.c_int), ct.c_int, P(u32), P(u32)]
+        L.or_unpack.argtypes = [ct.c_int, P(ct.c_int), P(ct.c_int), P(u32), P(u32)]
+        L.or_polar2.argtypes = [P(d), P(d)]
+        L.or_polar3.argtypes = [P(d), P(d)]
+        L.or_kirchhoff.argtypes = [P(Phys), P(d), P(d)]
+        L.or_n_nodes.argtypes = [P(Phys)]
+        L.or_p2g.argtypes = [P(Phys), i64, P(d), P(d)]
+        L.or_p2g.restype = i64
+        L.or_grid_update.argtypes = [P(Phys), P(d)]
+        L.or_g2p.argtypes = [P(Phys), i64, P(d), P(d)]
+        L.or_g2p.restype = i64
+        L.or_step_fp64.argtypes = [P(Phys), i64, P(d), P(d)]
+        L.or_step_fp64.restype = i64
+        L.or_encode_state.argtypes = [P(Codec), i64, P(d), u32, P(u32), P(i64)]
+        L.or_decode_state.argtypes = [P(Codec), i64, P(u32), P(d)]
+        L.or_step_quant.argtypes = [P(Phys), P(Codec), i64, P(u32), u32, P(d), P(d), P(i64)]
+        L.or_tile_keys.argtypes = [P(Phys), i64, P(d), P(i64)]
+        L.or_stable_sort.argtypes = [i64, P(i64), i64, P(i64)]
+        L.or_n_keys.argtypes = [P(Phys)]
+        L.or_n_keys.restype = i64
+        L.or_mean_sq_pos.argtypes = [ct.c_int, ct.c_int, i64, P(d)]
+        L.or_mean_sq_pos.restype = d
+        L.or_scheme_solve.argtypes = [P(SolveIn), P(SolveOut)]
+        L.or_scheme_bruteforce.argtypes = [P(SolveIn), ct.c_int, ct.c_int, P(SolveOut)]
+        if hasattr(L, "or_adjoint_step"):
+            _bind_adjoint(L)
+        _lib = L
+    return _lib
+
+
+def _bind_adjoint(L):
+    P = ct.POINTER
+    d, i64 = ct.c_double, ct.c_int64
+    L.or_adjoint_step.argtypes = [P(Phys), i64, P(d), P(d), P(d), P(d)]
+
+
+def _p(a, ctype):
+    return a.ctypes.data_as(ct.POINTER(ctype))
+
+
+# ------------------------------------------------------------------------------ codec
+def philox(ctr, key):
+    c = (ct.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ct.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ct.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def dither_draw(seed, slot, step, comp):
+    return int(lib().or_dither_draw(seed, slot, step, comp))
+
+
+def encode(v, bits, frac, offset, dither=False, r=0):
+    fl = ct.c_int(0)
+    u = lib().or_encode(float(v), bits, frac, int(offset), int(bool(dither)), int(r), ct.byref(fl))
+    return int(u), int(fl.value)
+
+
+def decode(u, frac, offset):
+    return float(lib().or_decode(int(u), frac, int(offset)))
+
+
+def n_comp(dim, material):
+    return int(lib().or_n_comp(dim, MATERIALS.get(material, material)))
+
+
+def comp_fields(dim, material):
+    nc = n_comp(dim, material)
+    out = []
+    for c in range(nc):
+        out.append(0 if c < dim else 1 if c < 2 * dim else 2 if c < 2 * dim + dim * dim else 3)
+    return out
+
+
+def layout(dim, material, bits, container=(0, 0, 0, 0)):
+    nc = n_comp(dim, material)
+    b = (ct.c_int * MAX_COMP)(*bits)
+    cont = (ct.c_int * 4)(*container)
+    pos = (ct.c_int * MAX_COMP)()
+    nw = ct.c_int(0)
+    rc = lib().or_layout(dim, MATERIALS.get(material, material), b, cont, pos, ct.byref(nw))
+    if rc != 0:
+        raise ValueError("layout rejected")
+    return [int(pos[c]) for c in range(nc)], int(nw.value)
+
+
+def pack(bits, bitpos, n_words, u):
+    nc = len(bits)
+    b = (ct.c_int * MAX_COMP)(*bits)
+    p = (ct.c_int * MAX_COMP)(*bitpos)
+    uu = (ct.c_uint32 * MAX_COMP)(*[int(x) for x in u])
+    w = (ct.c_uint32 * max(n_words, 1))()
+    lib().or_pack(nc, b, p, n_words, uu, w)
+    return [int(w[i]) for i in range(n_words)]
+
+
+def unpack(bits, bitpos, words):
+    nc = len(bits)
+    b = (ct.c_int * MAX_COMP)(*bits)
+    p = (ct.c_int * MAX_COMP)(*bitpos)
+    w = (ct.c_uint32 * (len(words) + 1))(*[int(x) for x in words])
+    uu = (ct.c_uint32 * MAX_COMP)()
+    lib().or_unpack(nc, b, p, w, uu)
+    return [int(uu[c]) for c in range(nc)]
+
+
+# ------------------------------------------------------------------------------ scenes
+def make_phys(scene):
+    ph = Phys()
+    ph.dim = scene["dim"]
+    ph.material = MATERIALS[scene["material"]]
+    ph.grid_log2 = scene["grid_log2"]
+    ph.bound = scene.get("bound", 3)
+    ph.dt = scene["dt"]
+    ph.E = scene.get("E", 0.0)
+    ph.nu = scene.get("nu", 0.0)
+    ph.bulk = scene.get("bulk", 0.0)
+    ph.p_vol = scene["p_vol"]
+    ph.p_mass = scene["p_vol"] * scene.get("rho", 1.0)
+    g = list(scene.get("gravity", (0.0, -9.8, 0.0))) + [0.0, 0.0, 0.0]
+    for a in range(3):
+        ph.gravity[a] = g[a]
+    return ph
+
+
+def make_codec(scene, scheme):
+    """Expand a per-field scheme {"x": {bits, frac, offset, container}, ...} into the
+    per-component codec.  Field order is x, v, C, then F (or J)."""
+    dim, mat = scene["dim"], scene["material"]
+    nc = n_comp(dim, mat)
+    fields = comp_fields(dim, mat)
+    names = ["x", "v", "C", "J" if mat == "fluid" else "F"]
+    bits = [scheme[names[h]]["bits"] for h in fields]
+    container = [scheme[names[h]].get("container", 0) for h in range(4)]
+    pos, nw = layout(dim, mat, bits, container)
+    cd = Codec()
+    cd.n_comp = nc
+    cd.n_words = nw
+    for c in range(nc):
+        f = scheme[names[fields[c]]]
+        cd.bits[c] = f["bits"]
+        cd.frac[c] = f["frac"]
+        cd.offset[c] = int(f["offset"])
+        cd.bitpos[c] = pos[c]
+        cd.field[c] = fields[c]
+    cd.seed = int(scene.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    cd.dither = int(bool(scene.get("dither", True)))
+    return cd
+
+
+def n_nodes(ph):
+    return int(lib().or_n_nodes(ct.byref(ph)))
+
+
+def kirchhoff(ph, FJ):
+    FJ = np.ascontiguousarray(FJ, dtype=np.float64).ravel()
+    tau = np.zeros(9)
+    lib().or_kirchhoff(ct.byref(ph), _p(FJ, ct.c_double), _p(tau, ct.c_double))
+    return tau[: ph.dim * ph.dim].reshape(ph.dim, ph.dim)
+
+
+def polar(F):
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    R = np.zeros_like(F)
+    if F.shape == (2, 2):
+        lib().or_polar2(_p(F, ct.c_double), _p(R, ct.c_double))
+    else:
+        lib().or_polar3(_p(F, ct.c_double), _p(R, ct.c_double))
+    return R
+
+
+def p2g(ph, s):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    grid = np.zeros(n_nodes(ph) * (1 + ph.dim))
+    oog = lib().or_p2g(ct.byref(ph), s.shape[0], _p(s, ct.c_double), _p(grid, ct.c_double))
+    return grid.reshape(-1, 1 + ph.dim), int(oog)
+
+
+def grid_update(ph, grid):
+    g = np.ascontiguousarray(grid, dtype=np.float64).copy()
+    lib().or_grid_update(ct.byref(ph), _p(g, ct.c_double))
+    return g
+
+
+def g2p(ph, grid, s):
+    g = np.ascontiguousarray(grid, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64).copy()
+    lib().or_g2p(ct.byref(ph), s.shape[0], _p(g, ct.c_double), _p(s, ct.c_double))
+    return s
+
+
+def step_fp64(ph, s, grid=None):
+    s = np.ascontiguousarray(s, dtype=np.float64).copy()
+    if grid is None:
+        grid = np.zeros(n_nodes(ph) * (1 + ph.dim))
+    lib().or_step_fp64(ct.byref(ph), s.shape[0], _p(s, ct.c_double), _p(grid, ct.c_double))
+    return s
+
+
+def encode_state(cd, s, step, stats=None):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    N = s.shape[0]
+    w = np.zeros((N, cd.n_words), dtype=np.uint32)
+    st = stats if stats is not None else np.zeros(N_STATS, dtype=np.int64)
+    lib().or_encode_state(ct.byref(cd), N, _p(s, ct.c_double), step, _p(w, ct.c_uint32),
+                          _p(st, ct.c_int64))
+    return w
+
+
+def decode_state(cd, words):
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    N = words.shape[0]
+    s = np.zeros((N, cd.n_comp))
+    lib().or_decode_state(ct.byref(cd), N, _p(words, ct.c_uint32), _p(s, ct.c_double))
+    return s
+
+
+def tile_keys(ph, s):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    k = np.zeros(s.shape[0], dtype=np.int64)
+    lib().or_tile_keys(ct.byref(ph), s.shape[0], _p(s, ct.c_double), _p(k, ct.c_int64))
+    return k
+
+
+def n_keys(ph):
+    return int(lib().or_n_keys(ct.byref(ph)))
+
+
+def stable_sort(keys, nkeys):
+    keys = np.ascontiguousarray(keys, dtype=np.int64)
+    perm = np.zeros(keys.shape[0], dtype=np.int64)
+    lib().or_stable_sort(keys.shape[0], _p(keys, ct.c_int64), nkeys, _p(perm, ct.c_int64))
+    return perm
+
+
+def mean_sq_pos(dim, s):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    return float(lib().or_mean_sq_pos(dim, s.shape[1], s.shape[0], _p(s, ct.c_double)))
+
+
+class QuantRollout:
+    """Oracle rollout of the quantized simulation (Eq. 1) with the same slot ordering as
+    the device path: encode at step 0, stable re-sort by tile key at step 0 and after
+    every ``resort_every``-th step."""
+
+    def __init__(self, scene, scheme, s0):
+        self.ph = make_phys(scene)
+        self.cd = make_codec(scene, scheme)
+        self.resort_every = int(scene.get("resort_every", 8))
+        s0 = np.ascontiguousarray(s0, dtype=np.float64)
+        self.N = s0.shape[0]
+        self.stats = np.zeros(N_STATS, dtype=np.int64)
+        self.words = encode_state(self.cd, s0, 0, self.stats)
+        self.ids = np.arange(self.N, dtype=np.int64)
+        self.t = 0
+        self.grid = np.zeros(n_nodes(self.ph) * (1 + self.ph.dim))
+        self.s = np.zeros((self.N, self.cd.n_comp))
+        self.resort()
+
+    def resort(self):
+        s = decode_state(self.cd, self.words)
+        perm = stable_sort(tile_keys(self.ph, s), n_keys(self.ph))
+        self.words = np.ascontiguousarray(self.words[perm])
+        self.ids = self.ids[perm]
+
+    def step(self, n=1):
+        for _ in range(n):
+            self.t += 1
+            lib().or_step_quant(ct.byref(self.ph), ct.byref(self.cd), self.N,
+                                _p(self.words, ct.c_uint32), self.t, _p(self.s, ct.c_double),
+                                _p(self.grid, ct.c_double), _p(self.stats, ct.c_int64))
+            if self.resort_every > 0 and self.t % self.resort_every == 0:
+                self.resort()
+
+    def state(self):
+        return decode_state(self.cd, self.words)
+
+
+class Fp64Rollout:
+    """Oracle rollout of the unquantized FP64 simulation, with the same ordering."""
+
+    def __init__(self, scene, s0):
+        self.ph = make_phys(scene)
+        self.resort_every = int(scene.get("resort_every", 8))
+        self.s = np.ascontiguousarray(s0, dtype=np.float64).copy()
+        self.N = self.s.shape[0]
+        self.ids = np.arange(self.N, dtype=np.int64)
+        self.grid = np.zeros(n_nodes(self.ph) * (1 + self.ph.dim))
+        self.t = 0
+        self.resort()
+
+    def resort(self):
+        perm = stable_sort(tile_keys(self.ph, self.s), n_keys(self.ph))
+        self.s = np.ascontiguousarray(self.s[perm])
+        self.ids = self.ids[perm]
+
+    def step(self, n=1):
+        for _ in range(n):
+            self.t += 1
+            lib().or_step_fp64(ct.byref(self.ph), self.N, _p(self.s, ct.c_double),
+                               _p(self.grid, ct.c_double))
+            if self.resort_every > 0 and self.t % self.resort_every == 0:
+                self.resort()
+
+
+# ------------------------------------------------------------------------------ solve
+def _solve_in(P, g, lo, hi, z, eps, mode, rounding, kappa):
+    si = SolveIn()
+    si.H = len(P)
+    for h in range(len(P)):
+        si.P[h] = P[h]
+        si.g[h] = g[h]
+        si.lo[h] = lo[h]
+        si.hi[h] = hi[h]
+    si.kappa = kappa
+    si.z = z
+    si.eps = eps
+    si.mode = 0 if mode == "error" else 1
+    si.rounding = 0 if rounding == "paper" else 1
+    return si
+
+
+def _solve_out(so, H):
+    return {
+        "delta_cont": [so.delta_cont[h] for h in range(H)],
+        "bits_paper": [so.bits_paper[h] for h in range(H)],
+        "bits": [so.bits[h] for h in range(H)],
+        "frac": [so.frac[h] for h in range(H)],
+        "offset": [int(so.offset[h]) for h in range(H)],
+        "pred_err": so.pred_err,
+        "total_bits": so.total_bits,
+    }
+
+
+def scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper", kappa=2.0):
+    si = _solve_in(P, g, lo, hi, z, eps, mode, rounding, kappa)
+    so = SolveOut()
+    rc = lib().or_scheme_solve(ct.byref(si), ct.byref(so))
+    if rc != 0:
+        raise ValueError(f"oracle scheme solve failed ({rc})")
+    return _solve_out(so, len(P))
+
+
+def scheme_bruteforce(P, g, lo, hi, z, eps, mode="error", kappa=2.0, frac_lo=-8, frac_hi=40):
+    si = _solve_in(P, g, lo, hi, z, eps, mode, "exact", kappa)
+    so = SolveOut()
+    rc = lib().or_scheme_bruteforce(ct.byref(si), frac_lo, frac_hi, ct.byref(so))
+    if rc != 0:
+        raise ValueError(f"oracle brute force failed ({rc})")
+    return _solve_out(so, len(P))

@@ -1,0 +1,152 @@
+/*
+ * oracle.h -- CPU oracle for the quantized MLS-MPM time step of
+ * "Automatic Quantization for Physics-Based Simulation" (Liu et al., SIGGRAPH 2022).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded FP64 restatement
+ * of what the hot path computes, used to check the CUDA library.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or helper with the CUDA library, and it never calls into it.
+ *
+ * Conventions
+ *   - Particle state is an AoS array of doubles, n_comp values per particle, in the
+ *     canonical component order  x[d], v[d], C[d*d] (row major), then F[d*d] (row major,
+ *     elastic materials) or J (fluid).
+ *   - Grid nodes: n = 2^grid_log2 nodes per axis, dx = 1/n, node (i,j[,k]) sits at
+ *     (i,j[,k])*dx.  The oracle's grid is a dense row-major array of (1+d) doubles per
+ *     node: mass, then momentum (after P2G) or velocity (after the grid update).
+ *   - Packed words: AoS, n_words 32-bit words per particle; record bit b is bit (b & 31)
+ *     of word (b >> 5); a component occupies bits [bitpos, bitpos + bits).
+ *
+ * Parity status of each function is listed in its comment; every function here is
+ * pinned by a "not gpu" test against facts fixed by the paper or by mathematics.
+ */
+#ifndef QMPM_ORACLE_H
+#define QMPM_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_COMP 24
+
+enum { OR_NEOHOOKEAN = 0, OR_COROTATED = 1, OR_FLUID = 2 };
+enum { OR_FIELD_X = 0, OR_FIELD_V = 1, OR_FIELD_C = 2, OR_FIELD_F = 3 };
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int material;       /* OR_NEOHOOKEAN, OR_COROTATED, OR_FLUID */
+    int grid_log2;      /* n = 2^grid_log2 */
+    int bound;          /* sticky-wall width in nodes */
+    double dt;
+    double E, nu;       /* Young's modulus, Poisson ratio (elastic) */
+    double bulk;        /* bulk modulus K (fluid) */
+    double p_vol, p_mass;
+    double gravity[3];
+} or_phys_t;
+
+typedef struct {
+    int n_comp;
+    int n_words;
+    int bits[OR_MAX_COMP];
+    int frac[OR_MAX_COMP];          /* resolution 2^-frac */
+    int64_t offset[OR_MAX_COMP];    /* value = (u + offset) * 2^-frac */
+    int bitpos[OR_MAX_COMP];
+    int field[OR_MAX_COMP];         /* 0..3: x, v, C, F/J */
+    uint64_t seed;                  /* dither hash key */
+    int dither;                     /* 1: dithered store (Sec. 5), 0: round to nearest */
+} or_codec_t;
+
+/* stats: per field h (0..3): saturations, round-ups, round-downs; then out-of-grid count */
+#define OR_STAT_SAT(h)  (h)
+#define OR_STAT_UP(h)   (4 + (h))
+#define OR_STAT_DOWN(h) (8 + (h))
+#define OR_STAT_OOG     12
+#define OR_N_STATS      13
+
+/* ---- counter-based generator (Philox4x32-10, Salmon et al. SC'11) ---- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* dither draw for (slot, step, comp): Philox(ctr={slot, step, comp/4, 0}, key=seed)[comp%4] */
+uint32_t or_dither_draw(uint64_t seed, uint32_t slot, uint32_t step, int comp);
+
+/* ---- fixed-point codec (Sec. 3.1 Eq. 3, Sec. 5 Eq. 11) ---- */
+uint32_t or_encode(double v, int bits, int frac, int64_t offset, int dither, uint32_t r, int *flags);
+double or_decode(uint32_t u, int frac, int64_t offset);
+#define OR_FLAG_SAT  1
+#define OR_FLAG_UP   2
+#define OR_FLAG_DOWN 4
+
+/* ---- bit pack / bit struct placement (Sec. 7) ---- */
+int or_n_comp(int dim, int material);
+int or_comp_field(int dim, int material, int comp);
+/* container[h]: 0 = bit pack stream, 32 or 64 = bit struct containers.  Returns 0 or -1. */
+int or_layout(int dim, int material, const int *bits, const int container[4],
+              int *bitpos, int *n_words);
+void or_pack(int n_comp, const int *bits, const int *bitpos, int n_words,
+             const uint32_t *u, uint32_t *words);
+void or_unpack(int n_comp, const int *bits, const int *bitpos, const uint32_t *words,
+               uint32_t *u);
+
+/* ---- MLS-MPM pieces ---- */
+void or_lame(double E, double nu, double *mu, double *lambda);
+void or_polar2(const double F[4], double R[4]);
+void or_polar3(const double F[9], double R[9]);
+/* Kirchhoff stress tau (d*d, row major) of one particle's F (or J for the fluid) */
+void or_kirchhoff(const or_phys_t *ph, const double *FJ, double *tau);
+int or_n_nodes(const or_phys_t *ph);
+int64_t or_p2g(const or_phys_t *ph, int64_t N, const double *s, double *grid);
+void or_grid_update(const or_phys_t *ph, double *grid);
+int64_t or_g2p(const or_phys_t *ph, int64_t N, const double *grid, double *s);
+int64_t or_step_fp64(const or_phys_t *ph, int64_t N, double *s, double *grid_scratch);
+
+/* ---- quantized state ---- */
+void or_encode_state(const or_codec_t *cd, int64_t N, const double *s, uint32_t step,
+                     uint32_t *words, int64_t *stats);
+void or_decode_state(const or_codec_t *cd, int64_t N, const uint32_t *words, double *s);
+/* one quantized step: decode -> FP64 step -> dithered encode with step index `step` */
+void or_step_quant(const or_phys_t *ph, const or_codec_t *cd, int64_t N, uint32_t *words,
+                   uint32_t step, double *s_scratch, double *grid_scratch, int64_t *stats);
+
+/* ---- particle ordering ---- */
+/* tile key of each particle: origin block of the 2^d-block tile that holds its stencil */
+void or_tile_keys(const or_phys_t *ph, int64_t N, const double *s, int64_t *keys);
+/* stable counting sort: perm[i] = old slot of the particle placed at new slot i */
+void or_stable_sort(int64_t N, const int64_t *keys, int64_t n_keys, int64_t *perm);
+int64_t or_n_keys(const or_phys_t *ph);
+
+/* ---- measurement ---- */
+double or_mean_sq_pos(int dim, int n_comp, int64_t N, const double *s);
+
+/* ---- scheme solve (Sec. 4.2 Eq. 8-10, Algorithm 1) ---- */
+typedef struct {
+    int H;
+    double P[8];        /* number of variables of type h */
+    double g[8];        /* accumulated squared gradients, Eq. 8 */
+    double lo[8], hi[8];/* recorded ranges */
+    double kappa;       /* range factor (Sec. 3.1) */
+    double z;           /* reference evaluation value */
+    double eps;         /* eps_err or eps_mem */
+    int mode;           /* 0 = error bound (Eq. 6), 1 = memory bound (Eq. 7) */
+    int rounding;       /* 0 = paper ceil (Alg. 1), 1 = exact integer */
+} or_solve_in_t;
+
+typedef struct {
+    double delta_cont[8];   /* continuous optimum Delta_h */
+    int bits_paper[8];      /* b_h = ceil(-log2(Delta_h / R_h)) */
+    int bits[8];            /* power-of-two scheme: total bits n_h */
+    int frac[8];            /* Delta_h = 2^-frac */
+    int64_t offset[8];
+    double pred_err;        /* (1/12) sum Delta_h^2 g_h for the final scheme */
+    double total_bits;      /* sum P_h n_h */
+} or_solve_out_t;
+
+int or_scheme_solve(const or_solve_in_t *in, or_solve_out_t *out);
+/* brute force over integer frac_h in [lo, hi] for error mode (min bits s.t. error) or
+ * memory mode (min error s.t. bits); returns the optimum's frac_h / bits */
+int or_scheme_bruteforce(const or_solve_in_t *in, int frac_lo, int frac_hi, or_solve_out_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

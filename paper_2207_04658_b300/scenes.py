@@ -1,0 +1,148 @@
+"""Seeded synthetic scenes: initial particle states and the workload definitions.
+
+This module holds no arithmetic of the method (no transfer, no codec, no solve); it only
+draws initial positions and states.  Both the CUDA path and the CPU oracle consume what
+it produces.  Every draw comes from one Philox stream per scene (numpy's Philox bit
+generator keyed by the scene seed).
+
+State layout: float64 array [N, n_comp] in the canonical component order
+x[d], v[d], C[d*d] (row major), then F[d*d] (row major) or J for the fluid.
+
+The workloads stand in for the paper's procedural scenes (falling elastic blocks,
+Sec. 8.1; dam breaks, Sec. 8.1 and 8.3), at the sizes of the benchmark configurations.
+"""
+import math
+
+import numpy as np
+
+
+def rng(seed):
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def n_comp(dim, material):
+    return 2 * dim + dim * dim + (1 if material == "fluid" else dim * dim)
+
+
+def jitter_box(gen, lo, size, strata):
+    """One uniform sample per stratum of a regular lattice of ``strata`` cells covering
+    the axis-aligned box [lo, lo + size).  Returns [prod(strata), d] float64."""
+    lo = np.asarray(lo, dtype=np.float64)
+    size = np.asarray(size, dtype=np.float64)
+    strata = [int(s) for s in strata]
+    d = len(strata)
+    axes = [np.arange(s, dtype=np.float64) for s in strata]
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, d)
+    cell = size / np.asarray(strata, dtype=np.float64)
+    u = gen.random(grid.shape)
+    return lo + (grid + u) * cell
+
+
+def initial_state(dim, material, x, v0=None):
+    """Rest state: given positions, uniform velocity v0, C = 0, F = I (or J = 1)."""
+    N = x.shape[0]
+    s = np.zeros((N, n_comp(dim, material)), dtype=np.float64)
+    s[:, :dim] = x
+    if v0 is not None:
+        s[:, dim:2 * dim] = np.asarray(v0, dtype=np.float64)
+    off = 2 * dim + dim * dim
+    if material == "fluid":
+        s[:, off] = 1.0
+    else:
+        for a in range(dim):
+            s[:, off + a * dim + a] = 1.0
+    return s
+
+
+def place_cubes(gen, count, side, lo=0.1, hi=0.9, max_tries=100000):
+    """Non-overlapping axis-aligned cube corners inside [lo, hi]^3 by rejection."""
+    corners = []
+    tries = 0
+    while len(corners) < count:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place non-overlapping cubes")
+        c = lo + gen.random(3) * (hi - lo - side)
+        if all(np.any(np.abs(c - o) >= side) for o in corners):
+            corners.append(c)
+    return np.array(corners)
+
+
+# ---------------------------------------------------------------------------- workloads
+def block2d_scene(n_strata=(128, 64), grid_log2=7, seed=1, steps=500, resort_every=8):
+    """2D neo-Hookean block: jitter-sampled in the square [0.4, 0.6]^2 (8,192 particles
+    with the default 128 x 64 strata), 128^2 grid, E = 1e3, nu = 0.2, rho = 1,
+    g = -9.8, dt = 1e-4, sticky walls."""
+    N = int(np.prod(n_strata))
+    scene = dict(name="block2d", dim=2, material="neohookean", grid_log2=grid_log2, bound=3,
+                 dt=1e-4, E=1e3, nu=0.2, bulk=0.0, rho=1.0, p_vol=0.2 * 0.2 / N,
+                 gravity=(0.0, -9.8, 0.0), seed=seed, dither=True, steps=steps,
+                 resort_every=resort_every)
+    x = jitter_box(rng(seed), (0.4, 0.4), (0.2, 0.2), n_strata)
+    return scene, initial_state(2, "neohookean", x)
+
+
+def block2d_scheme():
+    """Fixed 16-bit scheme of the 2D block: x on [0,1) (Delta 2^-16), v on [-4,4]
+    (2^-13), C on [-64,64] (2^-9), F on [0,2] (2^-15); bit pack."""
+    return {
+        "x": dict(bits=16, frac=16, offset=0, container=0),
+        "v": dict(bits=16, frac=13, offset=-4 * 2 ** 13, container=0),
+        "C": dict(bits=16, frac=9, offset=-64 * 2 ** 9, container=0),
+        "F": dict(bits=16, frac=15, offset=0, container=0),
+    }
+
+
+def cubes3d_scene(n_cubes=16, cube_cells=40, ppc_axis=2, grid_log2=8, seed=2, steps=1000,
+                  material="corotated", E=5e3, nu=0.3, dt=5e-5, resort_every=8):
+    """3D elastic cubes (fixed-corotated by default): ``n_cubes`` cubes of side
+    cube_cells * dx at seeded non-overlapping corners in [0.1, 0.9]^3, ppc_axis^3
+    jittered particles per cell (8 by default).  The defaults give 16 x 512,000 =
+    8,192,000 particles on a 256^3 grid."""
+    n = 1 << grid_log2
+    side = cube_cells / n
+    gen = rng(seed)
+    corners = place_cubes(gen, n_cubes, side)
+    strata = (cube_cells * ppc_axis,) * 3
+    xs = [jitter_box(gen, c, (side,) * 3, strata) for c in corners]
+    x = np.concatenate(xs, axis=0)
+    N = x.shape[0]
+    scene = dict(name="cubes3d", dim=3, material=material, grid_log2=grid_log2, bound=3,
+                 dt=dt, E=E, nu=nu, bulk=0.0, rho=1.0, p_vol=n_cubes * side ** 3 / N,
+                 gravity=(0.0, -9.8, 0.0), seed=seed, dither=True, steps=steps,
+                 resort_every=resort_every)
+    return scene, initial_state(3, material, x)
+
+
+def dambreak3d_scene(column_cells=256, ppc_axis=2, grid_log2=9, seed=3, steps=500,
+                     bulk=400.0, dt=2e-5, resort_every=8):
+    """3D weakly compressible dam break: a cubic column of column_cells^3 cells at the
+    low corner (starting at the sticky wall, 3 dx), ppc_axis^3 jittered particles per
+    cell.  Defaults: 256^3 cells x 8 = 2^27 particles on a 512^3 grid, K = 400."""
+    n = 1 << grid_log2
+    lo = 3.0 / n
+    side = column_cells / n
+    x = jitter_box(rng(seed), (lo, lo, lo), (side,) * 3, (column_cells * ppc_axis,) * 3)
+    N = x.shape[0]
+    scene = dict(name="dambreak3d", dim=3, material="fluid", grid_log2=grid_log2, bound=3,
+                 dt=dt, E=0.0, nu=0.0, bulk=bulk, rho=1.0, p_vol=side ** 3 / N,
+                 gravity=(0.0, -9.8, 0.0), seed=seed, dither=True, steps=steps,
+                 resort_every=resort_every)
+    return scene, initial_state(3, "fluid", x)
+
+
+def fixed_scheme_3d(material, x_bits=21, v=(16, -8.0, 8.0), C=(16, -512.0, 512.0),
+                    F=(16, 0.0, 2.0), J=(16, 0.0, 2.0), x_container=64):
+    """A hand-written 3D scheme: x as 3 x ``x_bits`` on [0, 1) in one 64-bit container,
+    the other fields bit-packed with the given (bits, lo, hi) and the coarsest
+    power-of-two resolution whose window covers [lo, hi]."""
+    def field(bits, lo, hi):
+        k = int(math.floor(bits - math.log2(hi - lo)))
+        return dict(bits=bits, frac=k, offset=int(math.floor(lo * 2 ** k)), container=0)
+    sch = {"x": dict(bits=x_bits, frac=x_bits, offset=0, container=x_container),
+           "v": field(*v), "C": field(*C)}
+    if material == "fluid":
+        sch["J"] = field(*J)
+    else:
+        sch["F"] = field(*F)
+    return sch

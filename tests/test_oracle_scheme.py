@@ -1,0 +1,125 @@
+"""Pins of the oracle's bit-allocation solve (Sec. 4: Eq. 6-10, Algorithm 1): the
+analytic Lagrange optimum against a numerical optimizer, and the integer schemes
+against exhaustive enumeration.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+
+def random_problem(gen, H):
+    P = gen.integers(1000, 100000, H).astype(float)
+    g = 10.0 ** gen.uniform(-6, 2, H)
+    lo = gen.uniform(-5, 0, H)
+    hi = lo + 10.0 ** gen.uniform(-1, 1.5, H)
+    z = float(10.0 ** gen.uniform(-2, 3))
+    return P, g, lo, hi, z
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_error_bound_lagrange_matches_optimizer(oracle, seed):
+    gen = np.random.default_rng(seed)
+    H = int(gen.integers(2, 6))
+    P, g, lo, hi, z = random_problem(gen, H)
+    eps = 0.01
+    out = oracle.scheme_solve(P, g, lo, hi, z, eps, mode="error")
+    # numerical optimum of the continuous problem of Eq. 9 in y = log2(Delta)
+    R = 2.0 * (hi - lo)
+    target = (eps * z) ** 2
+
+    def obj(y):
+        return -np.sum(P * (y - np.log2(R))) / P.sum()
+
+    def con(y):
+        return 1.0 - np.sum(np.exp2(2 * y) * g) / 12.0 / target
+
+    y0 = np.log2(np.asarray(out["delta_cont"])) - 1.0
+    res = minimize(obj, y0, constraints=[{"type": "ineq", "fun": con}], method="SLSQP",
+                   options={"ftol": 1e-14, "maxiter": 500})
+    assert res.success
+    assert np.allclose(np.exp2(res.x), out["delta_cont"], rtol=1e-5)
+    # the optimum sits on the constraint: E[dz] = (eps z)^2
+    d = np.asarray(out["delta_cont"])
+    assert abs(np.sum(d * d * g) / 12.0 / target - 1.0) < 1e-12
+    # Algorithm 1's bit count
+    assert out["bits_paper"] == [max(1, math.ceil(-math.log2(d[h] / R[h]))) for h in range(H)]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_memory_bound_lagrange_matches_optimizer(oracle, seed):
+    gen = np.random.default_rng(100 + seed)
+    H = int(gen.integers(2, 6))
+    P, g, lo, hi, z = random_problem(gen, H)
+    eps = float(gen.uniform(0.3, 0.7))
+    out = oracle.scheme_solve(P, g, lo, hi, z, eps, mode="memory")
+    R = 2.0 * (hi - lo)
+    B = eps * 32 * P.sum()
+
+    def obj(y):
+        return np.sum(np.exp2(2 * y) * g) / 12.0
+
+    def con(y):
+        return (B - np.sum(P * (np.log2(R) - y))) / P.sum()
+
+    y0 = np.log2(np.asarray(out["delta_cont"])) + 0.5
+    scale = obj(y0)
+    res = minimize(lambda y: obj(y) / scale, y0, constraints=[{"type": "ineq", "fun": con}],
+                   method="SLSQP", options={"ftol": 1e-15, "maxiter": 1000})
+    assert res.success
+    assert np.allclose(np.exp2(res.x), out["delta_cont"], rtol=1e-4)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_error_bound_exact_integer_equals_bruteforce(oracle, seed):
+    gen = np.random.default_rng(200 + seed)
+    H = int(gen.integers(1, 5))
+    P, g, lo, hi, z = random_problem(gen, H)
+    eps = float(10.0 ** gen.uniform(-3, -1))
+    exact = oracle.scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="exact")
+    paper = oracle.scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper")
+    brute = oracle.scheme_bruteforce(P, g, lo, hi, z, eps, mode="error", frac_lo=-10, frac_hi=45)
+    target = (eps * z) ** 2
+    assert exact["total_bits"] == brute["total_bits"]
+    assert exact["pred_err"] <= target and paper["pred_err"] <= target
+    assert paper["total_bits"] >= brute["total_bits"]
+    # the ceil solution is at most one bit per variable above the optimum's power-of-two
+    # rounding plus the window rounding
+    assert paper["total_bits"] <= brute["total_bits"] + 2 * P.sum()
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_memory_bound_integer_equals_bruteforce(oracle, seed):
+    gen = np.random.default_rng(300 + seed)
+    H = int(gen.integers(1, 4))
+    P, g, lo, hi, z = random_problem(gen, H)
+    eps = float(gen.uniform(0.3, 0.7))
+    exact = oracle.scheme_solve(P, g, lo, hi, z, eps, mode="memory", rounding="exact")
+    greedy = oracle.scheme_solve(P, g, lo, hi, z, eps, mode="memory", rounding="paper")
+    brute = oracle.scheme_bruteforce(P, g, lo, hi, z, eps, mode="memory")
+    budget = eps * 32 * P.sum()
+    assert exact["total_bits"] <= budget and greedy["total_bits"] <= budget
+    assert math.isclose(exact["pred_err"], brute["pred_err"], rel_tol=1e-12)
+    assert greedy["pred_err"] >= brute["pred_err"] * (1 - 1e-12)
+
+
+def test_equal_types_get_equal_resolution(oracle):
+    # symmetric problem: the Lagrange condition gives one Delta for all types (Eq. 10)
+    P = [1000.0] * 3
+    g = [2.0] * 3
+    out = oracle.scheme_solve(P, g, [0, 0, 0], [1, 1, 1], 5.0, 0.01)
+    d = out["delta_cont"]
+    assert max(d) == pytest.approx(min(d), rel=1e-15)
+    assert d[0] == pytest.approx(math.sqrt(12 * 1000 * (0.05) ** 2 / (2.0 * 3000)), rel=1e-15)
+
+
+def test_windows_cover_the_widened_range(oracle):
+    gen = np.random.default_rng(9)
+    for mode in ("error", "memory"):
+        P, g, lo, hi, z = random_problem(gen, 4)
+        out = oracle.scheme_solve(P, g, lo, hi, z, 0.4 if mode == "memory" else 0.01, mode=mode)
+        for h in range(4):
+            d = 2.0 ** -out["frac"][h]
+            mid, R = (lo[h] + hi[h]) / 2, 2.0 * (hi[h] - lo[h])
+            assert out["offset"][h] * d <= mid - R / 2
+            assert (out["offset"][h] + 2 ** out["bits"][h] - 1) * d >= mid + R / 2
