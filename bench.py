@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: quantized MLS-MPM particle-steps/s on one B300 (per GPU, replicas).
+
+One "step" is one MLS-MPM time step of the whole scene on bit-packed fixed-point state
+(P2G, grid update, G2P, dithered store, and the periodic tile re-sort), run by the
+library's kernels on device-resident state.  Default workload: 3D fixed-corotated elastic
+cubes, 16 x 512,000 = 8,192,000 particles, 256^3 grid, dt 5e-5 (synthetic scene:
+seeded jittered cubes).  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank steps its own replica of the scene (independent seeds, no
+collective on the data path): weak scaling, value = all particle-steps / max rank time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "quantized vs FP32 MPM particle-steps/s at rel err<=0.01; %HBM peak; p99 latency"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cubes3d", choices=["cubes3d", "dambreak3d", "block2d"])
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="fraction of the workload's cubes/columns (for quick runs only)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ workloads
+def workload(name, scale=1.0, seed_offset=0):
+    from paper_2207_04658_b300 import scenes
+    if name == "cubes3d":
+        n_cubes = max(1, int(round(16 * scale)))
+        sc, s0 = scenes.cubes3d_scene(n_cubes=n_cubes, seed=2 + seed_offset)
+        sch = scenes.fixed_scheme_3d("corotated")
+        desc = {"workload": "3D fixed-corotated elastic cubes", "particles": int(s0.shape[0]),
+                "cubes": n_cubes, "grid": "256^3", "dt": sc["dt"], "E": sc["E"], "nu": sc["nu"],
+                "ppc": 8, "scheme": "x 3x21 bits in one 64-bit container; v 16 bits on [-8,8], "
+                "C 16 bits on [-512,512], F 16 bits on [0,2], bit pack, dithered",
+                "resort_every": sc["resort_every"]}
+    elif name == "dambreak3d":
+        cells = max(8, int(round(256 * scale ** (1 / 3))))
+        sc, s0 = scenes.dambreak3d_scene(column_cells=cells, seed=3 + seed_offset)
+        sch = scenes.fixed_scheme_3d("fluid", C=(16, -2048.0, 2048.0))
+        desc = {"workload": "3D weakly compressible dam break", "particles": int(s0.shape[0]),
+                "grid": "512^3", "dt": sc["dt"], "bulk": sc["bulk"], "ppc": 8,
+                "resort_every": sc["resort_every"]}
+    else:
+        sc, s0 = scenes.block2d_scene(seed=1 + seed_offset)
+        sch = scenes.block2d_scheme()
+        desc = {"workload": "2D neo-Hookean block", "particles": int(s0.shape[0]), "grid": "128^2",
+                "dt": sc["dt"], "resort_every": sc["resort_every"]}
+    return sc, s0, sch, desc
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = [num(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ our arm
+def time_scene(qmpm, torch, sc, s0, sch, steps, warmup, dist_ctx):
+    stream = torch.cuda.current_stream()
+    g = qmpm.Scene(sc, sch, s0, stream=stream.cuda_stream, profile=True)
+    for _ in range(warmup):
+        g.step(1)
+    torch.cuda.synchronize()
+    g.profile(reset=True)
+    dist_ctx.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        g.step(1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dist_ctx.barrier()
+    ms = t0.elapsed_time(t1)
+    prof = g.profile(reset=True)
+    st = g.readback(state=False, ids=False)["stats"]
+    return g, ms, prof, st
+
+
+def e2e_scene(qmpm, torch, g, steps, warmup):
+    """End to end through qmpm_step_host: every step copies the packed state from pinned
+    host memory, steps it and copies it back."""
+    r = g.readback(state=False, words=True, ids=False)
+    words = r["words"]
+    hin = torch.from_numpy(words.copy()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(max(1, warmup)):
+        qmpm.qmpm_step_host(g.h, 1, hin.data_ptr(), hout.data_ptr())
+    t = time.perf_counter()
+    for _ in range(steps):
+        qmpm.qmpm_step_host(g.h, 1, hin.data_ptr(), hout.data_ptr())
+        hin, hout = hout, hin
+    el = time.perf_counter() - t
+    return el, int(words.nbytes)
+
+
+def kernel_traffic(desc, n_particles):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, scaled to
+    this workload's particle count; None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_2207_04658_b300", "csrc", "step.cu"), "rb").read()
+        if rec.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        if rec.get("workload") != desc["workload"]:
+            return None
+        return rec["dram_bytes_per_launch"] * n_particles / rec["particles"]
+    except Exception:
+        return None
+
+
+def cpu_baseline(name, sample_steps=2):
+    """The oracle (single-threaded FP64 C) on a bounded sample of the same workload: the
+    first cube (or a slice of the column) on the full grid, `sample_steps` quantized steps."""
+    import oracle
+    sc, s0, sch, desc = workload(name)
+    if name == "cubes3d":
+        n = 512_000
+        sample = f"first cube of 16 ({n} particles) on the full 256^3 grid, {sample_steps} steps"
+    elif name == "dambreak3d":
+        n = 256_000
+        sample = f"first {n} particles of the column on the full 512^3 grid, {sample_steps} steps"
+    else:
+        n = s0.shape[0]
+        sample = f"whole scene, {sample_steps} steps"
+    s0 = s0[:n]
+    ro = oracle.QuantRollout(sc, sch, s0)
+    t = time.perf_counter()
+    ro.step(sample_steps)
+    el = time.perf_counter() - t
+    return {"value": n * sample_steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": sample}
+
+
+class DistCtx:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            self.dist = dist
+
+    def init(self, torch):
+        if self.dist is not None:
+            torch.cuda.set_device(self.local)
+            self.dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, torch, v):
+        if self.dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def run_ours(args):
+    import torch
+    from paper_2207_04658_b300 import build, qmpm
+    build.build()
+    dc = DistCtx()
+    dc.init(torch)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    peak_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
+
+    sc, s0, sch, desc = workload(args.workload, args.scale, seed_offset=dc.rank)
+    N = s0.shape[0]
+    clocks = ClockSampler(dc.local)
+    clocks.start()
+    g, ms, prof, st = time_scene(qmpm, torch, sc, s0, sch, args.steps, args.warmup, dc)
+    clk = clocks.stop()
+    ms_max = dc.max(torch, ms)
+    W = g.n_words
+    value = dc.world * N * args.steps / (ms_max / 1e3)
+
+    # dominant kernel: the fused step kernel
+    step_avg_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    node_bytes = 16
+    nodes = st["active_blocks"] * (64 if sc["dim"] == 3 else 16)
+    alg_bytes = N * 2 * 4 * W + nodes * 2 * node_bytes
+    achieved = alg_bytes / (step_avg_ms / 1e3) / 1e9
+    traffic = kernel_traffic(desc, N)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                "peak_source": peak_note, "kernel": "step_kernel (G2P -> dithered store -> P2G)",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": round(step_avg_ms, 4)}
+    breakdown = {"step_ms_per_step": round(prof["step_ms"] / args.steps, 4),
+                 "clear_ms_per_step": round(prof["clear_ms"] / args.steps, 4),
+                 "sort_ms_per_step": round(prof["sort_ms"] / args.steps, 4),
+                 "launch_gap_ms_per_step": round((ms - prof["step_ms"] - prof["clear_ms"]
+                                                  - prof["sort_ms"]) / args.steps, 4)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dc.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "gpu_launches": int(prof["kernel_launches"]),
+            "config": dict(desc, replicas=dc.world, l2="inputs larger than L2 (packed state "
+                           f"{N * 4 * W / 1e6:.0f} MB per replica)",
+                           bytes_per_particle_quantized=4 * W, bytes_per_particle_fp32=4 * g.n_comp,
+                           compression=round(g.n_comp / W, 3), parallelism=f"replicas{dc.world}"),
+            "roofline": roofline, "breakdown": breakdown, "clocks": clk,
+            "stats": {"active_blocks": st["active_blocks"], "out_of_tile": st["out_of_tile"]}}
+    if not args.no_e2e:
+        el, nbytes = e2e_scene(qmpm, torch, g, max(3, args.steps // 4), 1)
+        k = max(3, args.steps // 4)
+        el = dc.max(torch, el)
+        line["e2e"] = {"value": dc.world * N * k / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes,
+                       "path": "qmpm_step_host: pinned host words -> device, P2G, step, -> host"}
+    g.close()
+    if not args.no_fp32:
+        g32, ms32, prof32, st32 = time_scene(qmpm, torch, sc, s0, None, args.steps, args.warmup, dc)
+        ms32 = dc.max(torch, ms32)
+        v32 = dc.world * N * args.steps / (ms32 / 1e3)
+        s32 = prof32["step_ms"] / max(1, prof32["step_launches"])
+        alg32 = N * 2 * 4 * g32.n_words + st32["active_blocks"] * (64 if sc["dim"] == 3 else 16) * 32
+        line["fp32"] = {"value": v32, "unit": UNIT, "ms_per_step": ms32 / args.steps,
+                        "step_kernel_ms": round(s32, 4),
+                        "step_kernel_gbs": round(alg32 / (s32 / 1e3) / 1e9, 1),
+                        "quantized_over_fp32": round(value / v32, 4)}
+        g32.close()
+    if dc.rank == 0 and dc.world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if dc.rank == 0:
+        print(json.dumps(line), flush=True)
+    if dc.dist is not None:
+        dc.dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle (single-threaded FP64 C, as it stands) on a
+    bounded sample of the same workload, each step one quantized oracle step."""
+    dc = DistCtx()
+    if dc.rank != 0:
+        return
+    import oracle
+    sc, s0, sch, desc = workload(args.workload, args.scale)
+    n = {"cubes3d": 64_000, "dambreak3d": 64_000}.get(args.workload, s0.shape[0])
+    sample = f"first {n} particles of the scene on its full grid, one quantized oracle step per step"
+    ro = oracle.QuantRollout(sc, sch, s0[:n])
+    ro.step(args.warmup)
+    t = time.perf_counter()
+    ro.step(args.steps)
+    el = time.perf_counter() - t
+    v = n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

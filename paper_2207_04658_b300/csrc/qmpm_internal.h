@@ -1,0 +1,156 @@
+// qmpm_internal.h -- internal types of libqmpm shared by its translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qmpm.h"
+
+namespace qmpm {
+
+constexpr int kMaxComp = QMPM_MAX_COMP;
+constexpr int kThreads = 256;       // threads per CTA of the step kernels
+constexpr int kMaxChunk = 256;      // particles per work item (one per thread)
+
+// Per-component codec constants, precomputed on the host from the scheme.
+struct CompCodec {
+    int32_t word;       // word holding the component's first bit
+    int32_t shift;      // bit offset inside that word
+    int32_t straddle;   // 1 if the component continues in word + 1
+    uint32_t mask;      // (1 << bits) - 1
+    int32_t offset;     // L: value = (u + L) * 2^-frac
+    uint32_t umax;      // 2^bits - 1
+    float enc_scale;    // 2^frac
+    float dec_scale;    // 2^-frac
+    float dec_bias;     // L * 2^-frac
+    int32_t field;      // 0..3
+};
+
+// Work item of the step kernels: a run of sorted particles that share one tile.
+struct Chunk {
+    uint32_t start;     // first slot
+    uint32_t count;     // <= chunk size
+    uint32_t key;       // tile key: linear index of the tile's origin block
+    uint32_t pad;
+};
+
+struct StepParams {
+    // physics
+    int32_t n, nb, bound, n_comp;
+    float dt, inv_dx, dx, Dinv;
+    float p_mass, stress_coef;  // stress_coef = -dt * p_vol * Dinv
+    float mu, lambda, bulk;
+    float gravity[3];
+    // codec
+    int32_t n_words;
+    int32_t dither;
+    uint32_t seed_lo, seed_hi;
+    uint32_t step;              // dither step index of this step's store
+    CompCodec comp[kMaxComp];
+    // data
+    uint32_t *words;            // word planes
+    int64_t ld;                 // plane stride
+    const Chunk *chunks;
+    const uint32_t *n_chunks;   // device scalar
+    const float4 *grid_in;      // P2G result of the current state (G2P source)
+    float4 *grid_out;           // zeroed target of the next P2G
+    uint8_t *touched_out;       // blocks of grid_out that received mass
+    unsigned long long *stats;  // QMPM_FLAG_STATS counters (13) or null
+};
+
+// Event records of QMPM_FLAG_PROFILE: (start, end, kind) per launch group.
+struct Profile {
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t n[4] = {0, 0, 0, 0};
+};
+
+struct Ctx {
+    qmpm_scene_t scene;
+    qmpm_scheme_t scheme;
+    bool quant;
+    int n_comp;
+    int W;                      // words per particle
+    int64_t N, ld;
+    int n, nb;
+    int64_t n_blocks;           // nb^d
+    int64_t block_nodes;        // 4^d
+    int chunk;
+    cudaStream_t stream;
+    bool own_stream;
+    int n_sms;
+    int grid_ctas;              // persistent CTAs of the step kernels
+
+    uint32_t *words[2];         // word planes (ping-pong for the re-sort gather)
+    int64_t *ids[2];
+    int cur;                    // which words/ids buffer is live
+    float4 *grid[2];            // the two grid buffers
+    uint8_t *touched[2];
+    int gcur;                   // grid buffer holding the P2G of the live state
+    bool primed;                // grid[gcur] holds the P2G of the live state
+
+    // sort and chunk scratch
+    uint32_t *keys[2], *vals[2];
+    uint32_t *digit_counts;     // 256 * n_tiles
+    uint32_t *scan_partials;
+    int64_t max_scan_partials;
+    uint32_t *seg_begin, *seg_end, *key_chunks; // per key
+    Chunk *chunks;
+    uint32_t *n_chunks;
+    int64_t max_chunks;
+    int key_bits;
+
+    struct Profile *prof;       // event records (QMPM_FLAG_PROFILE), owned
+    int64_t launches;           // kernel launches since the last profile reset
+
+    unsigned long long *d_stats; // 16 counters
+    double *d_z;
+    int64_t steps;
+    CompCodec cc[kMaxComp];
+};
+
+// kernels launched by one re-sort: keys, radix passes (hist, 3 scan, scatter), gather,
+// segments, chunk counts, 3 scan, emit
+inline int64_t resort_launches(int key_bits) { return 9 + 5 * (int64_t)(key_bits / 8); }
+
+// scheme.cpp
+int layout(int dim, int material, qmpm_scheme_t *scheme, std::string &err);
+int n_comp(int dim, int material);
+int comp_field(int dim, int comp);
+void build_codec(const qmpm_scheme_t &s, int dim, int material, CompCodec *cc);
+
+// sort.cu
+int resort(Ctx &c, std::string &err);
+int64_t sort_scratch_tiles(int64_t N);
+cudaError_t exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *partials, int64_t max_partials,
+                               cudaStream_t s);
+
+// step.cu
+cudaError_t launch_encode_init(Ctx &c, const double *d_state);
+cudaError_t launch_p2g(Ctx &c);
+cudaError_t launch_g2p2g(Ctx &c, uint32_t step);
+cudaError_t launch_clear(Ctx &c, int buf);
+cudaError_t launch_decode_f64(Ctx &c, double *d_state);
+cudaError_t launch_measure(Ctx &c);
+cudaError_t launch_count_flags(Ctx &c, const uint8_t *flags, int64_t n, unsigned long long *d_out);
+cudaError_t launch_pack_f32(int dim, int material, const CompCodec *cc, int n_comp, int W, uint64_t seed,
+                            int dither, uint32_t step, const float *d_vals, int64_t N, uint32_t *d_words,
+                            int64_t ld, unsigned long long *d_stats, cudaStream_t s);
+cudaError_t launch_unpack_f32(int dim, int material, const CompCodec *cc, int n_comp,
+                              const uint32_t *d_words, int64_t N, int64_t ld, float *d_vals,
+                              cudaStream_t s);
+void fill_params(const Ctx &c, StepParams &p);
+
+}  // namespace qmpm
+
+// The opaque handle type of the C ABI is the context itself.
+struct qmpm_ctx : public qmpm::Ctx {
+};

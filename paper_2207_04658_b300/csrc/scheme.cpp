@@ -1,0 +1,335 @@
+// scheme.cpp -- host side of libqmpm: record layout (bit pack / bit struct, Sec. 7),
+// per-component codec constants, and the bit-allocation solve (Sec. 4, Algorithm 1).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "qmpm_internal.h"
+
+namespace qmpm {
+
+int n_comp(int dim, int material)
+{
+    return 2 * dim + dim * dim + (material == QMPM_FLUID ? 1 : dim * dim);
+}
+
+int comp_field(int dim, int comp)
+{
+    if (comp < dim) return QMPM_FIELD_X;
+    if (comp < 2 * dim) return QMPM_FIELD_V;
+    if (comp < 2 * dim + dim * dim) return QMPM_FIELD_C;
+    return QMPM_FIELD_F;
+}
+
+int layout(int dim, int material, qmpm_scheme_t *s, std::string &err)
+{
+    if ((dim != 2 && dim != 3) || material < 0 || material > 2) {
+        err = "dim must be 2 or 3 and material 0..2";
+        return QMPM_ERR_INVALID_ARG;
+    }
+    const int nc = n_comp(dim, material);
+    if (!s->quantized) {
+        s->n_words = nc;
+        for (int c = 0; c < nc; ++c) s->bitpos[c] = 32 * c;
+        return QMPM_OK;
+    }
+    for (int h = 0; h < 4; ++h) {
+        const qmpm_field_t &f = s->field[h];
+        if (f.bits < 1 || f.bits > QMPM_MAX_FIELD_BITS) {
+            err = "field " + std::to_string(h) + ": bits must be in 1..24 for FP32 compute";
+            return QMPM_ERR_SCHEME;
+        }
+        if (f.offset <= -(int64_t(1) << 24) || f.offset >= (int64_t(1) << 24)) {
+            err = "field " + std::to_string(h) + ": |offset| must be below 2^24";
+            return QMPM_ERR_SCHEME;
+        }
+        if (f.frac < -100 || f.frac > 100) {
+            err = "field " + std::to_string(h) + ": frac out of range";
+            return QMPM_ERR_SCHEME;
+        }
+        if (f.container != 0 && f.container != 32 && f.container != 64) {
+            err = "field " + std::to_string(h) + ": container must be 0, 32 or 64";
+            return QMPM_ERR_SCHEME;
+        }
+    }
+    int64_t cursor = 0;  // next free record bit
+    int c = 0;
+    for (int h = 0; h < 4; ++h) {
+        const int bits = s->field[h].bits;
+        const int cw = s->field[h].container;
+        int last = c;
+        while (last < nc && comp_field(dim, last) == h) ++last;
+        if (cw == 0) {
+            // bit pack: the stream simply continues
+            for (; c < last; ++c) {
+                s->bitpos[c] = (int32_t)cursor;
+                cursor += bits;
+            }
+        } else {
+            // bit struct: fill containers of cw bits starting on a word boundary
+            int64_t box = (cursor + 31) & ~int64_t(31);
+            int fill = 0;
+            for (; c < last; ++c) {
+                if (fill + bits > cw) {
+                    box += cw;
+                    fill = 0;
+                }
+                s->bitpos[c] = (int32_t)(box + fill);
+                fill += bits;
+            }
+            cursor = box + cw;
+        }
+    }
+    s->n_words = (int32_t)((cursor + 31) / 32);
+    return QMPM_OK;
+}
+
+void build_codec(const qmpm_scheme_t &s, int dim, int material, CompCodec *cc)
+{
+    const int nc = n_comp(dim, material);
+    for (int c = 0; c < nc; ++c) {
+        CompCodec &k = cc[c];
+        const int h = comp_field(dim, c);
+        k.field = h;
+        if (!s.quantized) {
+            k.word = c;
+            k.shift = 0;
+            k.straddle = 0;
+            k.mask = 0xFFFFFFFFu;
+            k.offset = 0;
+            k.umax = 0xFFFFFFFFu;
+            k.enc_scale = k.dec_scale = 1.0f;
+            k.dec_bias = 0.0f;
+            continue;
+        }
+        const qmpm_field_t &f = s.field[h];
+        k.word = s.bitpos[c] >> 5;
+        k.shift = s.bitpos[c] & 31;
+        k.straddle = (k.shift + f.bits > 32) ? 1 : 0;
+        k.mask = (f.bits >= 32) ? 0xFFFFFFFFu : ((1u << f.bits) - 1u);
+        k.offset = (int32_t)f.offset;
+        k.umax = k.mask;
+        k.enc_scale = std::ldexp(1.0f, f.frac);
+        k.dec_scale = std::ldexp(1.0f, -f.frac);
+        k.dec_bias = (float)std::ldexp((double)f.offset, -f.frac);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Bit-allocation solve.  R_h = kappa (hi - lo), the window [mid - R/2, mid + R/2].
+// With resolution 2^-k the window needs L = floor(lo' 2^k) and the fewest n such that
+// 2^n - 1 >= ceil(hi' 2^k) - L.
+// ---------------------------------------------------------------------------------
+namespace {
+
+struct Window {
+    double lo, hi, R;
+};
+
+Window window_of(const qmpm_solve_in_t &in, int h)
+{
+    const double mid = 0.5 * (in.lo[h] + in.hi[h]);
+    double R = in.kappa * (in.hi[h] - in.lo[h]);
+    if (!(R > 0.0)) R = std::ldexp(1.0, -30);
+    return {mid - 0.5 * R, mid + 0.5 * R, R};
+}
+
+int bits_at(int k, const Window &w)
+{
+    const double L = std::floor(std::ldexp(w.lo, k));
+    const double need = std::ceil(std::ldexp(w.hi, k)) - L + 1.0;
+    int n = 1;
+    while (n < 64 && std::ldexp(1.0, n) < need) ++n;
+    return n;
+}
+
+int finest_frac(int n, const Window &w)
+{
+    int k = (int)std::floor((double)n - std::log2(w.hi - w.lo)) + 4;
+    while (k > -200 && bits_at(k, w) > n) --k;
+    return k;
+}
+
+double predicted(const qmpm_solve_in_t &in, const int *frac)
+{
+    double e = 0.0;
+    for (int h = 0; h < in.H; ++h) e += std::ldexp(1.0, -2 * frac[h]) * in.g[h];
+    return e / 12.0;
+}
+
+// Visit every integer vector v with lo[h] <= v[h] <= hi[h].
+template <class F>
+void odometer(int H, const int *lo, const int *hi, F &&visit)
+{
+    int v[8];
+    for (int h = 0; h < H; ++h) v[h] = lo[h];
+    for (;;) {
+        visit(v);
+        int h = 0;
+        for (; h < H; ++h) {
+            if (v[h] < hi[h]) {
+                ++v[h];
+                break;
+            }
+            v[h] = lo[h];
+        }
+        if (h == H) return;
+    }
+}
+
+}  // namespace
+
+}  // namespace qmpm
+
+using namespace qmpm;
+
+extern "C" int qmpm_scheme_solve_impl(const qmpm_solve_in_t *in, qmpm_solve_out_t *out, std::string &err)
+{
+    if (!in || !out || in->H < 1 || in->H > 8 || !(in->eps > 0.0)) {
+        err = "qmpm_scheme_solve: need 1 <= H <= 8 and eps > 0";
+        return QMPM_ERR_INVALID_ARG;
+    }
+    std::memset(out, 0, sizeof(*out));
+    const int H = in->H;
+    std::array<Window, 8> win{};
+    double sumP = 0.0;
+    for (int h = 0; h < H; ++h) {
+        win[h] = window_of(*in, h);
+        sumP += in->P[h];
+    }
+    int frac[8], bits[8];
+
+    if (in->mode == 0) {
+        // Eq. 10 and Algorithm 1
+        const double bound = (in->eps * in->z) * (in->eps * in->z);
+        int k0[8], lo[8], hi[8];
+        for (int h = 0; h < H; ++h) {
+            if (in->g[h] > 0.0) {
+                const double d = std::sqrt(12.0 * in->P[h] * bound / (in->g[h] * sumP));
+                out->delta_cont[h] = d;
+                out->bits_paper[h] = std::max(1, (int)std::ceil(-std::log2(d / win[h].R)));
+                k0[h] = (int)std::ceil(-std::log2(d));
+                lo[h] = k0[h] - 3;
+                hi[h] = k0[h] + 3;
+            } else {
+                out->delta_cont[h] = std::numeric_limits<double>::infinity();
+                out->bits_paper[h] = 1;
+                k0[h] = lo[h] = hi[h] = finest_frac(1, win[h]);
+            }
+        }
+        if (in->rounding == 0) {
+            std::copy(k0, k0 + H, frac);
+        } else {
+            double best_bits = std::numeric_limits<double>::infinity(), best_err = best_bits;
+            int best[8];
+            odometer(H, lo, hi, [&](const int *v) {
+                const double e = predicted(*in, v);
+                if (e > bound) return;
+                double tb = 0.0;
+                for (int h = 0; h < H; ++h) tb += in->P[h] * bits_at(v[h], win[h]);
+                if (tb < best_bits || (tb == best_bits && e < best_err)) {
+                    best_bits = tb;
+                    best_err = e;
+                    std::copy(v, v + H, best);
+                }
+            });
+            if (best_bits == std::numeric_limits<double>::infinity()) {
+                err = "qmpm_scheme_solve: no feasible scheme in the search window";
+                return QMPM_ERR_SCHEME;
+            }
+            std::copy(best, best + H, frac);
+        }
+        for (int h = 0; h < H; ++h) bits[h] = bits_at(frac[h], win[h]);
+    } else {
+        // memory bound: Delta_h^2 g_h = c P_h, c from the bit budget
+        const double budget = in->eps * 32.0 * sumP;
+        double B = budget, Pg = 0.0, a = 0.0, b = 0.0;
+        for (int h = 0; h < H; ++h) {
+            if (in->g[h] > 0.0) {
+                Pg += in->P[h];
+                a += in->P[h] * std::log2(win[h].R);
+                b += in->P[h] * std::log2(in->P[h] / in->g[h]);
+            } else {
+                B -= in->P[h];
+            }
+        }
+        const double log2c = Pg > 0.0 ? (2.0 * a - b - 2.0 * B) / Pg : 0.0;
+        for (int h = 0; h < H; ++h) {
+            double bc = 1.0;
+            if (in->g[h] > 0.0) {
+                const double d = std::sqrt(std::exp2(log2c) * in->P[h] / in->g[h]);
+                out->delta_cont[h] = d;
+                bc = std::log2(win[h].R / d);
+            } else {
+                out->delta_cont[h] = std::numeric_limits<double>::infinity();
+            }
+            out->bits_paper[h] = std::max(1, (int)std::floor(bc));
+        }
+        auto err_at_bits = [&](int h, int n) {
+            return std::ldexp(1.0, -2 * finest_frac(n, win[h])) * in->g[h] / 12.0;
+        };
+        if (in->rounding == 0) {
+            double used = 0.0;
+            for (int h = 0; h < H; ++h) {
+                bits[h] = out->bits_paper[h];
+                used += in->P[h] * bits[h];
+            }
+            for (;;) {
+                int pick = -1;
+                double gain_best = 0.0;
+                for (int h = 0; h < H; ++h) {
+                    if (in->g[h] <= 0.0 || bits[h] >= 32 || used + in->P[h] > budget) continue;
+                    const double gain = (err_at_bits(h, bits[h]) - err_at_bits(h, bits[h] + 1)) / in->P[h];
+                    if (gain > gain_best) {
+                        gain_best = gain;
+                        pick = h;
+                    }
+                }
+                if (pick < 0) break;
+                bits[pick] += 1;
+                used += in->P[pick];
+            }
+        } else {
+            int lo[8], hi[8], best[8];
+            for (int h = 0; h < H; ++h) {
+                lo[h] = std::max(1, out->bits_paper[h] - 3);
+                hi[h] = std::min(32, out->bits_paper[h] + 3);
+                if (in->g[h] <= 0.0) lo[h] = hi[h] = 1;
+            }
+            double best_err = std::numeric_limits<double>::infinity(), best_used = best_err;
+            odometer(H, lo, hi, [&](const int *v) {
+                double used = 0.0, e = 0.0;
+                for (int h = 0; h < H; ++h) {
+                    used += in->P[h] * v[h];
+                    e += err_at_bits(h, v[h]);
+                }
+                if (used > budget) return;
+                if (e < best_err || (e == best_err && used < best_used)) {
+                    best_err = e;
+                    best_used = used;
+                    std::copy(v, v + H, best);
+                }
+            });
+            if (best_err == std::numeric_limits<double>::infinity()) {
+                err = "qmpm_scheme_solve: no scheme fits the memory budget";
+                return QMPM_ERR_SCHEME;
+            }
+            std::copy(best, best + H, bits);
+        }
+        for (int h = 0; h < H; ++h) frac[h] = finest_frac(bits[h], win[h]);
+    }
+    double tb = 0.0;
+    for (int h = 0; h < H; ++h) {
+        out->bits[h] = bits[h];
+        out->frac[h] = frac[h];
+        out->offset[h] = (int64_t)std::floor(std::ldexp(win[h].lo, frac[h]));
+        tb += in->P[h] * bits[h];
+    }
+    out->pred_err = predicted(*in, frac);
+    out->total_bits = tb;
+    return QMPM_OK;
+}

@@ -1,0 +1,773 @@
+// step.cu -- the MLS-MPM step kernels of libqmpm (Sec. 8.1's simulator, quantized as in
+// Sec. 3.1 Eq. 1 with the dithered store of Sec. 5 and the bit pack of Sec. 7).
+//
+// One launch advances the whole scene by one step, fused as G2P(t) -> store -> P2G(t+1):
+//   1. stage the tile's 8^d grid nodes of the P2G result of step t into shared memory,
+//      turning momentum into velocity with gravity and sticky walls on the way (the
+//      grid update),
+//   2. decode each particle's packed record (words staged in shared memory),
+//   3. G2P: gather v, C; x += dt v; F = (I + dt C) F (or J = (1 + dt tr C) J),
+//   4. dithered encode of the new state, whole-word stores back to HBM,
+//   5. P2G of step t+1 from the decoded quantized values into a shared-memory tile,
+//      flushed to the other grid buffer with one vector atomic per touched node.
+// Work item: a chunk of up to 256 sorted particles that share one tile (2^d blocks of
+// 4^d nodes); one thread per particle; persistent CTAs stride over the chunk list.
+// Particles that drifted out of their tile since the last re-sort take a slow path
+// through global memory.
+#include <cstdio>
+
+#include "device_common.cuh"
+
+namespace qmpm {
+
+template <int DIM, int MAT>
+struct Traits {
+    static constexpr int NC = 2 * DIM + DIM * DIM + (MAT == QMPM_FLUID ? 1 : DIM * DIM);
+    static constexpr int TN = DIM == 2 ? 64 : 512;  // tile nodes (8^d)
+    static constexpr int NOFF = DIM == 2 ? 9 : 27;  // stencil nodes (3^d)
+};
+
+// ------------------------------------------------------------------------------ materials
+// 3D polar factor by the scaled Newton iteration X <- (g X + X^-T / g) / 2 with
+// determinant scaling g = |det X|^(-1/3) (Higham 1986; Byers & Xu 2008).  X^-T is the
+// cofactor matrix (rows: cross products of the other two rows) over det X.
+__device__ __forceinline__ void polar3(const float *F, float *R)
+{
+    float X[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) X[i] = F[i];
+    for (int it = 0; it < 10; ++it) {
+        const float c0 = X[4] * X[8] - X[5] * X[7], c1 = X[5] * X[6] - X[3] * X[8],
+                    c2 = X[3] * X[7] - X[4] * X[6];
+        const float c3 = X[7] * X[2] - X[8] * X[1], c4 = X[8] * X[0] - X[6] * X[2],
+                    c5 = X[6] * X[1] - X[7] * X[0];
+        const float c6 = X[1] * X[5] - X[2] * X[4], c7 = X[2] * X[3] - X[0] * X[5],
+                    c8 = X[0] * X[4] - X[1] * X[3];
+        const float det = X[0] * c0 + X[1] * c1 + X[2] * c2;
+        const float g = rcbrtf(fabsf(det));
+        const float a = 0.5f * g, b = 0.5f / (g * det);
+        const float cof[9] = {c0, c1, c2, c3, c4, c5, c6, c7, c8};
+        float diff = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float nx = a * X[i] + b * cof[i];
+            diff += (nx - X[i]) * (nx - X[i]);
+            X[i] = nx;
+        }
+        if (diff < 1e-10f) break;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = X[i];
+}
+
+// Kirchhoff stress tau (row major DIM x DIM).
+template <int DIM, int MAT>
+__device__ __forceinline__ void kirchhoff(const float *FJ, const StepParams &P, float *tau)
+{
+    if (MAT == QMPM_FLUID) {
+        const float J = FJ[0];
+        const float p = P.bulk * (J - 1.0f) * J;
+#pragma unroll
+        for (int i = 0; i < DIM * DIM; ++i) tau[i] = (i % (DIM + 1) == 0) ? p : 0.0f;
+        return;
+    }
+    const float *F = FJ;
+    float J;
+    if (DIM == 2)
+        J = F[0] * F[3] - F[1] * F[2];
+    else
+        J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+            F[2] * (F[3] * F[7] - F[4] * F[6]);
+    if (MAT == QMPM_NEOHOOKEAN) {
+        const float vol = P.lambda * logf(J);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) {
+                float ff = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) ff += F[a * DIM + k] * F[b * DIM + k];
+                tau[a * DIM + b] = P.mu * (ff - (a == b ? 1.0f : 0.0f)) + (a == b ? vol : 0.0f);
+            }
+    } else {
+        float R[DIM * DIM];
+        if (DIM == 2) {
+            const float x = F[0] + F[3], y = F[2] - F[1];
+            const float h = hypotf(x, y);
+            const float c = h > 0.0f ? x / h : 1.0f, s = h > 0.0f ? y / h : 0.0f;
+            R[0] = c;
+            R[1] = -s;
+            R[2] = s;
+            R[3] = c;
+        } else {
+            polar3(F, R);
+        }
+        const float vol = P.lambda * (J - 1.0f) * J;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) acc += (F[a * DIM + k] - R[a * DIM + k]) * F[b * DIM + k];
+                tau[a * DIM + b] = 2.0f * P.mu * acc + (a == b ? vol : 0.0f);
+            }
+    }
+}
+
+// ------------------------------------------------------------------------------ grid update
+// Node velocity for G2P: v = mv / m + dt g where m > 0 (else 0); zero within `bound`
+// nodes of a wall (sticky).  Used both when staging a tile and on the slow path.
+template <int DIM>
+__device__ __forceinline__ float4 node_velocity(float4 mm, int gx, int gy, int gz, const StepParams &P)
+{
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const int hi = P.n - 1 - P.bound;
+    bool wall = gx < P.bound || gx > hi || gy < P.bound || gy > hi;
+    if (DIM == 3) wall = wall || gz < P.bound || gz > hi;
+    if (mm.x > 0.0f && !wall) {
+        v.x = mm.y / mm.x + P.dt * P.gravity[0];
+        v.y = mm.z / mm.x + P.dt * P.gravity[1];
+        if (DIM == 3) v.z = mm.w / mm.x + P.dt * P.gravity[2];
+    }
+    return v;
+}
+
+// stencil base per axis, clamped to [0, n-3]; returns true if clamped (out of grid)
+template <int DIM>
+__device__ __forceinline__ bool stencil(const float *x, const StepParams &P, int *base, float (*w)[3],
+                                        float *f)
+{
+    bool out = false;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const float fx = x[a] * P.inv_dx;
+        int b = __float2int_rd(fx - 0.5f);
+        if (b < 0) {
+            b = 0;
+            out = true;
+        }
+        if (b > P.n - 3) {
+            b = P.n - 3;
+            out = true;
+        }
+        base[a] = b;
+        f[a] = fx - (float)b;
+        const float d0 = 1.5f - f[a], d1 = f[a] - 1.0f, d2 = f[a] - 0.5f;
+        w[a][0] = 0.5f * d0 * d0;
+        w[a][1] = 0.75f - d1 * d1;
+        w[a][2] = 0.5f * d2 * d2;
+    }
+    return out;
+}
+
+template <int DIM>
+__device__ __forceinline__ int tile_index(int i, int j, int k)
+{
+    return DIM == 2 ? (i * 8 + j) : ((i * 8 + j) * 8 + k);
+}
+
+__device__ __forceinline__ void stat_add(unsigned long long *stats, int idx, unsigned long long v)
+{
+    if (v) atomicAdd(stats + idx, v);
+}
+
+// ------------------------------------------------------------------------------ step kernel
+template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P>
+__global__ void __launch_bounds__(kThreads, 2) step_kernel(const __grid_constant__ StepParams P)
+{
+    using Tr = Traits<DIM, MAT>;
+    constexpr int NC = Tr::NC, TN = Tr::TN;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *tile_v = reinterpret_cast<float4 *>(smem_raw);
+    float4 *tile_p = tile_v + TN;
+    uint32_t *sw = reinterpret_cast<uint32_t *>(tile_p + TN);
+    const int tid = threadIdx.x;
+    uint32_t *my = sw + tid;  // this thread's column of record words, stride kThreads
+
+    unsigned long long cnt_sat[4] = {0, 0, 0, 0}, cnt_up[4] = {0, 0, 0, 0}, cnt_dn[4] = {0, 0, 0, 0};
+    unsigned long long cnt_oog = 0, cnt_oot = 0;
+
+    const uint32_t n_chunks = *P.n_chunks;
+    for (uint32_t ci = blockIdx.x; ci < n_chunks; ci += gridDim.x) {
+        const Chunk ch = P.chunks[ci];
+        int T0, T1, T2 = 0;
+        if (DIM == 2) {
+            T1 = ch.key % P.nb;
+            T0 = ch.key / P.nb;
+        } else {
+            T2 = ch.key % P.nb;
+            T1 = (ch.key / P.nb) % P.nb;
+            T0 = ch.key / (P.nb * P.nb);
+        }
+        const int o0 = 4 * (T0 - 1), o1 = 4 * (T1 - 1), o2 = 4 * (T2 - 1);  // tile origin node
+
+        // 1. stage the grid tile (velocities) and clear the P2G tile
+        for (int t = tid; t < TN; t += kThreads) {
+            const int i = DIM == 2 ? (t >> 3) : (t >> 6), j = DIM == 2 ? (t & 7) : ((t >> 3) & 7);
+            const int k = DIM == 2 ? 0 : (t & 7);
+            if (DO_G2P) {
+                const float4 mm = P.grid_in[node_addr<DIM>(P.nb, o0 + i, o1 + j, o2 + k)];
+                tile_v[t] = node_velocity<DIM>(mm, o0 + i, o1 + j, o2 + k, P);
+            }
+            tile_p[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        // 2. this thread's packed record
+        const bool active = tid < (int)ch.count;
+        const int64_t slot = (int64_t)ch.start + tid;
+        if (active)
+            for (int j = 0; j < P.n_words; ++j) my[j * kThreads] = P.words[j * P.ld + slot];
+        __syncthreads();
+
+        if (active) {
+            float val[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (QUANT)
+                    val[c] = decode_u(extract(my, kThreads, P.comp[c]), P.comp[c]);
+                else
+                    val[c] = __uint_as_float(my[c * kThreads]);
+            }
+            float *x = val, *v = val + DIM, *C = val + 2 * DIM, *FJ = val + 2 * DIM + DIM * DIM;
+
+            if (DO_G2P) {
+                // 3. G2P and particle update
+                int base[3] = {0, 0, 0};
+                float w[3][3], f[3];
+                stencil<DIM>(x, P, base, w, f);
+                const int l0 = base[0] - o0, l1 = base[1] - o1, l2 = DIM == 3 ? base[2] - o2 : 0;
+                const bool in_tile = l0 >= 0 && l0 <= 5 && l1 >= 0 && l1 <= 5 && l2 >= 0 && l2 <= 5;
+                float vn[3] = {0.0f, 0.0f, 0.0f}, B[DIM * DIM];
+#pragma unroll
+                for (int q = 0; q < DIM * DIM; ++q) B[q] = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
+                            const float wt = w[0][i] * w[1][j] * (DIM == 3 ? w[2][k] : 1.0f);
+                            float4 gv;
+                            if (in_tile)
+                                gv = tile_v[tile_index<DIM>(l0 + i, l1 + j, l2 + k)];
+                            else {
+                                const int gx = base[0] + i, gy = base[1] + j, gz = DIM == 3 ? base[2] + k : 0;
+                                gv = node_velocity<DIM>(P.grid_in[node_addr<DIM>(P.nb, gx, gy, gz)], gx, gy, gz, P);
+                            }
+                            const float gva[3] = {gv.x, gv.y, gv.z};
+                            const float dp[3] = {((float)i - f[0]) * P.dx, ((float)j - f[1]) * P.dx,
+                                                 DIM == 3 ? ((float)k - f[2]) * P.dx : 0.0f};
+#pragma unroll
+                            for (int a = 0; a < DIM; ++a) {
+                                vn[a] += wt * gva[a];
+#pragma unroll
+                                for (int b = 0; b < DIM; ++b) B[a * DIM + b] += wt * gva[a] * dp[b];
+                            }
+                        }
+                if (STATS && !in_tile) cnt_oot += 1;
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    v[a] = vn[a];
+                    x[a] += P.dt * vn[a];
+#pragma unroll
+                    for (int b = 0; b < DIM; ++b) C[a * DIM + b] = P.Dinv * B[a * DIM + b];
+                }
+                if (MAT == QMPM_FLUID) {
+                    float tr = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) tr += C[a * DIM + a];
+                    FJ[0] = (1.0f + P.dt * tr) * FJ[0];
+                } else {
+                    float Fn[DIM * DIM];
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                        for (int b = 0; b < DIM; ++b) {
+                            float acc = FJ[a * DIM + b];
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) acc += P.dt * C[a * DIM + k] * FJ[k * DIM + b];
+                            Fn[a * DIM + b] = acc;
+                        }
+#pragma unroll
+                    for (int q = 0; q < DIM * DIM; ++q) FJ[q] = Fn[q];
+                }
+
+                // 4. store: dithered encode (Sec. 5) and whole-word writes
+                if (QUANT) {
+                    for (int j = 0; j < P.n_words; ++j) my[j * kThreads] = 0u;
+                    uint4 rnd = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        if (P.dither && (c & 3) == 0)
+                            rnd = philox4x32_10(make_uint4((uint32_t)slot, P.step, (uint32_t)(c >> 2), 0u),
+                                                P.seed_lo, P.seed_hi);
+                        int fl;
+                        const uint32_t u = encode_f32(val[c], P.comp[c], P.dither != 0, uint4_at(rnd, c & 3), fl);
+                        insert(my, kThreads, P.comp[c], u);
+                        val[c] = decode_u(u, P.comp[c]);  // the stored (quantized) value
+                        if (STATS) {
+                            // the field of component c (x, v, C, F/J), folded at compile time
+                            const int h = c < DIM ? 0 : c < 2 * DIM ? 1 : c < 2 * DIM + DIM * DIM ? 2 : 3;
+                            cnt_sat[h] += (fl & 1);
+                            cnt_up[h] += (fl >> 1) & 1;
+                            cnt_dn[h] += (fl >> 2) & 1;
+                        }
+                    }
+                    for (int j = 0; j < P.n_words; ++j) __stcs(P.words + j * P.ld + slot, my[j * kThreads]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) __stcs(P.words + c * P.ld + slot, __float_as_uint(val[c]));
+                }
+            }
+
+            // 5. P2G of the (stored) state into the shared tile
+            {
+                int base[3] = {0, 0, 0};
+                float w[3][3], f[3];
+                const bool oog = stencil<DIM>(x, P, base, w, f);
+                if (STATS && oog) cnt_oog += 1;
+                const int l0 = base[0] - o0, l1 = base[1] - o1, l2 = DIM == 3 ? base[2] - o2 : 0;
+                const bool in_tile = l0 >= 0 && l0 <= 5 && l1 >= 0 && l1 <= 5 && l2 >= 0 && l2 <= 5;
+                float tau[DIM * DIM], A[DIM * DIM];
+                kirchhoff<DIM, MAT>(FJ, P, tau);
+#pragma unroll
+                for (int q = 0; q < DIM * DIM; ++q) A[q] = P.stress_coef * tau[q] + P.p_mass * C[q];
+                float mv[3];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) mv[a] = P.p_mass * v[a];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
+                            const float wt = w[0][i] * w[1][j] * (DIM == 3 ? w[2][k] : 1.0f);
+                            const float dp[3] = {((float)i - f[0]) * P.dx, ((float)j - f[1]) * P.dx,
+                                                 DIM == 3 ? ((float)k - f[2]) * P.dx : 0.0f};
+                            float mom[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+                            for (int a = 0; a < DIM; ++a) {
+                                float acc = mv[a];
+#pragma unroll
+                                for (int b = 0; b < DIM; ++b) acc += A[a * DIM + b] * dp[b];
+                                mom[a] = wt * acc;
+                            }
+                            const float wm = wt * P.p_mass;
+                            if (in_tile) {
+                                float *dst = reinterpret_cast<float *>(tile_p + tile_index<DIM>(l0 + i, l1 + j, l2 + k));
+                                atomicAdd(dst + 0, wm);
+                                atomicAdd(dst + 1, mom[0]);
+                                atomicAdd(dst + 2, mom[1]);
+                                if (DIM == 3) atomicAdd(dst + 3, mom[2]);
+                            } else {
+                                const int gx = base[0] + i, gy = base[1] + j, gz = DIM == 3 ? base[2] + k : 0;
+                                atomicAdd(P.grid_out + node_addr<DIM>(P.nb, gx, gy, gz),
+                                          make_float4(wm, mom[0], mom[1], DIM == 3 ? mom[2] : 0.0f));
+                                P.touched_out[block_of<DIM>(P.nb, gx, gy, gz)] = 1;
+                            }
+                        }
+                if (STATS && !DO_G2P && !in_tile) cnt_oot += 1;
+            }
+        }
+        __syncthreads();
+
+        // flush the P2G tile: one vector atomic per node that received mass
+        for (int t = tid; t < TN; t += kThreads) {
+            const float4 a = tile_p[t];
+            if (a.x != 0.0f) {
+                const int i = DIM == 2 ? (t >> 3) : (t >> 6), j = DIM == 2 ? (t & 7) : ((t >> 3) & 7);
+                const int k = DIM == 2 ? 0 : (t & 7);
+                atomicAdd(P.grid_out + node_addr<DIM>(P.nb, o0 + i, o1 + j, o2 + k), a);
+            }
+        }
+        if (tid < (1 << DIM) && ch.count > 0) {
+            const int i = tid & 1, j = (tid >> 1) & 1, k = (tid >> 2) & 1;
+            const int64_t blk = DIM == 2 ? (int64_t)(T0 + i) * P.nb + (T1 + j)
+                                         : ((int64_t)(T0 + i) * P.nb + (T1 + j)) * P.nb + (T2 + k);
+            P.touched_out[blk] = 1;
+        }
+        __syncthreads();
+    }
+
+    if (STATS) {
+        // warp-aggregated counters
+        for (int h = 0; h < 4; ++h) {
+            cnt_sat[h] = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt_sat[h]);
+            cnt_up[h] = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt_up[h]);
+            cnt_dn[h] = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt_dn[h]);
+        }
+        cnt_oog = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt_oog);
+        cnt_oot = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt_oot);
+        if ((tid & 31) == 0) {
+            for (int h = 0; h < 4; ++h) {
+                stat_add(P.stats, h, cnt_sat[h]);
+                stat_add(P.stats, 4 + h, cnt_up[h]);
+                stat_add(P.stats, 8 + h, cnt_dn[h]);
+            }
+            stat_add(P.stats, 12, cnt_oog);
+            stat_add(P.stats, 13, cnt_oot);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ grid clear
+// Zero the blocks of a grid buffer that were touched and reset their flags: a warp reads
+// 32 flags and zeroes every flagged block with coalesced 16-byte stores.
+template <int DIM>
+__global__ void clear_kernel(float4 *grid, uint8_t *touched, int64_t n_blocks)
+{
+    constexpr int BN = DIM == 2 ? 16 : 64;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b0 = warp * 32; b0 < n_blocks; b0 += n_warps * 32) {
+        const int64_t b = b0 + lane;
+        const bool t = b < n_blocks && touched[b];
+        unsigned mask = __ballot_sync(0xFFFFFFFFu, t);
+        if (t) touched[b] = 0;
+        while (mask) {
+            const int l = __ffs(mask) - 1;
+            mask &= mask - 1;
+            float4 *blk = grid + (b0 + l) * BN;
+            for (int q = lane; q < BN; q += 32) blk[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ codec kernels
+// Initial state (FP64 AoS from the host) -> word planes, dithered store of step 0.
+template <bool QUANT>
+__global__ void encode_init_kernel(const __grid_constant__ StepParams P, const double *s, int64_t N)
+{
+    extern __shared__ uint32_t sw_init[];
+    const int tid = threadIdx.x;
+    uint32_t *my = sw_init + tid;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + tid;
+    if (p >= N) return;
+    if (!QUANT) {
+        for (int c = 0; c < P.n_comp; ++c) P.words[c * P.ld + p] = __float_as_uint((float)s[p * P.n_comp + c]);
+        return;
+    }
+    for (int j = 0; j < P.n_words; ++j) my[j * blockDim.x] = 0u;
+    uint4 rnd = make_uint4(0, 0, 0, 0);
+    for (int c = 0; c < P.n_comp; ++c) {
+        if (P.dither && (c & 3) == 0)
+            rnd = philox4x32_10(make_uint4((uint32_t)p, 0u, (uint32_t)(c >> 2), 0u), P.seed_lo, P.seed_hi);
+        int fl;
+        const uint32_t u = encode_f64(s[p * P.n_comp + c], P.comp[c], P.dither != 0, uint4_at(rnd, c & 3), fl);
+        if (P.stats && fl) {
+            const int h = P.comp[c].field;
+            atomicAdd(P.stats + ((fl & 1) ? h : (fl & 2) ? 4 + h : 8 + h), 1ull);
+        }
+        uint32_t *w = my;
+        const CompCodec &cc = P.comp[c];
+        w[cc.word * blockDim.x] |= u << cc.shift;
+        if (cc.straddle) w[(cc.word + 1) * blockDim.x] |= u >> (32 - cc.shift);
+    }
+    for (int j = 0; j < P.n_words; ++j) P.words[j * P.ld + p] = my[j * blockDim.x];
+}
+
+// Word planes -> FP64 AoS (exact decode), for readback.
+template <bool QUANT>
+__global__ void decode_f64_kernel(const __grid_constant__ StepParams P, double *s, int64_t N)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    for (int c = 0; c < P.n_comp; ++c) {
+        const CompCodec &cc = P.comp[c];
+        if (!QUANT) {
+            s[p * P.n_comp + c] = (double)__uint_as_float(P.words[c * P.ld + p]);
+            continue;
+        }
+        uint32_t lo = P.words[cc.word * P.ld + p] >> cc.shift;
+        if (cc.straddle) lo |= P.words[(cc.word + 1) * P.ld + p] << (32 - cc.shift);
+        s[p * P.n_comp + c] = decode_f64(lo & cc.mask, cc);
+    }
+}
+
+// z = (1/N) sum |x|^2 accumulated in FP64 (position measurement).
+template <int DIM, bool QUANT>
+__global__ void measure_kernel(const __grid_constant__ StepParams P, int64_t N, double *z)
+{
+    __shared__ double red[kThreads / 32];
+    double acc = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const CompCodec &cc = P.comp[a];
+            double xa;
+            if (!QUANT) {
+                xa = (double)__uint_as_float(P.words[a * P.ld + p]);
+            } else {
+                uint32_t lo = P.words[cc.word * P.ld + p] >> cc.shift;
+                if (cc.straddle) lo |= P.words[(cc.word + 1) * P.ld + p] << (32 - cc.shift);
+                xa = decode_f64(lo & cc.mask, cc);
+            }
+            acc += xa * xa;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+        atomicAdd(z, t / (double)N);
+    }
+}
+
+__global__ void count_flags_kernel(const uint8_t *flags, int64_t n, unsigned long long *out)
+{
+    unsigned long long acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += flags[i] ? 1ull : 0ull;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+cudaError_t launch_count_flags(Ctx &c, const uint8_t *flags, int64_t n, unsigned long long *d_out)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)c.n_sms * 8) blocks = (int64_t)c.n_sms * 8;
+    if (blocks < 1) blocks = 1;
+    count_flags_kernel<<<(unsigned)blocks, 256, 0, c.stream>>>(flags, n, d_out);
+    return cudaGetLastError();
+}
+
+// FP32 values [N][nc] -> word planes with the dithered store of `step` (codec tests).
+__global__ void pack_f32_kernel(const __grid_constant__ StepParams P, const float *vals, int64_t N)
+{
+    extern __shared__ uint32_t sw_pack[];
+    const int tid = threadIdx.x;
+    uint32_t *my = sw_pack + tid;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + tid;
+    if (p >= N) return;
+    for (int j = 0; j < P.n_words; ++j) my[j * blockDim.x] = 0u;
+    uint4 rnd = make_uint4(0, 0, 0, 0);
+    for (int c = 0; c < P.n_comp; ++c) {
+        if (P.dither && (c & 3) == 0)
+            rnd = philox4x32_10(make_uint4((uint32_t)p, P.step, (uint32_t)(c >> 2), 0u), P.seed_lo, P.seed_hi);
+        int fl;
+        const uint32_t u = encode_f32(vals[p * P.n_comp + c], P.comp[c], P.dither != 0, uint4_at(rnd, c & 3), fl);
+        if (P.stats && fl) {
+            const int h = P.comp[c].field;
+            atomicAdd(P.stats + ((fl & 1) ? h : (fl & 2) ? 4 + h : 8 + h), 1ull);
+        }
+        const CompCodec &cc = P.comp[c];
+        my[cc.word * blockDim.x] |= u << cc.shift;
+        if (cc.straddle) my[(cc.word + 1) * blockDim.x] |= u >> (32 - cc.shift);
+    }
+    for (int j = 0; j < P.n_words; ++j) P.words[j * P.ld + p] = my[j * blockDim.x];
+}
+
+__global__ void unpack_f32_kernel(const __grid_constant__ StepParams P, float *vals, int64_t N)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    for (int c = 0; c < P.n_comp; ++c) {
+        const CompCodec &cc = P.comp[c];
+        uint32_t lo = P.words[cc.word * P.ld + p] >> cc.shift;
+        if (cc.straddle) lo |= P.words[(cc.word + 1) * P.ld + p] << (32 - cc.shift);
+        vals[p * P.n_comp + c] = decode_u(lo & cc.mask, cc);
+    }
+}
+
+// ------------------------------------------------------------------------------ launchers
+void fill_params(const Ctx &c, StepParams &p)
+{
+    memset(&p, 0, sizeof(p));
+    const qmpm_scene_t &s = c.scene;
+    p.n = c.n;
+    p.nb = c.nb;
+    p.bound = s.bound;
+    p.n_comp = c.n_comp;
+    p.dt = (float)s.dt;
+    p.inv_dx = (float)c.n;
+    p.dx = 1.0f / (float)c.n;
+    p.Dinv = 4.0f * (float)c.n * (float)c.n;
+    p.p_mass = (float)s.p_mass;
+    p.stress_coef = (float)(-s.dt * s.p_vol * 4.0 * (double)c.n * (double)c.n);
+    const double mu = s.E / (2.0 * (1.0 + s.nu));
+    const double la = s.E * s.nu / ((1.0 + s.nu) * (1.0 - 2.0 * s.nu));
+    p.mu = (float)mu;
+    p.lambda = (float)la;
+    p.bulk = (float)s.bulk;
+    for (int a = 0; a < 3; ++a) p.gravity[a] = (float)s.gravity[a];
+    p.n_words = c.W;
+    p.dither = s.dither;
+    p.seed_lo = (uint32_t)s.seed;
+    p.seed_hi = (uint32_t)(s.seed >> 32);
+    for (int q = 0; q < c.n_comp; ++q) p.comp[q] = c.cc[q];
+    p.words = c.words[c.cur];
+    p.ld = c.ld;
+    p.chunks = c.chunks;
+    p.n_chunks = c.n_chunks;
+    p.stats = (s.flags & QMPM_FLAG_STATS) ? c.d_stats : nullptr;
+}
+
+static size_t step_smem(const Ctx &c)
+{
+    const int TN = c.scene.dim == 2 ? 64 : 512;
+    return (size_t)2 * TN * sizeof(float4) + (size_t)c.W * kThreads * sizeof(uint32_t);
+}
+
+template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P>
+static cudaError_t launch_step_t(Ctx &c, const StepParams &p)
+{
+    auto kern = step_kernel<DIM, MAT, QUANT, STATS, DO_G2P>;
+    const size_t smem = step_smem(c);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<c.grid_ctas, kThreads, smem, c.stream>>>(p);
+    return cudaGetLastError();
+}
+
+template <bool DO_G2P>
+static cudaError_t dispatch_step(Ctx &c, const StepParams &p)
+{
+    const bool st = (c.scene.flags & QMPM_FLAG_STATS) != 0;
+    const int key = (c.scene.dim == 3 ? 100 : 0) + c.scene.material * 10 + (c.quant ? 2 : 0) + (st ? 1 : 0);
+#define QMPM_CASE(D, M, Q, S)                                                                      \
+    case (D == 3 ? 100 : 0) + M * 10 + (Q ? 2 : 0) + (S ? 1 : 0):                                    \
+        return launch_step_t<D, M, Q, S, DO_G2P>(c, p);
+#define QMPM_CASES_DM(D, M) QMPM_CASE(D, M, false, false) QMPM_CASE(D, M, true, false) QMPM_CASE(D, M, true, true) \
+    QMPM_CASE(D, M, false, true)
+    switch (key) {
+        QMPM_CASES_DM(2, 0)
+        QMPM_CASES_DM(2, 1)
+        QMPM_CASES_DM(2, 2)
+        QMPM_CASES_DM(3, 0)
+        QMPM_CASES_DM(3, 1)
+        QMPM_CASES_DM(3, 2)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef QMPM_CASES_DM
+#undef QMPM_CASE
+}
+
+cudaError_t launch_p2g(Ctx &c)
+{
+    StepParams p;
+    fill_params(c, p);
+    p.grid_in = nullptr;
+    p.grid_out = c.grid[c.gcur];
+    p.touched_out = c.touched[c.gcur];
+    p.step = 0;
+    return dispatch_step<false>(c, p);
+}
+
+cudaError_t launch_g2p2g(Ctx &c, uint32_t step)
+{
+    StepParams p;
+    fill_params(c, p);
+    p.grid_in = c.grid[c.gcur];
+    p.grid_out = c.grid[1 - c.gcur];
+    p.touched_out = c.touched[1 - c.gcur];
+    p.step = step;
+    return dispatch_step<true>(c, p);
+}
+
+cudaError_t launch_clear(Ctx &c, int buf)
+{
+    const int threads = 256;
+    const int64_t warps_needed = (c.n_blocks + 31) / 32;
+    int64_t ctas = (warps_needed + threads / 32 - 1) / (threads / 32);
+    if (ctas > (int64_t)c.n_sms * 8) ctas = (int64_t)c.n_sms * 8;
+    if (ctas < 1) ctas = 1;
+    if (c.scene.dim == 2)
+        clear_kernel<2><<<(unsigned)ctas, threads, 0, c.stream>>>(c.grid[buf], c.touched[buf], c.n_blocks);
+    else
+        clear_kernel<3><<<(unsigned)ctas, threads, 0, c.stream>>>(c.grid[buf], c.touched[buf], c.n_blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_init(Ctx &c, const double *d_state)
+{
+    StepParams p;
+    fill_params(c, p);
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((c.N + threads - 1) / threads);
+    const size_t smem = (size_t)c.W * threads * sizeof(uint32_t);
+    if (c.quant)
+        encode_init_kernel<true><<<blocks, threads, smem, c.stream>>>(p, d_state, c.N);
+    else
+        encode_init_kernel<false><<<blocks, threads, 0, c.stream>>>(p, d_state, c.N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_f64(Ctx &c, double *d_state)
+{
+    StepParams p;
+    fill_params(c, p);
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((c.N + threads - 1) / threads);
+    if (c.quant)
+        decode_f64_kernel<true><<<blocks, threads, 0, c.stream>>>(p, d_state, c.N);
+    else
+        decode_f64_kernel<false><<<blocks, threads, 0, c.stream>>>(p, d_state, c.N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure(Ctx &c)
+{
+    StepParams p;
+    fill_params(c, p);
+    cudaError_t e = cudaMemsetAsync(c.d_z, 0, sizeof(double), c.stream);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (c.N + kThreads - 1) / kThreads;
+    if (blocks > (int64_t)c.n_sms * 8) blocks = (int64_t)c.n_sms * 8;
+    if (blocks < 1) blocks = 1;
+    const unsigned b = (unsigned)blocks;
+    if (c.scene.dim == 2) {
+        if (c.quant) measure_kernel<2, true><<<b, kThreads, 0, c.stream>>>(p, c.N, c.d_z);
+        else measure_kernel<2, false><<<b, kThreads, 0, c.stream>>>(p, c.N, c.d_z);
+    } else {
+        if (c.quant) measure_kernel<3, true><<<b, kThreads, 0, c.stream>>>(p, c.N, c.d_z);
+        else measure_kernel<3, false><<<b, kThreads, 0, c.stream>>>(p, c.N, c.d_z);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_f32(int dim, int material, const CompCodec *cc, int nc, int W, uint64_t seed, int dither,
+                            uint32_t step, const float *d_vals, int64_t N, uint32_t *d_words, int64_t ld,
+                            unsigned long long *d_stats, cudaStream_t s)
+{
+    (void)dim;
+    (void)material;
+    StepParams p;
+    memset(&p, 0, sizeof(p));
+    p.n_comp = nc;
+    p.n_words = W;
+    p.dither = dither;
+    p.seed_lo = (uint32_t)seed;
+    p.seed_hi = (uint32_t)(seed >> 32);
+    p.step = step;
+    for (int q = 0; q < nc; ++q) p.comp[q] = cc[q];
+    p.words = d_words;
+    p.ld = ld;
+    p.stats = d_stats;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    if (N > 0) pack_f32_kernel<<<blocks, threads, (size_t)W * threads * sizeof(uint32_t), s>>>(p, d_vals, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_f32(int dim, int material, const CompCodec *cc, int nc, const uint32_t *d_words,
+                              int64_t N, int64_t ld, float *d_vals, cudaStream_t s)
+{
+    (void)dim;
+    (void)material;
+    StepParams p;
+    memset(&p, 0, sizeof(p));
+    p.n_comp = nc;
+    for (int q = 0; q < nc; ++q) p.comp[q] = cc[q];
+    p.words = const_cast<uint32_t *>(d_words);
+    p.ld = ld;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    if (N > 0) unpack_f32_kernel<<<blocks, threads, 0, s>>>(p, d_vals, N);
+    return cudaGetLastError();
+}
+
+}  // namespace qmpm

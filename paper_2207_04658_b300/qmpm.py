@@ -1,0 +1,336 @@
+"""Thin Python binding of ``libqmpm.so`` (the C ABI in ``include/qmpm.h``).
+
+Argument marshalling only: every step of the simulation runs in the library's CUDA
+kernels.  The functions keep the C names (``qmpm_init``, ``qmpm_step``, ...); ``Scene``
+wraps a handle.  Loading fails loudly if the library is missing: there is no CPU
+fallback.  PyTorch is used only for device buffers and streams.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import scenes as _scenes
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqmpm.so")
+
+MAX_COMP = 24
+MATERIALS = {"neohookean": 0, "corotated": 1, "fluid": 2}
+FLAG_STATS, FLAG_STRICT, FLAG_PROFILE = 1, 2, 4
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "SCHEME", -4: "CUDA", -5: "TIMEOUT",
+          -6: "OVERFLOW"}
+
+
+class QmpmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qmpm error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class qmpm_scene_t(ct.Structure):
+    _fields_ = [("dim", ct.c_int32), ("material", ct.c_int32), ("grid_log2", ct.c_int32),
+                ("bound", ct.c_int32), ("n_particles", ct.c_int64), ("dt", ct.c_double),
+                ("E", ct.c_double), ("nu", ct.c_double), ("bulk", ct.c_double),
+                ("p_vol", ct.c_double), ("p_mass", ct.c_double), ("gravity", ct.c_double * 3),
+                ("seed", ct.c_uint64), ("dither", ct.c_int32), ("resort_every", ct.c_int32),
+                ("chunk", ct.c_int32), ("flags", ct.c_int32)]
+
+
+class qmpm_field_t(ct.Structure):
+    _fields_ = [("bits", ct.c_int32), ("frac", ct.c_int32), ("offset", ct.c_int64),
+                ("container", ct.c_int32)]
+
+
+class qmpm_scheme_t(ct.Structure):
+    _fields_ = [("quantized", ct.c_int32), ("field", qmpm_field_t * 4), ("n_words", ct.c_int32),
+                ("bitpos", ct.c_int32 * MAX_COMP)]
+
+
+class qmpm_stats_t(ct.Structure):
+    _fields_ = [("saturations", ct.c_int64 * 4), ("round_ups", ct.c_int64 * 4),
+                ("round_downs", ct.c_int64 * 4), ("out_of_grid", ct.c_int64),
+                ("out_of_tile", ct.c_int64), ("steps", ct.c_int64), ("active_blocks", ct.c_int64),
+                ("error_word", ct.c_int32), ("n_words", ct.c_int32)]
+
+    def as_dict(self):
+        return {"saturations": list(self.saturations), "round_ups": list(self.round_ups),
+                "round_downs": list(self.round_downs), "out_of_grid": self.out_of_grid,
+                "out_of_tile": self.out_of_tile, "steps": self.steps,
+                "active_blocks": self.active_blocks, "error_word": self.error_word,
+                "n_words": self.n_words}
+
+
+class qmpm_profile_t(ct.Structure):
+    _fields_ = [("step_ms", ct.c_double), ("step_launches", ct.c_int64), ("clear_ms", ct.c_double),
+                ("clear_launches", ct.c_int64), ("sort_ms", ct.c_double), ("sort_calls", ct.c_int64),
+                ("p2g_ms", ct.c_double), ("p2g_launches", ct.c_int64),
+                ("kernel_launches", ct.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class qmpm_solve_in_t(ct.Structure):
+    _fields_ = [("H", ct.c_int32), ("P", ct.c_double * 8), ("g", ct.c_double * 8),
+                ("lo", ct.c_double * 8), ("hi", ct.c_double * 8), ("kappa", ct.c_double),
+                ("z", ct.c_double), ("eps", ct.c_double), ("mode", ct.c_int32),
+                ("rounding", ct.c_int32)]
+
+
+class qmpm_solve_out_t(ct.Structure):
+    _fields_ = [("delta_cont", ct.c_double * 8), ("bits_paper", ct.c_int32 * 8),
+                ("bits", ct.c_int32 * 8), ("frac", ct.c_int32 * 8), ("offset", ct.c_int64 * 8),
+                ("pred_err", ct.c_double), ("total_bits", ct.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/qmpm.h
+_P = ct.POINTER
+_SIGNATURES = [
+    ("qmpm_scheme_layout", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t)]),
+    ("qmpm_scheme_solve", ct.c_int, [_P(qmpm_solve_in_t), _P(qmpm_solve_out_t)]),
+    ("qmpm_init", ct.c_int, [_P(qmpm_scene_t), _P(qmpm_scheme_t), _P(ct.c_double), ct.c_void_p,
+                             _P(ct.c_void_p)]),
+    ("qmpm_step", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("qmpm_readback", ct.c_int, [ct.c_void_p, _P(ct.c_double), _P(ct.c_uint32), _P(ct.c_int64),
+                                 _P(qmpm_stats_t)]),
+    ("qmpm_measure", ct.c_int, [ct.c_void_p, _P(ct.c_double)]),
+    ("qmpm_step_host", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
+    ("qmpm_profile", ct.c_int, [ct.c_void_p, _P(qmpm_profile_t), ct.c_int32]),
+    ("qmpm_state_device", ct.c_int, [ct.c_void_p, _P(ct.c_void_p), _P(ct.c_int64),
+                                     _P(ct.c_void_p)]),
+    ("qmpm_destroy", ct.c_int, [ct.c_void_p]),
+    ("qmpm_last_error", ct.c_char_p, []),
+    ("qmpm_pack_f32", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t), ct.c_uint64, ct.c_int32,
+                                 ct.c_uint32, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int64,
+                                 _P(qmpm_stats_t), ct.c_void_p]),
+    ("qmpm_unpack_f32", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t), ct.c_void_p,
+                                   ct.c_int64, ct.c_int64, ct.c_void_p, ct.c_void_p]),
+]
+OPTIONAL_SIGNATURES = []
+
+
+def lib():
+    """Load libqmpm.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2207_04658_b300.build`")
+        L = ct.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES + OPTIONAL_SIGNATURES:
+            if not hasattr(L, name):
+                continue
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise QmpmError(rc, lib().qmpm_last_error().decode())
+    return rc
+
+
+def _dptr(a, ctype):
+    return a.ctypes.data_as(ct.POINTER(ctype))
+
+
+# ---------------------------------------------------------------------------- structs
+def make_scene_struct(scene, n_particles, flags=0):
+    s = qmpm_scene_t()
+    s.dim = scene["dim"]
+    s.material = MATERIALS[scene["material"]]
+    s.grid_log2 = scene["grid_log2"]
+    s.bound = scene.get("bound", 3)
+    s.n_particles = int(n_particles)
+    s.dt = scene["dt"]
+    s.E = scene.get("E", 0.0)
+    s.nu = scene.get("nu", 0.0)
+    s.bulk = scene.get("bulk", 0.0)
+    s.p_vol = scene["p_vol"]
+    s.p_mass = scene["p_vol"] * scene.get("rho", 1.0)
+    g = list(scene.get("gravity", (0.0, -9.8, 0.0))) + [0.0, 0.0, 0.0]
+    for a in range(3):
+        s.gravity[a] = g[a]
+    s.seed = int(scene.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    s.dither = int(bool(scene.get("dither", True)))
+    s.resort_every = int(scene.get("resort_every", 8))
+    s.chunk = int(scene.get("chunk", 0))
+    s.flags = int(flags)
+    return s
+
+
+FIELD_NAMES = ("x", "v", "C", "F")
+
+
+def make_scheme_struct(scheme, dim=None, material=None):
+    """Per-field scheme {"x": {bits, frac, offset, container}, "v", "C", "F" or "J"}; None
+    gives the FP32 state.  The layout is filled in when dim and material are given."""
+    sch = qmpm_scheme_t()
+    if scheme is None:
+        sch.quantized = 0
+    else:
+        sch.quantized = 1
+        for h, name in enumerate(FIELD_NAMES):
+            f = scheme[name] if name in scheme else scheme["J"]
+            sch.field[h].bits = int(f["bits"])
+            sch.field[h].frac = int(f["frac"])
+            sch.field[h].offset = int(f["offset"])
+            sch.field[h].container = int(f.get("container", 0))
+    if dim is not None:
+        qmpm_scheme_layout(dim, MATERIALS[material], sch)
+    return sch
+
+
+# ---------------------------------------------------------------------------- C names
+def qmpm_scheme_layout(dim, material, scheme_struct):
+    _check(lib().qmpm_scheme_layout(dim, material, ct.byref(scheme_struct)))
+    return scheme_struct
+
+
+def qmpm_scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper", kappa=2.0):
+    si = qmpm_solve_in_t()
+    si.H = len(P)
+    for h in range(len(P)):
+        si.P[h], si.g[h], si.lo[h], si.hi[h] = P[h], g[h], lo[h], hi[h]
+    si.kappa, si.z, si.eps = kappa, z, eps
+    si.mode = 0 if mode == "error" else 1
+    si.rounding = 0 if rounding == "paper" else 1
+    so = qmpm_solve_out_t()
+    _check(lib().qmpm_scheme_solve(ct.byref(si), ct.byref(so)))
+    H = len(P)
+    return {"delta_cont": list(so.delta_cont)[:H], "bits_paper": list(so.bits_paper)[:H],
+            "bits": list(so.bits)[:H], "frac": list(so.frac)[:H],
+            "offset": [int(v) for v in so.offset][:H], "pred_err": so.pred_err,
+            "total_bits": so.total_bits}
+
+
+def qmpm_init(scene_struct, scheme_struct, h_state, stream=0):
+    h = ct.c_void_p()
+    st = np.ascontiguousarray(h_state, dtype=np.float64)
+    _check(lib().qmpm_init(ct.byref(scene_struct), ct.byref(scheme_struct), _dptr(st, ct.c_double),
+                           ct.c_void_p(stream), ct.byref(h)))
+    return h
+
+
+def qmpm_step(h, nsteps):
+    _check(lib().qmpm_step(h, int(nsteps)))
+
+
+def qmpm_readback(h, h_state=None, h_words=None, h_ids=None, stats=None):
+    _check(lib().qmpm_readback(
+        h,
+        _dptr(h_state, ct.c_double) if h_state is not None else None,
+        _dptr(h_words, ct.c_uint32) if h_words is not None else None,
+        _dptr(h_ids, ct.c_int64) if h_ids is not None else None,
+        ct.byref(stats) if stats is not None else None))
+
+
+def qmpm_measure(h):
+    z = ct.c_double(0.0)
+    _check(lib().qmpm_measure(h, ct.byref(z)))
+    return z.value
+
+
+def qmpm_step_host(h, nsteps, h_words_in_ptr, h_words_out_ptr):
+    _check(lib().qmpm_step_host(h, int(nsteps), ct.c_void_p(h_words_in_ptr),
+                                ct.c_void_p(h_words_out_ptr)))
+
+
+def qmpm_profile(h, reset=True):
+    p = qmpm_profile_t()
+    _check(lib().qmpm_profile(h, ct.byref(p), int(reset)))
+    return p.as_dict()
+
+
+def qmpm_state_device(h):
+    w, ld, ids = ct.c_void_p(), ct.c_int64(), ct.c_void_p()
+    _check(lib().qmpm_state_device(h, ct.byref(w), ct.byref(ld), ct.byref(ids)))
+    return w.value, ld.value, ids.value
+
+
+def qmpm_destroy(h):
+    _check(lib().qmpm_destroy(h))
+
+
+def qmpm_pack_f32(dim, material, scheme_struct, seed, dither, step, d_vals_ptr, N, d_words_ptr, ld,
+                  stats=None, stream=0):
+    _check(lib().qmpm_pack_f32(dim, material, ct.byref(scheme_struct), int(seed) & (2**64 - 1),
+                               int(dither), int(step), ct.c_void_p(d_vals_ptr), int(N),
+                               ct.c_void_p(d_words_ptr), int(ld),
+                               ct.byref(stats) if stats is not None else None, ct.c_void_p(stream)))
+
+
+def qmpm_unpack_f32(dim, material, scheme_struct, d_words_ptr, N, ld, d_vals_ptr, stream=0):
+    _check(lib().qmpm_unpack_f32(dim, material, ct.byref(scheme_struct), ct.c_void_p(d_words_ptr),
+                                 int(N), int(ld), ct.c_void_p(d_vals_ptr), ct.c_void_p(stream)))
+
+
+# ---------------------------------------------------------------------------- Scene
+class Scene:
+    """One simulation resident on the device (a qmpm handle)."""
+
+    def __init__(self, scene, scheme, state0, stream=0, stats=False, strict=False, profile=False):
+        self.scene = dict(scene)
+        self.dim = scene["dim"]
+        self.material = scene["material"]
+        state0 = np.ascontiguousarray(state0, dtype=np.float64)
+        self.N = state0.shape[0]
+        self.n_comp = _scenes.n_comp(self.dim, self.material)
+        assert state0.shape[1] == self.n_comp
+        flags = ((FLAG_STATS if stats else 0) | (FLAG_STRICT if strict else 0)
+                 | (FLAG_PROFILE if profile else 0))
+        self._scene_struct = make_scene_struct(scene, self.N, flags)
+        self._scheme_struct = make_scheme_struct(scheme, self.dim, self.material)
+        self.quantized = scheme is not None
+        self.n_words = self._scheme_struct.n_words
+        self.h = qmpm_init(self._scene_struct, self._scheme_struct, state0, stream)
+
+    def step(self, n=1):
+        qmpm_step(self.h, n)
+
+    def measure(self):
+        return qmpm_measure(self.h)
+
+    def readback(self, state=True, words=False, ids=True):
+        out = {}
+        hs = np.empty((self.N, self.n_comp)) if state else None
+        hw = np.empty((self.n_words, self.N), dtype=np.uint32) if words else None
+        hi = np.empty(self.N, dtype=np.int64) if ids else None
+        st = qmpm_stats_t()
+        qmpm_readback(self.h, hs, hw, hi, st)
+        if state:
+            out["state"] = hs
+        if words:
+            out["words"] = hw
+        if ids:
+            out["ids"] = hi
+        out["stats"] = st.as_dict()
+        return out
+
+    def state_by_id(self):
+        r = self.readback(state=True, ids=True)
+        s = np.empty_like(r["state"])
+        s[r["ids"]] = r["state"]
+        return s
+
+    def profile(self, reset=True):
+        return qmpm_profile(self.h, reset)
+
+    def packed_bytes_per_particle(self):
+        return 4 * self.n_words
+
+    def close(self):
+        if self.h is not None:
+            qmpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

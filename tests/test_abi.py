@@ -1,0 +1,106 @@
+"""The C ABI library loads, exports every entry point include/qmpm.h declares, and its
+host-only parts (record layout, scheme solve) agree with the oracle.  No GPU needed:
+only pure-host entry points are called."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "qmpm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(qmpm_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2207_04658_b300 import build, qmpm
+    build.build()
+    qmpm.lib()
+    return qmpm
+
+
+def test_library_exports_every_declared_symbol(q):
+    names = declared_functions()
+    assert "qmpm_init" in names and "qmpm_scheme_solve" in names and len(names) >= 12
+    L = ct.CDLL(q.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_declared_symbols(q):
+    bound = {n for n, _, _ in q._SIGNATURES + q.OPTIONAL_SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+CASES = [(2, "neohookean"), (2, "fluid"), (3, "corotated"), (3, "fluid")]
+
+
+@pytest.mark.parametrize("dim,material", CASES)
+def test_layout_matches_oracle(q, oracle, dim, material):
+    gen = np.random.default_rng(dim * 7 + len(material))
+    for trial in range(50):
+        bits = [int(b) for b in gen.integers(1, 25, 4)]
+        cont = [int(c) for c in gen.choice([0, 32, 64], 4)]
+        scheme = {n: dict(bits=bits[h], frac=10, offset=-5, container=cont[h])
+                  for h, n in enumerate(["x", "v", "C", "J" if material == "fluid" else "F"])}
+        s = q.make_scheme_struct(scheme, dim, material)
+        fields = oracle.comp_fields(dim, material)
+        pos, nw = oracle.layout(dim, material, [bits[h] for h in fields], cont)
+        assert s.n_words == nw
+        assert [s.bitpos[c] for c in range(len(fields))] == pos
+
+
+def test_layout_rejects_bad_schemes(q):
+    base = {n: dict(bits=16, frac=10, offset=0) for n in ["x", "v", "C", "F"]}
+    for field, key, val in [("x", "bits", 25), ("v", "bits", 0), ("C", "offset", 2 ** 24),
+                            ("F", "container", 48)]:
+        bad = {k: dict(v) for k, v in base.items()}
+        bad[field][key] = val
+        with pytest.raises(q.QmpmError) as ei:
+            q.make_scheme_struct(bad, 3, "corotated")
+        assert ei.value.code == -3
+    with pytest.raises(q.QmpmError):
+        q.make_scheme_struct(base, 4, "corotated")
+
+
+@pytest.mark.parametrize("mode,rounding", [("error", "paper"), ("error", "exact"),
+                                           ("memory", "paper"), ("memory", "exact")])
+def test_scheme_solve_matches_oracle(q, oracle, mode, rounding):
+    gen = np.random.default_rng(len(mode) * 10 + len(rounding))
+    for trial in range(20):
+        H = int(gen.integers(1, 6))
+        P = gen.integers(1000, 100000, H).astype(float)
+        g = 10.0 ** gen.uniform(-6, 2, H)
+        lo = gen.uniform(-5, 0, H)
+        hi = lo + 10.0 ** gen.uniform(-1, 1.5, H)
+        z = float(10.0 ** gen.uniform(-2, 3))
+        eps = float(10.0 ** gen.uniform(-3, -1)) if mode == "error" else float(gen.uniform(0.3, 0.7))
+        a = q.qmpm_scheme_solve(P, g, lo, hi, z, eps, mode=mode, rounding=rounding)
+        b = oracle.scheme_solve(P, g, lo, hi, z, eps, mode=mode, rounding=rounding)
+        assert a["bits"] == b["bits"] and a["frac"] == b["frac"] and a["offset"] == b["offset"]
+        assert a["bits_paper"] == b["bits_paper"]
+        assert np.allclose(a["delta_cont"], b["delta_cont"], rtol=1e-12)
+        assert a["pred_err"] == pytest.approx(b["pred_err"], rel=1e-12)
+
+
+def test_scheme_solve_rejects_bad_input(q):
+    with pytest.raises(q.QmpmError):
+        q.qmpm_scheme_solve([], [], [], [], 1.0, 0.01)
+    with pytest.raises(q.QmpmError):
+        q.qmpm_scheme_solve([1.0], [1.0], [0.0], [1.0], 1.0, 0.0)
+
+
+def test_missing_library_fails_loudly(monkeypatch, q):
+    import importlib
+    from paper_2207_04658_b300 import qmpm as qm
+    monkeypatch.setattr(qm, "_lib", None)
+    monkeypatch.setattr(qm, "LIB_PATH", "/nonexistent/libqmpm.so")
+    with pytest.raises(ImportError):
+        qm.lib()

@@ -1,0 +1,215 @@
+"""Device MLS-MPM step vs the oracle, through the C ABI.
+
+Bars (floating point, FP32 device vs FP64 oracle):
+  - initial encode + tile sort: bit-exact words and slot order;
+  - one quantized step from the same packed state: every packed component within
+    2 quantization steps (atomic ordering and FP32 rounding can move a value across a
+    rounding or dither threshold);
+  - FP32 state, one step: |gpu - oracle| <= 1e-5 (|oracle| + scale of the field);
+  - rollouts: the position measurement z within the error bound of the oracle's."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    from paper_2207_04658_b300 import qmpm
+    assert torch.cuda.is_available()
+    qmpm.lib()
+    return qmpm
+
+
+def small_scenes():
+    from paper_2207_04658_b300 import scenes
+    out = []
+    sc, s0 = scenes.block2d_scene(n_strata=(64, 32))
+    out.append(("block2d", sc, s0, scenes.block2d_scheme()))
+    sc, s0 = scenes.cubes3d_scene(n_cubes=2, cube_cells=10, ppc_axis=2, grid_log2=6, seed=5)
+    out.append(("cubes3d", sc, s0, scenes.fixed_scheme_3d("corotated")))
+    sc, s0 = scenes.cubes3d_scene(n_cubes=2, cube_cells=8, ppc_axis=2, grid_log2=5, seed=6,
+                                  material="neohookean", dt=1e-4)
+    out.append(("nh3d", sc, s0, scenes.fixed_scheme_3d("neohookean", x_container=0)))
+    sc, s0 = scenes.dambreak3d_scene(column_cells=12, ppc_axis=2, grid_log2=6, dt=5e-5)
+    out.append(("dam3d", sc, s0, scenes.fixed_scheme_3d("fluid", C=(16, -2048.0, 2048.0))))
+    return out
+
+
+SCENES = small_scenes()
+IDS = [s[0] for s in SCENES]
+
+
+def quanta(oracle, scene, scheme):
+    cd = oracle.make_codec(scene, scheme)
+    return np.array([2.0 ** -cd.frac[c] for c in range(cd.n_comp)])
+
+
+@pytest.mark.parametrize("case", range(len(SCENES)), ids=IDS)
+def test_init_encode_and_sort_bit_exact(q, oracle, case):
+    name, sc, s0, sch = SCENES[case]
+    g = q.Scene(sc, sch, s0)
+    r = g.readback(state=False, words=True, ids=True)
+    o = oracle.QuantRollout(sc, sch, s0)
+    assert np.array_equal(r["ids"], o.ids)
+    assert np.array_equal(r["words"].T, o.words)
+    g.close()
+
+
+@pytest.mark.parametrize("case", range(len(SCENES)), ids=IDS)
+def test_one_quantized_step_within_two_quanta(q, oracle, case):
+    name, sc, s0, sch = SCENES[case]
+    g = q.Scene(sc, sch, s0, stats=True)
+    o = oracle.QuantRollout(sc, sch, s0)
+    g.step(1)
+    o.step(1)
+    r = g.readback(state=True, ids=True)
+    assert np.array_equal(r["ids"], o.ids)
+    d = np.abs(r["state"] - o.state()) / quanta(oracle, sc, sch)[None]
+    assert d.max() <= 2.0 + 1e-9, f"max {d.max()} quanta at {np.unravel_index(d.argmax(), d.shape)}"
+    # most components agree exactly
+    assert (d == 0).mean() > 0.95
+    assert sum(r["stats"]["saturations"]) == 0
+    g.close()
+
+
+@pytest.mark.parametrize("case", range(len(SCENES)), ids=IDS)
+def test_fp32_step_matches_fp64(q, oracle, case):
+    name, sc, s0, sch = SCENES[case]
+    sc = dict(sc, resort_every=0)
+    g = q.Scene(sc, None, s0)
+    o = oracle.Fp64Rollout(sc, s0)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+    r = g.readback(state=True, ids=True)
+    ref = np.empty_like(o.s)
+    ref[o.ids] = o.s
+    got = np.empty_like(r["state"])
+    got[r["ids"]] = r["state"]
+    dim = sc["dim"]
+    nc = got.shape[1]
+    n = 1 << sc["grid_log2"]
+    vmax = np.abs(ref[:, dim:2 * dim]).max()
+    # field scales: the domain for x, the largest speed for v, the velocity-gradient unit
+    # |v| / dx (times D^-1 dx^2 = 4) for C, and 1 for F or J
+    bounds = [0, dim, 2 * dim, 2 * dim + dim * dim, nc]
+    scales = [1.0, vmax + 1e-30, max(np.abs(ref[:, 2 * dim:2 * dim + dim * dim]).max(), 4 * vmax * n), 1.0]
+    for (a, b), scale in zip(zip(bounds[:-1], bounds[1:]), scales):
+        err = np.abs(got[:, a:b] - ref[:, a:b])
+        assert np.all(err <= 1e-5 * (np.abs(ref[:, a:b]) + scale)), (name, a, b, err.max(), scale)
+    g.close()
+
+
+@pytest.mark.parametrize("case", [0, 1, 3], ids=[IDS[0], IDS[1], IDS[3]])
+def test_quantized_rollout_tracks_oracle(q, oracle, case):
+    name, sc, s0, sch = SCENES[case]
+    steps = 40
+    g = q.Scene(sc, sch, s0, stats=True)
+    o = oracle.QuantRollout(sc, sch, s0)
+    g.step(steps)
+    o.step(steps)
+    r = g.readback(state=True, ids=True)
+    got = np.empty_like(r["state"])
+    got[r["ids"]] = r["state"]
+    ref = np.empty_like(got)
+    ref[o.ids] = o.state()
+    dim = sc["dim"]
+    zg, zo = oracle.mean_sq_pos(dim, got), oracle.mean_sq_pos(dim, ref)
+    assert abs(zg - zo) <= 1e-4 * abs(zo)
+    assert abs(g.measure() - zg) <= 1e-12 * abs(zg)
+    # positions stay within a few position quanta of the oracle's
+    dq = np.abs(got[:, :dim] - ref[:, :dim]) / quanta(oracle, sc, sch)[None, :dim]
+    assert np.percentile(dq, 99) <= 8
+    g.close()
+
+
+def test_drift_out_of_tile_slow_path(q, oracle):
+    # no re-sort after initialisation: particles leave their tiles and take the slow
+    # path; the result still matches the oracle's identical ordering
+    from paper_2207_04658_b300 import scenes
+    sc, s0 = scenes.cubes3d_scene(n_cubes=1, cube_cells=8, ppc_axis=2, grid_log2=5, seed=8,
+                                  material="corotated", dt=1e-4)
+    s0[:, 3:6] = np.array([30.0, -20.0, 25.0])  # fast uniform motion: ~3 cells in 30 steps
+    sc = dict(sc, resort_every=0)
+    sch = scenes.fixed_scheme_3d("corotated", v=(16, -64.0, 64.0))
+    g = q.Scene(sc, sch, s0, stats=True)
+    o = oracle.QuantRollout(sc, sch, s0)
+    for _ in range(30):
+        g.step(1)
+        o.step(1)
+    r = g.readback(state=True, ids=True)
+    assert r["stats"]["out_of_tile"] > 0
+    assert np.array_equal(r["ids"], o.ids)
+    d = np.abs(r["state"] - o.state()) / quanta(oracle, sc, sch)[None]
+    assert np.percentile(d, 99.9) <= 8
+
+
+def test_walls_stop_particles(q, oracle):
+    # a block dropped onto the floor: sticky wall nodes carry zero velocity
+    from paper_2207_04658_b300 import scenes
+    sc, s0 = scenes.block2d_scene(n_strata=(32, 16))
+    s0[:, 1] -= 0.4 - 3.2 / 128  # rest just above the wall band
+    s0[:, 3] = -2.0
+    sch = scenes.block2d_scheme()
+    g = q.Scene(sc, sch, s0)
+    o = oracle.QuantRollout(sc, sch, s0)
+    g.step(30)
+    o.step(30)
+    got = g.state_by_id()
+    ref = np.empty_like(got)
+    ref[o.ids] = o.state()
+    assert got[:, 1].min() >= 0.5 / 128
+    d = np.abs(got - ref) / quanta(oracle, sc, sch)[None]
+    assert np.percentile(d, 99) <= 8
+
+
+def test_empty_and_single_particle(q, oracle):
+    from paper_2207_04658_b300 import scenes
+    sc, s0 = scenes.block2d_scene(n_strata=(4, 4))
+    sch = scenes.block2d_scheme()
+    g = q.Scene(sc, sch, s0[:0])
+    g.step(3)
+    r = g.readback(state=True, words=True, ids=True)
+    assert r["state"].shape == (0, 12) and g.measure() == 0.0
+    g.close()
+    g = q.Scene(sc, sch, s0[:1])
+    o = oracle.QuantRollout(sc, sch, s0[:1])
+    g.step(5)
+    o.step(5)
+    d = np.abs(g.readback()["state"] - o.state()) / quanta(oracle, sc, sch)[None]
+    assert d.max() <= 2
+
+
+def test_strict_mode_reports_saturation(q):
+    from paper_2207_04658_b300 import scenes
+    sc, s0 = scenes.block2d_scene(n_strata=(16, 8))
+    sch = scenes.block2d_scheme()
+    sch["v"] = dict(bits=4, frac=13, offset=-8, container=0)  # |v| < 1e-3 only
+    s0[:, 2:4] = 1.0
+    g = q.Scene(sc, sch, s0, stats=True, strict=True)
+    with pytest.raises(q.QmpmError) as ei:
+        g.readback()
+    assert ei.value.code == -6
+
+
+def test_step_host_round_trip(q, oracle):
+    # the end-to-end entry point (host words in and out) gives the resident result
+    import torch
+    from paper_2207_04658_b300 import scenes
+    name, sc, s0, sch = SCENES[1]
+    a = q.Scene(sc, sch, s0)
+    b = q.Scene(sc, sch, s0)
+    w = a.readback(state=False, words=True, ids=False)["words"]
+    hin = torch.from_numpy(w.copy()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    q.qmpm_step_host(b.h, 1, hin.data_ptr(), hout.data_ptr())
+    a.step(1)
+    wa = a.readback(state=True, words=True, ids=False)
+    sb = b.readback(state=True, ids=False)["state"]
+    d = np.abs(wa["state"] - sb) / quanta(oracle, sc, sch)[None]
+    assert d.max() <= 2
+    assert np.array_equal(hout.numpy(), b.readback(state=False, words=True, ids=False)["words"])
