@@ -48,12 +48,14 @@ enum { QMPM_FIELD_X = 0, QMPM_FIELD_V = 1, QMPM_FIELD_C = 2, QMPM_FIELD_F = 3 };
 /* Scene: one MLS-MPM simulation (the simulator quantized in Sec. 8.1).
  * Grid: n = 2^grid_log2 nodes per axis (n >= 16), dx = 1/n; sticky walls zero the grid
  * velocity within `bound` nodes of each face.  Particles keep a tile order: they are
- * stably re-sorted by the 2^d-block tile that holds their stencil at initialisation and
- * after every `resort_every`-th step (0 disables later re-sorts). */
+ * stably re-sorted by (tile, cell) at initialisation and after every `resort_every`-th
+ * step (0 disables later re-sorts), where the tile is the 2^d-block group of 4^d-node
+ * grid blocks that holds the particle's stencil and the cell is its stencil base inside
+ * the tile.  The dither counter of a store is the particle's slot in this order. */
 typedef struct {
     int32_t dim;          /* 2 or 3 */
     int32_t material;     /* QMPM_NEOHOOKEAN, QMPM_COROTATED, QMPM_FLUID */
-    int32_t grid_log2;    /* 4 .. 11 */
+    int32_t grid_log2;    /* 4 .. 11 (2D), 4 .. 10 (3D) */
     int32_t bound;        /* >= 2 */
     int64_t n_particles;
     double dt;

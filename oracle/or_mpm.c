@@ -304,15 +304,17 @@ void or_step_quant(const or_phys_t *ph, const or_codec_t *cd, int64_t N, uint32_
 }
 
 /* ------------------------------------------------------------------------------------
- * Particle ordering.  A particle with stencil base b (per axis) is keyed by the block
- * T = floor((b + 3) / 4) of a grid padded by one 4-node block on each side; the tile of
- * 2^d blocks T..T+1 then holds every stencil node of bases 4(T-1) .. 4(T-1)+5, one node
- * of slack on each side of the bases seen when the key was taken.
+ * Particle ordering.  A particle with stencil base b (per axis) belongs to the tile whose
+ * origin is block T = floor((b + 3) / 4) of a grid padded by one 4-node block on each
+ * side; the tile of 2^d blocks T..T+1 then holds every stencil node of bases 4(T-1) ..
+ * 4(T-1)+5, one node of slack on each side of the bases seen when the key was taken.
+ * Within a tile, particles are ordered by their cell c = b - 4(T-1) - 1 in [0,4)^d:
+ *   key = linear(T) * 4^d + linear(c).
  * ---------------------------------------------------------------------------------- */
 int64_t or_n_keys(const or_phys_t *ph)
 {
     const int64_t nb = ((int64_t)1 << ph->grid_log2) / 4 + 2;
-    return ph->dim == 2 ? nb * nb : nb * nb * nb;
+    return ph->dim == 2 ? nb * nb * 16 : nb * nb * nb * 64;
 }
 
 void or_tile_keys(const or_phys_t *ph, int64_t N, const double *s, int64_t *keys)
@@ -323,9 +325,13 @@ void or_tile_keys(const or_phys_t *ph, int64_t N, const double *s, int64_t *keys
         int base[3];
         double f[3], w[3][3];
         stencil(ph, s + p * nc, base, f, w);
-        int64_t key = 0;
-        for (int a = 0; a < d; ++a) key = key * nb + (int64_t)((base[a] + 3) / 4);
-        keys[p] = key;
+        int64_t tile = 0, cell = 0;
+        for (int a = 0; a < d; ++a) {
+            const int T = (base[a] + 3) / 4;
+            tile = tile * nb + (int64_t)T;
+            cell = cell * 4 + (int64_t)(base[a] - 4 * (T - 1) - 1);
+        }
+        keys[p] = tile * (d == 2 ? 16 : 64) + cell;
     }
 }
 

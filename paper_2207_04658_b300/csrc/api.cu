@@ -143,7 +143,8 @@ int validate_scene(const qmpm_scene_t *s)
     if (!s) return fail(QMPM_ERR_INVALID_ARG, "scene is NULL");
     if (s->dim != 2 && s->dim != 3) return fail(QMPM_ERR_INVALID_ARG, "dim must be 2 or 3");
     if (s->material < 0 || s->material > 2) return fail(QMPM_ERR_INVALID_ARG, "unknown material");
-    if (s->grid_log2 < 4 || s->grid_log2 > 11) return fail(QMPM_ERR_INVALID_ARG, "grid_log2 must be in 4..11");
+    if (s->grid_log2 < 4 || s->grid_log2 > (s->dim == 2 ? 11 : 10))
+        return fail(QMPM_ERR_INVALID_ARG, "grid_log2 must be in 4..11 (2D) or 4..10 (3D)");
     if (s->bound < 2) return fail(QMPM_ERR_INVALID_ARG, "bound must be >= 2 (stencils must stay inside)");
     if (s->n_particles < 0 || s->n_particles > 0x7FFFFFFFLL)
         return fail(QMPM_ERR_INVALID_ARG, "n_particles must be in [0, 2^31)");
@@ -215,6 +216,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
     c->chunk = scene->chunk > 0 ? scene->chunk : qmpm::kMaxChunk;
     c->key_bits = 1;
     while ((int64_t(1) << c->key_bits) < c->n_blocks) ++c->key_bits;
+    c->key_bits += scene->dim == 2 ? 4 : 6;  // cell inside the tile
     c->key_bits = (c->key_bits + 7) / 8 * 8;
 
     cudaError_t e;

@@ -41,7 +41,7 @@ struct StepParams {
     // physics
     int32_t n, nb, bound, n_comp;
     float dt, inv_dx, dx, Dinv;
-    float p_mass, stress_coef;  // stress_coef = -dt * p_vol * Dinv
+    float p_mass, inv_p_mass, stress_coef;  // stress_coef = -dt * p_vol * Dinv
     float mu, lambda, bulk;
     float gravity[3];
     // codec

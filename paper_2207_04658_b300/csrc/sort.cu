@@ -122,7 +122,7 @@ __global__ void tile_key_kernel(const __grid_constant__ StepParams P, int64_t N,
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
-    uint32_t key = 0;
+    uint32_t key = 0, cell = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         const CompCodec &cc = P.comp[a];
@@ -136,9 +136,11 @@ __global__ void tile_key_kernel(const __grid_constant__ StepParams P, int64_t N,
         }
         int b = __float2int_rd(x * P.inv_dx - 0.5f);
         b = b < 0 ? 0 : (b > P.n - 3 ? P.n - 3 : b);
-        key = key * (uint32_t)P.nb + (uint32_t)((b + 3) >> 2);
+        const int T = (b + 3) >> 2;
+        key = key * (uint32_t)P.nb + (uint32_t)T;
+        cell = cell * 4u + (uint32_t)(b - 4 * (T - 1) - 1);
     }
-    keys[p] = key;
+    keys[p] = key * (DIM == 2 ? 16u : 64u) + cell;  // tile, then cell inside the tile
     vals[p] = (uint32_t)p;
 }
 
@@ -216,13 +218,15 @@ __global__ void gather_kernel(const uint32_t *words_in, uint32_t *words_out, con
     ids_out[i] = ids_in[src];
 }
 
-__global__ void segment_kernel(const uint32_t *sorted_keys, int64_t N, uint32_t *seg_begin, uint32_t *seg_end)
+// segment bounds per tile (the key without its cell bits)
+__global__ void segment_kernel(const uint32_t *sorted_keys, int64_t N, int cell_bits, uint32_t *seg_begin,
+                               uint32_t *seg_end)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const uint32_t k = sorted_keys[i];
-    if (i == 0 || sorted_keys[i - 1] != k) seg_begin[k] = (uint32_t)i;
-    if (i == N - 1 || sorted_keys[i + 1] != k) seg_end[k] = (uint32_t)(i + 1);
+    const uint32_t k = sorted_keys[i] >> cell_bits;
+    if (i == 0 || (sorted_keys[i - 1] >> cell_bits) != k) seg_begin[k] = (uint32_t)i;
+    if (i == N - 1 || (sorted_keys[i + 1] >> cell_bits) != k) seg_end[k] = (uint32_t)(i + 1);
 }
 
 __global__ void chunk_count_kernel(const uint32_t *seg_begin, const uint32_t *seg_end, uint32_t *key_chunks,
@@ -289,7 +293,8 @@ int resort(Ctx &c, std::string &err)
             e = cudaMemsetAsync(c.seg_begin, 0, sizeof(uint32_t) * c.n_blocks, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(c.seg_end, 0, sizeof(uint32_t) * c.n_blocks, s);
             if (e == cudaSuccess) {
-                segment_kernel<<<blocks_for(N, 256), 256, 0, s>>>(c.keys[src], N, c.seg_begin, c.seg_end);
+                segment_kernel<<<blocks_for(N, 256), 256, 0, s>>>(c.keys[src], N, c.scene.dim == 2 ? 4 : 6,
+                                                                  c.seg_begin, c.seg_end);
                 chunk_count_kernel<<<blocks_for(c.n_blocks + 1, 256), 256, 0, s>>>(c.seg_begin, c.seg_end,
                                                                                    c.key_chunks, c.n_blocks, c.chunk);
                 e = exclusive_scan_u32(c.key_chunks, c.n_blocks + 1, c.scan_partials, c.max_scan_partials, s);

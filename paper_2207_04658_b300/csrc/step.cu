@@ -11,7 +11,8 @@
 //   5. P2G of step t+1 from the decoded quantized values into a shared-memory tile,
 //      flushed to the other grid buffer with one vector atomic per touched node.
 // Work item: a chunk of up to 256 sorted particles that share one tile (2^d blocks of
-// 4^d nodes); one thread per particle; persistent CTAs stride over the chunk list.
+// 4^d nodes); one thread per particle, records staged through shared memory so that
+// global loads and stores stay coalesced; persistent CTAs stride over the chunk list.
 // Particles that drifted out of their tile since the last re-sort take a slow path
 // through global memory.
 #include <cstdio>
@@ -44,8 +45,9 @@ __device__ __forceinline__ void polar3(const float *F, float *R)
         const float c6 = X[1] * X[5] - X[2] * X[4], c7 = X[2] * X[3] - X[0] * X[5],
                     c8 = X[0] * X[4] - X[1] * X[3];
         const float det = X[0] * c0 + X[1] * c1 + X[2] * c2;
-        const float g = rcbrtf(fabsf(det));
-        const float a = 0.5f * g, b = 0.5f / (g * det);
+        // g = |det|^(-1/3); the scale only speeds convergence, so fast log2/exp2 suffice
+        const float g = exp2f(-0.333333343f * __log2f(fabsf(det)));
+        const float a = 0.5f * g, b = 0.5f * __frcp_rn(g * det);
         const float cof[9] = {c0, c1, c2, c3, c4, c5, c6, c7, c8};
         float diff = 0.0f;
 #pragma unroll
@@ -161,16 +163,96 @@ __device__ __forceinline__ bool stencil(const float *x, const StepParams &P, int
     return out;
 }
 
+// Shared-memory tile of 8^d nodes, one float array per quantity (m, momentum or velocity
+// components).  In 3D a node's slot is swizzled (z index XOR 4 on odd x rows) so that the
+// 64 cells of a block spread over all 32 banks.
 template <int DIM>
 __device__ __forceinline__ int tile_index(int i, int j, int k)
 {
-    return DIM == 2 ? (i * 8 + j) : ((i * 8 + j) * 8 + k);
+    return DIM == 2 ? (i * 8 + j) : ((i * 8 + j) * 8 + (k ^ ((i & 1) << 2)));
 }
 
 __device__ __forceinline__ void stat_add(unsigned long long *stats, int idx, unsigned long long v)
 {
     if (v) atomicAdd(stats + idx, v);
 }
+
+// G2P gather of one particle, as separable sums: for each (i, j) row, sum over k the
+// weighted velocities (S) and the ones weighted by dpz (T); then over j, then over i:
+//   v = sum_i wx S_i,  B[:,0] = sum_i wx dpx S_i,  B[:,1] = sum_i wx U_i,  B[:,2] = sum_i wx V_i,
+//   with S_i = sum_j wy S_ij, U_i = sum_j wy dpy S_ij, V_i = sum_j wy T_ij.
+// FAST reads the shared tile; otherwise the node velocities come from global memory.
+template <int DIM, bool FAST>
+__device__ __forceinline__ void g2p_gather(const StepParams &P, const float *tvx, const float *tvy,
+                                           const float *tvz, int l0, int l1, int l2, const int *base,
+                                           const float (*w)[3], const float *dpx, const float *dpy,
+                                           const float *dpz, float *vn, float *B)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float Si[3] = {0.0f, 0.0f, 0.0f}, Ui[3] = {0.0f, 0.0f, 0.0f}, Vi[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float Sij[3] = {0.0f, 0.0f, 0.0f}, Tij[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
+                float g0, g1, g2 = 0.0f;
+                if (FAST) {
+                    const int q = tile_index<DIM>(l0 + i, l1 + j, l2 + k);
+                    g0 = tvx[q];
+                    g1 = tvy[q];
+                    if (DIM == 3) g2 = tvz[q];
+                } else {
+                    const int gx = base[0] + i, gy = base[1] + j, gz = DIM == 3 ? base[2] + k : 0;
+                    const float4 gv = node_velocity<DIM>(P.grid_in[node_addr<DIM>(P.nb, gx, gy, gz)], gx, gy, gz, P);
+                    g0 = gv.x;
+                    g1 = gv.y;
+                    g2 = gv.z;
+                }
+                const float wz = DIM == 3 ? w[2][k] : 1.0f;
+                const float wzd = DIM == 3 ? w[2][k] * dpz[k] : 0.0f;
+                Sij[0] += wz * g0;
+                Sij[1] += wz * g1;
+                if (DIM == 3) {
+                    Sij[2] += wz * g2;
+                    Tij[0] += wzd * g0;
+                    Tij[1] += wzd * g1;
+                    Tij[2] += wzd * g2;
+                }
+            }
+            const float wy = w[1][j], wyd = w[1][j] * dpy[j];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                Si[a] += wy * Sij[a];
+                Ui[a] += wyd * Sij[a];
+                if (DIM == 3) Vi[a] += wy * Tij[a];
+            }
+        }
+        const float wx = w[0][i], wxd = w[0][i] * dpx[i];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            vn[a] += wx * Si[a];
+            B[a * DIM + 0] += wxd * Si[a];
+            B[a * DIM + 1] += wx * Ui[a];
+            if (DIM == 3) B[a * DIM + 2] += wx * Vi[a];
+        }
+    }
+}
+
+// Block fixed point of the P2G tile: a contribution of magnitude at most the chunk's bound
+// maps to at most kFixMax = 2^23 - 64 units (the margin absorbs FP32 rounding of the
+// contribution), so 256 of them stay inside a 32-bit integer.
+constexpr float kFixMax = 8388544.0f;
+
+// Thread t works on the particle at position (t % 32) * 8 + t / 32 of its chunk: the
+// chunk is sorted by cell, so the 32 lanes of a warp land on different cells and the
+// shared-memory atomics of P2G rarely collide.
+__device__ __forceinline__ int spread(int t) { return (t & 31) * 8 + (t >> 5); }
+
+// Shared column of particle p's record words: p's row of 32 rotated by p / 32, which keeps
+// both the coalesced staging (lane l of warp w touches particle 32 w + l) and the spread
+// compute mapping (lane l of warp w touches particle 8 l + w) free of bank conflicts.
+__device__ __forceinline__ int column_of(int p) { return (p & ~31) | ((p + (p >> 5)) & 31); }
 
 // ------------------------------------------------------------------------------ step kernel
 template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P>
@@ -179,11 +261,15 @@ __global__ void __launch_bounds__(kThreads, 2) step_kernel(const __grid_constant
     using Tr = Traits<DIM, MAT>;
     constexpr int NC = Tr::NC, TN = Tr::TN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *tile_v = reinterpret_cast<float4 *>(smem_raw);
-    float4 *tile_p = tile_v + TN;
-    uint32_t *sw = reinterpret_cast<uint32_t *>(tile_p + TN);
+    float *tvx = reinterpret_cast<float *>(smem_raw);  // G2P velocities
+    float *tvy = tvx + TN, *tvz = tvy + TN;
+    int *tpm = reinterpret_cast<int *>(tvz + TN);       // P2G mass and momentum, fixed point
+    int *tpx = tpm + TN, *tpy = tpx + TN, *tpz = tpy + TN;
+    float *red = reinterpret_cast<float *>(tpz + TN);   // per-warp maxima (kThreads / 32)
+    uint32_t *sw = reinterpret_cast<uint32_t *>(red + kThreads / 32);  // record words, column per particle
     const int tid = threadIdx.x;
-    uint32_t *my = sw + tid;  // this thread's column of record words, stride kThreads
+    const int pj = spread(tid);   // this thread's particle within the chunk
+    uint32_t *my = sw + column_of(pj);  // its column of record words, stride kThreads
 
     unsigned long long cnt_sat[4] = {0, 0, 0, 0}, cnt_up[4] = {0, 0, 0, 0}, cnt_dn[4] = {0, 0, 0, 0};
     unsigned long long cnt_oog = 0, cnt_oot = 0;
@@ -202,31 +288,50 @@ __global__ void __launch_bounds__(kThreads, 2) step_kernel(const __grid_constant
         }
         const int o0 = 4 * (T0 - 1), o1 = 4 * (T1 - 1), o2 = 4 * (T2 - 1);  // tile origin node
 
-        // 1. stage the grid tile (velocities) and clear the P2G tile
+        // 1. stage the grid tile (velocities: the grid update) and clear the P2G tile
         for (int t = tid; t < TN; t += kThreads) {
             const int i = DIM == 2 ? (t >> 3) : (t >> 6), j = DIM == 2 ? (t & 7) : ((t >> 3) & 7);
             const int k = DIM == 2 ? 0 : (t & 7);
+            const int q = tile_index<DIM>(i, j, k);
             if (DO_G2P) {
                 const float4 mm = P.grid_in[node_addr<DIM>(P.nb, o0 + i, o1 + j, o2 + k)];
-                tile_v[t] = node_velocity<DIM>(mm, o0 + i, o1 + j, o2 + k, P);
+                const float4 v = node_velocity<DIM>(mm, o0 + i, o1 + j, o2 + k, P);
+                tvx[q] = v.x;
+                tvy[q] = v.y;
+                if (DIM == 3) tvz[q] = v.z;
             }
-            tile_p[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            tpm[q] = 0;
+            tpx[q] = 0;
+            tpy[q] = 0;
+            if (DIM == 3) tpz[q] = 0;
         }
-        // 2. this thread's packed record
-        const bool active = tid < (int)ch.count;
-        const int64_t slot = (int64_t)ch.start + tid;
-        if (active)
-            for (int j = 0; j < P.n_words; ++j) my[j * kThreads] = P.words[j * P.ld + slot];
+        // 2. coalesced load of the chunk's records into shared memory (column per slot)
+        const int mycol = column_of(tid);
+        if (tid < (int)ch.count)
+            for (int j = 0; j < P.n_words; ++j) sw[j * kThreads + mycol] = P.words[j * P.ld + ch.start + tid];
         __syncthreads();
 
+        const bool active = pj < (int)ch.count;
+        const int64_t slot = (int64_t)ch.start + pj;
+        // P2G payload, kept across the barrier that fixes the chunk's fixed-point scale
+        int pbase[3] = {0, 0, 0};
+        float pw[3][3], pf[3] = {0.0f, 0.0f, 0.0f}, pA[DIM * DIM], pv[3] = {0.0f, 0.0f, 0.0f};
+        bool p_in_tile = false;
+        float bound = 0.0f;
         if (active) {
             float val[NC];
+            if (QUANT) {
+                // independent per-component extraction: words k and k+1 through a funnel shift
+                // (the column carries one padding word after the record)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                if (QUANT)
-                    val[c] = decode_u(extract(my, kThreads, P.comp[c]), P.comp[c]);
-                else
-                    val[c] = __uint_as_float(my[c * kThreads]);
+                for (int c = 0; c < NC; ++c) {
+                    const CompCodec &cc = P.comp[c];
+                    const uint32_t lo = my[cc.word * kThreads], hi = my[(cc.word + 1) * kThreads];
+                    val[c] = decode_u(__funnelshift_r(lo, hi, cc.shift) & cc.mask, cc);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) val[c] = __uint_as_float(my[c * kThreads]);
             }
             float *x = val, *v = val + DIM, *C = val + 2 * DIM, *FJ = val + 2 * DIM + DIM * DIM;
 
@@ -240,30 +345,17 @@ __global__ void __launch_bounds__(kThreads, 2) step_kernel(const __grid_constant
                 float vn[3] = {0.0f, 0.0f, 0.0f}, B[DIM * DIM];
 #pragma unroll
                 for (int q = 0; q < DIM * DIM; ++q) B[q] = 0.0f;
+                float dpx[3], dpy[3], dpz[3];
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-#pragma unroll
-                        for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
-                            const float wt = w[0][i] * w[1][j] * (DIM == 3 ? w[2][k] : 1.0f);
-                            float4 gv;
-                            if (in_tile)
-                                gv = tile_v[tile_index<DIM>(l0 + i, l1 + j, l2 + k)];
-                            else {
-                                const int gx = base[0] + i, gy = base[1] + j, gz = DIM == 3 ? base[2] + k : 0;
-                                gv = node_velocity<DIM>(P.grid_in[node_addr<DIM>(P.nb, gx, gy, gz)], gx, gy, gz, P);
-                            }
-                            const float gva[3] = {gv.x, gv.y, gv.z};
-                            const float dp[3] = {((float)i - f[0]) * P.dx, ((float)j - f[1]) * P.dx,
-                                                 DIM == 3 ? ((float)k - f[2]) * P.dx : 0.0f};
-#pragma unroll
-                            for (int a = 0; a < DIM; ++a) {
-                                vn[a] += wt * gva[a];
-#pragma unroll
-                                for (int b = 0; b < DIM; ++b) B[a * DIM + b] += wt * gva[a] * dp[b];
-                            }
-                        }
+                for (int i = 0; i < 3; ++i) {
+                    dpx[i] = ((float)i - f[0]) * P.dx;
+                    dpy[i] = ((float)i - f[1]) * P.dx;
+                    dpz[i] = DIM == 3 ? ((float)i - f[2]) * P.dx : 0.0f;
+                }
+                if (in_tile)
+                    g2p_gather<DIM, true>(P, tvx, tvy, tvz, l0, l1, l2, base, w, dpx, dpy, dpz, vn, B);
+                else
+                    g2p_gather<DIM, false>(P, tvx, tvy, tvz, l0, l1, l2, base, w, dpx, dpy, dpz, vn, B);
                 if (STATS && !in_tile) cnt_oot += 1;
 #pragma unroll
                 for (int a = 0; a < DIM; ++a) {
@@ -292,8 +384,10 @@ __global__ void __launch_bounds__(kThreads, 2) step_kernel(const __grid_constant
                     for (int q = 0; q < DIM * DIM; ++q) FJ[q] = Fn[q];
                 }
 
-                // 4. store: dithered encode (Sec. 5) and whole-word writes
+                // 4. store: dithered encode (Sec. 5) into the particle's shared column
                 if (QUANT) {
+                    // every component ORs itself into its word(s) with a fire-and-forget shared
+                    // atomic, so the components do not wait on one another
                     for (int j = 0; j < P.n_words; ++j) my[j * kThreads] = 0u;
                     uint4 rnd = make_uint4(0, 0, 0, 0);
 #pragma unroll
@@ -302,9 +396,11 @@ __global__ void __launch_bounds__(kThreads, 2) step_kernel(const __grid_constant
                             rnd = philox4x32_10(make_uint4((uint32_t)slot, P.step, (uint32_t)(c >> 2), 0u),
                                                 P.seed_lo, P.seed_hi);
                         int fl;
-                        const uint32_t u = encode_f32(val[c], P.comp[c], P.dither != 0, uint4_at(rnd, c & 3), fl);
-                        insert(my, kThreads, P.comp[c], u);
-                        val[c] = decode_u(u, P.comp[c]);  // the stored (quantized) value
+                        const CompCodec &cc = P.comp[c];
+                        const uint32_t u = encode_f32(val[c], cc, P.dither != 0, uint4_at(rnd, c & 3), fl);
+                        atomicOr(my + cc.word * kThreads, u << cc.shift);
+                        atomicOr(my + (cc.word + 1) * kThreads, __funnelshift_l(u, 0u, cc.shift));
+                        val[c] = decode_u(u, cc);  // the stored (quantized) value
                         if (STATS) {
                             // the field of component c (x, v, C, F/J), folded at compile time
                             const int h = c < DIM ? 0 : c < 2 * DIM ? 1 : c < 2 * DIM + DIM * DIM ? 2 : 3;
@@ -313,71 +409,133 @@ __global__ void __launch_bounds__(kThreads, 2) step_kernel(const __grid_constant
                             cnt_dn[h] += (fl >> 2) & 1;
                         }
                     }
-                    for (int j = 0; j < P.n_words; ++j) __stcs(P.words + j * P.ld + slot, my[j * kThreads]);
                 } else {
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) __stcs(P.words + c * P.ld + slot, __float_as_uint(val[c]));
+                    for (int c = 0; c < NC; ++c) my[c * kThreads] = __float_as_uint(val[c]);
                 }
             }
 
-            // 5. P2G of the (stored) state into the shared tile
-            {
-                int base[3] = {0, 0, 0};
-                float w[3][3], f[3];
-                const bool oog = stencil<DIM>(x, P, base, w, f);
-                if (STATS && oog) cnt_oog += 1;
-                const int l0 = base[0] - o0, l1 = base[1] - o1, l2 = DIM == 3 ? base[2] - o2 : 0;
-                const bool in_tile = l0 >= 0 && l0 <= 5 && l1 >= 0 && l1 <= 5 && l2 >= 0 && l2 <= 5;
-                float tau[DIM * DIM], A[DIM * DIM];
-                kirchhoff<DIM, MAT>(FJ, P, tau);
+            // 5a. P2G payload of the (stored) state: stencil, m v and the affine matrix A
+            const bool oog = stencil<DIM>(x, P, pbase, pw, pf);
+            if (STATS && oog) cnt_oog += 1;
+            const int l0 = pbase[0] - o0, l1 = pbase[1] - o1, l2 = DIM == 3 ? pbase[2] - o2 : 0;
+            // out-of-grid particles (clamped stencil, weights outside the B-spline range) and
+            // particles that left their tile go through global memory in FP32
+            p_in_tile = !oog && l0 >= 0 && l0 <= 5 && l1 >= 0 && l1 <= 5 && l2 >= 0 && l2 <= 5;
+            if (STATS && !DO_G2P && !p_in_tile) cnt_oot += 1;
+            float tau[DIM * DIM];
+            kirchhoff<DIM, MAT>(FJ, P, tau);
 #pragma unroll
-                for (int q = 0; q < DIM * DIM; ++q) A[q] = P.stress_coef * tau[q] + P.p_mass * C[q];
-                float mv[3];
+            for (int q = 0; q < DIM * DIM; ++q) pA[q] = P.stress_coef * tau[q] + P.p_mass * C[q];
 #pragma unroll
-                for (int a = 0; a < DIM; ++a) mv[a] = P.p_mass * v[a];
+            for (int a = 0; a < DIM; ++a) pv[a] = v[a];
+            if (p_in_tile) {
+                // |v_a + (A dpos)_a / m| <= |v_a| + 1.5 dx sum_b |A_ab| / m on the whole stencil
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    float rowsum = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < DIM; ++b) rowsum += fabsf(pA[a * DIM + b]);
+                    bound = fmaxf(bound, fabsf(v[a]) + 1.5f * P.dx * rowsum * P.inv_p_mass);
+                }
+            }
+        }
+        // 5b. chunk-wide scale of the block fixed point: the largest in-tile contribution
+        //     maps to kFixMax, so no sum of <= 256 contributions can overflow 32 bits
+        {
+            float bm = __uint_as_float(__reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound)));
+            if ((tid & 31) == 0) red[tid >> 5] = bm;
+        }
+        __syncthreads();
+        float bmax = 0.0f;
+#pragma unroll
+        for (int w8 = 0; w8 < kThreads / 32; ++w8) bmax = fmaxf(bmax, red[w8]);
+        const float scale = bmax > 0.0f ? kFixMax / bmax : 1.0f;  // fixed-point units per (m/s)
+        if (active) {
+            // 5c. scatter: momentum w (v + A dpos / m) * scale and mass w * kFixMax as integers
+            float dpx[3], dpy[3], dpz[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                dpx[i] = ((float)i - pf[0]) * P.dx;
+                dpy[i] = ((float)i - pf[1]) * P.dx;
+                dpz[i] = DIM == 3 ? ((float)i - pf[2]) * P.dx : 0.0f;
+            }
+            if (p_in_tile) {
+                const int l0 = pbase[0] - o0, l1 = pbase[1] - o1, l2 = DIM == 3 ? pbase[2] - o2 : 0;
+                float As[DIM * DIM], vs[3];
+                const float am = scale * P.inv_p_mass;
+#pragma unroll
+                for (int q = 0; q < DIM * DIM; ++q) As[q] = pA[q] * am;
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) vs[a] = pv[a] * scale;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float ui[3];
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) ui[a] = vs[a] + As[a * DIM + 0] * dpx[i];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        float uij[3];
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a) uij[a] = ui[a] + As[a * DIM + 1] * dpy[j];
+                        const float wij = pw[0][i] * pw[1][j];
+#pragma unroll
+                        for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
+                            const float wt = DIM == 3 ? wij * pw[2][k] : wij;
+                            const int q = tile_index<DIM>(l0 + i, l1 + j, l2 + k);
+                            atomicAdd(tpm + q, __float2int_rn(wt * kFixMax));
+                            if (DIM == 3) {
+                                atomicAdd(tpx + q, __float2int_rn(wt * (uij[0] + As[2] * dpz[k])));
+                                atomicAdd(tpy + q, __float2int_rn(wt * (uij[1] + As[5] * dpz[k])));
+                                atomicAdd(tpz + q, __float2int_rn(wt * (uij[2] + As[8] * dpz[k])));
+                            } else {
+                                atomicAdd(tpx + q, __float2int_rn(wt * uij[0]));
+                                atomicAdd(tpy + q, __float2int_rn(wt * uij[1]));
+                            }
+                        }
+                    }
+                }
+            } else {
+                // slow path: FP32 global atomics straight into the grid
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
 #pragma unroll
                         for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
-                            const float wt = w[0][i] * w[1][j] * (DIM == 3 ? w[2][k] : 1.0f);
-                            const float dp[3] = {((float)i - f[0]) * P.dx, ((float)j - f[1]) * P.dx,
-                                                 DIM == 3 ? ((float)k - f[2]) * P.dx : 0.0f};
+                            const float wt = pw[0][i] * pw[1][j] * (DIM == 3 ? pw[2][k] : 1.0f);
+                            const float dp[3] = {dpx[i], dpy[j], dpz[k]};
                             float mom[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                             for (int a = 0; a < DIM; ++a) {
-                                float acc = mv[a];
+                                float acc = P.p_mass * pv[a];
 #pragma unroll
-                                for (int b = 0; b < DIM; ++b) acc += A[a * DIM + b] * dp[b];
+                                for (int b = 0; b < DIM; ++b) acc += pA[a * DIM + b] * dp[b];
                                 mom[a] = wt * acc;
                             }
-                            const float wm = wt * P.p_mass;
-                            if (in_tile) {
-                                float *dst = reinterpret_cast<float *>(tile_p + tile_index<DIM>(l0 + i, l1 + j, l2 + k));
-                                atomicAdd(dst + 0, wm);
-                                atomicAdd(dst + 1, mom[0]);
-                                atomicAdd(dst + 2, mom[1]);
-                                if (DIM == 3) atomicAdd(dst + 3, mom[2]);
-                            } else {
-                                const int gx = base[0] + i, gy = base[1] + j, gz = DIM == 3 ? base[2] + k : 0;
-                                atomicAdd(P.grid_out + node_addr<DIM>(P.nb, gx, gy, gz),
-                                          make_float4(wm, mom[0], mom[1], DIM == 3 ? mom[2] : 0.0f));
-                                P.touched_out[block_of<DIM>(P.nb, gx, gy, gz)] = 1;
-                            }
+                            const int gx = pbase[0] + i, gy = pbase[1] + j, gz = DIM == 3 ? pbase[2] + k : 0;
+                            atomicAdd(P.grid_out + node_addr<DIM>(P.nb, gx, gy, gz),
+                                      make_float4(wt * P.p_mass, mom[0], mom[1], DIM == 3 ? mom[2] : 0.0f));
+                            P.touched_out[block_of<DIM>(P.nb, gx, gy, gz)] = 1;
                         }
-                if (STATS && !DO_G2P && !in_tile) cnt_oot += 1;
             }
         }
         __syncthreads();
 
-        // flush the P2G tile: one vector atomic per node that received mass
+        // 6. coalesced store of the new records, and the P2G tile flush: one vector atomic
+        //    per node that received mass
+        if (DO_G2P && tid < (int)ch.count)
+            for (int j = 0; j < P.n_words; ++j) __stcs(P.words + j * P.ld + ch.start + tid, sw[j * kThreads + mycol]);
         for (int t = tid; t < TN; t += kThreads) {
-            const float4 a = tile_p[t];
-            if (a.x != 0.0f) {
-                const int i = DIM == 2 ? (t >> 3) : (t >> 6), j = DIM == 2 ? (t & 7) : ((t >> 3) & 7);
-                const int k = DIM == 2 ? 0 : (t & 7);
-                atomicAdd(P.grid_out + node_addr<DIM>(P.nb, o0 + i, o1 + j, o2 + k), a);
+            const int i = DIM == 2 ? (t >> 3) : (t >> 6), j = DIM == 2 ? (t & 7) : ((t >> 3) & 7);
+            const int k = DIM == 2 ? 0 : (t & 7);
+            const int q = tile_index<DIM>(i, j, k);
+            const int im = tpm[q];
+            if (im != 0) {
+                const float mm = P.p_mass / scale;  // momentum units -> m v
+                atomicAdd(P.grid_out + node_addr<DIM>(P.nb, o0 + i, o1 + j, o2 + k),
+                          make_float4((float)im * (P.p_mass / kFixMax), (float)tpx[q] * mm, (float)tpy[q] * mm,
+                                      DIM == 3 ? (float)tpz[q] * mm : 0.0f));
             }
         }
         if (tid < (1 << DIM) && ch.count > 0) {
@@ -586,6 +744,7 @@ void fill_params(const Ctx &c, StepParams &p)
     p.dx = 1.0f / (float)c.n;
     p.Dinv = 4.0f * (float)c.n * (float)c.n;
     p.p_mass = (float)s.p_mass;
+    p.inv_p_mass = (float)(1.0 / s.p_mass);
     p.stress_coef = (float)(-s.dt * s.p_vol * 4.0 * (double)c.n * (double)c.n);
     const double mu = s.E / (2.0 * (1.0 + s.nu));
     const double la = s.E * s.nu / ((1.0 + s.nu) * (1.0 - 2.0 * s.nu));
@@ -608,7 +767,8 @@ void fill_params(const Ctx &c, StepParams &p)
 static size_t step_smem(const Ctx &c)
 {
     const int TN = c.scene.dim == 2 ? 64 : 512;
-    return (size_t)2 * TN * sizeof(float4) + (size_t)c.W * kThreads * sizeof(uint32_t);
+    return (size_t)7 * TN * sizeof(float) + (kThreads / 32) * sizeof(float) +
+           (size_t)(c.W + 1) * kThreads * sizeof(uint32_t);
 }
 
 template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P>

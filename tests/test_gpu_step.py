@@ -98,9 +98,19 @@ def test_fp32_step_matches_fp64(q, oracle, case):
     # |v| / dx (times D^-1 dx^2 = 4) for C, and 1 for F or J
     bounds = [0, dim, 2 * dim, 2 * dim + dim * dim, nc]
     scales = [1.0, vmax + 1e-30, max(np.abs(ref[:, 2 * dim:2 * dim + dim * dim]).max(), 4 * vmax * n), 1.0]
-    for (a, b), scale in zip(zip(bounds[:-1], bounds[1:]), scales):
+    # stiffness floor: the stress is K (J - 1) J or mu (F F^T - I) + ..., so an FP32
+    # rounding of J or F near 1 (2^-24) is amplified into a pressure error of about
+    # stiffness * 2^-24, which one step turns into a velocity error of dt * n * that
+    # (impulse over one cell) and a C error of 4 n times the velocity error
+    mu = sc.get("E", 0.0) / (2 * (1 + sc.get("nu", 0.0)))
+    lam = sc.get("E", 0.0) * sc.get("nu", 0.0) / ((1 + sc.get("nu", 0.0)) * (1 - 2 * sc.get("nu", 0.0)))
+    stiff = sc.get("bulk", 0.0) if sc["material"] == "fluid" else 2 * mu + abs(lam)
+    dv = 4 * sc["dt"] * n * stiff * 2.0 ** -24
+    floors = [0.0, dv, 4 * n * dv, 0.0]
+    for (a, b), scale, floor in zip(zip(bounds[:-1], bounds[1:]), scales, floors):
         err = np.abs(got[:, a:b] - ref[:, a:b])
-        assert np.all(err <= 1e-5 * (np.abs(ref[:, a:b]) + scale)), (name, a, b, err.max(), scale)
+        tol = 1e-5 * (np.abs(ref[:, a:b]) + scale) + floor
+        assert np.all(err <= tol), (name, a, b, err.max(), scale, floor)
     g.close()
 
 
@@ -149,22 +159,40 @@ def test_drift_out_of_tile_slow_path(q, oracle):
 
 
 def test_walls_stop_particles(q, oracle):
-    # a block dropped onto the floor: sticky wall nodes carry zero velocity
+    # a block driven into the floor: sticky wall nodes carry zero velocity.  The step at
+    # contact matches the oracle within two quanta; over 30 steps the positions stay within
+    # a few quanta and nothing enters the wall band
     from paper_2207_04658_b300 import scenes
     sc, s0 = scenes.block2d_scene(n_strata=(32, 16))
-    s0[:, 1] -= 0.4 - 3.2 / 128  # rest just above the wall band
-    s0[:, 3] = -2.0
+    s0[:, 1] -= 0.4 - 3.6 / 128  # the block's bottom row sits half a cell above the wall band
+    s0[:, 3] = -0.5
     sch = scenes.block2d_scheme()
-    g = q.Scene(sc, sch, s0)
+    sch["C"] = dict(bits=16, frac=6, offset=-512 * 2 ** 6, container=0)  # [-512, 512]
+    sch["F"] = dict(bits=16, frac=14, offset=-2 * 2 ** 14, container=0)  # [-2, 2]: signed shear
+    g = q.Scene(sc, sch, s0, stats=True)
     o = oracle.QuantRollout(sc, sch, s0)
-    g.step(30)
-    o.step(30)
-    got = g.state_by_id()
+    qt = quanta(oracle, sc, sch)[None]
+    for step in range(30):
+        g.step(1)
+        o.step(1)
+        if step == 0:
+            r = g.readback(state=True, ids=True)
+            assert np.array_equal(r["ids"], o.ids)
+            assert (np.abs(r["state"] - o.state()) / qt).max() <= 2.0
+    r = g.readback(state=True, ids=True)
+    got = np.empty_like(r["state"])
+    got[r["ids"]] = r["state"]
     ref = np.empty_like(got)
     ref[o.ids] = o.state()
-    assert got[:, 1].min() >= 0.5 / 128
-    d = np.abs(got - ref) / quanta(oracle, sc, sch)[None]
+    assert sum(r["stats"]["saturations"]) == 0 and o.stats[:4].sum() == 0
+    assert got[:, 1].min() >= 0.5 / 128 and ref[:, 1].min() >= 0.5 / 128
+    d = np.abs(got[:, :2] - ref[:, :2]) / qt[:, :2]
     assert np.percentile(d, 99) <= 8
+    # the particles at the wall have been stopped (the rest of the block is still moving:
+    # the elastic wave has not crossed it yet)
+    for st in (got, ref):
+        low = st[:, 1] < 4.0 / 128
+        assert low.sum() > 10 and np.abs(st[low, 3]).mean() < 0.25
 
 
 def test_empty_and_single_particle(q, oracle):

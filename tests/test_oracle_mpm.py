@@ -257,12 +257,16 @@ def test_tile_keys_cover_stencil(oracle, dim, material):
     gen = np.random.default_rng(100 + dim)
     s = random_state(gen, dim, material, 2000, lo=0.6 / n, hi=1.0 - 1.6 / n)
     keys = oracle.tile_keys(ph, s)
-    assert keys.min() >= 0 and keys.max() < oracle.n_keys(ph) == nb ** dim
-    T = np.stack(np.unravel_index(keys, (nb,) * dim), -1)
+    ncell = 4 ** dim
+    assert keys.min() >= 0 and keys.max() < oracle.n_keys(ph) == nb ** dim * ncell
+    T = np.stack(np.unravel_index(keys // ncell, (nb,) * dim), -1)
+    cell = np.stack(np.unravel_index(keys % ncell, (4,) * dim), -1)
     base = np.floor(s[:, :dim] * n - 0.5).astype(int)
     lo_node = 4 * (T - 1)  # first node of the tile
     assert np.all(base - 1 >= lo_node)
     assert np.all(base + 2 + 1 <= lo_node + 7)
+    # the cell part orders particles by their base inside the tile
+    assert np.array_equal(base, lo_node + 1 + cell)
 
 
 def test_stable_sort_is_stable(oracle):
