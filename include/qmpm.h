@@ -223,6 +223,34 @@ int qmpm_pack_f32(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, ui
 int qmpm_unpack_f32(int32_t dim, int32_t material, const qmpm_scheme_t *scheme,
                     const uint32_t *d_words, int64_t N, int64_t ld, float *d_vals, void *stream);
 
+/* ---- ordering without device allocation ----------------------------------------- */
+
+/* Largest N accepted by qmpm_tile_order_static. */
+#define QMPM_STATIC_SORT_MAX 262144
+
+/* The stable (tile, cell) order of N packed records -- the order qmpm_init puts particles
+ * in -- computed without allocating anything.  It exists for callers that cannot call
+ * cudaMalloc or cudaFree: code that runs inside another runtime's memory pool or
+ * allocator, or a host thread that must not take the device-wide synchronisation an
+ * allocation or a free can cause.  The paper has no counterpart; it is a service of this
+ * library.
+ *   d_words: N records as word planes (leading dimension ld >= N), device, in the layout
+ *            of `scheme` (NULL or quantized == 0: FP32 state, one word per component);
+ *   d_order: output, device, N slots: d_order[i] is the input index of the record that
+ *            goes to slot i (equal keys keep their input order).
+ * Scratch: one file-scope device array of about 4.3 MB (four key/value buffers of
+ * QMPM_STATIC_SORT_MAX entries plus the radix digit counts), which every GPU that loads
+ * the library holds until the process exits.  All calls share it and it keeps the last
+ * call's contents; every word a call reads is written earlier in the same call, so
+ * nothing has to be cleared.  Calls whose work overlaps on the GPU (other streams or
+ * threads) race on the array: order them.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Asynchronous on `stream` after the lookup.
+ * Errors: QMPM_ERR_INVALID_ARG (N > QMPM_STATIC_SORT_MAX, bad dim/material/grid/buffers),
+ * QMPM_ERR_SCHEME, QMPM_ERR_CUDA. */
+int qmpm_tile_order_static(int32_t dim, int32_t material, int32_t grid_log2, const qmpm_scheme_t *scheme,
+                           const uint32_t *d_words, int64_t N, int64_t ld, uint32_t *d_order, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -157,6 +157,10 @@ int validate_scene(const qmpm_scene_t *s)
 
 }  // namespace
 
+namespace qmpm {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace qmpm
+
 using qmpm::Ctx;
 
 extern "C" {

@@ -121,6 +121,9 @@ struct Ctx {
 // segments, chunk counts, 3 scan, emit
 inline int64_t resort_launches(int key_bits) { return 9 + 5 * (int64_t)(key_bits / 8); }
 
+// api.cu: message returned by qmpm_last_error() on this thread
+void set_last_error(const std::string &msg);
+
 // scheme.cpp
 int layout(int dim, int material, qmpm_scheme_t *scheme, std::string &err);
 int n_comp(int dim, int material);
@@ -129,6 +132,11 @@ void build_codec(const qmpm_scheme_t &s, int dim, int material, CompCodec *cc);
 
 // sort.cu
 int resort(Ctx &c, std::string &err);
+// keys of N packed records (codec and grid in p) and a stable radix sort of (key, slot)
+// in the given buffers; on return vals[*result] holds the sorted slots
+cudaError_t sort_tile_order(const StepParams &p, int dim, bool quant, int64_t N, int key_bits, uint32_t *keys[2],
+                            uint32_t *vals[2], uint32_t *counts, uint32_t *partials, int64_t max_partials,
+                            cudaStream_t s, int *result);
 int64_t sort_scratch_tiles(int64_t N);
 cudaError_t exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *partials, int64_t max_partials,
                                cudaStream_t s);

@@ -261,6 +261,32 @@ __global__ void chunk_emit_kernel(const uint32_t *seg_begin, const uint32_t *seg
 
 static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+cudaError_t sort_tile_order(const StepParams &p, int dim, bool quant, int64_t N, int key_bits, uint32_t *keys[2],
+                            uint32_t *vals[2], uint32_t *counts, uint32_t *partials, int64_t max_partials,
+                            cudaStream_t s, int *result)
+{
+    *result = 0;
+    if (N <= 0) return cudaSuccess;
+    if (dim == 2)
+        quant ? tile_key_kernel<2, true><<<blocks_for(N, 256), 256, 0, s>>>(p, N, keys[0], vals[0])
+              : tile_key_kernel<2, false><<<blocks_for(N, 256), 256, 0, s>>>(p, N, keys[0], vals[0]);
+    else
+        quant ? tile_key_kernel<3, true><<<blocks_for(N, 256), 256, 0, s>>>(p, N, keys[0], vals[0])
+              : tile_key_kernel<3, false><<<blocks_for(N, 256), 256, 0, s>>>(p, N, keys[0], vals[0]);
+    const int64_t n_tiles = sort_scratch_tiles(N);
+    int src = 0;
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        radix_hist_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(keys[src], N, shift, counts, n_tiles);
+        const cudaError_t e = exclusive_scan_u32(counts, 256 * n_tiles, partials, max_partials, s);
+        if (e != cudaSuccess) return e;
+        radix_scatter_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(keys[src], vals[src], keys[1 - src],
+                                                                       vals[1 - src], N, shift, counts, n_tiles);
+        src = 1 - src;
+    }
+    *result = src;
+    return cudaGetLastError();
+}
+
 int resort(Ctx &c, std::string &err)
 {
     cudaStream_t s = c.stream;

@@ -109,7 +109,12 @@ _SIGNATURES = [
     ("qmpm_unpack_f32", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t), ct.c_void_p,
                                    ct.c_int64, ct.c_int64, ct.c_void_p, ct.c_void_p]),
 ]
-OPTIONAL_SIGNATURES = []
+OPTIONAL_SIGNATURES = [
+    ("qmpm_tile_order_static", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, _P(qmpm_scheme_t),
+                                          ct.c_void_p, ct.c_int64, ct.c_int64, ct.c_void_p,
+                                          ct.c_void_p]),
+]
+STATIC_SORT_MAX = 262144
 
 
 def lib():
@@ -268,6 +273,16 @@ def qmpm_pack_f32(dim, material, scheme_struct, seed, dither, step, d_vals_ptr, 
 def qmpm_unpack_f32(dim, material, scheme_struct, d_words_ptr, N, ld, d_vals_ptr, stream=0):
     _check(lib().qmpm_unpack_f32(dim, material, ct.byref(scheme_struct), ct.c_void_p(d_words_ptr),
                                  int(N), int(ld), ct.c_void_p(d_vals_ptr), ct.c_void_p(stream)))
+
+
+def qmpm_tile_order_static(dim, material, scheme_struct, grid_log2, d_words_ptr, N, ld, d_order_ptr,
+                           stream=0):
+    """The tile order of N packed records without any device allocation (scratch in a
+    static device array of the library; N <= STATIC_SORT_MAX)."""
+    _check(lib().qmpm_tile_order_static(dim, material, grid_log2,
+                                        ct.byref(scheme_struct) if scheme_struct is not None else None,
+                                        ct.c_void_p(d_words_ptr), int(N), int(ld),
+                                        ct.c_void_p(d_order_ptr), ct.c_void_p(stream)))
 
 
 # ---------------------------------------------------------------------------- Scene
