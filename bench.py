@@ -42,23 +42,38 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--fixed-scheme", action="store_true",
+                    help="hand-written scheme instead of the solved one (quick runs)")
+    ap.add_argument("--scheme-json", default=None,
+                    help="load a scheme saved by --save-scheme instead of solving it again")
+    ap.add_argument("--save-scheme", default=None, help="write the solved scheme to this file")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="fraction of the workload's cubes/columns (for quick runs only)")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------------------ workloads
-def workload(name, scale=1.0, seed_offset=0):
+def solved_cubes_scheme(eps=0.01):
+    """The cubes' scheme from the bit-allocation solve (Eq. 10) at relative error eps on
+    the final particle positions, with sensitivities from the half-resolution scene."""
+    from paper_2207_04658_b300 import autoquant
+    scheme, rep = autoquant.cubes3d_scheme(eps)
+    return scheme, rep
+
+
+def workload(name, scale=1.0, seed_offset=0, scheme=None):
     from paper_2207_04658_b300 import scenes
     if name == "cubes3d":
         n_cubes = max(1, int(round(16 * scale)))
         sc, s0 = scenes.cubes3d_scene(n_cubes=n_cubes, seed=2 + seed_offset)
-        sch = scenes.fixed_scheme_3d("corotated")
+        sch = scheme if scheme is not None else scenes.fixed_scheme_3d("corotated")
         desc = {"workload": "3D fixed-corotated elastic cubes", "particles": int(s0.shape[0]),
                 "cubes": n_cubes, "grid": "256^3", "dt": sc["dt"], "E": sc["E"], "nu": sc["nu"],
-                "ppc": 8, "scheme": "x 3x21 bits in one 64-bit container; v 16 bits on [-8,8], "
-                "C 16 bits on [-512,512], F 16 bits on [0,2], bit pack, dithered",
-                "resort_every": sc["resort_every"]}
+                "rho": sc["rho"], "ppc": 8, "initial_speed": 3.0,
+                "scheme": {k: [f["bits"], f["frac"]] for k, f in sch.items()},
+                "scheme_source": "qmpm_scheme_solve, eps 0.01 on final positions" if scheme is not None
+                else "fixed", "resort_every": sc["resort_every"]}
     elif name == "dambreak3d":
         cells = max(8, int(round(256 * scale ** (1 / 3))))
         sc, s0 = scenes.dambreak3d_scene(column_cells=cells, seed=3 + seed_offset)
@@ -195,14 +210,36 @@ def issue_peak(peaks):
     return 148 * 4 * mhz * 1e6
 
 
+def accuracy(qmpm, sc, s0, sch):
+    """Full rollouts (the scene's step count) of the quantized and the FP32 state from the
+    same initial state: relative error of z = mean |x|^2 and RMS per-particle position
+    error over RMS position (the bound the scheme was solved for)."""
+    steps = int(sc.get("steps", 1000))
+    out = {}
+    for name, scheme in (("quant", sch), ("fp32", None)):
+        g = qmpm.Scene(sc, scheme, s0, stats=True)
+        g.step(steps)
+        out[name] = (g.measure(), g.state_by_id(), g.readback(state=False, ids=False)["stats"])
+        g.close()
+    zq, zf = out["quant"][0], out["fp32"][0]
+    d = out["quant"][1][:, :sc["dim"]] - out["fp32"][1][:, :sc["dim"]]
+    rms_err = float(np.sqrt((d ** 2).sum(1).mean()))
+    rms_pos = float(np.sqrt((out["fp32"][1][:, :sc["dim"]] ** 2).sum(1).mean()))
+    return {"steps": steps, "z_quant": zq, "z_fp32": zf, "z_rel_err": abs(zq - zf) / abs(zf),
+            "rms_pos_err_rel": rms_err / rms_pos, "saturations": out["quant"][2]["saturations"],
+            "reference": "FP32 run of the same kernels (the FP64 oracle is too slow at this size)"}
+
+
 def cpu_baseline(name, sample_steps=2):
     """The oracle (single-threaded FP64 C) on a bounded sample of the same workload: the
-    first cube (or a slice of the column) on the full grid, `sample_steps` quantized steps."""
+    first cube (or a slice of the column) on the full grid, `sample_steps` quantized steps.
+    It takes the hand-written scheme (its inputs never come from the CUDA path; its cost
+    does not depend on the bit widths)."""
     import oracle
     sc, s0, sch, desc = workload(name)
     if name == "cubes3d":
         n = 512_000
-        sample = f"first cube of 16 ({n} particles) on the full 256^3 grid, {sample_steps} steps"
+        sample = f"first cube of 16 ({n} particles) on the full 256^3 grid, {sample_steps} steps, hand-written scheme"
     elif name == "dambreak3d":
         n = 256_000
         sample = f"first {n} particles of the column on the full 512^3 grid, {sample_steps} steps"
@@ -256,7 +293,23 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     peak_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
 
-    sc, s0, sch, desc = workload(args.workload, args.scale, seed_offset=dc.rank)
+    solve_info = None
+    scheme = None
+    if args.scheme_json:
+        with open(args.scheme_json) as f:
+            saved = json.load(f)
+        scheme, solve_info = saved["scheme"], saved["solve"]
+    elif args.workload == "cubes3d" and not args.fixed_scheme:
+        scheme, rep = solved_cubes_scheme(0.01)
+        solve_info = {"bits": rep["solve"]["bits"], "frac": rep["solve"]["frac"],
+                      "pred_err": rep["solve"]["pred_err"],
+                      "bound": (0.01 * rep["sensitivities"]["z"]) ** 2,
+                      "sensitivity_run": "16 cubes at half resolution (1,024,000 particles, 128^3), "
+                                         "1000 steps, 2 Gaussian seeds on x_T"}
+    if args.save_scheme and scheme is not None and dc.rank == 0:
+        with open(args.save_scheme, "w") as f:
+            json.dump({"scheme": scheme, "solve": solve_info}, f)
+    sc, s0, sch, desc = workload(args.workload, args.scale, seed_offset=dc.rank, scheme=scheme)
     N = s0.shape[0]
     clocks = ClockSampler(dc.local)
     clocks.start()
@@ -324,6 +377,10 @@ def run_ours(args):
                         "step_kernel_gbs": round(alg32 / (s32 / 1e3) / 1e9, 1),
                         "quantized_over_fp32": round(value / v32, 4)}
         g32.close()
+    if solve_info is not None:
+        line["scheme_solve"] = solve_info
+    if not args.no_accuracy and dc.rank == 0:
+        line["accuracy"] = accuracy(qmpm, sc, s0, sch)
     if dc.rank == 0 and dc.world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if dc.rank == 0:

@@ -209,6 +209,37 @@ int qmpm_destroy(qmpm_handle h);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *qmpm_last_error(void);
 
+/* ---- reverse mode (Sec. 6, Eq. 12-13) and the sensitivities of Eq. 8 ------------ */
+
+#define QMPM_MEASURE_MEAN_SQ_POS 0 /* z = (1/N) sum |x_T|^2, seed 2 x_T / N */
+#define QMPM_MEASURE_USER 1        /* seed dz/ds_T supplied by the caller (z reported as
+                                      the mean square position) */
+#define QMPM_MEASURE_KINETIC_ENERGY 2 /* z = (1/2) m sum |v_T|^2, seed m v_T (Sec. 8.1) */
+
+typedef struct {
+    double z;          /* the measurement of s_T (kinetic energy for that measure, else the
+                          mean square position) */
+    double g[4];       /* Eq. 8: sum over t = 0..T and over the field's variables of (dz/ds_t)^2 */
+    double lo[4];      /* smallest value of each field over the states t = 0..T */
+    double hi[4];      /* largest value (Algorithm 1's range update) */
+    int64_t P[4];      /* variables per field: N times the field's components */
+} qmpm_adjoint_out_t;
+
+/* Reverse mode over T steps from the handle's current state, in FP32 (the state is decoded
+ * first if the handle is quantized; gradients are taken in full precision as in the
+ * paper's workflow).  The call runs its own forward (particle order fixed, no re-sort),
+ * keeps a checkpoint every ckpt_every steps and recomputes each segment from its
+ * checkpoint while reversing it (adjoint kernel G of Eq. 13), and accumulates the squared
+ * sensitivities g_h of Eq. 8, which qmpm_scheme_solve takes.  The handle's own state is
+ * not advanced.
+ *   measure:  QMPM_MEASURE_MEAN_SQ_POS, QMPM_MEASURE_KINETIC_ENERGY or QMPM_MEASURE_USER
+ *             (then d_seed = dz/ds_T, device, [N][n_comp] in the handle's slot order);
+ *   d_grad0:  optional output dz/ds_0, device, [N][n_comp], slot order.
+ * Allocates O((T/ckpt_every + ckpt_every) N n_comp) floats of device memory for the call.
+ * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_OOM, QMPM_ERR_CUDA. */
+int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_t measure, const float *d_seed,
+                 float *d_grad0, qmpm_adjoint_out_t *out);
+
 /* ---- codec on device buffers (Sec. 3.1 Eq. 3, Sec. 5 Eq. 11, Sec. 7) ------------ */
 
 /* Encode N particles of FP32 values d_vals ([N][n_comp], device) into d_words

@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+_lib_omp = None
 
 NEOHOOKEAN, COROTATED, FLUID = 0, 1, 2
 MATERIALS = {"neohookean": NEOHOOKEAN, "corotated": COROTATED, "fluid": FLUID}
@@ -51,57 +52,65 @@ class SolveOut(ct.Structure):
                 ("pred_err", ct.c_double), ("total_bits", ct.c_double)]
 
 
-def lib():
-    global _lib
+def lib(threaded=False):
+    """The sequential oracle library, or (``threaded``) its OpenMP build for long FP64
+    reference rollouts."""
+    global _lib, _lib_omp
+    if threaded:
+        if _lib_omp is None:
+            _lib_omp = _bind(ct.CDLL(_build.build(threaded=True)))
+        return _lib_omp
     if _lib is None:
-        path = _build.build()
-        L = ct.CDLL(path)
-        P = ct.POINTER
-        d, i64, u32 = ct.c_double, ct.c_int64, ct.c_uint32
-        L.or_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
-        L.or_dither_draw.argtypes = [ct.c_uint64, u32, u32, ct.c_int]
-        L.or_dither_draw.restype = u32
-        L.or_encode.argtypes = [d, ct.c_int, ct.c_int, i64, ct.c_int, u32, P(ct.c_int)]
-        L.or_encode.restype = u32
-        L.or_decode.argtypes = [u32, ct.c_int, i64]
-        L.or_decode.restype = d
-        L.or_n_comp.argtypes = [ct.c_int, ct.c_int]
-        L.or_layout.argtypes = [ct.c_int, ct.c_int, P(ct.c_int), P(ct.c_int), P(ct.c_int),
-                                P(ct.c_int)]
-        L.or_pack.argtypes = [ct.c_int, P(ct.c_int), P(ct.c_int), ct.c_int, P(u32), P(u32)]
-        L.or_unpack.argtypes = [ct.c_int, P(ct.c_int), P(ct.c_int), P(u32), P(u32)]
-        L.or_polar2.argtypes = [P(d), P(d)]
-        L.or_polar3.argtypes = [P(d), P(d)]
-        L.or_kirchhoff.argtypes = [P(Phys), P(d), P(d)]
-        L.or_n_nodes.argtypes = [P(Phys)]
-        L.or_p2g.argtypes = [P(Phys), i64, P(d), P(d)]
-        L.or_p2g.restype = i64
-        L.or_grid_update.argtypes = [P(Phys), P(d)]
-        L.or_g2p.argtypes = [P(Phys), i64, P(d), P(d)]
-        L.or_g2p.restype = i64
-        L.or_step_fp64.argtypes = [P(Phys), i64, P(d), P(d)]
-        L.or_step_fp64.restype = i64
-        L.or_encode_state.argtypes = [P(Codec), i64, P(d), u32, P(u32), P(i64)]
-        L.or_decode_state.argtypes = [P(Codec), i64, P(u32), P(d)]
-        L.or_step_quant.argtypes = [P(Phys), P(Codec), i64, P(u32), u32, P(d), P(d), P(i64)]
-        L.or_tile_keys.argtypes = [P(Phys), i64, P(d), P(i64)]
-        L.or_stable_sort.argtypes = [i64, P(i64), i64, P(i64)]
-        L.or_n_keys.argtypes = [P(Phys)]
-        L.or_n_keys.restype = i64
-        L.or_mean_sq_pos.argtypes = [ct.c_int, ct.c_int, i64, P(d)]
-        L.or_mean_sq_pos.restype = d
-        L.or_scheme_solve.argtypes = [P(SolveIn), P(SolveOut)]
-        L.or_scheme_bruteforce.argtypes = [P(SolveIn), ct.c_int, ct.c_int, P(SolveOut)]
-        if hasattr(L, "or_adjoint_step"):
-            _bind_adjoint(L)
-        _lib = L
+        _lib = _bind(ct.CDLL(_build.build()))
     return _lib
+
+
+def _bind(L):
+    P = ct.POINTER
+    d, i64, u32 = ct.c_double, ct.c_int64, ct.c_uint32
+    L.or_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+    L.or_dither_draw.argtypes = [ct.c_uint64, u32, u32, ct.c_int]
+    L.or_dither_draw.restype = u32
+    L.or_encode.argtypes = [d, ct.c_int, ct.c_int, i64, ct.c_int, u32, P(ct.c_int)]
+    L.or_encode.restype = u32
+    L.or_decode.argtypes = [u32, ct.c_int, i64]
+    L.or_decode.restype = d
+    L.or_n_comp.argtypes = [ct.c_int, ct.c_int]
+    L.or_layout.argtypes = [ct.c_int, ct.c_int, P(ct.c_int), P(ct.c_int), P(ct.c_int),
+                            P(ct.c_int)]
+    L.or_pack.argtypes = [ct.c_int, P(ct.c_int), P(ct.c_int), ct.c_int, P(u32), P(u32)]
+    L.or_unpack.argtypes = [ct.c_int, P(ct.c_int), P(ct.c_int), P(u32), P(u32)]
+    L.or_polar2.argtypes = [P(d), P(d)]
+    L.or_polar3.argtypes = [P(d), P(d)]
+    L.or_kirchhoff.argtypes = [P(Phys), P(d), P(d)]
+    L.or_n_nodes.argtypes = [P(Phys)]
+    L.or_p2g.argtypes = [P(Phys), i64, P(d), P(d)]
+    L.or_p2g.restype = i64
+    L.or_grid_update.argtypes = [P(Phys), P(d)]
+    L.or_g2p.argtypes = [P(Phys), i64, P(d), P(d)]
+    L.or_g2p.restype = i64
+    L.or_step_fp64.argtypes = [P(Phys), i64, P(d), P(d)]
+    L.or_step_fp64.restype = i64
+    L.or_encode_state.argtypes = [P(Codec), i64, P(d), u32, P(u32), P(i64)]
+    L.or_decode_state.argtypes = [P(Codec), i64, P(u32), P(d)]
+    L.or_step_quant.argtypes = [P(Phys), P(Codec), i64, P(u32), u32, P(d), P(d), P(i64)]
+    L.or_tile_keys.argtypes = [P(Phys), i64, P(d), P(i64)]
+    L.or_stable_sort.argtypes = [i64, P(i64), i64, P(i64)]
+    L.or_n_keys.argtypes = [P(Phys)]
+    L.or_n_keys.restype = i64
+    L.or_mean_sq_pos.argtypes = [ct.c_int, ct.c_int, i64, P(d)]
+    L.or_mean_sq_pos.restype = d
+    L.or_scheme_solve.argtypes = [P(SolveIn), P(SolveOut)]
+    L.or_scheme_bruteforce.argtypes = [P(SolveIn), ct.c_int, ct.c_int, P(SolveOut)]
+    if hasattr(L, "or_adjoint_step"):
+        _bind_adjoint(L)
+    return L
 
 
 def _bind_adjoint(L):
     P = ct.POINTER
     d, i64 = ct.c_double, ct.c_int64
-    L.or_adjoint_step.argtypes = [P(Phys), i64, P(d), P(d), P(d), P(d)]
+    L.or_adjoint_step.argtypes = [P(Phys), i64, P(d), P(d), P(d)]
 
 
 def _p(a, ctype):
@@ -286,10 +295,10 @@ def decode_state(cd, words):
     return s
 
 
-def tile_keys(ph, s):
+def tile_keys(ph, s, threaded=False):
     s = np.ascontiguousarray(s, dtype=np.float64)
     k = np.zeros(s.shape[0], dtype=np.int64)
-    lib().or_tile_keys(ct.byref(ph), s.shape[0], _p(s, ct.c_double), _p(k, ct.c_int64))
+    lib(threaded).or_tile_keys(ct.byref(ph), s.shape[0], _p(s, ct.c_double), _p(k, ct.c_int64))
     return k
 
 
@@ -350,7 +359,8 @@ class QuantRollout:
 class Fp64Rollout:
     """Oracle rollout of the unquantized FP64 simulation, with the same ordering."""
 
-    def __init__(self, scene, s0):
+    def __init__(self, scene, s0, threaded=False):
+        self.threaded = threaded
         self.ph = make_phys(scene)
         self.resort_every = int(scene.get("resort_every", 8))
         self.s = np.ascontiguousarray(s0, dtype=np.float64).copy()
@@ -361,17 +371,80 @@ class Fp64Rollout:
         self.resort()
 
     def resort(self):
-        perm = stable_sort(tile_keys(self.ph, self.s), n_keys(self.ph))
+        perm = stable_sort(tile_keys(self.ph, self.s, self.threaded), n_keys(self.ph))
         self.s = np.ascontiguousarray(self.s[perm])
         self.ids = self.ids[perm]
 
     def step(self, n=1):
         for _ in range(n):
             self.t += 1
-            lib().or_step_fp64(ct.byref(self.ph), self.N, _p(self.s, ct.c_double),
-                               _p(self.grid, ct.c_double))
+            lib(self.threaded).or_step_fp64(ct.byref(self.ph), self.N, _p(self.s, ct.c_double),
+                                            _p(self.grid, ct.c_double))
             if self.resort_every > 0 and self.t % self.resort_every == 0:
                 self.resort()
+
+
+# ------------------------------------------------------------------------------ adjoint
+def adjoint_step(ph, s, sbn):
+    """Adjoint of state s_t from the adjoint of s_{t+1} (Sec. 6, Eq. 13)."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    sbn = np.ascontiguousarray(sbn, dtype=np.float64)
+    sb = np.zeros_like(s)
+    lib().or_adjoint_step(ct.byref(ph), s.shape[0], _p(s, ct.c_double), _p(sbn, ct.c_double),
+                          _p(sb, ct.c_double))
+    return sb
+
+
+def mean_sq_pos_seed(dim, s):
+    """dz/ds for z = (1/N) sum |x|^2."""
+    g = np.zeros_like(s)
+    g[:, :dim] = 2.0 * s[:, :dim] / s.shape[0]
+    return g
+
+
+def kinetic_energy(ph, s):
+    """z = (1/2) m sum |v|^2 (the kinetic energy used as evaluation function in Sec. 8.1)."""
+    d = ph.dim
+    return 0.5 * ph.p_mass * float((s[:, d:2 * d] ** 2).sum())
+
+
+def kinetic_energy_seed(ph, s):
+    g = np.zeros_like(s)
+    g[:, ph.dim:2 * ph.dim] = ph.p_mass * s[:, ph.dim:2 * ph.dim]
+    return g
+
+
+def rollout_fp64(ph, s0, T):
+    """States s_0 .. s_T of the FP64 step (no re-ordering)."""
+    states = [np.ascontiguousarray(s0, dtype=np.float64).copy()]
+    for _ in range(T):
+        states.append(step_fp64(ph, states[-1]))
+    return states
+
+
+def rollout_adjoint(ph, s0, T, seed_fn=None):
+    """Reverse mode over a T-step FP64 rollout: returns z, the adjoints dz/ds_t for
+    t = 0..T, and g_h = sum_t sum_i (dz/ds_t[h, i])^2 per field (Eq. 8)."""
+    dim = ph.dim
+    states = rollout_fp64(ph, s0, T)
+    if seed_fn == "kinetic":
+        z = kinetic_energy(ph, states[-1])
+        sb = kinetic_energy_seed(ph, states[-1])
+    else:
+        z = mean_sq_pos(dim, states[-1])
+        sb = seed_fn(states[-1]) if seed_fn else mean_sq_pos_seed(dim, states[-1])
+    adj = [None] * (T + 1)
+    adj[T] = sb
+    for t in range(T - 1, -1, -1):
+        adj[t] = adjoint_step(ph, states[t], adj[t + 1])
+    nc = states[0].shape[1]
+    fields = comp_fields(dim, {0: "neohookean", 1: "corotated", 2: "fluid"}[ph.material])
+    g = np.zeros(4)
+    for a in adj:
+        sq = (a * a).sum(axis=0)
+        for c in range(nc):
+            g[fields[c]] += sq[c]
+    return z, adj, g
 
 
 # ------------------------------------------------------------------------------ solve

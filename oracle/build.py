@@ -9,22 +9,27 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["or_codec.c", "or_mpm.c", "or_scheme.c", "or_adjoint.c"]
 LIB = os.path.join(HERE, "liboracle.so")
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, threaded: bool = False) -> str:
+    """The sequential oracle (default), or the OpenMP build of the same sources that only
+    long FP64 reference rollouts use (``threaded``)."""
+    lib = LIB_OMP if threaded else LIB
     srcs = [os.path.join(HERE, s) for s in SOURCES if os.path.exists(os.path.join(HERE, s))]
-    deps = srcs + [os.path.join(HERE, "oracle.h")]
-    if not force and os.path.exists(LIB):
-        lib_m = os.path.getmtime(LIB)
+    deps = srcs + [os.path.join(HERE, "oracle.h"), os.path.abspath(__file__)]
+    if not force and os.path.exists(lib):
+        lib_m = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= lib_m for d in deps):
-            return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+            return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
-           "-o", tmp] + srcs + ["-lm"]
+           "-Wno-unknown-pragmas"] + (["-fopenmp"] if threaded else []) + ["-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
+    print(build(force="--force" in sys.argv, threaded=True))

@@ -16,6 +16,10 @@
  *
  * A particle whose stencil base leaves [0, n-3] on some axis is "out of grid": its base
  * is clamped to the range (its weights then extrapolate) and it is counted.
+ *
+ * The OpenMP pragmas only matter in the separate threaded build used for long FP64
+ * reference rollouts; there the P2G sums are atomic, so their order (and the last bits of
+ * the grid) varies from run to run.  The default build ignores them and is sequential.
  */
 #include "oracle.h"
 
@@ -179,6 +183,7 @@ int64_t or_p2g(const or_phys_t *ph, int64_t N, const double *s, double *grid)
     memset(grid, 0, sizeof(double) * (size_t)or_n_nodes(ph) * (size_t)stride);
     int64_t oog = 0;
     const int n_off = d == 2 ? 9 : 27;
+#pragma omp parallel for schedule(static) reduction(+ : oog)
     for (int64_t p = 0; p < N; ++p) {
         const double *x = s + p * nc, *v = x + d, *C = x + 2 * d, *FJ = x + 2 * d + d * d;
         int base[3];
@@ -200,10 +205,12 @@ int64_t or_p2g(const or_phys_t *ph, int64_t N, const double *s, double *grid)
                 idx[a] = base[a] + off[a];
             }
             double *g = grid + node_index(d, n, idx) * stride;
+#pragma omp atomic
             g[0] += weight * ph->p_mass;
             for (int a = 0; a < d; ++a) {
                 double Ad = 0.0;
                 for (int b = 0; b < d; ++b) Ad += A[a * d + b] * dpos[b];
+#pragma omp atomic
                 g[1 + a] += weight * (ph->p_mass * v[a] + Ad);
             }
         }
@@ -215,6 +222,7 @@ void or_grid_update(const or_phys_t *ph, double *grid)
 {
     const int d = ph->dim, n = 1 << ph->grid_log2, stride = 1 + d;
     const int64_t nn = or_n_nodes(ph);
+#pragma omp parallel for schedule(static)
     for (int64_t node = 0; node < nn; ++node) {
         int idx[3];
         if (d == 2) { idx[0] = (int)(node / n); idx[1] = (int)(node % n); }
@@ -240,6 +248,7 @@ int64_t or_g2p(const or_phys_t *ph, int64_t N, const double *grid, double *s)
     const double dx = 1.0 / (double)n, Dinv = 4.0 * (double)n * (double)n;
     const int n_off = d == 2 ? 9 : 27;
     int64_t oog = 0;
+#pragma omp parallel for schedule(static) reduction(+ : oog)
     for (int64_t p = 0; p < N; ++p) {
         double *x = s + p * nc, *v = x + d, *C = x + 2 * d, *FJ = x + 2 * d + d * d;
         int base[3];
@@ -321,6 +330,7 @@ void or_tile_keys(const or_phys_t *ph, int64_t N, const double *s, int64_t *keys
 {
     const int d = ph->dim, nc = or_n_comp(d, ph->material);
     const int64_t nb = ((int64_t)1 << ph->grid_log2) / 4 + 2;
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < N; ++p) {
         int base[3];
         double f[3], w[3][3];

@@ -93,7 +93,8 @@ int or_scheme_solve(const or_solve_in_t *in, or_solve_out_t *out)
                 out->delta_cont[h] = d;
                 out->bits_paper[h] = (int)ceil(-log2(d / R[h]));
                 if (out->bits_paper[h] < 1) out->bits_paper[h] = 1;
-                frac0[h] = (int)ceil(-log2(d));
+                /* b_h >= 1 bounds the resolution by half the widened range */
+                frac0[h] = (int)ceil(-log2(fmin(d, 0.5 * R[h])));
             } else {
                 out->delta_cont[h] = INFINITY;
                 out->bits_paper[h] = 1;

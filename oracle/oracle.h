@@ -118,6 +118,10 @@ int64_t or_n_keys(const or_phys_t *ph);
 /* ---- measurement ---- */
 double or_mean_sq_pos(int dim, int n_comp, int64_t N, const double *s);
 
+/* ---- reverse mode (Sec. 6, Eq. 12-13) ---- */
+/* sb = adjoint of s_t given sbn = adjoint of s_{t+1} = F(s_t) (FP64 step of or_step_fp64) */
+void or_adjoint_step(const or_phys_t *ph, int64_t N, const double *s, const double *sbn, double *sb);
+
 /* ---- scheme solve (Sec. 4.2 Eq. 8-10, Algorithm 1) ---- */
 typedef struct {
     int H;

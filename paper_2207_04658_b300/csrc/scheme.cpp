@@ -212,7 +212,8 @@ extern "C" int qmpm_scheme_solve_impl(const qmpm_solve_in_t *in, qmpm_solve_out_
                 const double d = std::sqrt(12.0 * in->P[h] * bound / (in->g[h] * sumP));
                 out->delta_cont[h] = d;
                 out->bits_paper[h] = std::max(1, (int)std::ceil(-std::log2(d / win[h].R)));
-                k0[h] = (int)std::ceil(-std::log2(d));
+                // at least one bit (Algorithm 1): the resolution is at most half the range
+                k0[h] = (int)std::ceil(-std::log2(std::min(d, 0.5 * win[h].R)));
                 lo[h] = k0[h] - 3;
                 hi[h] = k0[h] + 3;
             } else {

@@ -84,6 +84,17 @@ class qmpm_solve_out_t(ct.Structure):
                 ("pred_err", ct.c_double), ("total_bits", ct.c_double)]
 
 
+class qmpm_adjoint_out_t(ct.Structure):
+    _fields_ = [("z", ct.c_double), ("g", ct.c_double * 4), ("lo", ct.c_double * 4),
+                ("hi", ct.c_double * 4), ("P", ct.c_int64 * 4)]
+
+    def as_dict(self):
+        return {"z": self.z, "g": list(self.g), "lo": list(self.lo), "hi": list(self.hi),
+                "P": list(self.P)}
+
+
+MEASURE_MEAN_SQ_POS, MEASURE_USER, MEASURE_KINETIC_ENERGY = 0, 1, 2
+
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/qmpm.h
@@ -103,6 +114,8 @@ _SIGNATURES = [
                                      _P(ct.c_void_p)]),
     ("qmpm_destroy", ct.c_int, [ct.c_void_p]),
     ("qmpm_last_error", ct.c_char_p, []),
+    ("qmpm_adjoint", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
+                                ct.c_void_p, _P(qmpm_adjoint_out_t)]),
     ("qmpm_pack_f32", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t), ct.c_uint64, ct.c_int32,
                                  ct.c_uint32, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int64,
                                  _P(qmpm_stats_t), ct.c_void_p]),
@@ -275,6 +288,13 @@ def qmpm_unpack_f32(dim, material, scheme_struct, d_words_ptr, N, ld, d_vals_ptr
                                  int(N), int(ld), ct.c_void_p(d_vals_ptr), ct.c_void_p(stream)))
 
 
+def qmpm_adjoint(h, T, ckpt_every=32, measure=MEASURE_MEAN_SQ_POS, d_seed_ptr=0, d_grad0_ptr=0):
+    out = qmpm_adjoint_out_t()
+    _check(lib().qmpm_adjoint(h, int(T), int(ckpt_every), int(measure), ct.c_void_p(d_seed_ptr),
+                              ct.c_void_p(d_grad0_ptr), ct.byref(out)))
+    return out.as_dict()
+
+
 def qmpm_tile_order_static(dim, material, scheme_struct, grid_log2, d_words_ptr, N, ld, d_order_ptr,
                            stream=0):
     """The tile order of N packed records without any device allocation (scratch in a
@@ -349,3 +369,90 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------- differentiation
+def _torch():
+    import torch
+    return torch
+
+
+class Rollout:
+    """Differentiable FP32 rollout: ``Rollout.apply(state0, scene, T, ckpt_every)`` returns
+    the state after T steps (rows in the input particle order).  Forward: qmpm_init and
+    qmpm_step on FP32 state; backward: qmpm_adjoint (Sec. 6) with the incoming gradient
+    as seed, checkpointing every ``ckpt_every`` steps.  After a backward pass
+    ``Rollout.last`` holds the adjoint's z, g_h (Eq. 8), ranges and variable counts."""
+
+    last = None
+
+    @staticmethod
+    def _fn():
+        torch = _torch()
+
+        class _Rollout(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, state0, scene, T, ckpt_every):
+                s0 = state0.detach().cpu().double().numpy()
+                sc = dict(scene, resort_every=0)
+                g = Scene(sc, None, s0)
+                g.step(int(T))
+                out = g.state_by_id()
+                g.close()
+                ctx.save_for_backward(state0)
+                ctx.scene, ctx.T, ctx.k = sc, int(T), int(ckpt_every)
+                return torch.from_numpy(out).to(state0.dtype).to(state0.device)
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                (state0,) = ctx.saved_tensors
+                s0 = state0.detach().cpu().double().numpy()
+                g = Scene(ctx.scene, None, s0)
+                ids = g.readback(state=False, ids=True)["ids"]
+                seed = grad_out.detach().float().cpu().numpy()[ids]  # slot order
+                d_seed = torch.from_numpy(np_ascontig(seed)).cuda()
+                d_grad = torch.empty_like(d_seed)
+                info = qmpm_adjoint(g.h, ctx.T, ctx.k, MEASURE_USER, d_seed.data_ptr(),
+                                    d_grad.data_ptr())
+                g.close()
+                Rollout.last = info
+                grad_slot = d_grad.cpu().numpy()
+                grad = np.empty_like(grad_slot)
+                grad[ids] = grad_slot
+                return torch.from_numpy(grad).to(state0.dtype).to(state0.device), None, None, None
+
+        return _Rollout
+
+    @classmethod
+    def apply(cls, state0, scene, T, ckpt_every=32):
+        return cls._fn().apply(state0, scene, T, ckpt_every)
+
+
+def np_ascontig(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+FIELD_KEYS = ("x", "v", "C", "F")
+
+
+def sensitivities(scene, state0, T, ckpt_every=32, measure=MEASURE_MEAN_SQ_POS):
+    """Algorithm 1's forward and backward pass on FP32 state: z (mean |x_T|^2 or the
+    kinetic energy), the accumulated squared gradients g_h (Eq. 8) and the recorded range
+    of each field."""
+    g = Scene(dict(scene, resort_every=0), None, state0)
+    info = qmpm_adjoint(g.h, T, ckpt_every, measure)
+    g.close()
+    return info
+
+
+def solve_scheme(info, eps, mode="error", rounding="paper", kappa=2.0, containers=(0, 0, 0, 0),
+                 material="corotated"):
+    """Scheme from the adjoint's sensitivities (Eq. 10 / Algorithm 1, or the memory-bound
+    form): returns the per-field scheme dict consumed by Scene and the solve report."""
+    res = qmpm_scheme_solve(info["P"], info["g"], info["lo"], info["hi"], info["z"], eps, mode=mode,
+                            rounding=rounding, kappa=kappa)
+    names = ["x", "v", "C", "J" if material == "fluid" else "F"]
+    scheme = {names[h]: dict(bits=int(res["bits"][h]), frac=int(res["frac"][h]),
+                             offset=int(res["offset"][h]), container=int(containers[h]))
+              for h in range(4)}
+    return scheme, res

@@ -94,11 +94,16 @@ def block2d_scheme():
 
 
 def cubes3d_scene(n_cubes=16, cube_cells=40, ppc_axis=2, grid_log2=8, seed=2, steps=1000,
-                  material="corotated", E=5e3, nu=0.3, dt=5e-5, resort_every=8):
-    """3D elastic cubes (fixed-corotated by default): ``n_cubes`` cubes of side
-    cube_cells * dx at seeded non-overlapping corners in [0.1, 0.9]^3, ppc_axis^3
-    jittered particles per cell (8 by default).  The defaults give 16 x 512,000 =
-    8,192,000 particles on a 256^3 grid."""
+                  material="corotated", E=5e3, nu=0.3, rho=4.0, dt=5e-5, speed=3.0,
+                  resort_every=8):
+    """3D elastic cubes (fixed-corotated by default) thrown together: ``n_cubes`` cubes of
+    side cube_cells * dx at seeded non-overlapping corners in [0.1, 0.9]^3, ppc_axis^3
+    jittered particles per cell (8 by default), each cube moving at ``speed`` toward the
+    centre of the domain (plus gravity), so that cubes collide within the run.  The
+    defaults give 16 x 512,000 = 8,192,000 particles on a 256^3 grid; with E = 5e3,
+    nu = 0.3 and rho = 4 the P-wave speed is 41 m/s and dt = 5e-5 is half the cell
+    crossing time (CFL 0.5).  The same seed at half resolution (cube_cells=20,
+    grid_log2=7) is the same scene with 1,024,000 particles."""
     n = 1 << grid_log2
     side = cube_cells / n
     gen = rng(seed)
@@ -107,11 +112,20 @@ def cubes3d_scene(n_cubes=16, cube_cells=40, ppc_axis=2, grid_log2=8, seed=2, st
     xs = [jitter_box(gen, c, (side,) * 3, strata) for c in corners]
     x = np.concatenate(xs, axis=0)
     N = x.shape[0]
+    per = strata[0] ** 3
+    v = np.zeros((N, 3))
+    for i, c in enumerate(corners):
+        to_centre = 0.5 - (c + 0.5 * side)
+        nrm = np.linalg.norm(to_centre)
+        if nrm > 0 and speed > 0:
+            v[i * per:(i + 1) * per] = speed * to_centre / nrm
     scene = dict(name="cubes3d", dim=3, material=material, grid_log2=grid_log2, bound=3,
-                 dt=dt, E=E, nu=nu, bulk=0.0, rho=1.0, p_vol=n_cubes * side ** 3 / N,
+                 dt=dt, E=E, nu=nu, bulk=0.0, rho=rho, p_vol=n_cubes * side ** 3 / N,
                  gravity=(0.0, -9.8, 0.0), seed=seed, dither=True, steps=steps,
                  resort_every=resort_every)
-    return scene, initial_state(3, material, x)
+    s = initial_state(3, material, x)
+    s[:, 3:6] = v
+    return scene, s
 
 
 def dambreak3d_scene(column_cells=256, ppc_axis=2, grid_log2=9, seed=3, steps=500,
@@ -132,7 +146,7 @@ def dambreak3d_scene(column_cells=256, ppc_axis=2, grid_log2=9, seed=3, steps=50
 
 
 def fixed_scheme_3d(material, x_bits=21, v=(16, -8.0, 8.0), C=(16, -512.0, 512.0),
-                    F=(16, 0.0, 2.0), J=(16, 0.0, 2.0), x_container=64):
+                    F=(16, -0.5, 1.5), J=(16, 0.0, 2.0), x_container=64):
     """A hand-written 3D scheme: x as 3 x ``x_bits`` on [0, 1) in one 64-bit container,
     the other fields bit-packed with the given (bits, lo, hi) and the coarsest
     power-of-two resolution whose window covers [lo, hi]."""

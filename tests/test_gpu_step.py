@@ -159,40 +159,46 @@ def test_drift_out_of_tile_slow_path(q, oracle):
 
 
 def test_walls_stop_particles(q, oracle):
-    # a block driven into the floor: sticky wall nodes carry zero velocity.  The step at
-    # contact matches the oracle within two quanta; over 30 steps the positions stay within
-    # a few quanta and nothing enters the wall band
+    # a block driven into the floor: sticky wall nodes carry zero velocity.  After 100
+    # quantized oracle steps the block's bottom row is in contact (its stencils reach the
+    # wall band); one step from that state matches the oracle within two quanta.  After 100
+    # more steps the bottom row has been stopped and the block as a whole decelerated,
+    # while free fall would have sped it up to -0.5 - 9.8 * 0.02 = -0.696
     from paper_2207_04658_b300 import scenes
     sc, s0 = scenes.block2d_scene(n_strata=(32, 16))
-    s0[:, 1] -= 0.4 - 3.6 / 128  # the block's bottom row sits half a cell above the wall band
+    s0[:, 1] -= 0.4 - 3.6 / 128  # the block's bottom row sits 0.6 cells above the wall band
     s0[:, 3] = -0.5
     sch = scenes.block2d_scheme()
     sch["C"] = dict(bits=16, frac=6, offset=-512 * 2 ** 6, container=0)  # [-512, 512]
     sch["F"] = dict(bits=16, frac=14, offset=-2 * 2 ** 14, container=0)  # [-2, 2]: signed shear
-    g = q.Scene(sc, sch, s0, stats=True)
     o = oracle.QuantRollout(sc, sch, s0)
+    o.step(100)
+    s100 = o.state()  # exactly representable: re-encoding it reproduces the words
+    dx = 1.0 / 128
+    assert s100[:, 1].min() < 3.5 * dx
+    g = q.Scene(sc, sch, s100, stats=True)
+    o = oracle.QuantRollout(sc, sch, s100)
     qt = quanta(oracle, sc, sch)[None]
-    for step in range(30):
-        g.step(1)
-        o.step(1)
-        if step == 0:
-            r = g.readback(state=True, ids=True)
-            assert np.array_equal(r["ids"], o.ids)
-            assert (np.abs(r["state"] - o.state()) / qt).max() <= 2.0
+    g.step(1)
+    o.step(1)
+    r = g.readback(state=True, ids=True)
+    assert np.array_equal(r["ids"], o.ids)
+    assert (np.abs(r["state"] - o.state()) / qt).max() <= 2.0
+    g.step(99)
+    o.step(99)
     r = g.readback(state=True, ids=True)
     got = np.empty_like(r["state"])
     got[r["ids"]] = r["state"]
     ref = np.empty_like(got)
     ref[o.ids] = o.state()
     assert sum(r["stats"]["saturations"]) == 0 and o.stats[:4].sum() == 0
-    assert got[:, 1].min() >= 0.5 / 128 and ref[:, 1].min() >= 0.5 / 128
     d = np.abs(got[:, :2] - ref[:, :2]) / qt[:, :2]
-    assert np.percentile(d, 99) <= 8
-    # the particles at the wall have been stopped (the rest of the block is still moving:
-    # the elastic wave has not crossed it yet)
+    assert np.percentile(d, 99) <= 32
     for st in (got, ref):
+        assert st[:, 1].min() >= 2.5 * dx  # nothing is pushed into the wall band
         low = st[:, 1] <= np.percentile(st[:, 1], 5)  # the bottom row of the block
-        assert low.sum() > 10 and np.abs(st[low, 3]).mean() < 0.25
+        assert low.sum() > 10 and st[low, 3].mean() > -0.1
+        assert st[:, 3].mean() > -0.3
 
 
 def test_empty_and_single_particle(q, oracle):

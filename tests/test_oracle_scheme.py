@@ -123,3 +123,15 @@ def test_windows_cover_the_widened_range(oracle):
             mid, R = (lo[h] + hi[h]) / 2, 2.0 * (hi[h] - lo[h])
             assert out["offset"][h] * d <= mid - R / 2
             assert (out["offset"][h] + 2 ** out["bits"][h] - 1) * d >= mid + R / 2
+
+
+def test_resolution_never_coarser_than_half_the_range(oracle):
+    # Algorithm 1's b_h = ceil(-log2(Delta_h / R_h)) >= 1: a type whose error hardly matters
+    # (tiny g_h) still gets a resolution of at most R_h / 2, not Eq. 10's huge Delta_h
+    P = [1000.0, 1000.0]
+    g = [1.0, 1e-20]
+    out = oracle.scheme_solve(P, g, [0.0, -1e-4], [1.0, 1e-4], 1.0, 0.01)
+    assert out["delta_cont"][1] > 1e6
+    assert out["bits_paper"][1] == 1
+    R = 2.0 * 2e-4
+    assert 2.0 ** -out["frac"][1] <= R / 2
