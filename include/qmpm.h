@@ -171,6 +171,12 @@ int qmpm_scheme_solve(const qmpm_solve_in_t *in, qmpm_solve_out_t *out);
 int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const double *h_state,
               void *stream, qmpm_handle *out);
 
+/* Device memory a handle of this scene and scheme holds (resident_bytes), and the most it
+ * holds while qmpm_init runs (init_peak_bytes: plus the FP64 initial state).  Host only;
+ * either pointer may be NULL.  Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME. */
+int qmpm_footprint(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, int64_t *resident_bytes,
+                   int64_t *init_peak_bytes);
+
 /* Enqueue nsteps MLS-MPM steps (P2G, grid update, G2P, dithered store, Eq. 1) on the
  * handle's stream; returns without waiting.  Errors: QMPM_ERR_INVALID_ARG,
  * QMPM_ERR_CUDA (launch failure). */
@@ -239,6 +245,152 @@ typedef struct {
  * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_OOM, QMPM_ERR_CUDA. */
 int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_t measure, const float *d_seed,
                  float *d_grad0, qmpm_adjoint_out_t *out);
+
+/* ---- several scenes in one launch ------------------------------------------------- */
+
+typedef struct qmpm_batch *qmpm_batch_handle;
+
+#define QMPM_BATCH_GRAPHS 1 /* replay each half period (resort_every steps) as a CUDA graph */
+
+typedef struct {
+    int32_t n_members;
+    int32_t n_classes;        /* launch classes: (dim, material, quantized, stats) */
+    int32_t resort_every;
+    int32_t pad;
+    int64_t particles;        /* over all members */
+    int64_t steps;            /* batch steps run */
+    int64_t kernel_launches;  /* kernels launched directly or captured, since creation */
+    int64_t graph_launches;   /* graph replays */
+} qmpm_batch_info_t;
+
+/* A batch steps several scenes together: every step runs one persistent step launch per
+ * launch class over the concatenated chunk lists of its members (a work queue of
+ * (scene, chunk) items with per-scene parameters: grid, scheme, physics, buffers,
+ * dither step index), one clear launch for all consumed grid buffers, and each member's
+ * re-sort when it falls due.  Members keep their own state, results and step count: a
+ * scene stepped in a batch goes through the same sequence of stores and re-sorts as one
+ * stepped alone with the same resort_every (only the order of floating-point atomic
+ * additions differs).
+ *   stream: the batch's stream (NULL: the batch creates one); members' work is ordered on
+ *           it while they belong to the batch (qmpm_batch_add makes it wait for the
+ *           scene's stream, qmpm_batch_remove makes the scene's stream wait for it);
+ *   resort_every: the members' re-sort interval while in the batch (0: never);
+ *   flags: QMPM_BATCH_GRAPHS.
+ * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_CUDA. */
+int qmpm_batch_create(void *stream, int32_t resort_every, int32_t flags, qmpm_batch_handle *out);
+
+/* Add a scene (not in another batch; at most 256 members).  Membership changes rebuild the
+ * batch's tables (and graphs) at the next qmpm_batch_step. */
+int qmpm_batch_add(qmpm_batch_handle b, qmpm_handle h);
+int qmpm_batch_remove(qmpm_batch_handle b, qmpm_handle h);
+
+/* Enqueue nsteps steps of every member on the batch's stream (asynchronous).  With
+ * QMPM_BATCH_GRAPHS, runs of resort_every steps that start on a half-period boundary are
+ * graph replays.  A member may still be stepped or read alone between calls. */
+int qmpm_batch_step(qmpm_batch_handle b, int32_t nsteps);
+
+int qmpm_batch_info(qmpm_batch_handle b, qmpm_batch_info_t *out);
+
+/* Remove every member (their streams and re-sort intervals are restored) and free the
+ * batch. */
+int qmpm_batch_destroy(qmpm_batch_handle b);
+
+/* ---- autotuning ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t chunk;             /* best particles per work item (qmpm_scene_t.chunk) */
+    int32_t resort_every;      /* best re-sort interval */
+    double best_ms_per_step;
+    int32_t n_candidates;
+    int32_t from_cache;        /* 1: answered from this process's cache, nothing was timed */
+    int32_t chunk_cand[16], resort_cand[16];
+    double ms_per_step[16];    /* device time per step of each candidate, re-sorts included */
+} qmpm_tune_t;
+
+/* Time the step of this scene for every candidate chunk in {64, 128, 192, 256} and
+ * re-sort interval in {4, 8, 16, 32} (scratch scenes created from h_state on a private
+ * stream, each stepped 2 + trial_steps steps rounded up to whole re-sort periods) and
+ * return the fastest.  The result is cached per (dim, material, quantized, words per
+ * particle, grid, round(log2 N)) for the process; use_cache != 0 answers from the cache
+ * when it can.  The caller applies the result (qmpm_scene_t.chunk, .resort_every); it
+ * changes the particle order and so the dither draws, not the method.  Errors:
+ * QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME, QMPM_ERR_OOM, QMPM_ERR_CUDA. */
+int qmpm_autotune(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const double *h_state,
+                  int32_t trial_steps, int32_t use_cache, qmpm_tune_t *out);
+
+/* ---- serving: continuous batching of arriving scenes ------------------------------ */
+
+typedef struct qmpm_engine *qmpm_engine_handle;
+
+enum { QMPM_REQ_QUEUED = 0, QMPM_REQ_RUNNING = 1, QMPM_REQ_DONE = 2, QMPM_REQ_FAILED = 3 };
+
+typedef struct {
+    int64_t budget_bytes;  /* device memory the admitted scenes may hold (qmpm_footprint) */
+    int32_t resort_every;  /* the batch's re-sort interval; also the longest iteration */
+    int32_t max_active;    /* scenes stepping at once, 1 .. 256 */
+    int32_t flags;         /* QMPM_BATCH_GRAPHS */
+    int32_t pad;
+} qmpm_engine_config_t;
+
+typedef struct {
+    int64_t id;
+    int32_t status;        /* QMPM_REQ_DONE or QMPM_REQ_FAILED */
+    int32_t error;         /* QMPM_ERR_* of a failed request */
+    int32_t steps;
+    int32_t pad;
+    int64_t particles;
+    int64_t resident_bytes;
+    double t_submit, t_admit, t_done; /* seconds since the engine was created (host clock) */
+    double z;              /* mean square position of the final state (qmpm_measure) */
+} qmpm_request_t;
+
+typedef struct {
+    int64_t queued, active, finished;
+    int64_t bytes_in_use;
+    int64_t particle_steps;  /* stepped so far, all requests */
+    int64_t iterations;
+    int64_t kernel_launches, graph_launches;
+    double elapsed;          /* seconds since creation */
+} qmpm_engine_stats_t;
+
+/* A serving engine on the current device.  Requests (scene, scheme, initial state, step
+ * count) wait in a FIFO queue and are admitted, in order, while the next one's peak
+ * footprint fits under budget_bytes and fewer than max_active scenes run.  Admitted scenes
+ * step together in one batch (see qmpm_batch_*); each iteration runs up to resort_every
+ * steps, and scenes join and leave between iterations while the others keep running.  A
+ * new scene's upload, encode and sort run on a second stream, overlapping the batch.
+ * Finished scenes are measured, optionally read back, and freed.  Errors:
+ * QMPM_ERR_INVALID_ARG, QMPM_ERR_CUDA. */
+int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out);
+
+/* Queue a request; the engine copies h_state (host, as for qmpm_init).  keep_state != 0
+ * keeps the final state for qmpm_engine_result.  Thread-safe.  Errors:
+ * QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME.  A request larger than the budget fails with
+ * QMPM_ERR_OOM when it reaches the head of the queue. */
+int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qmpm_scheme_t *scheme,
+                       const double *h_state, int32_t steps, int32_t keep_state, int64_t *id);
+
+/* Run the loop on a background thread until qmpm_engine_stop (drain != 0: after every
+ * submitted request has finished). */
+int qmpm_engine_start(qmpm_engine_handle e);
+int qmpm_engine_stop(qmpm_engine_handle e, int32_t drain);
+
+/* Or run `iterations` iterations in the calling thread (not while the thread runs);
+ * *busy = 0 once nothing is queued, running or finishing. */
+int qmpm_engine_run(qmpm_engine_handle e, int32_t iterations, int32_t *busy);
+
+/* Take up to max finished requests (oldest first).  Thread-safe. */
+int qmpm_engine_poll(qmpm_engine_handle e, qmpm_request_t *out, int32_t max, int32_t *n_out);
+
+/* Final state of a polled request submitted with keep_state (decoded FP64, slot order, as
+ * qmpm_readback), kept until qmpm_engine_release.  Either pointer may be NULL. */
+int qmpm_engine_result(qmpm_engine_handle e, int64_t id, double *h_state, int64_t *h_ids);
+int qmpm_engine_release(qmpm_engine_handle e, int64_t id);
+
+int qmpm_engine_stats(qmpm_engine_handle e, qmpm_engine_stats_t *out);
+
+/* Stop the thread (without draining), free every scene and the engine. */
+int qmpm_engine_destroy(qmpm_engine_handle e);
 
 /* ---- codec on device buffers (Sec. 3.1 Eq. 3, Sec. 5 Eq. 11, Sec. 7) ------------ */
 

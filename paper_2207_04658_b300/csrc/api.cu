@@ -27,19 +27,23 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(QMPM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Device buffers come from the stream-ordered pool on the handle's stream: neither the
+// allocation nor the free synchronises the device, so scenes can come and go while other
+// scenes' work is in flight.
 template <class T>
-cudaError_t dalloc(T **p, size_t count)
+cudaError_t dalloc(T **p, size_t count, cudaStream_t s)
 {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    return cudaMallocAsync(reinterpret_cast<void **>(p), count * sizeof(T), s);
 }
 
 void release(qmpm_ctx *c)
 {
     if (!c) return;
-    auto fr = [](void *p) {
-        if (p) cudaFree(p);
+    const cudaStream_t s = c->stream;
+    auto fr = [s](void *p) {
+        if (p) cudaFreeAsync(p, s);
     };
     for (int i = 0; i < 2; ++i) {
         fr(c->words[i]);
@@ -161,6 +165,72 @@ namespace qmpm {
 void set_last_error(const std::string &msg) { g_err = msg; }
 }  // namespace qmpm
 
+namespace {
+
+// Scene, scheme and the derived sizes of a handle (no device work).
+int setup(qmpm_ctx *c, const qmpm_scene_t *scene, const qmpm_scheme_t *scheme)
+{
+    c->scene = *scene;
+    if (scheme && scheme->quantized) {
+        c->scheme = *scheme;
+    } else {
+        std::memset(&c->scheme, 0, sizeof(c->scheme));
+    }
+    std::string err;
+    const int rc = qmpm::layout(scene->dim, scene->material, &c->scheme, err);
+    if (rc != QMPM_OK) return fail(rc, err);
+    c->quant = c->scheme.quantized != 0;
+    c->n_comp = qmpm::n_comp(scene->dim, scene->material);
+    c->W = c->scheme.n_words;
+    qmpm::build_codec(c->scheme, scene->dim, scene->material, c->cc);
+    c->N = scene->n_particles;
+    c->ld = std::max<int64_t>(32, (c->N + 31) / 32 * 32);
+    c->n = 1 << scene->grid_log2;
+    c->nb = c->n / 4 + 2;
+    c->n_blocks = scene->dim == 2 ? (int64_t)c->nb * c->nb : (int64_t)c->nb * c->nb * c->nb;
+    c->block_nodes = scene->dim == 2 ? 16 : 64;
+    c->chunk = scene->chunk > 0 ? scene->chunk : qmpm::kMaxChunk;
+    c->key_bits = 1;
+    while ((int64_t(1) << c->key_bits) < c->n_blocks) ++c->key_bits;
+    c->key_bits += scene->dim == 2 ? 4 : 6;  // cell inside the tile
+    c->key_bits = (c->key_bits + 7) / 8 * 8;
+    const int64_t N1 = std::max<int64_t>(c->N, 1);
+    const int64_t n_tiles = qmpm::sort_scratch_tiles(N1);
+    const int64_t scan_len = std::max<int64_t>(256 * n_tiles, c->n_blocks + 1);
+    c->max_scan_partials = (scan_len + 4095) / 4096 + 1;
+    c->max_chunks = (c->N + c->chunk - 1) / c->chunk + std::min<int64_t>(c->N, c->n_blocks) + 1;
+    return QMPM_OK;
+}
+
+// Element counts of the handle's device buffers (qmpm_init allocates exactly these).
+struct Sizes {
+    size_t words, ids, grid, touched, keys, digit_counts, scan_partials, seg, key_chunks, chunks;
+    size_t bytes() const
+    {
+        return 2 * (words * 4 + ids * 8 + grid * 16 + touched + keys * 4 * 2) + digit_counts * 4 +
+               scan_partials * 4 + 2 * seg * 4 + key_chunks * 4 + chunks * sizeof(qmpm::Chunk) + 16 * 8 + 8;
+    }
+};
+
+Sizes sizes_of(const qmpm::Ctx &c)
+{
+    const int64_t N1 = std::max<int64_t>(c.N, 1);
+    Sizes z;
+    z.words = (size_t)c.W * c.ld;
+    z.ids = (size_t)c.ld;
+    z.grid = (size_t)(c.n_blocks * c.block_nodes);
+    z.touched = (size_t)c.n_blocks;
+    z.keys = (size_t)N1;
+    z.digit_counts = (size_t)(256 * qmpm::sort_scratch_tiles(N1));
+    z.scan_partials = (size_t)c.max_scan_partials;
+    z.seg = (size_t)c.n_blocks;
+    z.key_chunks = (size_t)c.n_blocks + 1;
+    z.chunks = (size_t)c.max_chunks;
+    return z;
+}
+
+}  // namespace
+
 using qmpm::Ctx;
 
 extern "C" {
@@ -195,68 +265,37 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
     qmpm_ctx *c = new (std::nothrow) qmpm_ctx();
     if (!c) return fail(QMPM_ERR_OOM, "host allocation failed");
     std::memset(static_cast<void *>(c), 0, sizeof(qmpm_ctx));
-    c->scene = *scene;
-    if (scheme && scheme->quantized) {
-        c->scheme = *scheme;
-    } else {
-        std::memset(&c->scheme, 0, sizeof(c->scheme));
-    }
-    std::string err;
-    rc = qmpm::layout(scene->dim, scene->material, &c->scheme, err);
+    c->stream = stream ? static_cast<cudaStream_t>(stream) : 0;
+    rc = setup(c, scene, scheme);
     if (rc != QMPM_OK) {
         release(c);
-        return fail(rc, err);
+        return rc;
     }
-    c->quant = c->scheme.quantized != 0;
-    c->n_comp = qmpm::n_comp(scene->dim, scene->material);
-    c->W = c->scheme.n_words;
-    qmpm::build_codec(c->scheme, scene->dim, scene->material, c->cc);
-    c->N = scene->n_particles;
-    c->ld = std::max<int64_t>(32, (c->N + 31) / 32 * 32);
-    c->n = 1 << scene->grid_log2;
-    c->nb = c->n / 4 + 2;
-    c->n_blocks = scene->dim == 2 ? (int64_t)c->nb * c->nb : (int64_t)c->nb * c->nb * c->nb;
-    c->block_nodes = scene->dim == 2 ? 16 : 64;
-    c->chunk = scene->chunk > 0 ? scene->chunk : qmpm::kMaxChunk;
-    c->key_bits = 1;
-    while ((int64_t(1) << c->key_bits) < c->n_blocks) ++c->key_bits;
-    c->key_bits += scene->dim == 2 ? 4 : 6;  // cell inside the tile
-    c->key_bits = (c->key_bits + 7) / 8 * 8;
-
     cudaError_t e;
-    if (stream) {
-        c->stream = static_cast<cudaStream_t>(stream);
-    } else {
-        c->stream = 0;
-    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, dev);
     if (c->n_sms <= 0) c->n_sms = 1;
-    c->grid_ctas = c->n_sms * 2;
 
-    const int64_t N1 = std::max<int64_t>(c->N, 1);
-    const int64_t n_tiles = qmpm::sort_scratch_tiles(N1);
-    const int64_t scan_len = std::max<int64_t>(256 * n_tiles, c->n_blocks + 1);
-    c->max_scan_partials = (scan_len + 4095) / 4096 + 1;
-    c->max_chunks = (c->N + c->chunk - 1) / c->chunk + std::min<int64_t>(c->N, c->n_blocks) + 1;
+    const Sizes z = sizes_of(*c);
+    const cudaStream_t st = c->stream;
     bool ok = true;
     for (int i = 0; i < 2 && ok; ++i) {
-        ok = ok && dalloc(&c->words[i], (size_t)c->W * c->ld) == cudaSuccess;
-        ok = ok && dalloc(&c->ids[i], (size_t)c->ld) == cudaSuccess;
-        ok = ok && dalloc(&c->grid[i], (size_t)(c->n_blocks * c->block_nodes)) == cudaSuccess;
-        ok = ok && dalloc(&c->touched[i], (size_t)c->n_blocks) == cudaSuccess;
-        ok = ok && dalloc(&c->keys[i], (size_t)N1) == cudaSuccess;
-        ok = ok && dalloc(&c->vals[i], (size_t)N1) == cudaSuccess;
+        ok = ok && dalloc(&c->words[i], z.words, st) == cudaSuccess;
+        ok = ok && dalloc(&c->ids[i], z.ids, st) == cudaSuccess;
+        ok = ok && dalloc(&c->grid[i], z.grid, st) == cudaSuccess;
+        ok = ok && dalloc(&c->touched[i], z.touched, st) == cudaSuccess;
+        ok = ok && dalloc(&c->keys[i], z.keys, st) == cudaSuccess;
+        ok = ok && dalloc(&c->vals[i], z.keys, st) == cudaSuccess;
     }
-    ok = ok && dalloc(&c->digit_counts, (size_t)(256 * n_tiles)) == cudaSuccess;
-    ok = ok && dalloc(&c->scan_partials, (size_t)c->max_scan_partials) == cudaSuccess;
-    ok = ok && dalloc(&c->seg_begin, (size_t)c->n_blocks) == cudaSuccess;
-    ok = ok && dalloc(&c->seg_end, (size_t)c->n_blocks) == cudaSuccess;
-    ok = ok && dalloc(&c->key_chunks, (size_t)c->n_blocks + 1) == cudaSuccess;
-    ok = ok && dalloc(&c->chunks, (size_t)c->max_chunks) == cudaSuccess;
-    ok = ok && dalloc(&c->d_stats, 16) == cudaSuccess;
-    ok = ok && dalloc(&c->d_z, 1) == cudaSuccess;
+    ok = ok && dalloc(&c->digit_counts, z.digit_counts, st) == cudaSuccess;
+    ok = ok && dalloc(&c->scan_partials, z.scan_partials, st) == cudaSuccess;
+    ok = ok && dalloc(&c->seg_begin, z.seg, st) == cudaSuccess;
+    ok = ok && dalloc(&c->seg_end, z.seg, st) == cudaSuccess;
+    ok = ok && dalloc(&c->key_chunks, z.key_chunks, st) == cudaSuccess;
+    ok = ok && dalloc(&c->chunks, z.chunks, st) == cudaSuccess;
+    ok = ok && dalloc(&c->d_stats, 16, st) == cudaSuccess;
+    ok = ok && dalloc(&c->d_z, 1, st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         release(c);
@@ -283,7 +322,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
     }
     if (c->N > 0) {
         double *d_state = nullptr;
-        e = cudaMalloc(&d_state, sizeof(double) * (size_t)c->N * c->n_comp);
+        e = cudaMallocAsync(reinterpret_cast<void **>(&d_state), sizeof(double) * (size_t)c->N * c->n_comp, c->stream);
         if (e != cudaSuccess) {
             release(c);
             return fail(QMPM_ERR_OOM, "device allocation of the initial state failed");
@@ -295,8 +334,8 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
             iota_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->ids[0], c->N);
             e = cudaGetLastError();
         }
+        cudaFreeAsync(d_state, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        cudaFree(d_state);
         if (e != cudaSuccess) {
             release(c);
             return cuda_fail(e, "initial encode");
@@ -318,11 +357,30 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
     return QMPM_OK;
 }
 
+int qmpm_footprint(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, int64_t *resident_bytes,
+                   int64_t *init_peak_bytes)
+{
+    int rc = validate_scene(scene);
+    if (rc != QMPM_OK) return rc;
+    qmpm_ctx *c = new (std::nothrow) qmpm_ctx();
+    if (!c) return fail(QMPM_ERR_OOM, "host allocation failed");
+    std::memset(static_cast<void *>(c), 0, sizeof(qmpm_ctx));
+    rc = setup(c, scene, scheme);
+    if (rc == QMPM_OK) {
+        const int64_t resident = (int64_t)sizes_of(*c).bytes();
+        if (resident_bytes) *resident_bytes = resident;
+        if (init_peak_bytes) *init_peak_bytes = resident + (int64_t)sizeof(double) * c->N * c->n_comp;
+    }
+    delete c;
+    return rc;
+}
+
 int qmpm_step(qmpm_handle h, int32_t nsteps)
 {
     if (!h || nsteps < 0) return fail(QMPM_ERR_INVALID_ARG, "bad handle or nsteps");
     Ctx &c = *h;
     std::string err;
+    if (nsteps > 0) qmpm::batch_invalidate(c.batch);
     if (!c.primed) {
         const int rc = prime(c);
         if (rc != QMPM_OK) return rc;
@@ -353,14 +411,14 @@ int qmpm_readback(qmpm_handle h, double *h_state, uint32_t *h_words, int64_t *h_
     cudaError_t e = cudaSuccess;
     if (h_state && c.N > 0) {
         double *d_state = nullptr;
-        e = cudaMalloc(&d_state, sizeof(double) * (size_t)c.N * c.n_comp);
+        e = cudaMallocAsync(reinterpret_cast<void **>(&d_state), sizeof(double) * (size_t)c.N * c.n_comp, c.stream);
         if (e != cudaSuccess) return fail(QMPM_ERR_OOM, "device allocation for readback failed");
         e = qmpm::launch_decode_f64(c, d_state);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_state, d_state, sizeof(double) * (size_t)c.N * c.n_comp, cudaMemcpyDeviceToHost,
                                 c.stream);
+        cudaFreeAsync(d_state, c.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-        cudaFree(d_state);
         if (e != cudaSuccess) return cuda_fail(e, "readback");
     }
     if (h_words && c.N > 0) {
@@ -424,6 +482,7 @@ int qmpm_step_host(qmpm_handle h, int32_t nsteps, const uint32_t *h_words_in, ui
                               cudaMemcpyHostToDevice, c.stream);
         if (e != cudaSuccess) return cuda_fail(e, "upload words");
         // the grid of the previous state is stale: clear it and redo the P2G
+        qmpm::batch_invalidate(c.batch);
         const int rc = do_clear(c, c.gcur);
         if (rc != QMPM_OK) return rc;
         c.primed = false;
@@ -491,6 +550,7 @@ int qmpm_state_device(qmpm_handle h, uint32_t **d_words, int64_t *ld, int64_t **
 int qmpm_destroy(qmpm_handle h)
 {
     if (!h) return QMPM_OK;
+    if (h->batch) qmpm_batch_remove(h->batch, h);
     cudaStreamSynchronize(h->stream);
     release(h);
     return QMPM_OK;

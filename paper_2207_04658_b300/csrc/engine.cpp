@@ -1,0 +1,481 @@
+// engine.cpp -- the serving loop of libqmpm (qmpm_engine_*): scenes arrive as requests
+// (scene, scheme, initial state, step count), wait in a FIFO queue, are admitted while their
+// device footprint fits the memory budget and a batch slot is free, step together in one
+// multi-scene batch (continuous batching: members join and leave between iterations while
+// the others keep running), and leave with their measurement and, on request, their final
+// state.  The loop runs on a background thread (qmpm_engine_start) or in the caller's thread
+// (qmpm_engine_run).
+//
+// Streams: scenes are created and measured on the engine's init stream, stepped on the
+// batch stream; a new scene's upload, encode and sort overlap the running batch, and the
+// stream-ordered allocator frees finished scenes without synchronising the device.  At most
+// two iterations are in flight on the batch stream.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "qmpm_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    int64_t id = 0;
+    qmpm_scene_t scene;
+    qmpm_scheme_t scheme;
+    bool has_scheme = false;
+    bool keep_state = false;
+    std::vector<double> state;  // initial state until admission, final state if kept
+    std::vector<int64_t> ids;
+    int32_t steps = 0;
+    int32_t done_steps = 0;
+    int64_t resident = 0, peak = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int32_t status = QMPM_REQ_QUEUED;
+    int32_t error = 0;
+    double z = 0;
+    qmpm_handle h = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    double *h_z = nullptr;  // pinned
+};
+
+}  // namespace
+
+struct qmpm_engine {
+    qmpm_engine_config_t cfg;
+    int dev = 0;
+    cudaStream_t init_stream = nullptr, step_stream = nullptr;
+    qmpm_batch_handle batch = nullptr;
+    double *pinned = nullptr;  // one z slot per request id modulo kSlots
+    static constexpr int kSlots = 4096;
+
+    std::mutex mu;  // guards queue, done, kept, next_id, counters read by the caller
+    std::condition_variable cv;
+    std::deque<Request *> queue;
+    std::vector<Request *> done;
+    std::map<int64_t, Request *> kept;
+    int64_t next_id = 1;
+    int64_t snap_active = 0, snap_bytes = 0, snap_particle_steps = 0, snap_iterations = 0;  // for stats
+    int64_t snap_launches = 0, snap_graph_launches = 0;
+
+    // loop-thread state
+    std::vector<Request *> active, finishing;
+    int64_t bytes_in_use = 0;
+    int64_t particle_steps = 0, iterations = 0, n_done = 0;
+    cudaEvent_t iter_ev[2] = {nullptr, nullptr};
+    bool iter_pending[2] = {false, false};
+    int iter_idx = 0;
+
+    std::thread worker;
+    std::atomic<bool> running{false}, stop_req{false}, drain{false};
+    Clock::time_point t0;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+int efail(int code, const std::string &msg)
+{
+    qmpm::set_last_error(msg);
+    return code;
+}
+
+void finish(qmpm_engine &e, Request *r, int32_t status)
+{
+    r->status = status;
+    r->t_done = e.now();
+    if (r->h) {
+        qmpm_destroy(r->h);
+        r->h = nullptr;
+        e.bytes_in_use -= r->resident;
+    }
+    if (r->done_ev) {
+        cudaEventDestroy(r->done_ev);
+        r->done_ev = nullptr;
+    }
+    if (!r->keep_state) {
+        std::vector<double>().swap(r->state);
+        std::vector<int64_t>().swap(r->ids);
+    }
+    std::lock_guard<std::mutex> lk(e.mu);
+    e.done.push_back(r);
+    e.n_done += 1;
+}
+
+// Requests whose measurement has reached the host.
+void collect(qmpm_engine &e)
+{
+    for (size_t i = 0; i < e.finishing.size();) {
+        Request *r = e.finishing[i];
+        const cudaError_t q = cudaEventQuery(r->done_ev);
+        if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        e.finishing.erase(e.finishing.begin() + i);
+        if (q != cudaSuccess) {
+            r->error = QMPM_ERR_CUDA;
+            finish(e, r, QMPM_REQ_FAILED);
+            continue;
+        }
+        r->z = *r->h_z;
+        if (r->keep_state) {
+            const qmpm::Ctx &c = *r->h;
+            r->state.resize((size_t)c.N * c.n_comp);
+            r->ids.resize((size_t)c.N);
+            const int rc = qmpm_readback(r->h, r->state.data(), nullptr, r->ids.data(), nullptr);
+            if (rc != QMPM_OK) {
+                r->error = rc;
+                finish(e, r, QMPM_REQ_FAILED);
+                continue;
+            }
+        }
+        finish(e, r, QMPM_REQ_DONE);
+    }
+}
+
+// FIFO admission while the next request's peak footprint fits and a batch slot is free.
+void admit(qmpm_engine &e)
+{
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(e.mu);
+            if (e.queue.empty()) return;
+            if ((int)e.active.size() >= e.cfg.max_active) return;
+            Request *f = e.queue.front();
+            if (e.bytes_in_use + f->peak > e.cfg.budget_bytes) {
+                if (f->peak > e.cfg.budget_bytes) {  // can never fit
+                    e.queue.pop_front();
+                    f->error = QMPM_ERR_OOM;
+                    r = f;
+                } else {
+                    return;
+                }
+            } else {
+                e.queue.pop_front();
+                r = f;
+            }
+        }
+        if (r->error) {
+            finish(e, r, QMPM_REQ_FAILED);
+            continue;
+        }
+        r->t_admit = e.now();
+        int rc = qmpm_init(&r->scene, r->has_scheme ? &r->scheme : nullptr, r->state.data(), e.init_stream, &r->h);
+        std::vector<double>().swap(r->state);
+        if (rc == QMPM_OK) {
+            e.bytes_in_use += r->resident;
+            if (r->steps > 0) rc = qmpm_batch_add(e.batch, r->h);
+        }
+        if (rc != QMPM_OK) {
+            r->error = rc;
+            finish(e, r, QMPM_REQ_FAILED);
+            continue;
+        }
+        r->status = QMPM_REQ_RUNNING;
+        if (r->steps == 0) {
+            // nothing to step: measure the initial state
+            qmpm::launch_measure(*r->h);
+            cudaMemcpyAsync(r->h_z, r->h->d_z, sizeof(double), cudaMemcpyDeviceToHost, r->h->stream);
+            cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+            cudaEventRecord(r->done_ev, r->h->stream);
+            e.finishing.push_back(r);
+        } else {
+            e.active.push_back(r);
+        }
+    }
+}
+
+// One iteration: completions, admissions, then up to resort_every steps of every member.
+// Returns the number of members stepped.
+int iterate(qmpm_engine &e)
+{
+    collect(e);
+    admit(e);
+    if (e.active.empty()) return 0;
+    int32_t L = e.cfg.resort_every > 0 ? e.cfg.resort_every : 8;
+    for (Request *r : e.active) L = std::min(L, r->steps - r->done_steps);
+    // at most two iterations in flight
+    if (e.iter_pending[e.iter_idx]) {
+        cudaEventSynchronize(e.iter_ev[e.iter_idx]);
+        e.iter_pending[e.iter_idx] = false;
+    }
+    int rc = qmpm_batch_step(e.batch, L);
+    if (rc == QMPM_OK) {
+        cudaEventRecord(e.iter_ev[e.iter_idx], e.step_stream);
+        e.iter_pending[e.iter_idx] = true;
+        e.iter_idx ^= 1;
+    }
+    const int stepped = (int)e.active.size();
+    for (size_t i = 0; i < e.active.size();) {
+        Request *r = e.active[i];
+        if (rc != QMPM_OK) {
+            qmpm_batch_remove(e.batch, r->h);
+            r->error = rc;
+            e.active.erase(e.active.begin() + i);
+            finish(e, r, QMPM_REQ_FAILED);
+            continue;
+        }
+        r->done_steps += L;
+        e.particle_steps += (int64_t)L * r->scene.n_particles;
+        if (r->done_steps >= r->steps) {
+            // leave the batch; measure on the scene's own stream after the batch's work
+            qmpm_batch_remove(e.batch, r->h);
+            qmpm::launch_measure(*r->h);
+            cudaMemcpyAsync(r->h_z, r->h->d_z, sizeof(double), cudaMemcpyDeviceToHost, r->h->stream);
+            cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+            cudaEventRecord(r->done_ev, r->h->stream);
+            e.active.erase(e.active.begin() + i);
+            e.finishing.push_back(r);
+            continue;
+        }
+        ++i;
+    }
+    e.iterations += 1;
+    std::lock_guard<std::mutex> lk(e.mu);
+    e.snap_active = (int64_t)e.active.size();
+    e.snap_bytes = e.bytes_in_use;
+    e.snap_particle_steps = e.particle_steps;
+    e.snap_iterations = e.iterations;
+    qmpm_batch_info_t bi;
+    if (qmpm_batch_info(e.batch, &bi) == QMPM_OK) {
+        e.snap_launches = bi.kernel_launches;
+        e.snap_graph_launches = bi.graph_launches;
+    }
+    return stepped;
+}
+
+// (called from the loop's thread, which alone changes active and finishing)
+bool idle(qmpm_engine &e)
+{
+    std::lock_guard<std::mutex> lk(e.mu);
+    return e.queue.empty() && e.active.empty() && e.finishing.empty();
+}
+
+void loop(qmpm_engine *e)
+{
+    cudaSetDevice(e->dev);
+    while (true) {
+        if (e->stop_req.load() && (!e->drain.load() || idle(*e))) break;
+        const int stepped = iterate(*e);
+        if (stepped == 0 && e->finishing.empty()) {
+            std::unique_lock<std::mutex> lk(e->mu);
+            e->cv.wait_for(lk, std::chrono::milliseconds(1),
+                           [e] { return !e->queue.empty() || e->stop_req.load(); });
+        } else if (stepped == 0) {
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+    }
+    collect(*e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out)
+{
+    if (!cfg || !out) return efail(QMPM_ERR_INVALID_ARG, "cfg or out is NULL");
+    if (cfg->budget_bytes <= 0 || cfg->max_active <= 0 || cfg->max_active > 256 || cfg->resort_every < 0)
+        return efail(QMPM_ERR_INVALID_ARG, "bad engine configuration");
+    *out = nullptr;
+    qmpm_engine *e = new (std::nothrow) qmpm_engine();
+    if (!e) return efail(QMPM_ERR_OOM, "host allocation failed");
+    e->cfg = *cfg;
+    e->t0 = Clock::now();
+    cudaGetDevice(&e->dev);
+    // keep freed scene memory in the pool between requests instead of returning it to the
+    // driver at every synchronisation (a setting of this process's pool only)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, e->dev) == cudaSuccess) {
+        uint64_t keep = ~uint64_t(0);
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaError_t ce = cudaStreamCreateWithFlags(&e->init_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&e->step_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->iter_ev[0], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->iter_ev[1], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaMallocHost(reinterpret_cast<void **>(&e->pinned), sizeof(double) * qmpm_engine::kSlots);
+    if (ce != cudaSuccess) {
+        qmpm_engine_destroy(e);
+        return efail(QMPM_ERR_CUDA, std::string("engine setup: ") + cudaGetErrorString(ce));
+    }
+    const int rc = qmpm_batch_create(e->step_stream, cfg->resort_every, cfg->flags, &e->batch);
+    if (rc != QMPM_OK) {
+        qmpm_engine_destroy(e);
+        return rc;
+    }
+    *out = e;
+    return QMPM_OK;
+}
+
+int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qmpm_scheme_t *scheme,
+                       const double *h_state, int32_t steps, int32_t keep_state, int64_t *id)
+{
+    if (!e || !scene || steps < 0 || (scene->n_particles > 0 && !h_state))
+        return efail(QMPM_ERR_INVALID_ARG, "bad request");
+    Request *r = new (std::nothrow) Request();
+    if (!r) return efail(QMPM_ERR_OOM, "host allocation failed");
+    r->scene = *scene;
+    r->has_scheme = scheme && scheme->quantized;
+    if (r->has_scheme) r->scheme = *scheme;
+    int rc = qmpm_footprint(scene, r->has_scheme ? scheme : nullptr, &r->resident, &r->peak);
+    if (rc != QMPM_OK) {
+        delete r;
+        return rc;
+    }
+    const int nc = 2 * scene->dim + scene->dim * scene->dim +
+                   (scene->material == QMPM_FLUID ? 1 : scene->dim * scene->dim);
+    r->state.assign(h_state, h_state + (size_t)scene->n_particles * nc);
+    r->steps = steps;
+    r->keep_state = keep_state != 0;
+    r->t_submit = e->now();
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        r->id = e->next_id++;
+        r->h_z = e->pinned + (r->id % qmpm_engine::kSlots);
+        e->queue.push_back(r);
+    }
+    e->cv.notify_one();
+    if (id) *id = r->id;
+    return QMPM_OK;
+}
+
+int qmpm_engine_run(qmpm_engine_handle e, int32_t iterations, int32_t *busy)
+{
+    if (!e || iterations < 0) return efail(QMPM_ERR_INVALID_ARG, "bad engine or iterations");
+    if (e->running.load()) return efail(QMPM_ERR_INVALID_ARG, "the engine's thread is running");
+    for (int i = 0; i < iterations; ++i) iterate(*e);
+    if (busy) *busy = idle(*e) ? 0 : 1;
+    return QMPM_OK;
+}
+
+int qmpm_engine_start(qmpm_engine_handle e)
+{
+    if (!e) return efail(QMPM_ERR_INVALID_ARG, "bad engine");
+    if (e->running.exchange(true)) return QMPM_OK;
+    e->stop_req = false;
+    e->worker = std::thread(loop, e);
+    return QMPM_OK;
+}
+
+int qmpm_engine_stop(qmpm_engine_handle e, int32_t drain)
+{
+    if (!e) return efail(QMPM_ERR_INVALID_ARG, "bad engine");
+    if (!e->running.load()) return QMPM_OK;
+    e->drain = drain != 0;
+    e->stop_req = true;
+    e->cv.notify_all();
+    e->worker.join();
+    e->running = false;
+    return QMPM_OK;
+}
+
+int qmpm_engine_poll(qmpm_engine_handle e, qmpm_request_t *out, int32_t max, int32_t *n_out)
+{
+    if (!e || (max > 0 && !out) || !n_out) return efail(QMPM_ERR_INVALID_ARG, "bad poll arguments");
+    std::lock_guard<std::mutex> lk(e->mu);
+    int32_t n = 0;
+    while (n < max && !e->done.empty()) {
+        Request *r = e->done.front();
+        e->done.erase(e->done.begin());
+        qmpm_request_t &o = out[n++];
+        std::memset(&o, 0, sizeof(o));
+        o.id = r->id;
+        o.status = r->status;
+        o.error = r->error;
+        o.steps = r->steps;
+        o.particles = r->scene.n_particles;
+        o.resident_bytes = r->resident;
+        o.t_submit = r->t_submit;
+        o.t_admit = r->t_admit;
+        o.t_done = r->t_done;
+        o.z = r->z;
+        if (r->keep_state && r->status == QMPM_REQ_DONE) e->kept[r->id] = r;
+        else delete r;
+    }
+    *n_out = n;
+    return QMPM_OK;
+}
+
+int qmpm_engine_result(qmpm_engine_handle e, int64_t id, double *h_state, int64_t *h_ids)
+{
+    if (!e) return efail(QMPM_ERR_INVALID_ARG, "bad engine");
+    std::lock_guard<std::mutex> lk(e->mu);
+    auto it = e->kept.find(id);
+    if (it == e->kept.end()) return efail(QMPM_ERR_INVALID_ARG, "no kept result for this id (poll it first)");
+    Request *r = it->second;
+    if (h_state) std::memcpy(h_state, r->state.data(), r->state.size() * sizeof(double));
+    if (h_ids) std::memcpy(h_ids, r->ids.data(), r->ids.size() * sizeof(int64_t));
+    return QMPM_OK;
+}
+
+int qmpm_engine_release(qmpm_engine_handle e, int64_t id)
+{
+    if (!e) return efail(QMPM_ERR_INVALID_ARG, "bad engine");
+    std::lock_guard<std::mutex> lk(e->mu);
+    auto it = e->kept.find(id);
+    if (it != e->kept.end()) {
+        delete it->second;
+        e->kept.erase(it);
+    }
+    return QMPM_OK;
+}
+
+int qmpm_engine_stats(qmpm_engine_handle e, qmpm_engine_stats_t *out)
+{
+    if (!e || !out) return efail(QMPM_ERR_INVALID_ARG, "bad engine or out");
+    std::memset(out, 0, sizeof(*out));
+    std::lock_guard<std::mutex> lk(e->mu);
+    out->queued = (int64_t)e->queue.size();
+    out->active = e->snap_active;
+    out->finished = e->n_done;
+    out->bytes_in_use = e->snap_bytes;
+    out->particle_steps = e->snap_particle_steps;
+    out->iterations = e->snap_iterations;
+    out->elapsed = e->now();
+    out->kernel_launches = e->snap_launches;
+    out->graph_launches = e->snap_graph_launches;
+    return QMPM_OK;
+}
+
+int qmpm_engine_destroy(qmpm_engine_handle e)
+{
+    if (!e) return QMPM_OK;
+    qmpm_engine_stop(e, 0);
+    if (e->step_stream) cudaStreamSynchronize(e->step_stream);
+    if (e->init_stream) cudaStreamSynchronize(e->init_stream);
+    for (Request *r : e->active) {
+        if (r->h) qmpm_destroy(r->h);
+        delete r;
+    }
+    for (Request *r : e->finishing) {
+        if (r->h) qmpm_destroy(r->h);
+        if (r->done_ev) cudaEventDestroy(r->done_ev);
+        delete r;
+    }
+    for (Request *r : e->queue) delete r;
+    for (Request *r : e->done) delete r;
+    for (auto &kv : e->kept) delete kv.second;
+    if (e->batch) qmpm_batch_destroy(e->batch);
+    for (auto ev : e->iter_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (e->pinned) cudaFreeHost(e->pinned);
+    if (e->init_stream) cudaStreamDestroy(e->init_stream);
+    if (e->step_stream) cudaStreamDestroy(e->step_stream);
+    delete e;
+    return QMPM_OK;
+}
+
+}  // extern "C"

@@ -9,6 +9,8 @@
 
 #include "../../include/qmpm.h"
 
+struct qmpm_batch;
+
 namespace qmpm {
 
 constexpr int kMaxComp = QMPM_MAX_COMP;
@@ -59,7 +61,21 @@ struct StepParams {
     float4 *grid_out;           // zeroed target of the next P2G
     uint8_t *touched_out;       // blocks of grid_out that received mass
     unsigned long long *stats;  // QMPM_FLAG_STATS counters (13) or null
+    const uint32_t *step_ctr;   // multi-scene launches: steps done so far (the store uses + 1)
 };
+
+// Grid buffer of one member of a multi-scene clear.
+struct ClearItem {
+    float4 *grid;
+    uint8_t *touched;
+    int64_t n_blocks;
+    int64_t first;              // first virtual block: sum of the previous members' counts,
+                                // each rounded up to a multiple of 32
+    int32_t block_nodes;
+    int32_t pad;
+};
+
+constexpr int kMaxMembers = 256;   // scenes of one multi-scene launch
 
 // Event records of QMPM_FLAG_PROFILE: (start, end, kind) per launch group.
 struct Profile {
@@ -87,7 +103,6 @@ struct Ctx {
     cudaStream_t stream;
     bool own_stream;
     int n_sms;
-    int grid_ctas;              // persistent CTAs of the step kernels
 
     uint32_t *words[2];         // word planes (ping-pong for the re-sort gather)
     int64_t *ids[2];
@@ -110,6 +125,8 @@ struct Ctx {
 
     struct Profile *prof;       // event records (QMPM_FLAG_PROFILE), owned
     int64_t launches;           // kernel launches since the last profile reset
+
+    qmpm_batch *batch;          // the batch the scene steps in, or null
 
     unsigned long long *d_stats; // 16 counters
     double *d_z;
@@ -156,6 +173,20 @@ cudaError_t launch_unpack_f32(int dim, int material, const CompCodec *cc, int n_
                               const uint32_t *d_words, int64_t N, int64_t ld, float *d_vals,
                               cudaStream_t s);
 void fill_params(const Ctx &c, StepParams &p);
+// parameters of the G2P -> store -> P2G launch of the live state (grid buffers by gcur)
+void step_params(const Ctx &c, StepParams &p, uint32_t step);
+size_t step_smem_bytes(int dim, int W);
+
+// multi-scene launches (batch.cu drives them): one persistent step kernel over the chunks
+// of n members of one (dim, material, quantized, stats) class; one clear over n grids;
+// the members' step counters advanced by one
+cudaError_t launch_step_multi(int dim, int material, bool quant, bool stats, const StepParams *d_tab, int n,
+                              size_t smem, int n_sms, cudaStream_t s);
+cudaError_t launch_clear_multi(const ClearItem *d_items, int n, int64_t virtual_blocks, int n_sms, cudaStream_t s);
+cudaError_t launch_advance(uint32_t *d_ctr, int n, cudaStream_t s);
+
+// batch.cu: a member's host-side state changed outside the batch (its tables are stale)
+void batch_invalidate(qmpm_batch *b);
 
 }  // namespace qmpm
 

@@ -94,6 +94,55 @@ class qmpm_adjoint_out_t(ct.Structure):
 
 
 MEASURE_MEAN_SQ_POS, MEASURE_USER, MEASURE_KINETIC_ENERGY = 0, 1, 2
+BATCH_GRAPHS = 1
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class qmpm_batch_info_t(ct.Structure):
+    _fields_ = [("n_members", ct.c_int32), ("n_classes", ct.c_int32), ("resort_every", ct.c_int32),
+                ("pad", ct.c_int32), ("particles", ct.c_int64), ("steps", ct.c_int64),
+                ("kernel_launches", ct.c_int64), ("graph_launches", ct.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class qmpm_tune_t(ct.Structure):
+    _fields_ = [("chunk", ct.c_int32), ("resort_every", ct.c_int32), ("best_ms_per_step", ct.c_double),
+                ("n_candidates", ct.c_int32), ("from_cache", ct.c_int32),
+                ("chunk_cand", ct.c_int32 * 16), ("resort_cand", ct.c_int32 * 16),
+                ("ms_per_step", ct.c_double * 16)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"chunk": self.chunk, "resort_every": self.resort_every,
+                "best_ms_per_step": self.best_ms_per_step, "from_cache": bool(self.from_cache),
+                "candidates": [(self.chunk_cand[i], self.resort_cand[i], self.ms_per_step[i])
+                               for i in range(n)]}
+
+
+class qmpm_engine_config_t(ct.Structure):
+    _fields_ = [("budget_bytes", ct.c_int64), ("resort_every", ct.c_int32), ("max_active", ct.c_int32),
+                ("flags", ct.c_int32), ("pad", ct.c_int32)]
+
+
+class qmpm_request_t(ct.Structure):
+    _fields_ = [("id", ct.c_int64), ("status", ct.c_int32), ("error", ct.c_int32), ("steps", ct.c_int32),
+                ("pad", ct.c_int32), ("particles", ct.c_int64), ("resident_bytes", ct.c_int64),
+                ("t_submit", ct.c_double), ("t_admit", ct.c_double), ("t_done", ct.c_double),
+                ("z", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class qmpm_engine_stats_t(ct.Structure):
+    _fields_ = [("queued", ct.c_int64), ("active", ct.c_int64), ("finished", ct.c_int64),
+                ("bytes_in_use", ct.c_int64), ("particle_steps", ct.c_int64), ("iterations", ct.c_int64),
+                ("kernel_launches", ct.c_int64), ("graph_launches", ct.c_int64), ("elapsed", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 _lib = None
 
@@ -116,6 +165,26 @@ _SIGNATURES = [
     ("qmpm_last_error", ct.c_char_p, []),
     ("qmpm_adjoint", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
                                 ct.c_void_p, _P(qmpm_adjoint_out_t)]),
+    ("qmpm_footprint", ct.c_int, [_P(qmpm_scene_t), _P(qmpm_scheme_t), _P(ct.c_int64), _P(ct.c_int64)]),
+    ("qmpm_batch_create", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, _P(ct.c_void_p)]),
+    ("qmpm_batch_add", ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    ("qmpm_batch_remove", ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    ("qmpm_batch_step", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("qmpm_batch_info", ct.c_int, [ct.c_void_p, _P(qmpm_batch_info_t)]),
+    ("qmpm_batch_destroy", ct.c_int, [ct.c_void_p]),
+    ("qmpm_autotune", ct.c_int, [_P(qmpm_scene_t), _P(qmpm_scheme_t), _P(ct.c_double), ct.c_int32, ct.c_int32,
+                                 _P(qmpm_tune_t)]),
+    ("qmpm_engine_create", ct.c_int, [_P(qmpm_engine_config_t), _P(ct.c_void_p)]),
+    ("qmpm_engine_submit", ct.c_int, [ct.c_void_p, _P(qmpm_scene_t), _P(qmpm_scheme_t), _P(ct.c_double),
+                                      ct.c_int32, ct.c_int32, _P(ct.c_int64)]),
+    ("qmpm_engine_start", ct.c_int, [ct.c_void_p]),
+    ("qmpm_engine_stop", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("qmpm_engine_run", ct.c_int, [ct.c_void_p, ct.c_int32, _P(ct.c_int32)]),
+    ("qmpm_engine_poll", ct.c_int, [ct.c_void_p, _P(qmpm_request_t), ct.c_int32, _P(ct.c_int32)]),
+    ("qmpm_engine_result", ct.c_int, [ct.c_void_p, ct.c_int64, _P(ct.c_double), _P(ct.c_int64)]),
+    ("qmpm_engine_release", ct.c_int, [ct.c_void_p, ct.c_int64]),
+    ("qmpm_engine_stats", ct.c_int, [ct.c_void_p, _P(qmpm_engine_stats_t)]),
+    ("qmpm_engine_destroy", ct.c_int, [ct.c_void_p]),
     ("qmpm_pack_f32", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t), ct.c_uint64, ct.c_int32,
                                  ct.c_uint32, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int64,
                                  _P(qmpm_stats_t), ct.c_void_p]),
@@ -305,6 +374,20 @@ def qmpm_tile_order_static(dim, material, scheme_struct, grid_log2, d_words_ptr,
                                         ct.c_void_p(d_order_ptr), ct.c_void_p(stream)))
 
 
+def qmpm_footprint(scene_struct, scheme_struct):
+    r, p = ct.c_int64(), ct.c_int64()
+    _check(lib().qmpm_footprint(ct.byref(scene_struct), ct.byref(scheme_struct), ct.byref(r), ct.byref(p)))
+    return r.value, p.value
+
+
+def qmpm_autotune(scene_struct, scheme_struct, h_state, trial_steps=32, use_cache=True):
+    st = np.ascontiguousarray(h_state, dtype=np.float64)
+    out = qmpm_tune_t()
+    _check(lib().qmpm_autotune(ct.byref(scene_struct), ct.byref(scheme_struct), _dptr(st, ct.c_double),
+                               int(trial_steps), int(bool(use_cache)), ct.byref(out)))
+    return out.as_dict()
+
+
 # ---------------------------------------------------------------------------- Scene
 class Scene:
     """One simulation resident on the device (a qmpm handle)."""
@@ -456,3 +539,109 @@ def solve_scheme(info, eps, mode="error", rounding="paper", kappa=2.0, container
                              offset=int(res["offset"][h]), container=int(containers[h]))
               for h in range(4)}
     return scheme, res
+
+
+# ---------------------------------------------------------------------------- Batch
+class Batch:
+    """Several scenes stepped together by multi-scene launches (qmpm_batch_*)."""
+
+    def __init__(self, resort_every=8, graphs=True, stream=0):
+        self.h = ct.c_void_p()
+        _check(lib().qmpm_batch_create(ct.c_void_p(stream), int(resort_every),
+                                       BATCH_GRAPHS if graphs else 0, ct.byref(self.h)))
+        self.members = []
+
+    def add(self, scene):
+        _check(lib().qmpm_batch_add(self.h, scene.h))
+        self.members.append(scene)
+
+    def remove(self, scene):
+        _check(lib().qmpm_batch_remove(self.h, scene.h))
+        self.members.remove(scene)
+
+    def step(self, n=1):
+        _check(lib().qmpm_batch_step(self.h, int(n)))
+
+    def info(self):
+        out = qmpm_batch_info_t()
+        _check(lib().qmpm_batch_info(self.h, ct.byref(out)))
+        return out.as_dict()
+
+    def close(self):
+        if self.h is not None:
+            _check(lib().qmpm_batch_destroy(self.h))
+            self.h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------- Engine
+class Engine:
+    """The serving loop (qmpm_engine_*): submit scenes, poll finished requests."""
+
+    def __init__(self, budget_bytes=120 * 2 ** 30, resort_every=8, max_active=64, graphs=True):
+        cfg = qmpm_engine_config_t()
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.resort_every = int(resort_every)
+        cfg.max_active = int(max_active)
+        cfg.flags = BATCH_GRAPHS if graphs else 0
+        self.h = ct.c_void_p()
+        _check(lib().qmpm_engine_create(ct.byref(cfg), ct.byref(self.h)))
+
+    def submit(self, scene, scheme, state0, steps, keep_state=False, flags=0):
+        state0 = np.ascontiguousarray(state0, dtype=np.float64)
+        sc = make_scene_struct(scene, state0.shape[0], flags)
+        sch = make_scheme_struct(scheme, scene["dim"], scene["material"])
+        rid = ct.c_int64()
+        _check(lib().qmpm_engine_submit(self.h, ct.byref(sc), ct.byref(sch), _dptr(state0, ct.c_double),
+                                        int(steps), int(bool(keep_state)), ct.byref(rid)))
+        return rid.value
+
+    def start(self):
+        _check(lib().qmpm_engine_start(self.h))
+
+    def stop(self, drain=True):
+        _check(lib().qmpm_engine_stop(self.h, int(bool(drain))))
+
+    def run(self, iterations=1):
+        busy = ct.c_int32()
+        _check(lib().qmpm_engine_run(self.h, int(iterations), ct.byref(busy)))
+        return bool(busy.value)
+
+    def poll(self, max_n=256):
+        buf = (qmpm_request_t * max_n)()
+        n = ct.c_int32()
+        _check(lib().qmpm_engine_poll(self.h, buf, int(max_n), ct.byref(n)))
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def result(self, rid, N, n_comp):
+        st = np.empty((N, n_comp), dtype=np.float64)
+        ids = np.empty(N, dtype=np.int64)
+        _check(lib().qmpm_engine_result(self.h, int(rid), _dptr(st, ct.c_double), _dptr(ids, ct.c_int64)))
+        out = np.empty_like(st)
+        out[ids] = st
+        return out
+
+    def release(self, rid):
+        _check(lib().qmpm_engine_release(self.h, int(rid)))
+
+    def stats(self):
+        out = qmpm_engine_stats_t()
+        _check(lib().qmpm_engine_stats(self.h, ct.byref(out)))
+        return out.as_dict()
+
+    def close(self):
+        if self.h is not None:
+            _check(lib().qmpm_engine_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
