@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--serving-duration", type=float, default=10.0,
+                    help="seconds of Poisson arrivals in the serving run (0: skip it)")
     ap.add_argument("--fixed-scheme", action="store_true",
                     help="hand-written scheme instead of the solved one (quick runs)")
     ap.add_argument("--scheme-json", default=None,
@@ -230,6 +232,68 @@ def accuracy(qmpm, sc, s0, sch):
             "reference": "FP32 run of the same kernels (the FP64 oracle is too slow at this size)"}
 
 
+def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64):
+    """The serving workload: Poisson arrivals of scenes (2D/3D x elastic/fluid, particle
+    counts log-uniform in [1e4, 4e6], grids 64^3..256^3 or 128^2..1024^2, schemes solved at
+    eps 0.1 or 0.01, 200 steps) submitted to the engine at their arrival times; rollout
+    latency (submit to finished, measured) percentiles and aggregate particle-steps/s."""
+    import queue
+    import threading
+    from paper_2207_04658_b300 import autoquant, scenes
+    t_solve = time.perf_counter()
+    schemes = autoquant.serving_schemes()
+    t_solve = time.perf_counter() - t_solve
+    reqs = scenes.serving_requests(rate=rate, duration=duration, seed=5)
+    eng = qmpm.Engine(budget_bytes=int(budget_gb * 2 ** 30), resort_every=8, max_active=max_active)
+    # a producer thread draws the scenes ahead of their arrival times (bounded look-ahead)
+    ready = queue.Queue(maxsize=16)
+
+    def produce():
+        for r in reqs:
+            sc, s0 = scenes.serving_scene(r["dim"], r["material"], r["n"], r["grid_log2"], r["seed"])
+            ready.put((r, sc, s0))
+        ready.put(None)
+
+    threading.Thread(target=produce, daemon=True).start()
+    eng.start()
+    t0 = time.perf_counter()
+    lateness = []
+    submitted = 0
+    particle_steps = 0
+    while True:
+        item = ready.get()
+        if item is None:
+            break
+        r, sc, s0 = item
+        wait = r["t"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        lateness.append(max(0.0, -wait))
+        eng.submit(sc, schemes[(r["dim"], r["material"], r["grid_log2"], r["eps"])], s0, sc["steps"])
+        submitted += 1
+        particle_steps += s0.shape[0] * sc["steps"]
+    eng.stop(drain=True)
+    recs = eng.poll(max_n=max(1, submitted))
+    st = eng.stats()
+    eng.close()
+    done = [r for r in recs if r["status"] == qmpm.REQ_DONE]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in done]) * 1e3
+    span = max(r["t_done"] for r in done) - min(r["t_submit"] for r in done) if done else float("nan")
+    return {"requests": submitted, "done": len(done), "failed": len(recs) - len(done),
+            "arrival_rate_per_s": rate, "duration_s": duration,
+            "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
+            "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None,
+            "mean_ms": round(float(lat.mean()), 2) if len(lat) else None,
+            "particle_steps_per_s": st["particle_steps"] / span if done else None, "unit": UNIT,
+            "particle_steps": st["particle_steps"], "offered_particle_steps": particle_steps,
+            "budget_gb": budget_gb, "max_active": max_active, "iterations": st["iterations"],
+            "graph_launches": st["graph_launches"], "kernel_launches": st["kernel_launches"],
+            "submit_lateness_p99_ms": round(float(np.percentile(lateness, 99)) * 1e3, 2) if lateness else None,
+            "scheme_solve_s": round(t_solve, 2),
+            "mix": "uniform over 2D neo-Hookean, 2D fluid, 3D fixed-corotated, 3D fluid; N log-uniform "
+                   "[1e4, 4e6]; eps uniform {0.1, 0.01}; 200 steps; schemes from Algorithm 1 per class and grid"}
+
+
 def cpu_baseline(name, sample_steps=2):
     """The oracle (single-threaded FP64 C) on a bounded sample of the same workload: the
     first cube (or a slice of the column) on the full grid, `sample_steps` quantized steps.
@@ -381,6 +445,8 @@ def run_ours(args):
         line["scheme_solve"] = solve_info
     if not args.no_accuracy and dc.rank == 0:
         line["accuracy"] = accuracy(qmpm, sc, s0, sch)
+    if args.serving_duration > 0:
+        line["serving"] = serving(qmpm, args.serving_duration)
     if dc.rank == 0 and dc.world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if dc.rank == 0:

@@ -254,9 +254,9 @@ typedef struct qmpm_batch *qmpm_batch_handle;
 
 typedef struct {
     int32_t n_members;
-    int32_t n_classes;        /* launch classes: (dim, material, quantized, stats) */
+    int32_t n_classes;        /* multi-scene launches: (dim, material, quantized, stats) classes */
     int32_t resort_every;
-    int32_t pad;
+    int32_t n_solo;           /* members with a launch of their own (at least 1024 chunks) */
     int64_t particles;        /* over all members */
     int64_t steps;            /* batch steps run */
     int64_t kernel_launches;  /* kernels launched directly or captured, since creation */
@@ -267,7 +267,8 @@ typedef struct {
  * launch class over the concatenated chunk lists of its members (a work queue of
  * (scene, chunk) items with per-scene parameters: grid, scheme, physics, buffers,
  * dither step index), one clear launch for all consumed grid buffers, and each member's
- * re-sort when it falls due.  Members keep their own state, results and step count: a
+ * re-sort when it falls due.  A member with at least 1024 chunks (about 260,000
+ * particles), which fills the GPU alone, gets a persistent launch of its own instead.  Members keep their own state, results and step count: a
  * scene stepped in a batch goes through the same sequence of stores and re-sorts as one
  * stepped alone with the same resort_every (only the order of floating-point atomic
  * additions differs).

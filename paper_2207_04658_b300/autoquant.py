@@ -20,7 +20,7 @@ def scheme_from_run(scene, state0, T, eps, mode="error", measure=qmpm.MEASURE_ME
     return scheme, {"solve": res, "sensitivities": info}
 
 
-def position_sensitivities(scene, state0, T, samples=2, ckpt_every=32, seed=0):
+def position_sensitivities(scene, state0, T, samples=2, ckpt_every=32, seed=0, reference="position"):
     """Sensitivities of the final particle positions as a whole: the evaluation is the
     vector of final positions x_T, and Eq. 8 summed over its N d outputs gives
     G_h = sum_m sum_t sum_i (d x_T,m / d e_{t,i})^2, the trace of J J^T over the
@@ -28,7 +28,8 @@ def position_sensitivities(scene, state0, T, samples=2, ckpt_every=32, seed=0):
     independent standard normal vectors u on x_T (E[(u^T J)^2] = trace(J J^T)).
     Returns the adjoint report with g replaced by G and z by sqrt(sum_m |x_T,m|^2)
     (so that (eps z)^2 bounds the summed squared position error, i.e. the RMS position
-    error stays below eps times the RMS position)."""
+    error stays below eps times the RMS position), or with reference="displacement" by
+    sqrt(sum_m |x_T,m - x_0,m|^2) (the RMS error below eps times the RMS displacement)."""
     import numpy as np
     import torch
     dim = scene["dim"]
@@ -43,11 +44,17 @@ def position_sensitivities(scene, state0, T, samples=2, ckpt_every=32, seed=0):
         d_seed = torch.from_numpy(u).cuda()
         info = qmpm.qmpm_adjoint(g.h, T, ckpt_every, qmpm.MEASURE_USER, d_seed.data_ptr())
         acc += np.asarray(info["g"])
-    g.close()
     out = dict(info)
     out["g"] = list(acc / samples)
-    out["z"] = float(np.sqrt(N * info["z"]))  # info["z"] is the mean square position of x_T
+    if reference == "displacement":
+        g.step(T)
+        xT = g.state_by_id()[:, :dim]
+        out["z"] = float(np.sqrt(((xT - state0[:, :dim]) ** 2).sum()))
+    else:
+        out["z"] = float(np.sqrt(N * info["z"]))  # info["z"] is the mean square position of x_T
+    g.close()
     out["samples"] = samples
+    out["reference"] = reference
     return out
 
 
@@ -62,3 +69,52 @@ def cubes3d_scheme(eps=0.01, T=None, samples=2, ckpt_every=32, material="corotat
     info = position_sensitivities(sc, s0, steps, samples=samples, ckpt_every=ckpt_every)
     scheme, res = qmpm.solve_scheme(info, eps, containers=(64, 0, 0, 0), material=material)
     return scheme, {"solve": res, "sensitivities": info}
+
+
+def widen_c_for_v_noise(scheme, info, grid_log2, kappa):
+    """The recorded C range comes from the unquantized run, where C of a rigidly moving body
+    is nearly zero; in the quantized run the dithered velocities (resolution Delta_v) make
+    the grid velocities noisy, and C = D^-1 sum_i w_i v_i (x_i - x_p)^T picks that noise up
+    with a gain of about 6 n (sum_i w_i |x_i - x_p| <= 1.5 dx, D^-1 = 4 / dx^2).  Keep C's
+    resolution and widen its window to the recorded range (times kappa) plus 6 n Delta_v on
+    each side.  Returns the scheme with the new C field."""
+    import math
+    n = 1 << grid_log2
+    dv = 2.0 ** -scheme["v"]["frac"]
+    c = dict(scheme["C"])
+    mid = 0.5 * (info["lo"][2] + info["hi"][2])
+    half = 0.5 * kappa * (info["hi"][2] - info["lo"][2]) + 6.0 * n * dv
+    k = c["frac"]
+    lo_i = math.floor((mid - half) * 2.0 ** k)
+    hi_i = math.ceil((mid + half) * 2.0 ** k)
+    bits = max(1, int(math.ceil(math.log2(hi_i - lo_i + 1))))
+    if bits > 24:
+        drop = bits - 24
+        k -= drop
+        lo_i, bits = lo_i >> drop, 24
+    c.update(bits=bits, frac=k, offset=int(lo_i))
+    return dict(scheme, C=c)
+
+
+def serving_schemes(eps_list=scenes.SERVING_EPS, n_rep=20000, samples=2, seed=11, reference="displacement",
+                    kappa=4.0):
+    """Schemes for the serving workload: for every class (2D/3D x elastic/fluid) and grid,
+    the sensitivities of the final positions of a representative scene of that class and
+    grid (about n_rep particles, the serving step count), then Eq. 10 at each error bound,
+    relative to the RMS displacement over the rollout (the bodies move a few cells in 200
+    steps; measured from the origin, the bound would allow errors of many cells).  The x
+    window is the unit domain (every request's body lies in it), the other windows the
+    representative's recorded ranges widened by kappa (4: a request's body differs from the
+    representative in size, so its fields spread further), C's also by the velocity noise it
+    picks up (widen_c_for_v_noise).  Returns {(dim, material, grid_log2, eps): scheme}."""
+    out = {}
+    for dim, material in scenes.SERVING_CLASSES:
+        for grid_log2 in scenes.SERVING_GRIDS[dim]:
+            sc, s0 = scenes.serving_scene(dim, material, n_rep, grid_log2, seed)
+            info = position_sensitivities(sc, s0, sc["steps"], samples=samples, ckpt_every=25,
+                                          reference=reference)
+            info["lo"][0], info["hi"][0] = 0.5 - 0.5 / kappa, 0.5 + 0.5 / kappa  # widened: [0, 1]
+            for eps in eps_list:
+                scheme, _ = qmpm.solve_scheme(info, eps, material=material, kappa=kappa)
+                out[(dim, material, grid_log2, eps)] = widen_c_for_v_noise(scheme, info, grid_log2, kappa)
+    return out

@@ -163,6 +163,14 @@ int validate_scene(const qmpm_scene_t *s)
 
 namespace qmpm {
 void set_last_error(const std::string &msg) { g_err = msg; }
+
+// Free a handle's device memory in order on its stream, without waiting for the stream.
+void destroy_nosync(qmpm_ctx *c)
+{
+    if (!c) return;
+    if (c->batch) qmpm_batch_remove(c->batch, c);
+    release(c);
+}
 }  // namespace qmpm
 
 namespace {

@@ -27,8 +27,20 @@ struct Group {
     int n;
 };
 
+// A member large enough to fill the GPU on its own steps in its own launch (parameters in
+// the constant bank run faster than the multi-scene kernel's shared-memory copy).
+struct Solo {
+    int dim, material;
+    bool quant, stats;
+    size_t smem;
+    qmpm::StepParams p;
+};
+
+constexpr int64_t kSoloChunks = 1024;  // about 260,000 particles
+
 struct Phase {
     std::vector<Group> groups;
+    std::vector<Solo> solos;
     int64_t clear_off;
     int n_clear;
     int64_t virtual_blocks;
@@ -60,6 +72,19 @@ struct qmpm_batch {
     uint32_t *d_ctr = nullptr;
     size_t ctr_cap = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};  // kernels each graph launches
+    bool fresh = false;                 // tables rebuilt during the current qmpm_batch_step
+    // pinned staging of the tables, two sets used in turn: a set is rewritten only after its
+    // previous upload (two plans back) has completed
+    struct Staging {
+        qmpm::StepParams *tab = nullptr;
+        qmpm::ClearItem *clr = nullptr;
+        uint32_t *ctr = nullptr;
+        size_t tab_cap = 0, clr_cap = 0, ctr_cap = 0;
+        cudaEvent_t uploaded = nullptr;
+        bool pending = false;
+    } staging[2];
+    int next_staging = 0;
     int64_t launches = 0;
     int64_t graph_launches = 0;
     int64_t steps = 0;
@@ -102,6 +127,19 @@ cudaError_t grow(T **p, size_t *cap, size_t need)
     return e;
 }
 
+template <class T>
+cudaError_t pinned_grow(T **p, size_t *cap, size_t need)
+{
+    if (need <= *cap) return cudaSuccess;
+    const size_t n = std::max<size_t>(need, 2 * *cap);
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(p), n * sizeof(T));
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
 struct HostState {
     int gcur, cur;
     int64_t steps;
@@ -122,6 +160,7 @@ int plan(qmpm_batch &b)
     for (int m = 0; m < n; ++m) {
         const qmpm::Ctx &c = *b.members[m];
         if (c.N == 0) continue;
+        if ((c.N + c.chunk - 1) / c.chunk >= kSoloChunks) continue;  // a solo member
         cls[std::make_tuple(c.scene.dim, c.scene.material, c.quant ? 1 : 0,
                             (c.scene.flags & QMPM_FLAG_STATS) ? 1 : 0)]
             .push_back(m);
@@ -149,6 +188,22 @@ int plan(qmpm_batch &b)
             }
             ph.groups.push_back(g);
         }
+        for (int m = 0; m < n; ++m) {
+            const qmpm::Ctx &c0 = *b.members[m];
+            if (c0.N == 0 || (c0.N + c0.chunk - 1) / c0.chunk < kSoloChunks) continue;
+            qmpm::Ctx c = c0;
+            c.gcur = st[m].gcur;
+            c.cur = st[m].cur;
+            Solo so;
+            so.dim = c.scene.dim;
+            so.material = c.scene.material;
+            so.quant = c.quant;
+            so.stats = (c.scene.flags & QMPM_FLAG_STATS) != 0;
+            so.smem = qmpm::step_smem_bytes(c.scene.dim, c.W);
+            qmpm::step_params(c, so.p, 0u);
+            so.p.step_ctr = b.d_ctr + m;
+            ph.solos.push_back(so);
+        }
         ph.clear_off = (int64_t)clr.size();
         int64_t first = 0;
         for (int m = 0; m < n; ++m) {
@@ -174,24 +229,40 @@ int plan(qmpm_batch &b)
             }
         }
     }
-    cudaError_t e = grow(&b.d_tab, &b.tab_cap, std::max<size_t>(tab.size(), 1));
-    if (e == cudaSuccess) e = grow(&b.d_clear, &b.clear_cap, std::max<size_t>(clr.size(), 1));
+    // device tables grow rarely (a free synchronises the device); the uploads are ordered
+    // on the batch stream after the work that still reads the previous tables
+    cudaError_t e = grow(&b.d_tab, &b.tab_cap, std::max<size_t>(tab.size(), 64 * (size_t)P));
+    if (e == cudaSuccess) e = grow(&b.d_clear, &b.clear_cap, std::max<size_t>(clr.size(), 64 * (size_t)P));
     if (e != cudaSuccess) return bfail(QMPM_ERR_OOM, "batch tables: device allocation failed");
-    // the tables hold d_ctr addresses: fix them now that d_ctr is final
-    e = cudaMemcpyAsync(b.d_tab, tab.data(), tab.size() * sizeof(qmpm::StepParams), cudaMemcpyHostToDevice,
-                        b.stream);
-    if (e == cudaSuccess && !clr.empty())
-        e = cudaMemcpyAsync(b.d_clear, clr.data(), clr.size() * sizeof(qmpm::ClearItem), cudaMemcpyHostToDevice,
+    auto &st_ = b.staging[b.next_staging];
+    b.next_staging ^= 1;
+    if (st_.pending) {
+        e = cudaEventSynchronize(st_.uploaded);  // this set's previous upload is done
+        st_.pending = false;
+        if (e != cudaSuccess) return bcuda(e, "batch tables");
+    }
+    e = pinned_grow(&st_.tab, &st_.tab_cap, std::max<size_t>(tab.size(), 1));
+    if (e == cudaSuccess) e = pinned_grow(&st_.clr, &st_.clr_cap, std::max<size_t>(clr.size(), 1));
+    if (e == cudaSuccess) e = pinned_grow(&st_.ctr, &st_.ctr_cap, (size_t)std::max(n, 1));
+    if (e != cudaSuccess) return bfail(QMPM_ERR_OOM, "batch tables: pinned allocation failed");
+    if (!tab.empty()) std::memcpy(st_.tab, tab.data(), tab.size() * sizeof(qmpm::StepParams));
+    if (!clr.empty()) std::memcpy(st_.clr, clr.data(), clr.size() * sizeof(qmpm::ClearItem));
+    for (int m = 0; m < n; ++m) st_.ctr[m] = (uint32_t)b.members[m]->steps;  // steps done so far
+    if (!tab.empty())
+        e = cudaMemcpyAsync(b.d_tab, st_.tab, tab.size() * sizeof(qmpm::StepParams), cudaMemcpyHostToDevice,
                             b.stream);
-    // step counters: the steps each member has done
-    std::vector<uint32_t> ctr(n);
-    for (int m = 0; m < n; ++m) ctr[m] = (uint32_t)b.members[m]->steps;
+    if (e == cudaSuccess && !clr.empty())
+        e = cudaMemcpyAsync(b.d_clear, st_.clr, clr.size() * sizeof(qmpm::ClearItem), cudaMemcpyHostToDevice,
+                            b.stream);
     if (e == cudaSuccess && n > 0)
-        e = cudaMemcpyAsync(b.d_ctr, ctr.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, b.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b.stream);  // the host vectors die here
+        e = cudaMemcpyAsync(b.d_ctr, st_.ctr, n * sizeof(uint32_t), cudaMemcpyHostToDevice, b.stream);
+    if (e == cudaSuccess && !st_.uploaded) e = cudaEventCreateWithFlags(&st_.uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(st_.uploaded, b.stream);
     if (e != cudaSuccess) return bcuda(e, "batch tables");
+    st_.pending = true;
     b.phase = 0;
     b.planned = true;
+    b.fresh = true;
     return QMPM_OK;
 }
 
@@ -201,6 +272,12 @@ int run_phase(qmpm_batch &b, int k, bool dry)
 {
     const Phase &ph = b.phases[k];
     if (!dry) {
+        for (const Solo &so : ph.solos) {
+            cudaError_t e = qmpm::launch_step_ctr(so.dim, so.material, so.quant, so.stats, &so.p, so.smem, b.n_sms,
+                                                  b.stream);
+            if (e != cudaSuccess) return bcuda(e, "batch member step");
+            b.launches += 1;
+        }
         for (const Group &g : ph.groups) {
             cudaError_t e = qmpm::launch_step_multi(g.dim, g.material, g.quant, g.stats, b.d_tab + g.tab_off, g.n,
                                                     g.smem, b.n_sms, b.stream);
@@ -234,7 +311,9 @@ int run_phase(qmpm_batch &b, int k, bool dry)
     return QMPM_OK;
 }
 
-// Capture both half periods as graphs, leaving the members' host state unchanged.
+// Capture both half periods as graphs, leaving the members' host state unchanged.  The
+// capture starts from the current phase (a half-period boundary): its half first, then
+// the other one from the state after it.
 int capture(qmpm_batch &b)
 {
     drop_graphs(b);
@@ -242,11 +321,18 @@ int capture(qmpm_batch &b)
     std::vector<HostState> keep;
     for (qmpm_ctx *c : b.members) keep.push_back({c->gcur, c->cur, c->steps});
     const int64_t keep_launches = b.launches, keep_steps = b.steps;
+    const int keep_phase = b.phase;
     int rc = QMPM_OK;
-    for (int h = 0; h < 2 && rc == QMPM_OK; ++h) {
+    for (int i = 0; i < 2 && rc == QMPM_OK; ++i) {
+        const int h = (keep_phase / half + i) % 2;
         cudaError_t e = cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return bcuda(e, "graph capture");
+        if (e != cudaSuccess) {
+            rc = bcuda(e, "graph capture");
+            break;
+        }
+        const int64_t before = b.launches;
         for (int k = h * half; k < (h + 1) * half && rc == QMPM_OK; ++k) rc = run_phase(b, k, false);
+        b.graph_kernels[h] = b.launches - before;
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(b.stream, &g);
         if (rc == QMPM_OK && e != cudaSuccess) rc = bcuda(e, "graph capture");
@@ -263,7 +349,7 @@ int capture(qmpm_batch &b)
     }
     b.launches = keep_launches;
     b.steps = keep_steps;
-    b.phase = 0;
+    b.phase = keep_phase;
     if (rc != QMPM_OK) drop_graphs(b);
     return rc;
 }
@@ -271,12 +357,18 @@ int capture(qmpm_batch &b)
 // Kernels' one-time attributes must be set before a capture (they are not stream work).
 int prepare_kernels(qmpm_batch &b)
 {
-    for (const Phase &ph : b.phases)
+    for (const Phase &ph : b.phases) {
+        for (const Solo &so : ph.solos) {
+            cudaError_t e = qmpm::launch_step_ctr(so.dim, so.material, so.quant, so.stats, nullptr, so.smem, b.n_sms,
+                                                  b.stream);
+            if (e != cudaSuccess) return bcuda(e, "batch member kernel setup");
+        }
         for (const Group &g : ph.groups) {
             cudaError_t e = qmpm::launch_step_multi(g.dim, g.material, g.quant, g.stats, nullptr, 0, g.smem, b.n_sms,
                                                     b.stream);
             if (e != cudaSuccess) return bcuda(e, "multi-scene kernel setup");
         }
+    }
     return QMPM_OK;
 }
 
@@ -284,7 +376,7 @@ int ensure_plan(qmpm_batch &b)
 {
     if (b.planned) return QMPM_OK;
     drop_graphs(b);
-    cudaError_t e = grow(&b.d_ctr, &b.ctr_cap, std::max<size_t>(b.members.size(), 1));
+    cudaError_t e = grow(&b.d_ctr, &b.ctr_cap, std::max<size_t>(b.members.size(), 64));
     if (e != cudaSuccess) return bfail(QMPM_ERR_OOM, "batch counters: device allocation failed");
     int rc = plan(b);
     if (rc != QMPM_OK) return rc;
@@ -381,10 +473,13 @@ int qmpm_batch_step(qmpm_batch_handle b, int32_t nsteps)
             const int r = qmpm_step(c, 0);  // P2G of a state uploaded since
             if (r != QMPM_OK) return r;
         }
+    b->fresh = false;
     int rc = ensure_plan(*b);
     if (rc != QMPM_OK) return rc;
     const int half = period(*b) / 2;
-    const bool graphs = (b->flags & QMPM_BATCH_GRAPHS) != 0;
+    // graphs pay off once replayed: a membership that just changed steps with direct
+    // launches, and is captured on a later call if it stays the same
+    const bool graphs = (b->flags & QMPM_BATCH_GRAPHS) != 0 && !b->fresh;
     while (nsteps > 0) {
         if (graphs && b->phase % half == 0 && nsteps >= half) {
             if (!b->graph[0]) {
@@ -395,6 +490,7 @@ int qmpm_batch_step(qmpm_batch_handle b, int32_t nsteps)
             cudaError_t e = cudaGraphLaunch(b->graph[h], b->stream);
             if (e != cudaSuccess) return bcuda(e, "graph launch");
             b->graph_launches += 1;
+            b->launches += b->graph_kernels[h];
             for (int k = h * half; k < (h + 1) * half; ++k) {
                 rc = run_phase(*b, k, true);
                 if (rc != QMPM_OK) return rc;
@@ -415,6 +511,7 @@ int qmpm_batch_info(qmpm_batch_handle b, qmpm_batch_info_t *out)
     std::memset(out, 0, sizeof(*out));
     out->n_members = (int32_t)b->members.size();
     out->n_classes = b->planned && !b->phases.empty() ? (int32_t)b->phases[0].groups.size() : 0;
+    out->n_solo = b->planned && !b->phases.empty() ? (int32_t)b->phases[0].solos.size() : 0;
     out->resort_every = b->S;
     out->steps = b->steps;
     out->kernel_launches = b->launches;
@@ -429,6 +526,12 @@ int qmpm_batch_destroy(qmpm_batch_handle b)
     while (!b->members.empty()) qmpm_batch_remove(b, b->members.back());
     cudaStreamSynchronize(b->stream);
     drop_graphs(*b);
+    for (auto &st : b->staging) {
+        if (st.uploaded) cudaEventDestroy(st.uploaded);
+        if (st.tab) cudaFreeHost(st.tab);
+        if (st.clr) cudaFreeHost(st.clr);
+        if (st.ctr) cudaFreeHost(st.ctr);
+    }
     if (b->d_tab) cudaFree(b->d_tab);
     if (b->d_clear) cudaFree(b->d_clear);
     if (b->d_ctr) cudaFree(b->d_ctr);

@@ -6,10 +6,11 @@
 // state.  The loop runs on a background thread (qmpm_engine_start) or in the caller's thread
 // (qmpm_engine_run).
 //
-// Streams: scenes are created and measured on the engine's init stream, stepped on the
-// batch stream; a new scene's upload, encode and sort overlap the running batch, and the
-// stream-ordered allocator frees finished scenes without synchronising the device.  At most
-// two iterations are in flight on the batch stream.
+// Threads and streams: admitted scenes are created (upload, encode, sort, P2G) by an init
+// thread, each on a stream of its own, while the loop thread keeps the batch stream busy;
+// they join the batch at the loop's next iteration.  Finished scenes are measured on their
+// own stream and freed by the stream-ordered allocator without synchronising the device.
+// At most two iterations are in flight on the batch stream.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -44,6 +45,7 @@ struct Request {
     int32_t error = 0;
     double z = 0;
     qmpm_handle h = nullptr;
+    cudaStream_t stream = nullptr;  // the scene's own stream (init, measurement, frees)
     cudaEvent_t done_ev = nullptr;
     double *h_z = nullptr;  // pinned
 };
@@ -53,14 +55,20 @@ struct Request {
 struct qmpm_engine {
     qmpm_engine_config_t cfg;
     int dev = 0;
-    cudaStream_t init_stream = nullptr, step_stream = nullptr;
+    cudaStream_t step_stream = nullptr;
     qmpm_batch_handle batch = nullptr;
     double *pinned = nullptr;  // one z slot per request id modulo kSlots
     static constexpr int kSlots = 4096;
 
-    std::mutex mu;  // guards queue, done, kept, next_id, counters read by the caller
-    std::condition_variable cv;
+    std::mutex mu;  // guards queue, to_init, ready, done, kept, next_id, reserved, counters
+    std::condition_variable cv, init_cv;
     std::deque<Request *> queue;
+    std::deque<Request *> to_init;   // admitted, waiting for the init thread
+    std::vector<Request *> ready;    // created, waiting to join the batch
+    int64_t reserved = 0;            // bytes of admitted scenes (peak until created, then resident)
+    int in_init = 0;                 // requests between admission and joining
+    std::thread init_worker;
+    bool init_stop = false;
     std::vector<Request *> done;
     std::map<int64_t, Request *> kept;
     int64_t next_id = 1;
@@ -69,7 +77,6 @@ struct qmpm_engine {
 
     // loop-thread state
     std::vector<Request *> active, finishing;
-    int64_t bytes_in_use = 0;
     int64_t particle_steps = 0, iterations = 0, n_done = 0;
     cudaEvent_t iter_ev[2] = {nullptr, nullptr};
     bool iter_pending[2] = {false, false};
@@ -95,9 +102,14 @@ void finish(qmpm_engine &e, Request *r, int32_t status)
     r->status = status;
     r->t_done = e.now();
     if (r->h) {
-        qmpm_destroy(r->h);
+        qmpm::destroy_nosync(r->h);  // frees ordered on the scene's stream, no wait
         r->h = nullptr;
-        e.bytes_in_use -= r->resident;
+        std::lock_guard<std::mutex> lk(e.mu);
+        e.reserved -= r->resident;
+    }
+    if (r->stream) {
+        cudaStreamDestroy(r->stream);  // released once its work is done
+        r->stream = nullptr;
     }
     if (r->done_ev) {
         cudaEventDestroy(r->done_ev);
@@ -144,40 +156,76 @@ void collect(qmpm_engine &e)
     }
 }
 
-// FIFO admission while the next request's peak footprint fits and a batch slot is free.
+// FIFO admission while the next request's peak footprint fits and a batch slot is free:
+// the request's bytes are reserved and it goes to the init thread.
 void admit(qmpm_engine &e)
 {
+    std::vector<Request *> too_big;
+    {
+        std::lock_guard<std::mutex> lk(e.mu);
+        while (!e.queue.empty()) {
+            Request *f = e.queue.front();
+            if (f->peak > e.cfg.budget_bytes) {  // can never fit
+                e.queue.pop_front();
+                f->error = QMPM_ERR_OOM;
+                too_big.push_back(f);
+                continue;
+            }
+            if ((int)e.active.size() + e.in_init >= e.cfg.max_active) break;
+            if (e.reserved + f->peak > e.cfg.budget_bytes) break;
+            e.queue.pop_front();
+            e.reserved += f->peak;
+            e.in_init += 1;
+            f->t_admit = e.now();
+            e.to_init.push_back(f);
+        }
+    }
+    e.init_cv.notify_one();
+    for (Request *r : too_big) finish(e, r, QMPM_REQ_FAILED);
+}
+
+// The init thread: create admitted scenes; the reservation drops from the peak footprint to
+// the resident one once the initial state is gone.
+void init_loop(qmpm_engine *e)
+{
+    cudaSetDevice(e->dev);
     for (;;) {
         Request *r = nullptr;
         {
-            std::lock_guard<std::mutex> lk(e.mu);
-            if (e.queue.empty()) return;
-            if ((int)e.active.size() >= e.cfg.max_active) return;
-            Request *f = e.queue.front();
-            if (e.bytes_in_use + f->peak > e.cfg.budget_bytes) {
-                if (f->peak > e.cfg.budget_bytes) {  // can never fit
-                    e.queue.pop_front();
-                    f->error = QMPM_ERR_OOM;
-                    r = f;
-                } else {
-                    return;
-                }
-            } else {
-                e.queue.pop_front();
-                r = f;
-            }
+            std::unique_lock<std::mutex> lk(e->mu);
+            e->init_cv.wait(lk, [e] { return e->init_stop || !e->to_init.empty(); });
+            if (e->to_init.empty()) return;
+            r = e->to_init.front();
+            e->to_init.pop_front();
         }
-        if (r->error) {
-            finish(e, r, QMPM_REQ_FAILED);
-            continue;
-        }
-        r->t_admit = e.now();
-        int rc = qmpm_init(&r->scene, r->has_scheme ? &r->scheme : nullptr, r->state.data(), e.init_stream, &r->h);
+        int rc = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess ? QMPM_OK
+                                                                                           : QMPM_ERR_CUDA;
+        if (rc == QMPM_OK)
+            rc = qmpm_init(&r->scene, r->has_scheme ? &r->scheme : nullptr, r->state.data(), r->stream, &r->h);
         std::vector<double>().swap(r->state);
-        if (rc == QMPM_OK) {
-            e.bytes_in_use += r->resident;
-            if (r->steps > 0) rc = qmpm_batch_add(e.batch, r->h);
+        std::lock_guard<std::mutex> lk(e->mu);
+        e->reserved -= r->peak - (rc == QMPM_OK ? r->resident : 0);
+        if (rc != QMPM_OK) {
+            r->h = nullptr;
+            r->error = rc;
         }
+        e->ready.push_back(r);
+        e->cv.notify_all();
+    }
+}
+
+// Created scenes join the batch (or, with nothing to step, go straight to measurement).
+void join_ready(qmpm_engine &e)
+{
+    std::vector<Request *> rd;
+    {
+        std::lock_guard<std::mutex> lk(e.mu);
+        rd.swap(e.ready);
+        e.in_init -= (int)rd.size();
+    }
+    for (Request *r : rd) {
+        int rc = r->error ? r->error : QMPM_OK;
+        if (rc == QMPM_OK && r->steps > 0) rc = qmpm_batch_add(e.batch, r->h);
         if (rc != QMPM_OK) {
             r->error = rc;
             finish(e, r, QMPM_REQ_FAILED);
@@ -185,7 +233,6 @@ void admit(qmpm_engine &e)
         }
         r->status = QMPM_REQ_RUNNING;
         if (r->steps == 0) {
-            // nothing to step: measure the initial state
             qmpm::launch_measure(*r->h);
             cudaMemcpyAsync(r->h_z, r->h->d_z, sizeof(double), cudaMemcpyDeviceToHost, r->h->stream);
             cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
@@ -203,6 +250,7 @@ int iterate(qmpm_engine &e)
 {
     collect(e);
     admit(e);
+    join_ready(e);
     if (e.active.empty()) return 0;
     int32_t L = e.cfg.resort_every > 0 ? e.cfg.resort_every : 8;
     for (Request *r : e.active) L = std::min(L, r->steps - r->done_steps);
@@ -245,7 +293,7 @@ int iterate(qmpm_engine &e)
     e.iterations += 1;
     std::lock_guard<std::mutex> lk(e.mu);
     e.snap_active = (int64_t)e.active.size();
-    e.snap_bytes = e.bytes_in_use;
+    e.snap_bytes = e.reserved;
     e.snap_particle_steps = e.particle_steps;
     e.snap_iterations = e.iterations;
     qmpm_batch_info_t bi;
@@ -260,7 +308,7 @@ int iterate(qmpm_engine &e)
 bool idle(qmpm_engine &e)
 {
     std::lock_guard<std::mutex> lk(e.mu);
-    return e.queue.empty() && e.active.empty() && e.finishing.empty();
+    return e.queue.empty() && e.in_init == 0 && e.active.empty() && e.finishing.empty();
 }
 
 void loop(qmpm_engine *e)
@@ -269,12 +317,10 @@ void loop(qmpm_engine *e)
     while (true) {
         if (e->stop_req.load() && (!e->drain.load() || idle(*e))) break;
         const int stepped = iterate(*e);
-        if (stepped == 0 && e->finishing.empty()) {
+        if (stepped == 0) {
             std::unique_lock<std::mutex> lk(e->mu);
-            e->cv.wait_for(lk, std::chrono::milliseconds(1),
-                           [e] { return !e->queue.empty() || e->stop_req.load(); });
-        } else if (stepped == 0) {
-            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            e->cv.wait_for(lk, std::chrono::microseconds(e->finishing.empty() ? 1000 : 50),
+                           [e] { return !e->queue.empty() || !e->ready.empty() || e->stop_req.load(); });
         }
     }
     collect(*e);
@@ -302,8 +348,7 @@ int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out)
         uint64_t keep = ~uint64_t(0);
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    cudaError_t ce = cudaStreamCreateWithFlags(&e->init_stream, cudaStreamNonBlocking);
-    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&e->step_stream, cudaStreamNonBlocking);
+    cudaError_t ce = cudaStreamCreateWithFlags(&e->step_stream, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->iter_ev[0], cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->iter_ev[1], cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaMallocHost(reinterpret_cast<void **>(&e->pinned), sizeof(double) * qmpm_engine::kSlots);
@@ -316,6 +361,7 @@ int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out)
         qmpm_engine_destroy(e);
         return rc;
     }
+    e->init_worker = std::thread(init_loop, e);
     *out = e;
     return QMPM_OK;
 }
@@ -454,15 +500,32 @@ int qmpm_engine_destroy(qmpm_engine_handle e)
 {
     if (!e) return QMPM_OK;
     qmpm_engine_stop(e, 0);
+    if (e->init_worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(e->mu);
+            e->init_stop = true;
+            for (Request *r : e->to_init) delete r;
+            e->to_init.clear();
+        }
+        e->init_cv.notify_all();
+        e->init_worker.join();
+    }
+    for (Request *r : e->ready) {
+        if (r->h) qmpm_destroy(r->h);
+        if (r->stream) cudaStreamDestroy(r->stream);
+        delete r;
+    }
+    e->ready.clear();
     if (e->step_stream) cudaStreamSynchronize(e->step_stream);
-    if (e->init_stream) cudaStreamSynchronize(e->init_stream);
     for (Request *r : e->active) {
         if (r->h) qmpm_destroy(r->h);
+        if (r->stream) cudaStreamDestroy(r->stream);
         delete r;
     }
     for (Request *r : e->finishing) {
         if (r->h) qmpm_destroy(r->h);
         if (r->done_ev) cudaEventDestroy(r->done_ev);
+        if (r->stream) cudaStreamDestroy(r->stream);
         delete r;
     }
     for (Request *r : e->queue) delete r;
@@ -472,7 +535,6 @@ int qmpm_engine_destroy(qmpm_engine_handle e)
     for (auto ev : e->iter_ev)
         if (ev) cudaEventDestroy(ev);
     if (e->pinned) cudaFreeHost(e->pinned);
-    if (e->init_stream) cudaStreamDestroy(e->init_stream);
     if (e->step_stream) cudaStreamDestroy(e->step_stream);
     delete e;
     return QMPM_OK;

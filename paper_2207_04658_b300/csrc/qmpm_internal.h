@@ -183,10 +183,19 @@ size_t step_smem_bytes(int dim, int W);
 cudaError_t launch_step_multi(int dim, int material, bool quant, bool stats, const StepParams *d_tab, int n,
                               size_t smem, int n_sms, cudaStream_t s);
 cudaError_t launch_clear_multi(const ClearItem *d_items, int n, int64_t virtual_blocks, int n_sms, cudaStream_t s);
+// one batch member in a launch of its own (p NULL: set the kernel's attributes only)
+cudaError_t launch_step_ctr(int dim, int material, bool quant, bool stats, const StepParams *p, size_t smem,
+                            int n_sms, cudaStream_t s);
 cudaError_t launch_advance(uint32_t *d_ctr, int n, cudaStream_t s);
 
 // batch.cu: a member's host-side state changed outside the batch (its tables are stale)
 void batch_invalidate(qmpm_batch *b);
+
+}  // namespace qmpm
+struct qmpm_ctx;
+namespace qmpm {
+// api.cu: free a handle with stream-ordered frees on its stream, without synchronising
+void destroy_nosync(qmpm_ctx *c);
 
 }  // namespace qmpm
 

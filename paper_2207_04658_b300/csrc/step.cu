@@ -480,6 +480,23 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>()) step
     if (STATS) flush_counters(cnt, P.stats);
 }
 
+// One scene of a batch stepped by its own launch (parameters in the constant bank, as the
+// step kernel), but with the dither step index from the member's device counter so that a
+// captured graph can be replayed.
+template <int DIM, int MAT, bool QUANT, bool STATS>
+__global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>())
+    step_kernel_ctr(const __grid_constant__ StepParams P)
+{
+    StepCounters cnt;
+    const int tid = threadIdx.x;
+    const int pj = spread(tid);
+    const uint32_t step = *P.step_ctr + 1u;
+    const uint32_t n_chunks = *P.n_chunks;
+    for (uint32_t ci = blockIdx.x; ci < n_chunks; ci += gridDim.x)
+        run_chunk<DIM, MAT, QUANT, STATS, true, true>(P, P.chunks[ci], step, cnt, tid, pj);
+    if (STATS) flush_counters(cnt, P.stats);
+}
+
 // Multi-scene launch: the work queue is the concatenation of the members' chunk lists
 // (member-major); each CTA strides over it, copying a member's parameters into shared
 // memory when its items move on to the next member.  The members share the template
@@ -868,6 +885,49 @@ cudaError_t launch_step_multi(int dim, int material, bool quant, bool stats, con
 #define QMPM_CASE(D, M, Q, S)                                                                      \
     case (D == 3 ? 100 : 0) + M * 10 + (Q ? 2 : 0) + (S ? 1 : 0):                                    \
         return launch_multi_t<D, M, Q, S>(d_tab, n, smem, n_sms, s);
+#define QMPM_CASES_DM(D, M) QMPM_CASE(D, M, false, false) QMPM_CASE(D, M, true, false) QMPM_CASE(D, M, true, true) \
+    QMPM_CASE(D, M, false, true)
+    switch (key) {
+        QMPM_CASES_DM(2, 0)
+        QMPM_CASES_DM(2, 1)
+        QMPM_CASES_DM(2, 2)
+        QMPM_CASES_DM(3, 0)
+        QMPM_CASES_DM(3, 1)
+        QMPM_CASES_DM(3, 2)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef QMPM_CASES_DM
+#undef QMPM_CASE
+}
+
+template <int DIM, int MAT, bool QUANT, bool STATS>
+static cudaError_t launch_ctr_t(const StepParams *p, size_t smem, int n_sms, cudaStream_t s)
+{
+    auto kern = step_kernel_ctr<DIM, MAT, QUANT, STATS>;
+    static size_t cached_smem = 0;
+    static int cached_per_sm = 0;
+    if (cached_smem != smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        cached_per_sm = per_sm > 0 ? per_sm : 1;
+        cached_smem = smem;
+    }
+    if (!p) return cudaSuccess;  // attributes only (before a stream capture)
+    kern<<<n_sms * cached_per_sm, kThreads, smem, s>>>(*p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_ctr(int dim, int material, bool quant, bool stats, const StepParams *p, size_t smem,
+                            int n_sms, cudaStream_t s)
+{
+    const int key = (dim == 3 ? 100 : 0) + material * 10 + (quant ? 2 : 0) + (stats ? 1 : 0);
+#define QMPM_CASE(D, M, Q, S)                                                                      \
+    case (D == 3 ? 100 : 0) + M * 10 + (Q ? 2 : 0) + (S ? 1 : 0):                                    \
+        return launch_ctr_t<D, M, Q, S>(p, smem, n_sms, s);
 #define QMPM_CASES_DM(D, M) QMPM_CASE(D, M, false, false) QMPM_CASE(D, M, true, false) QMPM_CASE(D, M, true, true) \
     QMPM_CASE(D, M, false, true)
     switch (key) {

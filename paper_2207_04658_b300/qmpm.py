@@ -100,7 +100,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 class qmpm_batch_info_t(ct.Structure):
     _fields_ = [("n_members", ct.c_int32), ("n_classes", ct.c_int32), ("resort_every", ct.c_int32),
-                ("pad", ct.c_int32), ("particles", ct.c_int64), ("steps", ct.c_int64),
+                ("n_solo", ct.c_int32), ("particles", ct.c_int64), ("steps", ct.c_int64),
                 ("kernel_launches", ct.c_int64), ("graph_launches", ct.c_int64)]
 
     def as_dict(self):
@@ -529,15 +529,24 @@ def sensitivities(scene, state0, T, ckpt_every=32, measure=MEASURE_MEAN_SQ_POS):
 
 
 def solve_scheme(info, eps, mode="error", rounding="paper", kappa=2.0, containers=(0, 0, 0, 0),
-                 material="corotated"):
+                 material="corotated", max_bits=24):
     """Scheme from the adjoint's sensitivities (Eq. 10 / Algorithm 1, or the memory-bound
-    form): returns the per-field scheme dict consumed by Scene and the solve report."""
+    form): returns the per-field scheme dict consumed by Scene and the solve report.  A
+    field the solve gives more than max_bits (the FP32 compute limit) keeps its window at
+    max_bits, one power of two coarser per bit dropped; the report lists such fields in
+    "capped" (their share of the error bound is then not met)."""
     res = qmpm_scheme_solve(info["P"], info["g"], info["lo"], info["hi"], info["z"], eps, mode=mode,
                             rounding=rounding, kappa=kappa)
     names = ["x", "v", "C", "J" if material == "fluid" else "F"]
-    scheme = {names[h]: dict(bits=int(res["bits"][h]), frac=int(res["frac"][h]),
-                             offset=int(res["offset"][h]), container=int(containers[h]))
-              for h in range(4)}
+    scheme, capped = {}, []
+    for h in range(4):
+        bits, frac, off = int(res["bits"][h]), int(res["frac"][h]), int(res["offset"][h])
+        if bits > max_bits:
+            drop = bits - max_bits
+            bits, frac, off = max_bits, frac - drop, off >> drop
+            capped.append(names[h])
+        scheme[names[h]] = dict(bits=bits, frac=frac, offset=off, container=int(containers[h]))
+    res["capped"] = capped
     return scheme, res
 
 

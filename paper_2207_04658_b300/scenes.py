@@ -160,3 +160,73 @@ def fixed_scheme_3d(material, x_bits=21, v=(16, -8.0, 8.0), C=(16, -512.0, 512.0
     else:
         sch["F"] = field(*F)
     return sch
+
+
+# ---------------------------------------------------------------------------- serving
+SERVING_CLASSES = [(2, "neohookean"), (2, "fluid"), (3, "corotated"), (3, "fluid")]
+SERVING_GRIDS = {2: (7, 8, 9, 10), 3: (6, 7, 8)}
+SERVING_EPS = (0.1, 0.01)
+SERVING_STEPS = 200
+
+
+def _wave_speed(dim, material, E, nu, rho, bulk):
+    if material == "fluid":
+        return math.sqrt(bulk / rho)
+    return math.sqrt(E * (1 - nu) / ((1 + nu) * (1 - 2 * nu)) / rho)
+
+
+def serving_scene(dim, material, n_particles, grid_log2, seed, steps=SERVING_STEPS):
+    """One serving request's scene: an elastic body (2D neo-Hookean E 1e3, nu 0.2, rho 1;
+    3D fixed-corotated E 5e3, nu 0.3, rho 4) thrown downward at 1 m/s from the middle of
+    the domain, or a fluid column (K 400, rho 1) at the low corner (a dam break).  About
+    n_particles jittered particles (k^d strata, k = round(n^(1/d))) in a box of n / ppc
+    cells, ppc = 4 (2D) or 8 (3D), capped at 60 % of the domain per axis (denser then);
+    dt = 0.3 dx / (wave speed + 1 m/s), at most 1e-4."""
+    n = 1 << grid_log2
+    dx = 1.0 / n
+    ppc = 4 if dim == 2 else 8
+    k = max(2, int(round(n_particles ** (1.0 / dim))))
+    side_cells = min(0.6 * n, (k ** dim / ppc) ** (1.0 / dim))
+    side = side_cells * dx
+    gen = rng(seed)
+    fluid = material == "fluid"
+    if fluid:
+        lo = np.full(dim, 3.0 * dx)
+    else:
+        lo = np.full(dim, 0.5 - side / 2)
+        lo[1] = min(0.55, 1.0 - 8 * dx - side)  # the top stays clear of the wall band
+    x = jitter_box(gen, lo, np.full(dim, side), (k,) * dim)
+    E, nu, rho, bulk = (0.0, 0.0, 1.0, 400.0) if fluid else ((1e3, 0.2, 1.0, 0.0) if dim == 2 else (5e3, 0.3, 4.0, 0.0))
+    c = _wave_speed(dim, material, E, nu, rho, bulk)
+    dt = min(1e-4, 0.3 * dx / (c + 1.0))
+    s0 = initial_state(dim, material, x)
+    if not fluid:
+        s0[:, dim + 1] = -1.0
+    scene = dict(name=f"serve{dim}d_{material}", dim=dim, material=material, grid_log2=grid_log2, bound=3,
+                 dt=dt, E=E, nu=nu, bulk=bulk, rho=rho, p_vol=side ** dim / x.shape[0],
+                 gravity=(0.0, -9.8, 0.0), seed=seed, dither=True, steps=steps, resort_every=8)
+    return scene, s0
+
+
+def serving_requests(rate=20.0, duration=15.0, seed=5, n_min=1e4, n_max=4e6):
+    """Poisson arrivals (rate per second over `duration` seconds) of requests: a class
+    (2D/3D x elastic/fluid, uniform), a particle count log-uniform in [n_min, n_max], a
+    grid uniform over the class's resolutions (raised to the first one whose 60 % box holds
+    the particles at no more than 32 per cell), an error bound from {0.1, 0.01} and 200
+    steps.  Returns a list of dicts (t, dim, material, n, grid_log2, eps, seed)."""
+    gen = rng(seed)
+    t = 0.0
+    out = []
+    while True:
+        t += float(gen.exponential(1.0 / rate))
+        if t > duration:
+            return out
+        dim, material = SERVING_CLASSES[int(gen.integers(0, len(SERVING_CLASSES)))]
+        n = int(round(math.exp(gen.uniform(math.log(n_min), math.log(n_max)))))
+        grids = SERVING_GRIDS[dim]
+        gi = int(gen.integers(0, len(grids)))
+        while gi + 1 < len(grids) and n > 32 * (0.6 * (1 << grids[gi])) ** dim:
+            gi += 1
+        eps = SERVING_EPS[int(gen.integers(0, len(SERVING_EPS)))]
+        out.append(dict(t=t, dim=dim, material=material, n=n, grid_log2=grids[gi], eps=eps,
+                        seed=int(gen.integers(1, 2 ** 31))))

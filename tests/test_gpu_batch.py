@@ -47,6 +47,13 @@ def mixed_scenes():
     return out
 
 
+def large_scene():
+    """A member large enough for a launch of its own (314,432 particles, 1,229 chunks)."""
+    from paper_2207_04658_b300 import scenes
+    sc, s0 = scenes.cubes3d_scene(n_cubes=1, cube_cells=34, grid_log2=7, seed=9, steps=100)
+    return sc, s0, scenes.fixed_scheme_3d("corotated")
+
+
 def quanta(scheme, dim, material, n_comp):
     from paper_2207_04658_b300 import scenes
     if scheme is None:
@@ -114,17 +121,19 @@ def alone(q, spec, steps):
 
 @pytest.mark.parametrize("graphs", [False, True])
 def test_batch_matches_scenes_stepped_alone(q, graphs):
-    specs = mixed_scenes()
-    T = 20  # two graph halves and a direct remainder with resort_every = 8
+    specs = mixed_scenes() + [large_scene()]
+    T = 28
     refs = [alone(q, spec, T) for spec in specs]
     members = [q.Scene(sc, sch, s0) for sc, s0, sch in specs]
     b = q.Batch(resort_every=8, graphs=graphs)
     for m in members:
         b.add(m)
-    b.step(T)
+    b.step(8)   # a new membership runs direct launches
+    b.step(20)  # then two graph replays of a half period (8 steps) and 4 direct steps
     info = b.info()
     assert info["n_members"] == len(specs) and info["steps"] == T
-    assert info["n_classes"] == 4  # the two 3D quantized corotated scenes share one launch
+    assert info["n_classes"] == 4  # the two small 3D quantized corotated scenes share one launch
+    assert info["n_solo"] == 1     # the large one has its own
     assert info["graph_launches"] == (2 if graphs else 0)
     for m, (sc, s0, sch), (r1, r2) in zip(members, specs, refs):
         assert_close(m.state_by_id(), r1, sch, sc, r2, T)
@@ -205,7 +214,9 @@ def run_engine(q, reqs, budget=8 * 2 ** 30, max_active=8, stagger=0):
             e.run(1)
     recs = {}
     peak_bytes = 0
-    for _ in range(100000):
+    import time
+    t_end = time.time() + 300
+    while time.time() < t_end:
         busy = e.run(1)
         peak_bytes = max(peak_bytes, e.stats()["bytes_in_use"])
         for r in e.poll():
