@@ -232,7 +232,7 @@ def accuracy(qmpm, sc, s0, sch):
             "reference": "FP32 run of the same kernels (the FP64 oracle is too slow at this size)"}
 
 
-def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64):
+def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
     """The serving workload: Poisson arrivals of scenes (2D/3D x elastic/fluid, particle
     counts log-uniform in [1e4, 4e6], grids 64^3..256^3 or 128^2..1024^2, schemes solved at
     eps 0.1 or 0.01, 200 steps) submitted to the engine at their arrival times; rollout
@@ -243,7 +243,10 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64):
     t_solve = time.perf_counter()
     schemes = autoquant.serving_schemes()
     t_solve = time.perf_counter() - t_solve
+    from paper_2207_04658_b300.replicas import shard
     reqs = scenes.serving_requests(rate=rate, duration=duration, seed=5)
+    if dc is not None and dc.world > 1:
+        reqs = shard(reqs, dc.rank, dc.world)  # replicas: each GPU serves every world-th request
     eng = qmpm.Engine(budget_bytes=int(budget_gb * 2 ** 30), resort_every=8, max_active=max_active)
     # a producer thread draws the scenes ahead of their arrival times (bounded look-ahead)
     ready = queue.Queue(maxsize=16)
@@ -279,7 +282,16 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64):
     done = [r for r in recs if r["status"] == qmpm.REQ_DONE]
     lat = np.array([r["t_done"] - r["t_submit"] for r in done]) * 1e3
     span = max(r["t_done"] for r in done) - min(r["t_submit"] for r in done) if done else float("nan")
-    return {"requests": submitted, "done": len(done), "failed": len(recs) - len(done),
+    if dc is not None and dc.world > 1:
+        import torch
+        # whole job: particle-steps of all ranks over the longest rank's span; the worst p99
+        ps = dc.sum(torch, st["particle_steps"])
+        span = dc.max(torch, span)
+        st["particle_steps"] = ps
+        p99_all = dc.max(torch, float(np.percentile(lat, 99)) if len(lat) else 0.0)
+    else:
+        p99_all = float(np.percentile(lat, 99)) if len(lat) else None
+    return {"p99_ms_all_ranks": round(p99_all, 2) if p99_all is not None else None,"requests": submitted, "done": len(done), "failed": len(recs) - len(done),
             "arrival_rate_per_s": rate, "duration_s": duration,
             "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
             "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None,
@@ -319,31 +331,9 @@ def cpu_baseline(name, sample_steps=2):
             "sample": sample}
 
 
-class DistCtx:
-    def __init__(self):
-        self.world = int(os.environ.get("WORLD_SIZE", "1"))
-        self.rank = int(os.environ.get("RANK", "0"))
-        self.local = int(os.environ.get("LOCAL_RANK", "0"))
-        self.dist = None
-        if self.world > 1:
-            import torch.distributed as dist
-            self.dist = dist
-
-    def init(self, torch):
-        if self.dist is not None:
-            torch.cuda.set_device(self.local)
-            self.dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
-
-    def barrier(self):
-        if self.dist is not None:
-            self.dist.barrier()
-
-    def max(self, torch, v):
-        if self.dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return float(t.item())
+def DistCtx():
+    from paper_2207_04658_b300.replicas import Replicas
+    return Replicas()
 
 
 def run_ours(args):
@@ -381,7 +371,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms_max = dc.max(torch, ms)
     W = g.n_words
-    value = dc.world * N * args.steps / (ms_max / 1e3)
+    from paper_2207_04658_b300.replicas import job_throughput
+    value = job_throughput(N * args.steps, dc.world, ms_max / 1e3)
 
     # dominant kernel: the fused step kernel
     step_avg_ms = prof["step_ms"] / max(1, prof["step_launches"])
@@ -446,13 +437,12 @@ def run_ours(args):
     if not args.no_accuracy and dc.rank == 0:
         line["accuracy"] = accuracy(qmpm, sc, s0, sch)
     if args.serving_duration > 0:
-        line["serving"] = serving(qmpm, args.serving_duration)
+        line["serving"] = serving(qmpm, args.serving_duration, dc=dc)
     if dc.rank == 0 and dc.world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if dc.rank == 0:
         print(json.dumps(line), flush=True)
-    if dc.dist is not None:
-        dc.dist.destroy_process_group()
+    dc.close()
 
 
 def run_reference(args):

@@ -229,19 +229,43 @@ typedef struct {
     double lo[4];      /* smallest value of each field over the states t = 0..T */
     double hi[4];      /* largest value (Algorithm 1's range update) */
     int64_t P[4];      /* variables per field: N times the field's components */
+    int64_t forward_steps; /* forward steps run, the first pass and the recomputation */
+    int32_t state_buffers; /* FP32 states held at once (checkpoints and recomputed ones) */
+    int32_t pad;
 } qmpm_adjoint_out_t;
+
+#define QMPM_CKPT_BISECTION 0 /* ckpt_every value: bisection checkpoints (Sec. 6) */
+
+/* The bisection schedule of qmpm_adjoint over T steps (Sec. 6, Fig. 7): the states
+ * s_0..s_T are the leaves of a binary tree whose inner nodes are checkpoints at the first
+ * leaf of their subtree; reversing step t needs s_t, recomputed from the nearest checkpoint
+ * on the path from the root, which places new checkpoints halfway on the way.  Op kinds:
+ *   QMPM_OP_ADVANCE: slot `to` := F^(t1 - t0)(state in slot `from`, which holds s_t0);
+ *   QMPM_OP_REVERSE: dz/ds_t0 = G(state s_t0 in slot `from`, dz/ds_(t0 + 1)).
+ * Writes up to max_ops ops to ops (may be NULL to count), the op count to *n_ops, and the
+ * number of state slots used to *n_slots (floor(log2 T) + 1 for T >= 1).  Host only.
+ * Errors: QMPM_ERR_INVALID_ARG (T < 0, or more ops than max_ops). */
+enum { QMPM_OP_ADVANCE = 0, QMPM_OP_REVERSE = 1 };
+typedef struct {
+    int32_t kind;
+    int32_t from, to;
+    int32_t t0, t1;
+} qmpm_rev_op_t;
+int qmpm_bisection_schedule(int32_t T, qmpm_rev_op_t *ops, int64_t max_ops, int64_t *n_ops, int32_t *n_slots);
 
 /* Reverse mode over T steps from the handle's current state, in FP32 (the state is decoded
  * first if the handle is quantized; gradients are taken in full precision as in the
  * paper's workflow).  The call runs its own forward (particle order fixed, no re-sort),
  * keeps a checkpoint every ckpt_every steps and recomputes each segment from its
  * checkpoint while reversing it (adjoint kernel G of Eq. 13), and accumulates the squared
- * sensitivities g_h of Eq. 8, which qmpm_scheme_solve takes.  The handle's own state is
- * not advanced.
+ * sensitivities g_h of Eq. 8, which qmpm_scheme_solve takes.  ckpt_every =
+ * QMPM_CKPT_BISECTION follows qmpm_bisection_schedule instead: O(log T) states held,
+ * about (T/2) log2 T forward steps recomputed.  The handle's own state is not advanced.
  *   measure:  QMPM_MEASURE_MEAN_SQ_POS, QMPM_MEASURE_KINETIC_ENERGY or QMPM_MEASURE_USER
  *             (then d_seed = dz/ds_T, device, [N][n_comp] in the handle's slot order);
  *   d_grad0:  optional output dz/ds_0, device, [N][n_comp], slot order.
- * Allocates O((T/ckpt_every + ckpt_every) N n_comp) floats of device memory for the call.
+ * Allocates O((T/ckpt_every + ckpt_every) N n_comp) floats (bisection: O(log T N n_comp))
+ * of device memory for the call.
  * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_OOM, QMPM_ERR_CUDA. */
 int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_t measure, const float *d_seed,
                  float *d_grad0, qmpm_adjoint_out_t *out);

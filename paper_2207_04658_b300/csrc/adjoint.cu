@@ -699,15 +699,51 @@ void pick(int dim, int mat, ForwardFn &f, ReverseFn &r)
     r = nullptr;
 }
 
+// The bisection schedule: slot d holds s_lo; reverse steps hi-1 .. lo.
+void bisect(int32_t lo, int32_t hi, int32_t d, std::vector<qmpm_rev_op_t> &ops, int32_t &slots)
+{
+    slots = std::max(slots, d + 1);
+    if (hi - lo == 1) {
+        ops.push_back({QMPM_OP_REVERSE, d, d, lo, hi});
+        return;
+    }
+    const int32_t mid = lo + (hi - lo + 1) / 2;  // the later half is the shorter one
+    ops.push_back({QMPM_OP_ADVANCE, d, d + 1, lo, mid});
+    bisect(mid, hi, d + 1, ops, slots);
+    bisect(lo, mid, d, ops, slots);
+}
+
 }  // namespace
 
 }  // namespace qmpm
+
+extern "C" int qmpm_bisection_schedule(int32_t T, qmpm_rev_op_t *ops, int64_t max_ops, int64_t *n_ops,
+                                       int32_t *n_slots)
+{
+    if (T < 0) {
+        qmpm::set_last_error("qmpm_bisection_schedule: T < 0");
+        return QMPM_ERR_INVALID_ARG;
+    }
+    std::vector<qmpm_rev_op_t> v;
+    int32_t slots = 1;
+    if (T > 0) qmpm::bisect(0, T, 0, v, slots);
+    if (n_ops) *n_ops = (int64_t)v.size();
+    if (n_slots) *n_slots = slots;
+    if (ops) {
+        if ((int64_t)v.size() > max_ops) {
+            qmpm::set_last_error("qmpm_bisection_schedule: more ops than max_ops");
+            return QMPM_ERR_INVALID_ARG;
+        }
+        std::copy(v.begin(), v.end(), ops);
+    }
+    return QMPM_OK;
+}
 
 extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_t measure, const float *d_seed,
                             float *d_grad0, qmpm_adjoint_out_t *out)
 {
     using namespace qmpm;
-    if (!h || T < 0 || ckpt_every < 1 ||
+    if (!h || T < 0 || ckpt_every < 0 ||
         (measure != QMPM_MEASURE_MEAN_SQ_POS && measure != QMPM_MEASURE_USER &&
          measure != QMPM_MEASURE_KINETIC_ENERGY) ||
         (measure == QMPM_MEASURE_USER && !d_seed && h->N > 0)) {
@@ -723,8 +759,16 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
     StepParams P;
     fill_params(c, P);
     const int64_t nn = dim == 2 ? (int64_t)c.n * c.n : (int64_t)c.n * c.n * c.n;
-    const int k = std::min<int32_t>(ckpt_every, std::max<int32_t>(T, 1));
-    const int64_t n_ckpt = T / k + 1;
+    const bool bisection = ckpt_every == QMPM_CKPT_BISECTION;
+    std::vector<qmpm_rev_op_t> sched;
+    int32_t n_slots = 1;
+    if (bisection && T > 0) bisect(0, T, 0, sched, n_slots);
+    const int k = bisection ? 1 : std::min<int32_t>(ckpt_every, std::max<int32_t>(T, 1));
+    // uniform: checkpoints every k steps plus a tape of one segment; bisection: one slot
+    // per tree level plus a scratch state for the recomputation
+    const int64_t n_ckpt = bisection ? n_slots : T / k + 1;
+    const int64_t tape_states = bisection ? 2 : k + 1;
+    int64_t fwd_steps = 0;
     const size_t state_bytes = sizeof(float) * (size_t)std::max<int64_t>(N, 1) * nc;
     cudaStream_t st = c.stream;
 
@@ -739,7 +783,7 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
         for (void *p : allocs) cudaFree(p);
     };
     float *ckpt = static_cast<float *>(alloc(state_bytes * (size_t)n_ckpt));
-    float *tape = static_cast<float *>(alloc(state_bytes * (size_t)(k + 1)));
+    float *tape = static_cast<float *>(alloc(state_bytes * (size_t)tape_states));
     float *sbA = static_cast<float *>(alloc(state_bytes));
     float *sbB = static_cast<float *>(alloc(state_bytes));
     float *gm = static_cast<float *>(alloc(sizeof(float) * (size_t)nn));
@@ -778,9 +822,10 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
     if (e == cudaSuccess) reduce(cur, 0, 1, 0);
     for (int t = 0; t < T && e == cudaSuccess; ++t) {
         e = fwd(P, cur, nxt, N, gm, gv, nn, st);
+        fwd_steps += 1;
         std::swap(cur, nxt);
         if (e == cudaSuccess) reduce(cur, 0, 1, 0);
-        if (e == cudaSuccess && (t + 1) % k == 0 && (t + 1) / k < n_ckpt)
+        if (e == cudaSuccess && !bisection && (t + 1) % k == 0 && (t + 1) / k < n_ckpt)
             e = cudaMemcpyAsync(ckpt + (size_t)((t + 1) / k) * NE, cur, state_bytes, cudaMemcpyDeviceToDevice, st);
     }
     // seed dz/ds_T
@@ -794,13 +839,40 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
     }
     if (e == cudaSuccess) reduce(cur, 0, 0, measure == QMPM_MEASURE_KINETIC_ENERGY ? 2 : 1);  // z of s_T
     if (e == cudaSuccess) reduce(sbA, 1, 0, 0);  // t = T term of Eq. 8
-    // backward over segments [t0, t1)
     float *sbn = sbA, *sb = sbB;
-    for (int64_t seg = (T > 0 ? (T - 1) / k : -1); seg >= 0 && e == cudaSuccess; --seg) {
+    if (bisection) {
+        // slot j of the schedule is checkpoint buffer j (slot 0 holds s_0); the recomputation
+        // ping-pongs between its target slot and the scratch state `tape`
+        for (size_t i = 0; i < sched.size() && e == cudaSuccess; ++i) {
+            const qmpm_rev_op_t &op = sched[i];
+            float *from = ckpt + (size_t)op.from * NE;
+            if (op.kind == QMPM_OP_ADVANCE) {
+                float *to = ckpt + (size_t)op.to * NE;
+                const int n_adv = op.t1 - op.t0;
+                // land on `to` after n_adv steps: start on the buffer of the right parity
+                float *a = (n_adv % 2 == 1) ? to : tape, *b2 = (n_adv % 2 == 1) ? tape : to;
+                const float *src = from;
+                for (int j = 0; j < n_adv && e == cudaSuccess; ++j) {
+                    float *dst = (j % 2 == 0) ? a : b2;
+                    e = fwd(P, src, dst, N, gm, gv, nn, st);
+                    fwd_steps += 1;
+                    src = dst;
+                }
+            } else {
+                e = rev(P, from, sbn, sb, N, gm, gv, gb, nn, st);
+                if (e == cudaSuccess) reduce(sb, 1, 0, 0);
+                std::swap(sbn, sb);
+            }
+        }
+    }
+    // backward over segments [t0, t1)
+    for (int64_t seg = (!bisection && T > 0 ? (T - 1) / k : -1); seg >= 0 && e == cudaSuccess; --seg) {
         const int t0 = (int)(seg * k), t1 = std::min<int>(T, (int)(seg + 1) * k);
         if (N > 0) e = cudaMemcpyAsync(tape, ckpt + (size_t)seg * NE, state_bytes, cudaMemcpyDeviceToDevice, st);
-        for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t)
+        for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t) {
             e = fwd(P, tape + (size_t)(t - t0) * NE, tape + (size_t)(t - t0 + 1) * NE, N, gm, gv, nn, st);
+            fwd_steps += 1;
+        }
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
             e = rev(P, tape + (size_t)(t - t0) * NE, sbn, sb, N, gm, gv, gb, nn, st);
             if (e == cudaSuccess) reduce(sb, 1, 0, 0);
@@ -829,6 +901,8 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
         }
         const int per[4] = {dim, dim, dim * dim, nc - 2 * dim - dim * dim};
         for (int q = 0; q < 4; ++q) out->P[q] = N * per[q];
+        out->forward_steps = fwd_steps;
+        out->state_buffers = (int32_t)(n_ckpt + tape_states);
     }
     return QMPM_OK;
 }

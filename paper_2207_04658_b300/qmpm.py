@@ -86,11 +86,22 @@ class qmpm_solve_out_t(ct.Structure):
 
 class qmpm_adjoint_out_t(ct.Structure):
     _fields_ = [("z", ct.c_double), ("g", ct.c_double * 4), ("lo", ct.c_double * 4),
-                ("hi", ct.c_double * 4), ("P", ct.c_int64 * 4)]
+                ("hi", ct.c_double * 4), ("P", ct.c_int64 * 4), ("forward_steps", ct.c_int64),
+                ("state_buffers", ct.c_int32), ("pad", ct.c_int32)]
 
     def as_dict(self):
         return {"z": self.z, "g": list(self.g), "lo": list(self.lo), "hi": list(self.hi),
-                "P": list(self.P)}
+                "P": list(self.P), "forward_steps": self.forward_steps,
+                "state_buffers": self.state_buffers}
+
+
+class qmpm_rev_op_t(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("from_", ct.c_int32), ("to", ct.c_int32), ("t0", ct.c_int32),
+                ("t1", ct.c_int32)]
+
+
+CKPT_BISECTION = 0
+OP_ADVANCE, OP_REVERSE = 0, 1
 
 
 MEASURE_MEAN_SQ_POS, MEASURE_USER, MEASURE_KINETIC_ENERGY = 0, 1, 2
@@ -166,6 +177,8 @@ _SIGNATURES = [
     ("qmpm_adjoint", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
                                 ct.c_void_p, _P(qmpm_adjoint_out_t)]),
     ("qmpm_footprint", ct.c_int, [_P(qmpm_scene_t), _P(qmpm_scheme_t), _P(ct.c_int64), _P(ct.c_int64)]),
+    ("qmpm_bisection_schedule", ct.c_int, [ct.c_int32, _P(qmpm_rev_op_t), ct.c_int64, _P(ct.c_int64),
+                                           _P(ct.c_int32)]),
     ("qmpm_batch_create", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, _P(ct.c_void_p)]),
     ("qmpm_batch_add", ct.c_int, [ct.c_void_p, ct.c_void_p]),
     ("qmpm_batch_remove", ct.c_int, [ct.c_void_p, ct.c_void_p]),
@@ -378,6 +391,15 @@ def qmpm_footprint(scene_struct, scheme_struct):
     r, p = ct.c_int64(), ct.c_int64()
     _check(lib().qmpm_footprint(ct.byref(scene_struct), ct.byref(scheme_struct), ct.byref(r), ct.byref(p)))
     return r.value, p.value
+
+
+def qmpm_bisection_schedule(T):
+    """The bisection reverse schedule over T steps: (ops as (kind, from, to, t0, t1), slots)."""
+    n, slots = ct.c_int64(), ct.c_int32()
+    _check(lib().qmpm_bisection_schedule(int(T), None, 0, ct.byref(n), ct.byref(slots)))
+    buf = (qmpm_rev_op_t * max(1, n.value))()
+    _check(lib().qmpm_bisection_schedule(int(T), buf, n.value, ct.byref(n), ct.byref(slots)))
+    return [(o.kind, o.from_, o.to, o.t0, o.t1) for o in buf[:n.value]], slots.value
 
 
 def qmpm_autotune(scene_struct, scheme_struct, h_state, trial_steps=32, use_cache=True):

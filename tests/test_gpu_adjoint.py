@@ -152,6 +152,22 @@ def test_checkpoint_interval_does_not_change_the_gradient(q):
         assert np.allclose(info["g"], info_ref["g"], rtol=1e-3)
 
 
+@pytest.mark.parametrize("T", [16, 37])
+def test_bisection_checkpointing_gives_the_same_gradient(q, T):
+    # Sec. 6: checkpoints on the bisection tree instead of uniform segments; O(log T)
+    # states held, the gradient unchanged (only FP32 atomic order differs)
+    import math
+    sc, s0 = small(3, "corotated", N_side=8, seed=4)
+    ref, info_ref = device_grad0(q, sc, s0, T, T)
+    got, info = device_grad0(q, sc, s0, T, q.CKPT_BISECTION)
+    close_by_field(got, ref, 3, rel=1e-3)
+    assert np.allclose(info["g"], info_ref["g"], rtol=1e-3)
+    depth = int(math.floor(math.log2(T)))
+    assert info["state_buffers"] == (depth + 1) + 2  # tree slots, the first-pass pair (one is scratch)
+    assert T < info["forward_steps"] <= T + math.ceil(T / 2) * (depth + 1)
+    assert info_ref["forward_steps"] == 2 * T - 1  # uniform, one segment: forward + recompute
+
+
 def test_rollout_autograd_function(q):
     import torch
     sc, s0 = small(2, "neohookean", N_side=16, seed=2)

@@ -1,0 +1,110 @@
+"""Host-only logic of the library, on the CPU: the bisection reverse schedule (Sec. 6), the
+device footprint used for admission, the serving workload generator and the scheme capping.
+No GPU: only pure-host entry points are called."""
+import math
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2207_04658_b300 import build, qmpm
+    build.build()
+    qmpm.lib()
+    return qmpm
+
+
+def simulate(ops, T):
+    """Run a schedule on symbolic states (a slot holds the index t of the state in it) and
+    check every op's preconditions: an advance starts from the state it claims, a reverse
+    finds s_t and dz/ds_(t+1).  Returns (forward steps, slots used)."""
+    slots = {0: 0}
+    lam = T  # dz/ds_lam is known
+    fwd = 0
+    for kind, frm, to, t0, t1 in ops:
+        assert slots.get(frm) == t0, (kind, frm, to, t0, t1, slots)
+        if kind == 0:
+            assert t1 > t0 and to != frm
+            slots[to] = t1
+            fwd += t1 - t0
+        else:
+            assert kind == 1 and t1 == t0 + 1 and lam == t1
+            lam = t0
+    assert lam == 0
+    return fwd, max(slots) + 1
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 5, 7, 8, 31, 32, 33, 100, 256, 1000, 4097])
+def test_bisection_schedule_reverses_every_step_in_log_memory(q, T):
+    ops, n_slots = q.qmpm_bisection_schedule(T)
+    fwd, used = simulate(ops, T)
+    assert used == n_slots
+    depth = int(math.floor(math.log2(T)))
+    assert n_slots == depth + 1  # O(log T) states: one per tree level
+    assert sum(1 for o in ops if o[0] == 1) == T
+    # each level of the tree recomputes at most the states of its half intervals
+    assert fwd <= math.ceil(T / 2) * (depth + 1) + T
+
+
+def test_bisection_matches_the_paper_illustration(q):
+    # Fig. 7's tree over s_0..s_4 reversed: checkpoints halve the distance to the state
+    # being recovered; s_3 comes from s_2, a checkpoint made halfway from s_0 to s_4
+    ops, slots = q.qmpm_bisection_schedule(4)
+    assert ops[0] == (0, 0, 1, 0, 2)  # s_2 from s_0
+    assert ops[1] == (0, 1, 2, 2, 3)  # s_3 from s_2
+    assert ops[2] == (1, 2, 2, 3, 4)  # reverse step 3
+    assert ops[3] == (1, 1, 1, 2, 3)  # reverse step 2 from the s_2 checkpoint
+    assert slots == 3
+
+
+def test_footprint_counts_the_buffers(q):
+    from paper_2207_04658_b300 import scenes
+    sc, s0 = scenes.cubes3d_scene(n_cubes=2, cube_cells=16, grid_log2=7)
+    N = s0.shape[0]
+    ss = q.make_scene_struct(sc, N)
+    r32, p32 = q.qmpm_footprint(ss, q.make_scheme_struct(None))
+    rq, pq = q.qmpm_footprint(ss, q.make_scheme_struct(scenes.fixed_scheme_3d("corotated"), 3, "corotated"))
+    ld = (N + 31) // 32 * 32
+    assert r32 - rq == 2 * 4 * ld * (24 - 13)  # word planes: 24 FP32 words vs 13 packed
+    assert p32 - r32 == 8 * N * 24 and pq - rq == 8 * N * 24  # the FP64 initial state
+    nb = 128 // 4 + 2
+    assert r32 > 2 * nb ** 3 * 64 * 16  # two grid buffers
+
+
+def test_serving_requests_follow_the_workload_definition():
+    from paper_2207_04658_b300 import scenes
+    reqs = scenes.serving_requests(rate=20.0, duration=50.0, seed=5)
+    t = np.array([r["t"] for r in reqs])
+    assert np.all(np.diff(t) > 0) and t[-1] <= 50.0
+    assert abs(len(reqs) / 50.0 - 20.0) < 3.0  # Poisson count: 1000 +- 3 sigma
+    n = np.array([r["n"] for r in reqs])
+    assert n.min() >= 1e4 * 0.99 and n.max() <= 4e6 * 1.01
+    # log-uniform: the median of log N sits mid-range
+    assert abs(np.median(np.log(n)) - 0.5 * (math.log(1e4) + math.log(4e6))) < 0.4
+    for r in reqs:
+        assert r["grid_log2"] in scenes.SERVING_GRIDS[r["dim"]] and r["eps"] in (0.1, 0.01)
+    classes = {(r["dim"], r["material"]) for r in reqs}
+    assert classes == set(scenes.SERVING_CLASSES)
+
+
+def test_serving_scene_fits_the_grid():
+    from paper_2207_04658_b300 import scenes
+    for dim, material in scenes.SERVING_CLASSES:
+        for g in scenes.SERVING_GRIDS[dim]:
+            sc, s0 = scenes.serving_scene(dim, material, 30000, g, 3)
+            dx = 1.0 / (1 << g)
+            x = s0[:, :dim]
+            assert x.min() >= 3 * dx and x.max() <= 1 - 4 * dx
+            assert sc["dt"] <= 0.3 * dx / (math.sqrt(400.0) if material == "fluid" else 1.0) + 1e-12
+
+
+def test_scheme_cap_keeps_the_window(q):
+    info = {"P": [300.0, 300.0, 900.0, 900.0], "g": [1e12, 1.0, 1e-6, 1.0],
+            "lo": [0.0, -1.0, -10.0, 0.5], "hi": [1.0, 1.0, 10.0, 1.5], "z": 1.0}
+    scheme, res = q.solve_scheme(info, 1e-4, material="corotated")
+    assert res["capped"] == ["x"] and scheme["x"]["bits"] == 24
+    d = 2.0 ** -scheme["x"]["frac"]
+    lo = scheme["x"]["offset"] * d
+    hi = (scheme["x"]["offset"] + 2 ** 24 - 1) * d
+    assert lo <= -0.5 and hi >= 1.5  # the kappa = 2 window of [0, 1]
