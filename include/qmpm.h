@@ -221,6 +221,11 @@ const char *qmpm_last_error(void);
 #define QMPM_MEASURE_USER 1        /* seed dz/ds_T supplied by the caller (z reported as
                                       the mean square position) */
 #define QMPM_MEASURE_KINETIC_ENERGY 2 /* z = (1/2) m sum |v_T|^2, seed m v_T (Sec. 8.1) */
+/* OR'ed into `measure`: the adjoint's forward follows the quantized trajectory of the
+ * handle's scheme (each step's state goes through the dithered store, Eq. 1), so the
+ * gradients and ranges are taken at the quantized solution -- one round of the iterative
+ * re-linearisation of Sec. 4.  Requires a quantized handle. */
+#define QMPM_ADJ_QUANTIZED_FORWARD 0x100
 
 typedef struct {
     double z;          /* the measurement of s_T (kinetic energy for that measure, else the

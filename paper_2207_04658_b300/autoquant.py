@@ -118,3 +118,31 @@ def serving_schemes(eps_list=scenes.SERVING_EPS, n_rep=20000, samples=2, seed=11
                 scheme, _ = qmpm.solve_scheme(info, eps, material=material, kappa=kappa)
                 out[(dim, material, grid_log2, eps)] = widen_c_for_v_noise(scheme, info, grid_log2, kappa)
     return out
+
+
+def iterate_scheme(scene, state0, T, eps, measure=qmpm.MEASURE_KINETIC_ENERGY, max_iter=6, ckpt_every=32,
+                   kappa=2.0, containers=(0, 0, 0, 0)):
+    """Algorithm 1 with the iterative re-linearisation the paper discusses (Sec. 4): the
+    first solve linearises at the full-precision run; every further round re-runs the
+    adjoint along the quantized trajectory of the current scheme (gradients and ranges at
+    the quantized solution) and solves again, keeping the error budget (eps z)^2 of the
+    full-precision z, until the scheme repeats (a fixed point or a two-cycle) or max_iter
+    rounds.  Returns (scheme, history), history a list of per-round dicts with the bits,
+    fractions and g_h."""
+    material = scene["material"]
+    info0 = qmpm.sensitivities(scene, state0, T, ckpt_every, measure)
+    z_ref = info0["z"]
+    scheme, res = qmpm.solve_scheme(info0, eps, kappa=kappa, containers=containers, material=material)
+    history = [{"bits": res["bits"], "frac": res["frac"], "g": info0["g"], "quantized_forward": False}]
+    seen = [scheme]
+    for _ in range(1, max_iter):
+        g = qmpm.Scene(dict(scene, resort_every=0), scheme, state0)
+        info = qmpm.qmpm_adjoint(g.h, T, ckpt_every, measure | qmpm.ADJ_QUANTIZED_FORWARD)
+        g.close()
+        info["z"] = z_ref
+        scheme, res = qmpm.solve_scheme(info, eps, kappa=kappa, containers=containers, material=material)
+        history.append({"bits": res["bits"], "frac": res["frac"], "g": info["g"], "quantized_forward": True})
+        if scheme in seen[-2:]:
+            break
+        seen.append(scheme)
+    return scheme, history

@@ -577,6 +577,24 @@ __global__ void adj_load_kernel(const __grid_constant__ StepParams P, int quant,
     }
 }
 
+// The quantized store of step `step` applied to an FP32 state in place: dithered encode
+// (slot p = particle index of the adjoint's fixed order) and decode of the stored value.
+// Used when the forward of the adjoint follows the quantized trajectory.
+__global__ void adj_quantize_kernel(const __grid_constant__ StepParams P, float *s, int64_t N, uint32_t step)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    uint4 rnd = make_uint4(0, 0, 0, 0);
+    for (int c = 0; c < P.n_comp; ++c) {
+        if (P.dither && (c & 3) == 0)
+            rnd = philox4x32_10(make_uint4((uint32_t)p, step, (uint32_t)(c >> 2), 0u), P.seed_lo, P.seed_hi);
+        const CompCodec &cc = P.comp[c];
+        int fl;
+        const uint32_t u = encode_f32(s[p * P.n_comp + c], cc, P.dither != 0, uint4_at(rnd, c & 3), fl);
+        s[p * P.n_comp + c] = decode_u(u, cc);
+    }
+}
+
 // Order-preserving integer image of a float (signed comparison of the images orders the
 // floats); the map is its own inverse on the bit patterns.
 __host__ __device__ __forceinline__ int ordered_key(float f)
@@ -743,7 +761,9 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
                             float *d_grad0, qmpm_adjoint_out_t *out)
 {
     using namespace qmpm;
-    if (!h || T < 0 || ckpt_every < 0 ||
+    const bool qfwd = (measure & QMPM_ADJ_QUANTIZED_FORWARD) != 0;
+    measure &= ~QMPM_ADJ_QUANTIZED_FORWARD;
+    if (!h || T < 0 || ckpt_every < 0 || (qfwd && !h->quant) ||
         (measure != QMPM_MEASURE_MEAN_SQ_POS && measure != QMPM_MEASURE_USER &&
          measure != QMPM_MEASURE_KINETIC_ENERGY) ||
         (measure == QMPM_MEASURE_USER && !d_seed && h->N > 0)) {
@@ -810,6 +830,17 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
         e = cudaGetLastError();
     }
     const int64_t NE = N * nc;
+    // one forward step s_t -> s_(t+1), through the quantized store of step t + 1 when the
+    // adjoint follows the quantized trajectory
+    auto step_fwd = [&](const float *a, float *b, int t) -> cudaError_t {
+        cudaError_t r = fwd(P, a, b, N, gm, gv, nn, st);
+        fwd_steps += 1;
+        if (r == cudaSuccess && qfwd && N > 0) {
+            adj_quantize_kernel<<<nblk(N), kAdjThreads, 0, st>>>(P, b, N, (uint32_t)(t + 1));
+            r = cudaGetLastError();
+        }
+        return r;
+    };
     auto reduce = [&](const float *a, int sq, int range, int z) {
         if (N == 0) return;
         unsigned b = std::min<unsigned>(nblk(N), (unsigned)c.n_sms * 8);
@@ -821,8 +852,7 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
     if (e == cudaSuccess && N > 0) e = cudaMemcpyAsync(cur, ckpt, state_bytes, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) reduce(cur, 0, 1, 0);
     for (int t = 0; t < T && e == cudaSuccess; ++t) {
-        e = fwd(P, cur, nxt, N, gm, gv, nn, st);
-        fwd_steps += 1;
+        e = step_fwd(cur, nxt, t);
         std::swap(cur, nxt);
         if (e == cudaSuccess) reduce(cur, 0, 1, 0);
         if (e == cudaSuccess && !bisection && (t + 1) % k == 0 && (t + 1) / k < n_ckpt)
@@ -854,8 +884,7 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
                 const float *src = from;
                 for (int j = 0; j < n_adv && e == cudaSuccess; ++j) {
                     float *dst = (j % 2 == 0) ? a : b2;
-                    e = fwd(P, src, dst, N, gm, gv, nn, st);
-                    fwd_steps += 1;
+                    e = step_fwd(src, dst, op.t0 + j);
                     src = dst;
                 }
             } else {
@@ -869,10 +898,8 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
     for (int64_t seg = (!bisection && T > 0 ? (T - 1) / k : -1); seg >= 0 && e == cudaSuccess; --seg) {
         const int t0 = (int)(seg * k), t1 = std::min<int>(T, (int)(seg + 1) * k);
         if (N > 0) e = cudaMemcpyAsync(tape, ckpt + (size_t)seg * NE, state_bytes, cudaMemcpyDeviceToDevice, st);
-        for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t) {
-            e = fwd(P, tape + (size_t)(t - t0) * NE, tape + (size_t)(t - t0 + 1) * NE, N, gm, gv, nn, st);
-            fwd_steps += 1;
-        }
+        for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t)
+            e = step_fwd(tape + (size_t)(t - t0) * NE, tape + (size_t)(t - t0 + 1) * NE, t);
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
             e = rev(P, tape + (size_t)(t - t0) * NE, sbn, sb, N, gm, gv, gb, nn, st);
             if (e == cudaSuccess) reduce(sb, 1, 0, 0);

@@ -101,6 +101,7 @@ class qmpm_rev_op_t(ct.Structure):
 
 
 CKPT_BISECTION = 0
+ADJ_QUANTIZED_FORWARD = 0x100
 OP_ADVANCE, OP_REVERSE = 0, 1
 
 

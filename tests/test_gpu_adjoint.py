@@ -243,3 +243,24 @@ def test_full_size_adjoint_directional_derivative(q):
     fd = (zs[0] - zs[1]) / (2 * h)
     ad = float((grad * delta).sum())
     assert abs(fd - ad) <= 2e-2 * abs(ad), (fd, ad)
+
+
+def test_quantized_forward_adjoint_and_iterative_relinearisation(q):
+    # Sec. 4: the linearisation can be re-taken at the quantized solution; the paper finds
+    # the iteration converges within six rounds and within about one bit of the first solve
+    import torch
+    from paper_2207_04658_b300 import autoquant
+    sc, s0 = impact_block()
+    T = 200
+    scheme, hist = autoquant.iterate_scheme(sc, s0, T, 0.01, measure=q.MEASURE_KINETIC_ENERGY, ckpt_every=25)
+    assert 2 <= len(hist) <= 6
+    assert all(np.isfinite(h["g"]).all() and min(h["g"]) > 0 for h in hist)
+    last, prev = hist[-1]["bits"], hist[-2]["bits"]
+    converged = last == prev or (len(hist) >= 3 and last == hist[-3]["bits"])
+    assert converged or len(hist) == 6
+    assert max(abs(a - b) for a, b in zip(hist[0]["bits"], last)) <= 2
+    # the quantized-forward adjoint needs a quantized handle
+    g = q.Scene(sc, None, s0)
+    with pytest.raises(q.QmpmError):
+        q.qmpm_adjoint(g.h, 4, 2, q.MEASURE_KINETIC_ENERGY | q.ADJ_QUANTIZED_FORWARD)
+    g.close()
