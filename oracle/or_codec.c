@@ -37,16 +37,22 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* The dither offset of Sec. 5 for one stored component.  The counter is
- * (slot, step, comp / 4, 0) and the key is the 64-bit scene seed; one Philox call
- * serves four consecutive components. */
+/* The dither threshold of Sec. 5 for one stored component, compared with the 32-bit
+ * fraction f of the value (round up when f > r).  A 16-bit uniform draw q is taken from the
+ * Philox block with counter (slot, step, comp / 8, 0) and key = the 64-bit scene seed:
+ * the low (comp even) or high (comp odd) half of word (comp / 2) % 4, so one call serves
+ * eight consecutive components.  The threshold sits in the middle of q's bucket of 2^16
+ * fractions, r = q 2^16 + 2^15, so P(round up) is the fraction rounded to 16 bits: exact
+ * to 2^-17, and zero-mean over the fraction. */
 uint32_t or_dither_draw(uint64_t seed, uint32_t slot, uint32_t step, int comp)
 {
-    uint32_t ctr[4] = {slot, step, (uint32_t)(comp >> 2), 0u};
+    uint32_t ctr[4] = {slot, step, (uint32_t)(comp >> 3), 0u};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t out[4];
     or_philox4x32_10(ctr, key, out);
-    return out[comp & 3];
+    const uint32_t w = out[(comp >> 1) & 3];
+    const uint32_t q = (comp & 1) ? (w >> 16) : (w & 0xFFFFu);
+    return (q << 16) | 0x8000u;
 }
 
 /* ------------------------------------------------------------------------------------

@@ -586,11 +586,11 @@ __global__ void adj_quantize_kernel(const __grid_constant__ StepParams P, float 
     if (p >= N) return;
     uint4 rnd = make_uint4(0, 0, 0, 0);
     for (int c = 0; c < P.n_comp; ++c) {
-        if (P.dither && (c & 3) == 0)
-            rnd = philox4x32_10(make_uint4((uint32_t)p, step, (uint32_t)(c >> 2), 0u), P.seed_lo, P.seed_hi);
+        if (P.dither && (c & 7) == 0)
+            rnd = philox4x32_10(make_uint4((uint32_t)p, step, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
         const CompCodec &cc = P.comp[c];
         int fl;
-        const uint32_t u = encode_f32(s[p * P.n_comp + c], cc, P.dither != 0, uint4_at(rnd, c & 3), fl);
+        const uint32_t u = encode_f32(s[p * P.n_comp + c], cc, P.dither != 0, dither_threshold(rnd, c), fl);
         s[p * P.n_comp + c] = decode_u(u, cc);
     }
 }

@@ -58,6 +58,8 @@ void release(qmpm_ctx *c)
     fr(c->seg_begin);
     fr(c->seg_end);
     fr(c->key_chunks);
+    fr(c->tile_idx);
+    fr(c->tile_first);
     fr(c->chunks);
     fr(c->d_stats);
     fr(c->d_z);
@@ -216,7 +218,7 @@ struct Sizes {
     size_t bytes() const
     {
         return 2 * (words * 4 + ids * 8 + grid * 16 + touched + keys * 4 * 2) + digit_counts * 4 +
-               scan_partials * 4 + 2 * seg * 4 + key_chunks * 4 + chunks * sizeof(qmpm::Chunk) + 16 * 8 + 8;
+               scan_partials * 4 + 3 * seg * 4 + 2 * key_chunks * 4 + chunks * sizeof(qmpm::Chunk) + 16 * 8 + 8;
     }
 };
 
@@ -302,6 +304,8 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
     ok = ok && dalloc(&c->seg_end, z.seg, st) == cudaSuccess;
     ok = ok && dalloc(&c->key_chunks, z.key_chunks, st) == cudaSuccess;
     ok = ok && dalloc(&c->chunks, z.chunks, st) == cudaSuccess;
+    ok = ok && dalloc(&c->tile_idx, z.key_chunks, st) == cudaSuccess;
+    ok = ok && dalloc(&c->tile_first, z.seg, st) == cudaSuccess;
     ok = ok && dalloc(&c->d_stats, 16, st) == cudaSuccess;
     ok = ok && dalloc(&c->d_z, 1, st) == cudaSuccess;
     if (!ok) {
@@ -310,6 +314,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
         return fail(QMPM_ERR_OOM, "device allocation failed");
     }
     c->n_chunks = c->key_chunks + c->n_blocks;
+    c->n_tiles = c->tile_idx + c->n_blocks;
     c->prof = new (std::nothrow) qmpm::Profile();
     if (!c->prof) {
         release(c);

@@ -11,8 +11,9 @@ namespace qmpm {
 
 // ------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of the 4x32 S-box,
-// keys bumped by the Weyl constants between rounds.  Used for the dither offset of
-// Sec. 5: counter (slot, step, comp / 4, 0), key = scene seed, word comp % 4.
+// keys bumped by the Weyl constants between rounds.  Used for the dither threshold of
+// Sec. 5: counter (slot, step, comp / 8, 0), key = scene seed; component comp takes the
+// 16-bit half comp % 2 of word (comp / 2) % 4 (dither_threshold).
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
@@ -32,6 +33,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 __device__ __forceinline__ uint32_t uint4_at(const uint4 &v, int i)
 {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Dither threshold of component c from the Philox block of its group of eight: a 16-bit
+// draw q placed mid-bucket among the 32-bit fractions, r = q 2^16 + 2^15 (round up when the
+// fraction f > r: probability f rounded to 16 bits).
+__device__ __forceinline__ uint32_t dither_threshold(const uint4 &blk, int c)
+{
+    const uint32_t w = uint4_at(blk, (c >> 1) & 3);
+    const uint32_t q = (c & 1) ? (w >> 16) : (w & 0xFFFFu);
+    return (q << 16) | 0x8000u;
 }
 
 // ------------------------------------------------------------------------------------

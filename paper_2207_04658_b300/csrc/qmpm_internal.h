@@ -31,12 +31,14 @@ struct CompCodec {
     int32_t field;      // 0..3
 };
 
-// Work item of the step kernels: a run of sorted particles that share one tile.
+// A run of sorted particles that share one tile.  The step kernels take a tile's chunks
+// together (one grid staging and one flush per tile): the first chunk of a tile carries
+// the tile's chunk count, the others 0.
 struct Chunk {
-    uint32_t start;     // first slot
-    uint32_t count;     // <= chunk size
-    uint32_t key;       // tile key: linear index of the tile's origin block
-    uint32_t pad;
+    uint32_t start;        // first slot
+    uint32_t count;        // <= chunk size
+    uint32_t key;          // tile key: linear index of the tile's origin block
+    uint32_t tile_chunks;  // chunks of the tile if this is its first, else 0
 };
 
 struct StepParams {
@@ -57,6 +59,8 @@ struct StepParams {
     int64_t ld;                 // plane stride
     const Chunk *chunks;
     const uint32_t *n_chunks;   // device scalar
+    const uint32_t *tile_first; // index of each non-empty tile's first chunk
+    const uint32_t *n_tiles;    // device scalar
     const float4 *grid_in;      // P2G result of the current state (G2P source)
     float4 *grid_out;           // zeroed target of the next P2G
     uint8_t *touched_out;       // blocks of grid_out that received mass
@@ -120,6 +124,9 @@ struct Ctx {
     uint32_t *seg_begin, *seg_end, *key_chunks; // per key
     Chunk *chunks;
     uint32_t *n_chunks;
+    uint32_t *tile_idx;         // per key: non-empty keys before it (exclusive scan); [n_blocks] = count
+    uint32_t *tile_first;       // per non-empty tile: its first chunk
+    uint32_t *n_tiles;          // = tile_idx + n_blocks
     int64_t max_chunks;
     int key_bits;
 
@@ -135,8 +142,8 @@ struct Ctx {
 };
 
 // kernels launched by one re-sort: keys, radix passes (hist, 3 scan, scatter), gather,
-// segments, chunk counts, 3 scan, emit
-inline int64_t resort_launches(int key_bits) { return 9 + 5 * (int64_t)(key_bits / 8); }
+// segments, chunk counts, 3 scan, chunk emit, tile flags, 3 scan, tile emit
+inline int64_t resort_launches(int key_bits) { return 14 + 5 * (int64_t)(key_bits / 8); }
 
 // api.cu: message returned by qmpm_last_error() on this thread
 void set_last_error(const std::string &msg);

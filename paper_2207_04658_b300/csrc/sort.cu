@@ -249,14 +249,33 @@ __global__ void chunk_emit_kernel(const uint32_t *seg_begin, const uint32_t *seg
     if (k >= n_keys) return;
     const uint32_t b = seg_begin[k], cnt = seg_end[k] - b;
     uint32_t out = chunk_base[k];
+    const uint32_t n = (cnt + chunk - 1) / chunk;
     for (uint32_t s = 0; s < cnt; s += chunk, ++out) {
         Chunk c;
         c.start = b + s;
         c.count = (cnt - s) < (uint32_t)chunk ? (cnt - s) : (uint32_t)chunk;
         c.key = (uint32_t)k;
-        c.pad = 0;
+        c.tile_chunks = s == 0 ? n : 0u;
         chunks[out] = c;
     }
+}
+
+// Non-empty tiles: flag per key (1 if the key has particles; entry n_keys is 0), scanned
+// into tile_idx, then each non-empty key writes the index of its first chunk at its rank.
+__global__ void tile_flag_kernel(const uint32_t *seg_begin, const uint32_t *seg_end, uint32_t *tile_idx,
+                                 int64_t n_keys)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n_keys) return;
+    tile_idx[k] = (k < n_keys && seg_end[k] > seg_begin[k]) ? 1u : 0u;
+}
+
+__global__ void tile_emit_kernel(const uint32_t *seg_begin, const uint32_t *seg_end, const uint32_t *tile_idx,
+                                 const uint32_t *chunk_base, uint32_t *tile_first, int64_t n_keys)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_keys || seg_end[k] <= seg_begin[k]) return;
+    tile_first[tile_idx[k]] = chunk_base[k];
 }
 
 static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -325,12 +344,20 @@ int resort(Ctx &c, std::string &err)
                                                                                    c.key_chunks, c.n_blocks, c.chunk);
                 e = exclusive_scan_u32(c.key_chunks, c.n_blocks + 1, c.scan_partials, c.max_scan_partials, s);
             }
-            if (e == cudaSuccess)
+            if (e == cudaSuccess) {
                 chunk_emit_kernel<<<blocks_for(c.n_blocks, 256), 256, 0, s>>>(c.seg_begin, c.seg_end, c.key_chunks,
                                                                               c.chunks, c.n_blocks, c.chunk);
+                tile_flag_kernel<<<blocks_for(c.n_blocks + 1, 256), 256, 0, s>>>(c.seg_begin, c.seg_end, c.tile_idx,
+                                                                                 c.n_blocks);
+                e = exclusive_scan_u32(c.tile_idx, c.n_blocks + 1, c.scan_partials, c.max_scan_partials, s);
+            }
+            if (e == cudaSuccess)
+                tile_emit_kernel<<<blocks_for(c.n_blocks, 256), 256, 0, s>>>(c.seg_begin, c.seg_end, c.tile_idx,
+                                                                             c.key_chunks, c.tile_first, c.n_blocks);
         }
     } else {
         e = cudaMemsetAsync(c.key_chunks + c.n_blocks, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c.tile_idx + c.n_blocks, 0, sizeof(uint32_t), s);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {

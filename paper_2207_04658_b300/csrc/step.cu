@@ -123,10 +123,6 @@ __device__ __forceinline__ void g2p_gather(const StepParams &P, const float *tvx
     }
 }
 
-// Block fixed point of the P2G tile: a contribution of magnitude at most the chunk's bound
-// maps to at most kFixMax = 2^23 - 64 units (the margin absorbs FP32 rounding of the
-// contribution), so 256 of them stay inside a 32-bit integer.
-constexpr float kFixMax = 8388544.0f;
 
 // Thread t works on the particle at position (t % 32) * 8 + t / 32 of its chunk: the
 // chunk is sorted by cell, so the 32 lanes of a warp land on different cells and the
@@ -184,7 +180,7 @@ constexpr size_t step_smem_fixed() { return (size_t)7 * (DIM == 2 ? 64 : 512) * 
 // index P.step, or `step` in a multi-scene launch (MULTI).  All threads of the CTA call it
 // together (it synchronises).
 template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P, bool MULTI = false>
-__device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, uint32_t step, StepCounters &cnt,
+__device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci0, uint32_t step, StepCounters &cnt,
                                           const int tid, const int pj)
 {
     using Tr = Traits<DIM, MAT>;
@@ -198,16 +194,29 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
     uint32_t *sw = reinterpret_cast<uint32_t *>(red + kThreads / 32);  // record words, column per particle
     uint32_t *my = sw + column_of(pj);  // its column of record words, stride kThreads
 
-    int T0, T1, T2 = 0;
+    const Chunk ch0 = P.chunks[ci0];
+    const uint32_t key = ch0.key;
+    int o0, o1, o2 = 0;  // tile origin node: 4 (T - 1) per axis, T the tile's origin block
     if (DIM == 2) {
-        T1 = ch.key % P.nb;
-        T0 = ch.key / P.nb;
+        o1 = 4 * ((int)(key % P.nb) - 1);
+        o0 = 4 * ((int)(key / P.nb) - 1);
     } else {
-        T2 = ch.key % P.nb;
-        T1 = (ch.key / P.nb) % P.nb;
-        T0 = ch.key / (P.nb * P.nb);
+        o2 = 4 * ((int)(key % P.nb) - 1);
+        o1 = 4 * ((int)((key / P.nb) % P.nb) - 1);
+        o0 = 4 * ((int)(key / (P.nb * P.nb)) - 1);
     }
-    const int o0 = 4 * (T0 - 1), o1 = 4 * (T1 - 1), o2 = 4 * (T2 - 1);  // tile origin node
+    // the tile's chunks: ch0 and the tile_chunks - 1 that follow it in the list; the block
+    // fixed point must hold all their contributions to a node: total particles <= 2^b
+    // gives each contribution at most 2^(31 - b) - 64 units
+    const int n_tile_chunks = (int)ch0.tile_chunks;
+    float kfix;
+    {
+        const Chunk chl = P.chunks[ci0 + n_tile_chunks - 1];
+        const uint32_t tile_particles = chl.start + chl.count - ch0.start;
+        const int tb = 32 - __clz((int)max(tile_particles, 2u) - 1);  // ceil(log2(particles))
+        kfix = (float)((1u << (31 - tb)) - 64u);
+    }
+
 
     // 1. stage the grid tile (velocities: the grid update) and clear the P2G tile
     for (int t = tid; t < TN; t += kThreads) {
@@ -226,8 +235,13 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
         tpy[q] = 0;
         if (DIM == 3) tpz[q] = 0;
     }
-    // 2. coalesced load of the chunk's records into shared memory (column per slot)
     const int mycol = column_of(tid);
+    // fixed-point units per (m/s) of the tile's momentum sums, a power of two; 0 while no
+    // chunk of the tile has had a non-zero momentum contribution (the sums are all zero)
+    float scale = 0.0f;
+    for (int jc = 0; jc < n_tile_chunks; ++jc) {
+    const Chunk ch = P.chunks[ci0 + jc];
+    // 2. coalesced load of the chunk's records into shared memory (column per slot)
     if (tid < (int)ch.count)
         for (int j = 0; j < P.n_words; ++j) sw[j * kThreads + mycol] = P.words[j * P.ld + ch.start + tid];
     __syncthreads();
@@ -313,12 +327,12 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
                 uint4 rnd = make_uint4(0, 0, 0, 0);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    if (P.dither && (c & 3) == 0)
-                        rnd = philox4x32_10(make_uint4((uint32_t)slot, MULTI ? step : P.step, (uint32_t)(c >> 2), 0u),
+                    if (P.dither && (c & 7) == 0)
+                        rnd = philox4x32_10(make_uint4((uint32_t)slot, MULTI ? step : P.step, (uint32_t)(c >> 3), 0u),
                                             P.seed_lo, P.seed_hi);
                     int fl;
                     const CompCodec &cc = P.comp[c];
-                    const uint32_t u = encode_f32(val[c], cc, P.dither != 0, uint4_at(rnd, c & 3), fl);
+                    const uint32_t u = encode_f32(val[c], cc, P.dither != 0, dither_threshold(rnd, c), fl);
                     atomicOr(my + cc.word * kThreads, u << cc.shift);
                     atomicOr(my + (cc.word + 1) * kThreads, __funnelshift_l(u, 0u, cc.shift));
                     val[c] = decode_u(u, cc);  // the stored (quantized) value
@@ -361,8 +375,8 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
             }
         }
     }
-    // 5b. chunk-wide scale of the block fixed point: the largest in-tile contribution
-    //     maps to kFixMax, so no sum of <= 256 contributions can overflow 32 bits
+    // 5b. scale of the block fixed point: the largest in-tile contribution maps inside
+    //     kfix, so no sum over the tile's particles can overflow 32 bits
     {
         float bm = __uint_as_float(__reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound)));
         if ((tid & 31) == 0) red[tid >> 5] = bm;
@@ -371,9 +385,23 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
     float bmax = 0.0f;
 #pragma unroll
     for (int w8 = 0; w8 < kThreads / 32; ++w8) bmax = fmaxf(bmax, red[w8]);
-    const float scale = bmax > 0.0f ? kFixMax / bmax : 1.0f;  // fixed-point units per (m/s)
+    // the largest power of two that maps this chunk's largest contribution inside kfix; a
+    // chunk that needs a smaller one than the tile's sums so far shifts those sums down first
+    const float want = bmax > 0.0f ? exp2f(floorf(log2f(kfix / bmax))) : 0.0f;
+    if (want > 0.0f && scale == 0.0f) {
+        scale = want;
+    } else if (want > 0.0f && want < scale) {
+        const int sh = (int)log2f(scale / want);
+        for (int t = tid; t < TN; t += kThreads) {
+            tpx[t] >>= sh;
+            tpy[t] >>= sh;
+            if (DIM == 3) tpz[t] >>= sh;
+        }
+        scale = want;
+        __syncthreads();
+    }
     if (active) {
-        // 5c. scatter: momentum w (v + A dpos / m) * scale and mass w * kFixMax as integers
+        // 5c. scatter: momentum w (v + A dpos / m) * scale and mass w * kfix as integers
         float dpx[3], dpy[3], dpz[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -384,11 +412,12 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
         if (p_in_tile) {
             const int l0 = pbase[0] - o0, l1 = pbase[1] - o1, l2 = DIM == 3 ? pbase[2] - o2 : 0;
             float As[DIM * DIM], vs[3];
-            const float am = scale * P.inv_p_mass;
+            const float s_use = scale > 0.0f ? scale : 1.0f;  // no momentum yet: any scale
+            const float am = s_use * P.inv_p_mass;
 #pragma unroll
             for (int q = 0; q < DIM * DIM; ++q) As[q] = pA[q] * am;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) vs[a] = pv[a] * scale;
+            for (int a = 0; a < DIM; ++a) vs[a] = pv[a] * s_use;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 float ui[3];
@@ -404,7 +433,7 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
                     for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
                         const float wt = DIM == 3 ? wij * pw[2][k] : wij;
                         const int q = tile_index<DIM>(l0 + i, l1 + j, l2 + k);
-                        atomicAdd(tpm + q, __float2int_rn(wt * kFixMax));
+                        atomicAdd(tpm + q, __float2int_rn(wt * kfix));
                         if (DIM == 3) {
                             atomicAdd(tpx + q, __float2int_rn(wt * (uij[0] + As[2] * dpz[k])));
                             atomicAdd(tpy + q, __float2int_rn(wt * (uij[1] + As[5] * dpz[k])));
@@ -443,23 +472,28 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const Chunk ch, u
     }
     __syncthreads();
 
-    // 6. coalesced store of the new records, and the P2G tile flush: one vector atomic
-    //    per node that received mass
+    // 6. coalesced store of the new records
     if (DO_G2P && tid < (int)ch.count)
         for (int j = 0; j < P.n_words; ++j) __stcs(P.words + j * P.ld + ch.start + tid, sw[j * kThreads + mycol]);
+    if (jc + 1 < n_tile_chunks) __syncthreads();  // the next chunk reuses the record columns
+    }  // chunks of the tile
+
+    // 7. the P2G tile flush: one vector atomic per node that received mass
     for (int t = tid; t < TN; t += kThreads) {
         const int i = DIM == 2 ? (t >> 3) : (t >> 6), j = DIM == 2 ? (t & 7) : ((t >> 3) & 7);
         const int k = DIM == 2 ? 0 : (t & 7);
         const int q = tile_index<DIM>(i, j, k);
         const int im = tpm[q];
         if (im != 0) {
-            const float mm = P.p_mass / scale;  // momentum units -> m v
+            const float mm = P.p_mass / (scale > 0.0f ? scale : 1.0f);  // momentum units -> m v
             atomicAdd(P.grid_out + node_addr<DIM>(P.nb, o0 + i, o1 + j, o2 + k),
-                      make_float4((float)im * (P.p_mass / kFixMax), (float)tpx[q] * mm, (float)tpy[q] * mm,
+                      make_float4((float)im * (P.p_mass / kfix), (float)tpx[q] * mm, (float)tpy[q] * mm,
                                   DIM == 3 ? (float)tpz[q] * mm : 0.0f));
         }
     }
-    if (tid < (1 << DIM) && ch.count > 0) {
+    if (tid < (1 << DIM)) {
+        // the tile's 2^d blocks: origin block T = o / 4 + 1 per axis
+        const int T0 = (o0 >> 2) + 1, T1 = (o1 >> 2) + 1, T2 = (o2 >> 2) + 1;
         const int i = tid & 1, j = (tid >> 1) & 1, k = (tid >> 2) & 1;
         const int64_t blk = DIM == 2 ? (int64_t)(T0 + i) * P.nb + (T1 + j)
                                      : ((int64_t)(T0 + i) * P.nb + (T1 + j)) * P.nb + (T2 + k);
@@ -474,9 +508,10 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>()) step
     StepCounters cnt;
     const int tid = threadIdx.x;
     const int pj = spread(tid);  // this thread's particle within each chunk
-    const uint32_t n_chunks = *P.n_chunks;
-    for (uint32_t ci = blockIdx.x; ci < n_chunks; ci += gridDim.x)
-        run_chunk<DIM, MAT, QUANT, STATS, DO_G2P>(P, P.chunks[ci], 0u, cnt, tid, pj);
+    const uint32_t n_tiles = *P.n_tiles;
+    for (uint32_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        run_chunk<DIM, MAT, QUANT, STATS, DO_G2P>(P, P.tile_first[ti], 0u, cnt, tid, pj);
+    }
     if (STATS) flush_counters(cnt, P.stats);
 }
 
@@ -491,13 +526,14 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>())
     const int tid = threadIdx.x;
     const int pj = spread(tid);
     const uint32_t step = *P.step_ctr + 1u;
-    const uint32_t n_chunks = *P.n_chunks;
-    for (uint32_t ci = blockIdx.x; ci < n_chunks; ci += gridDim.x)
-        run_chunk<DIM, MAT, QUANT, STATS, true, true>(P, P.chunks[ci], step, cnt, tid, pj);
+    const uint32_t n_tiles = *P.n_tiles;
+    for (uint32_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        run_chunk<DIM, MAT, QUANT, STATS, true, true>(P, P.tile_first[ti], step, cnt, tid, pj);
+    }
     if (STATS) flush_counters(cnt, P.stats);
 }
 
-// Multi-scene launch: the work queue is the concatenation of the members' chunk lists
+// Multi-scene launch: the work queue is the concatenation of the members' tile lists
 // (member-major); each CTA strides over it, copying a member's parameters into shared
 // memory when its items move on to the next member.  The members share the template
 // class (dimension, material, quantized or not); everything else (grid size, scheme,
@@ -512,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     static_assert(sizeof(StepParams) % 4 == 0, "StepParams is copied as 32-bit words");
     const int tid = threadIdx.x;
     const int pj = spread(tid);
-    if (tid < n_members) first[tid + 1] = *tab[tid].n_chunks;
+    if (tid < n_members) first[tid + 1] = *tab[tid].n_tiles;
     if (tid == 0) first[0] = 0;
     __syncthreads();
     if (tid == 0)
@@ -539,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             cur = lo;
             step = *Ps.step_ctr + 1u;
         }
-        run_chunk<DIM, MAT, QUANT, STATS, true, true>(Ps, Ps.chunks[item - first[lo]], step, cnt, tid, pj);
+        run_chunk<DIM, MAT, QUANT, STATS, true, true>(Ps, Ps.tile_first[item - first[lo]], step, cnt, tid, pj);
     }
     if (STATS && cur >= 0) flush_counters(cnt, Ps.stats);
 }
@@ -620,10 +656,10 @@ __global__ void encode_init_kernel(const __grid_constant__ StepParams P, const d
     for (int j = 0; j < P.n_words; ++j) my[j * blockDim.x] = 0u;
     uint4 rnd = make_uint4(0, 0, 0, 0);
     for (int c = 0; c < P.n_comp; ++c) {
-        if (P.dither && (c & 3) == 0)
-            rnd = philox4x32_10(make_uint4((uint32_t)p, 0u, (uint32_t)(c >> 2), 0u), P.seed_lo, P.seed_hi);
+        if (P.dither && (c & 7) == 0)
+            rnd = philox4x32_10(make_uint4((uint32_t)p, 0u, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
         int fl;
-        const uint32_t u = encode_f64(s[p * P.n_comp + c], P.comp[c], P.dither != 0, uint4_at(rnd, c & 3), fl);
+        const uint32_t u = encode_f64(s[p * P.n_comp + c], P.comp[c], P.dither != 0, dither_threshold(rnd, c), fl);
         if (P.stats && fl) {
             const int h = P.comp[c].field;
             atomicAdd(P.stats + ((fl & 1) ? h : (fl & 2) ? 4 + h : 8 + h), 1ull);
@@ -714,10 +750,10 @@ __global__ void pack_f32_kernel(const __grid_constant__ StepParams P, const floa
     for (int j = 0; j < P.n_words; ++j) my[j * blockDim.x] = 0u;
     uint4 rnd = make_uint4(0, 0, 0, 0);
     for (int c = 0; c < P.n_comp; ++c) {
-        if (P.dither && (c & 3) == 0)
-            rnd = philox4x32_10(make_uint4((uint32_t)p, P.step, (uint32_t)(c >> 2), 0u), P.seed_lo, P.seed_hi);
+        if (P.dither && (c & 7) == 0)
+            rnd = philox4x32_10(make_uint4((uint32_t)p, P.step, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
         int fl;
-        const uint32_t u = encode_f32(vals[p * P.n_comp + c], P.comp[c], P.dither != 0, uint4_at(rnd, c & 3), fl);
+        const uint32_t u = encode_f32(vals[p * P.n_comp + c], P.comp[c], P.dither != 0, dither_threshold(rnd, c), fl);
         if (P.stats && fl) {
             const int h = P.comp[c].field;
             atomicAdd(P.stats + ((fl & 1) ? h : (fl & 2) ? 4 + h : 8 + h), 1ull);
@@ -772,6 +808,8 @@ void fill_params(const Ctx &c, StepParams &p)
     p.ld = c.ld;
     p.chunks = c.chunks;
     p.n_chunks = c.n_chunks;
+    p.tile_first = c.tile_first;
+    p.n_tiles = c.n_tiles;
     p.stats = (s.flags & QMPM_FLAG_STATS) ? c.d_stats : nullptr;
 }
 

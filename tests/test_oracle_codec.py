@@ -16,11 +16,22 @@ def test_philox_known_answers(oracle):
 
 
 def test_dither_draw_counter(oracle):
-    # the draw of component c is word c % 4 of the Philox block (slot, step, c // 4, 0)
+    # the draw of component c is the 16-bit half c % 2 of word (c // 2) % 4 of the Philox
+    # block (slot, step, c // 8, 0), placed mid-bucket among the 32-bit fractions
     seed = 0x0123456789ABCDEF
-    for slot, step, comp in [(0, 0, 0), (5, 7, 3), (123456, 99, 13), (2**31, 2**20, 23)]:
-        block = oracle.philox([slot, step, comp // 4, 0], [seed & 0xFFFFFFFF, seed >> 32])
-        assert oracle.dither_draw(seed, slot, step, comp) == block[comp % 4]
+    for slot, step, comp in [(0, 0, 0), (5, 7, 3), (123456, 99, 13), (2**31, 2**20, 23), (9, 9, 8)]:
+        block = oracle.philox([slot, step, comp // 8, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        w = block[(comp // 2) % 4]
+        q = (w >> 16) if comp % 2 else (w & 0xFFFF)
+        assert oracle.dither_draw(seed, slot, step, comp) == (q << 16) | 0x8000
+
+
+def test_dither_round_up_probability_is_the_fraction(oracle):
+    # the probability of rounding up, counted exactly over all 2^16 draws q, equals the
+    # fraction rounded to 16 bits (so within 2^-17 of it), Sec. 5 Eq. 11
+    for f in [0, 1, 0x7FFF, 0x8000, 0x8001, 0x12345678, 0x80000000, 0xFFFF7FFF, 0xFFFF8000, 0xFFFFFFFF]:
+        ups = sum(1 for q in range(1 << 16) if f > ((q << 16) | 0x8000))
+        assert abs(ups / 65536.0 - f / 2.0 ** 32) <= 2.0 ** -17 + 1e-15
 
 
 @pytest.mark.parametrize("bits,frac,lo", [(16, 16, 0.0), (16, 13, -4.0), (12, 9, -4.0),
