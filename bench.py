@@ -185,7 +185,7 @@ def e2e_scene(qmpm, torch, g, steps, warmup):
     return el, int(words.nbytes)
 
 
-def kernel_counters(desc, n_particles):
+def kernel_counters(desc, n_particles, words=None):
     """DRAM bytes and warp instructions per launch of the step kernel from the committed
     ncu summary (a smaller case of the same workload), scaled by the particle count to
     this workload; (None, None) when the kernel source changed since the capture."""
@@ -198,6 +198,8 @@ def kernel_counters(desc, n_particles):
         if rec.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
             return None, None
         if rec.get("workload") != desc["workload"]:
+            return None, None
+        if words is not None and rec.get("words_per_particle") not in (None, words):
             return None, None
         f = n_particles / rec["particles"]
         return rec["dram_bytes_per_launch"] * f, rec["warp_instructions_per_launch"] * f
@@ -380,7 +382,7 @@ def run_ours(args):
     nodes = st["active_blocks"] * (64 if sc["dim"] == 3 else 16)
     alg_bytes = N * 2 * 4 * W + nodes * 2 * node_bytes
     achieved = alg_bytes / (step_avg_ms / 1e3) / 1e9
-    traffic, winst = kernel_counters(desc, N)
+    traffic, winst = kernel_counters(desc, N, W)
     hbm = {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
            "frac": round(achieved / hbm_peak, 4), "peak_source": peak_note,
            "alg_bytes_per_launch": alg_bytes}
