@@ -277,21 +277,21 @@ def step_fp64(ph, s, grid=None):
     return s
 
 
-def encode_state(cd, s, step, stats=None):
+def encode_state(cd, s, step, stats=None, threaded=False):
     s = np.ascontiguousarray(s, dtype=np.float64)
     N = s.shape[0]
     w = np.zeros((N, cd.n_words), dtype=np.uint32)
     st = stats if stats is not None else np.zeros(N_STATS, dtype=np.int64)
-    lib().or_encode_state(ct.byref(cd), N, _p(s, ct.c_double), step, _p(w, ct.c_uint32),
-                          _p(st, ct.c_int64))
+    lib(threaded).or_encode_state(ct.byref(cd), N, _p(s, ct.c_double), step, _p(w, ct.c_uint32),
+                                  _p(st, ct.c_int64))
     return w
 
 
-def decode_state(cd, words):
+def decode_state(cd, words, threaded=False):
     words = np.ascontiguousarray(words, dtype=np.uint32)
     N = words.shape[0]
     s = np.zeros((N, cd.n_comp))
-    lib().or_decode_state(ct.byref(cd), N, _p(words, ct.c_uint32), _p(s, ct.c_double))
+    lib(threaded).or_decode_state(ct.byref(cd), N, _p(words, ct.c_uint32), _p(s, ct.c_double))
     return s
 
 
@@ -323,14 +323,15 @@ class QuantRollout:
     the device path: encode at step 0, stable re-sort by tile key at step 0 and after
     every ``resort_every``-th step."""
 
-    def __init__(self, scene, scheme, s0):
+    def __init__(self, scene, scheme, s0, threaded=False):
+        self.threaded = threaded
         self.ph = make_phys(scene)
         self.cd = make_codec(scene, scheme)
         self.resort_every = int(scene.get("resort_every", 8))
         s0 = np.ascontiguousarray(s0, dtype=np.float64)
         self.N = s0.shape[0]
         self.stats = np.zeros(N_STATS, dtype=np.int64)
-        self.words = encode_state(self.cd, s0, 0, self.stats)
+        self.words = encode_state(self.cd, s0, 0, self.stats, threaded)
         self.ids = np.arange(self.N, dtype=np.int64)
         self.t = 0
         self.grid = np.zeros(n_nodes(self.ph) * (1 + self.ph.dim))
@@ -338,22 +339,22 @@ class QuantRollout:
         self.resort()
 
     def resort(self):
-        s = decode_state(self.cd, self.words)
-        perm = stable_sort(tile_keys(self.ph, s), n_keys(self.ph))
+        s = decode_state(self.cd, self.words, self.threaded)
+        perm = stable_sort(tile_keys(self.ph, s, self.threaded), n_keys(self.ph))
         self.words = np.ascontiguousarray(self.words[perm])
         self.ids = self.ids[perm]
 
     def step(self, n=1):
         for _ in range(n):
             self.t += 1
-            lib().or_step_quant(ct.byref(self.ph), ct.byref(self.cd), self.N,
+            lib(self.threaded).or_step_quant(ct.byref(self.ph), ct.byref(self.cd), self.N,
                                 _p(self.words, ct.c_uint32), self.t, _p(self.s, ct.c_double),
                                 _p(self.grid, ct.c_double), _p(self.stats, ct.c_int64))
             if self.resort_every > 0 and self.t % self.resort_every == 0:
                 self.resort()
 
     def state(self):
-        return decode_state(self.cd, self.words)
+        return decode_state(self.cd, self.words, self.threaded)
 
 
 class Fp64Rollout:

@@ -1,6 +1,8 @@
 /*
  * or_codec.c -- oracle: counter-based dither generator, fixed-point codec and the
  * bit pack / bit struct placement.  TEST INFRASTRUCTURE ONLY (see oracle.h).
+ * The OpenMP pragmas only matter in the threaded build used for full-size reference runs
+ * (particles are independent there); the default build ignores them.
  */
 #include "oracle.h"
 
@@ -217,29 +219,32 @@ void or_encode_state(const or_codec_t *cd, int64_t N, const double *s, uint32_t 
                      uint32_t *words, int64_t *stats)
 {
     const int nc = cd->n_comp;
-    uint32_t u[OR_MAX_COMP];
+    int64_t acc[OR_N_STATS] = {0};
+#pragma omp parallel for schedule(static) reduction(+ : acc[:OR_N_STATS])
     for (int64_t p = 0; p < N; ++p) {
+        uint32_t u[OR_MAX_COMP];
         for (int c = 0; c < nc; ++c) {
             uint32_t r = cd->dither ? or_dither_draw(cd->seed, (uint32_t)p, step, c) : 0u;
             int flags = 0;
             u[c] = or_encode(s[p * nc + c], cd->bits[c], cd->frac[c], cd->offset[c],
                              cd->dither, r, &flags);
-            if (stats) {
-                const int h = cd->field[c];
-                if (flags & OR_FLAG_SAT) stats[OR_STAT_SAT(h)] += 1;
-                if (flags & OR_FLAG_UP) stats[OR_STAT_UP(h)] += 1;
-                if (flags & OR_FLAG_DOWN) stats[OR_STAT_DOWN(h)] += 1;
-            }
+            const int h = cd->field[c];
+            if (flags & OR_FLAG_SAT) acc[OR_STAT_SAT(h)] += 1;
+            if (flags & OR_FLAG_UP) acc[OR_STAT_UP(h)] += 1;
+            if (flags & OR_FLAG_DOWN) acc[OR_STAT_DOWN(h)] += 1;
         }
         or_pack(nc, cd->bits, cd->bitpos, cd->n_words, u, words + p * cd->n_words);
     }
+    if (stats)
+        for (int i = 0; i < OR_N_STATS; ++i) stats[i] += acc[i];
 }
 
 void or_decode_state(const or_codec_t *cd, int64_t N, const uint32_t *words, double *s)
 {
     const int nc = cd->n_comp;
-    uint32_t u[OR_MAX_COMP];
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < N; ++p) {
+        uint32_t u[OR_MAX_COMP];
         or_unpack(nc, cd->bits, cd->bitpos, words + p * cd->n_words, u);
         for (int c = 0; c < nc; ++c)
             s[p * nc + c] = or_decode(u[c], cd->frac[c], cd->offset[c]);

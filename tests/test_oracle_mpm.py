@@ -317,3 +317,28 @@ def test_quantized_rollout_tracks_fp64(oracle):
     zf = oracle.mean_sq_pos(2, sf)
     assert abs(zq - zf) / zf < 1e-4
     assert np.abs(sq[:, :2] - sf[:, :2]).max() < 1e-3
+
+
+def test_threaded_build_matches_sequential(oracle):
+    # the OpenMP build (used only for full-size reference runs) sums P2G in another order:
+    # FP64 results agree to rounding, quantized ones to at most a quantum where that
+    # rounding crosses a dither threshold
+    from paper_2207_04658_b300 import scenes
+    sc, s0 = scenes.cubes3d_scene(n_cubes=1, cube_cells=8, grid_log2=5, seed=8)
+    sch = scenes.fixed_scheme_3d("corotated")
+    a = oracle.Fp64Rollout(sc, s0)
+    b = oracle.Fp64Rollout(sc, s0, threaded=True)
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.ids, b.ids)
+    assert np.allclose(a.s, b.s, rtol=1e-12, atol=1e-12)
+    qa = oracle.QuantRollout(sc, sch, s0)
+    qb = oracle.QuantRollout(sc, sch, s0, threaded=True)
+    qa.step(3)
+    qb.step(3)
+    assert np.array_equal(qa.ids, qb.ids)
+    d = np.abs(qa.state() - qb.state())
+    fields = oracle.comp_fields(3, "corotated")
+    quanta = np.array([2.0 ** -sch[["x", "v", "C", "F"][h]]["frac"] for h in fields])
+    assert (d <= quanta[None] * (1 + 1e-9)).all()
+    assert (d == 0).mean() > 0.999
