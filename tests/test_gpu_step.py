@@ -247,3 +247,35 @@ def test_step_host_round_trip(q, oracle):
     d = np.abs(wa["state"] - sb) / quanta(oracle, sc, sch)[None]
     assert d.max() <= 2
     assert np.array_equal(hout.numpy(), b.readback(state=False, words=True, ids=False)["words"])
+
+
+@pytest.mark.parametrize("dim,grid_log2", [(2, 11), (3, 10)])
+def test_largest_grids_free_fall(q, dim, grid_log2):
+    # the largest grids the ABI accepts (2048^2, 1024^3: 35 GB of 3D grid buffers): a small
+    # body far from the walls in free fall keeps its shape, falls with v = g t exactly in
+    # FP32 state (a uniform velocity field is reproduced by P2G + G2P) and touches only the
+    # blocks around it
+    from paper_2207_04658_b300 import scenes
+    n = 1 << grid_log2
+    dx = 1.0 / n
+    gen = np.random.default_rng(3)
+    x = scenes.jitter_box(gen, np.full(dim, 0.5), np.full(dim, 6 * dx), (12,) * dim)
+    s0 = scenes.initial_state(dim, "neohookean", x)
+    # dt large enough that each step's displacement is well above the FP32 resolution of x
+    # near 0.5; a soft material keeps the step within its CFL limit
+    sc = dict(dim=dim, material="neohookean", grid_log2=grid_log2, bound=3, dt=1e-4, E=1.0, nu=0.2,
+              bulk=0.0, rho=1.0, p_vol=(6 * dx) ** dim / x.shape[0], gravity=(0.0, -9.8, 0.0), seed=1,
+              dither=True, resort_every=8)
+    g = q.Scene(sc, None, s0, stats=True)
+    T = 100
+    g.step(T)
+    st = g.state_by_id()
+    stats = g.readback(state=False, ids=False)["stats"]
+    g.close()
+    vy = st[:, dim + 1]
+    assert np.allclose(vy, -9.8 * sc["dt"] * T, rtol=1e-4)
+    dy = st[:, 1] - s0[:, 1]
+    assert np.allclose(dy, -9.8 * sc["dt"] ** 2 * T * (T + 1) / 2, rtol=2e-3)
+    assert np.allclose(st[:, 0], s0[:, 0], atol=1e-6)
+    assert stats["out_of_grid"] == 0 and stats["out_of_tile"] == 0
+    assert 0 < stats["active_blocks"] <= 4 ** dim
