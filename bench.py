@@ -239,8 +239,6 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
     counts log-uniform in [1e4, 4e6], grids 64^3..256^3 or 128^2..1024^2, schemes solved at
     eps 0.1 or 0.01, 200 steps) submitted to the engine at their arrival times; rollout
     latency (submit to finished, measured) percentiles and aggregate particle-steps/s."""
-    import queue
-    import threading
     from paper_2207_04658_b300 import autoquant, scenes
     t_solve = time.perf_counter()
     schemes = autoquant.serving_schemes()
@@ -249,32 +247,29 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
     reqs = scenes.serving_requests(rate=rate, duration=duration, seed=5)
     if dc is not None and dc.world > 1:
         reqs = shard(reqs, dc.rank, dc.world)  # replicas: each GPU serves every world-th request
+    # the scenes are drawn before the clock starts (in parallel; numpy releases the GIL), and
+    # submitted without a copy at their arrival times
+    import concurrent.futures as cf
+
+    def draw(r):
+        return scenes.serving_scene(r["dim"], r["material"], r["n"], r["grid_log2"], r["seed"])
+
+    t_gen = time.perf_counter()
+    with cf.ThreadPoolExecutor(8) as ex:
+        drawn = list(ex.map(draw, reqs))
+    t_gen = time.perf_counter() - t_gen
     eng = qmpm.Engine(budget_bytes=int(budget_gb * 2 ** 30), resort_every=8, max_active=max_active)
-    # a producer thread draws the scenes ahead of their arrival times (bounded look-ahead)
-    ready = queue.Queue(maxsize=16)
-
-    def produce():
-        for r in reqs:
-            sc, s0 = scenes.serving_scene(r["dim"], r["material"], r["n"], r["grid_log2"], r["seed"])
-            ready.put((r, sc, s0))
-        ready.put(None)
-
-    threading.Thread(target=produce, daemon=True).start()
     eng.start()
     t0 = time.perf_counter()
     lateness = []
     submitted = 0
     particle_steps = 0
-    while True:
-        item = ready.get()
-        if item is None:
-            break
-        r, sc, s0 = item
+    for r, (sc, s0) in zip(reqs, drawn):
         wait = r["t"] - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
         lateness.append(max(0.0, -wait))
-        eng.submit(sc, schemes[(r["dim"], r["material"], r["grid_log2"], r["eps"])], s0, sc["steps"])
+        eng.submit(sc, schemes[(r["dim"], r["material"], r["grid_log2"], r["eps"])], s0, sc["steps"], borrow=True)
         submitted += 1
         particle_steps += s0.shape[0] * sc["steps"]
     eng.stop(drain=True)
@@ -303,7 +298,7 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
             "budget_gb": budget_gb, "max_active": max_active, "iterations": st["iterations"],
             "graph_launches": st["graph_launches"], "kernel_launches": st["kernel_launches"],
             "submit_lateness_p99_ms": round(float(np.percentile(lateness, 99)) * 1e3, 2) if lateness else None,
-            "scheme_solve_s": round(t_solve, 2),
+            "scheme_solve_s": round(t_solve, 2), "scene_generation_s": round(t_gen, 2),
             "mix": "uniform over 2D neo-Hookean, 2D fluid, 3D fixed-corotated, 3D fluid; N log-uniform "
                    "[1e4, 4e6]; eps uniform {0.1, 0.01}; 200 steps; schemes from Algorithm 1 per class and grid"}
 
@@ -433,6 +428,15 @@ def run_ours(args):
                         "step_kernel_ms": round(s32, 4),
                         "step_kernel_gbs": round(alg32 / (s32 / 1e3) / 1e9, 1),
                         "quantized_over_fp32": round(value / v32, 4)}
+        if not args.no_e2e:
+            # the same end-to-end path on FP32 state: four times the bytes over the host link
+            k = max(3, min(args.steps // 4, 50))
+            el32, nb32 = e2e_scene(qmpm, torch, g32, k, 1)
+            el32 = dc.max(torch, el32)
+            line["fp32"]["e2e"] = {"value": dc.world * N * k / el32, "unit": UNIT,
+                                   "h2d_bytes_per_step": nb32, "d2h_bytes_per_step": nb32}
+            if "e2e" in line:
+                line["e2e"]["quantized_over_fp32"] = round(line["e2e"]["value"] / line["fp32"]["e2e"]["value"], 3)
         g32.close()
     if solve_info is not None:
         line["scheme_solve"] = solve_info

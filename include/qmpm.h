@@ -393,12 +393,16 @@ typedef struct {
  * QMPM_ERR_INVALID_ARG, QMPM_ERR_CUDA. */
 int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out);
 
-/* Queue a request; the engine copies h_state (host, as for qmpm_init).  keep_state != 0
- * keeps the final state for qmpm_engine_result.  Thread-safe.  Errors:
- * QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME.  A request larger than the budget fails with
- * QMPM_ERR_OOM when it reaches the head of the queue. */
+#define QMPM_SUBMIT_KEEP_STATE 1 /* keep the final state for qmpm_engine_result */
+#define QMPM_SUBMIT_BORROW 2     /* read h_state at admission instead of copying it now: the
+                                    caller keeps it unchanged until the request is polled */
+
+/* Queue a request; the engine copies h_state (host, as for qmpm_init) unless flags has
+ * QMPM_SUBMIT_BORROW.  Thread-safe.  Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME.  A
+ * request larger than the budget fails with QMPM_ERR_OOM when it reaches the head of the
+ * queue. */
 int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qmpm_scheme_t *scheme,
-                       const double *h_state, int32_t steps, int32_t keep_state, int64_t *id);
+                       const double *h_state, int32_t steps, int32_t flags, int64_t *id);
 
 /* Run the loop on a background thread until qmpm_engine_stop (drain != 0: after every
  * submitted request has finished). */

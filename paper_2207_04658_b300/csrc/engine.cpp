@@ -36,6 +36,7 @@ struct Request {
     bool has_scheme = false;
     bool keep_state = false;
     std::vector<double> state;  // initial state until admission, final state if kept
+    const double *borrowed = nullptr;  // the caller's initial state (QMPM_SUBMIT_BORROW)
     std::vector<int64_t> ids;
     int32_t steps = 0;
     int32_t done_steps = 0;
@@ -201,7 +202,9 @@ void init_loop(qmpm_engine *e)
         int rc = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess ? QMPM_OK
                                                                                            : QMPM_ERR_CUDA;
         if (rc == QMPM_OK)
-            rc = qmpm_init(&r->scene, r->has_scheme ? &r->scheme : nullptr, r->state.data(), r->stream, &r->h);
+            rc = qmpm_init(&r->scene, r->has_scheme ? &r->scheme : nullptr,
+                           r->borrowed ? r->borrowed : r->state.data(), r->stream, &r->h);
+        r->borrowed = nullptr;  // the caller's buffer is no longer needed
         std::vector<double>().swap(r->state);
         std::lock_guard<std::mutex> lk(e->mu);
         e->reserved -= r->peak - (rc == QMPM_OK ? r->resident : 0);
@@ -367,7 +370,7 @@ int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out)
 }
 
 int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qmpm_scheme_t *scheme,
-                       const double *h_state, int32_t steps, int32_t keep_state, int64_t *id)
+                       const double *h_state, int32_t steps, int32_t flags, int64_t *id)
 {
     if (!e || !scene || steps < 0 || (scene->n_particles > 0 && !h_state))
         return efail(QMPM_ERR_INVALID_ARG, "bad request");
@@ -383,9 +386,12 @@ int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qm
     }
     const int nc = 2 * scene->dim + scene->dim * scene->dim +
                    (scene->material == QMPM_FLUID ? 1 : scene->dim * scene->dim);
-    r->state.assign(h_state, h_state + (size_t)scene->n_particles * nc);
+    if (flags & QMPM_SUBMIT_BORROW)
+        r->borrowed = h_state;
+    else
+        r->state.assign(h_state, h_state + (size_t)scene->n_particles * nc);
     r->steps = steps;
-    r->keep_state = keep_state != 0;
+    r->keep_state = (flags & QMPM_SUBMIT_KEEP_STATE) != 0;
     r->t_submit = e->now();
     {
         std::lock_guard<std::mutex> lk(e->mu);

@@ -107,6 +107,7 @@ OP_ADVANCE, OP_REVERSE = 0, 1
 
 MEASURE_MEAN_SQ_POS, MEASURE_USER, MEASURE_KINETIC_ENERGY = 0, 1, 2
 BATCH_GRAPHS = 1
+SUBMIT_KEEP_STATE, SUBMIT_BORROW = 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
@@ -623,15 +624,21 @@ class Engine:
         cfg.max_active = int(max_active)
         cfg.flags = BATCH_GRAPHS if graphs else 0
         self.h = ct.c_void_p()
+        self._borrowed = {}
         _check(lib().qmpm_engine_create(ct.byref(cfg), ct.byref(self.h)))
 
-    def submit(self, scene, scheme, state0, steps, keep_state=False, flags=0):
+    def submit(self, scene, scheme, state0, steps, keep_state=False, flags=0, borrow=False):
+        """Queue a request.  borrow=True lets the engine read state0 at admission instead of
+        copying it now; the array is held here until the request has been polled."""
         state0 = np.ascontiguousarray(state0, dtype=np.float64)
         sc = make_scene_struct(scene, state0.shape[0], flags)
         sch = make_scheme_struct(scheme, scene["dim"], scene["material"])
         rid = ct.c_int64()
+        sub = (SUBMIT_KEEP_STATE if keep_state else 0) | (SUBMIT_BORROW if borrow else 0)
         _check(lib().qmpm_engine_submit(self.h, ct.byref(sc), ct.byref(sch), _dptr(state0, ct.c_double),
-                                        int(steps), int(bool(keep_state)), ct.byref(rid)))
+                                        int(steps), sub, ct.byref(rid)))
+        if borrow:
+            self._borrowed[rid.value] = state0
         return rid.value
 
     def start(self):
@@ -649,7 +656,10 @@ class Engine:
         buf = (qmpm_request_t * max_n)()
         n = ct.c_int32()
         _check(lib().qmpm_engine_poll(self.h, buf, int(max_n), ct.byref(n)))
-        return [buf[i].as_dict() for i in range(n.value)]
+        out = [buf[i].as_dict() for i in range(n.value)]
+        for r in out:
+            self._borrowed.pop(r["id"], None)
+        return out
 
     def result(self, rid, N, n_comp):
         st = np.empty((N, n_comp), dtype=np.float64)
