@@ -493,3 +493,149 @@ def scheme_bruteforce(P, g, lo, hi, z, eps, mode="error", kappa=2.0, frac_lo=-8,
     if rc != 0:
         raise ValueError(f"oracle brute force failed ({rc})")
     return _solve_out(so, len(P))
+
+
+# ------------------------------------------------------------------------------ smoke
+class Smoke(ct.Structure):
+    _fields_ = [("n", ct.c_int), ("jacobi", ct.c_int), ("dt", ct.c_double), ("buoyancy", ct.c_double),
+                ("v_in", ct.c_double), ("src", ct.c_double * 4), ("seed", ct.c_uint64), ("dither", ct.c_int)]
+
+
+class SmokeScheme(ct.Structure):
+    _fields_ = [("bits", ct.c_int * 2), ("frac", ct.c_int * 2), ("offset", ct.c_int64 * 2)]
+
+
+def _bind_smoke(L):
+    P = ct.POINTER
+    d = ct.c_double
+    L.or_smoke_step.argtypes = [P(Smoke), P(SmokeScheme), ct.c_uint32, P(d), P(d), P(d), P(d)]
+    L.or_smoke_step.restype = ct.c_int64
+    L.or_smoke_measure.argtypes = [P(Smoke), P(d)]
+    L.or_smoke_measure.restype = d
+    L.or_smoke_inject.argtypes = [ct.c_int, ct.c_int, ct.c_uint32, ct.c_uint32, d]
+    L.or_smoke_follow.argtypes = [P(ct.c_uint32), ct.c_int64, d, d]
+    L.or_smoke_follow_report.argtypes = [P(ct.c_int64), P(d)]
+    L.or_smoke_record.argtypes = [P(ct.c_uint32), ct.c_int64]
+    L.or_smoke_recorded.restype = ct.c_int64
+
+
+def _smoke_lib():
+    L = lib()
+    if not hasattr(L, "_smoke_bound"):
+        _bind_smoke(L)
+        L._smoke_bound = True
+    return L
+
+
+def make_smoke(scene):
+    sm = Smoke()
+    sm.n = int(scene["n"])
+    sm.jacobi = int(scene.get("jacobi", 64))
+    sm.dt = float(scene["dt"])
+    sm.buoyancy = float(scene.get("buoyancy", 0.0))
+    sm.v_in = float(scene.get("v_in", 0.0))
+    for k, x in enumerate(scene.get("src", (0.0, 0.0, -1.0, -1.0))):
+        sm.src[k] = float(x)
+    sm.seed = int(scene.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    sm.dither = int(bool(scene.get("dither", True)))
+    return sm
+
+
+def make_smoke_scheme(scheme):
+    if scheme is None:
+        return None
+    sc = SmokeScheme()
+    for h, name in enumerate(("v", "p")):
+        sc.bits[h] = int(scheme[name]["bits"])
+        sc.frac[h] = int(scheme[name]["frac"])
+        sc.offset[h] = int(scheme[name]["offset"])
+    return sc
+
+
+class SmokeRollout:
+    """Oracle rollout of the 2D advection-reflection smoke (unquantized if scheme is None).
+    Fields: u [n][n+1] (x-faces), v [n+1][n] (y-faces), d and q [n][n], row = y index."""
+
+    def __init__(self, scene, scheme=None, u0=None, v0=None, d0=None):
+        _smoke_lib()
+        self.sm = make_smoke(scene)
+        self.sch = make_smoke_scheme(scheme)
+        n = self.sm.n
+        self.u = np.zeros((n, n + 1)) if u0 is None else np.array(u0, dtype=np.float64)
+        self.v = np.zeros((n + 1, n)) if v0 is None else np.array(v0, dtype=np.float64)
+        self.d = np.zeros((n, n)) if d0 is None else np.array(d0, dtype=np.float64)
+        self.q = np.zeros((n, n))
+        self.t = 0
+        self.saturations = 0
+
+    def step(self, k=1):
+        L = lib()
+        for _ in range(k):
+            self.t += 1
+            self.saturations += L.or_smoke_step(ct.byref(self.sm), ct.byref(self.sch) if self.sch is not None else None,
+                                                self.t, _p(self.u, ct.c_double), _p(self.v, ct.c_double),
+                                                _p(self.d, ct.c_double), _p(self.q, ct.c_double))
+
+    def measure(self):
+        return float((self.d ** 2).sum())
+
+
+def smoke_inject(active, field=0, idx=0, counter=0, delta=0.0):
+    _smoke_lib().or_smoke_inject(int(active), int(field), int(idx), int(counter), float(delta))
+
+
+class smoke_follow:
+    """Context: the quantized smoke oracle follows the kernel's stored codes (every store in
+    order, uint32) at near-ties within tau quanta; .report = (stores, adopted, violations,
+    largest adopted distance in quanta)."""
+
+    def __init__(self, codes, tau_v, tau_p):
+        self.codes = np.ascontiguousarray(codes, dtype=np.uint32)
+        self.tau = (float(tau_v), float(tau_p))
+        self.report = None
+
+    def __enter__(self):
+        _smoke_lib().or_smoke_follow(_p(self.codes, ct.c_uint32), self.codes.size, *self.tau)
+        return self
+
+    def __exit__(self, *exc):
+        L = _smoke_lib()
+        out = (ct.c_int64 * 3)()
+        md = ct.c_double()
+        L.or_smoke_follow_report(out, ct.byref(md))
+        L.or_smoke_follow(None, 0, 0.0, 0.0)
+        self.report = (int(out[0]), int(out[1]), int(out[2]), float(md.value))
+        return False
+
+
+def smoke_store_events(n, jacobi, T):
+    """Every quantized store of a T-step run: (type h, field, sample index, store counter)
+    with h = 0 velocity, 1 pressure; the order of the step's stores is velocity, jacobi
+    pressure iterates, velocity x 3, jacobi pressure iterates, velocity."""
+    ev = []
+    for t in range(1, T + 1):
+        c = 1024 * t
+        seq = ["v"] + ["p"] * jacobi + ["v", "v", "v"] + ["p"] * jacobi + ["v"]
+        for kind in seq:
+            c += 1
+            if kind == "v":
+                ev += [(0, 0, i, c) for i in range((n + 1) * n)] + [(0, 1, i, c) for i in range(n * (n + 1))]
+            else:
+                ev += [(1, 2, i, c) for i in range(n * n)]
+    return ev
+
+
+def smoke_codes(scene, scheme, T, u0=None, v0=None, d0=None):
+    """The quantized oracle's own code at every store of a T-step run, in store order."""
+    L = _smoke_lib()
+    n, J = int(scene["n"]), int(scene.get("jacobi", 64))
+    size = T * (5 * 2 * n * (n + 1) + 2 * J * n * n)
+    buf = np.zeros(size, dtype=np.uint32)
+    L.or_smoke_record(_p(buf, ct.c_uint32), size)
+    try:
+        r = SmokeRollout(scene, scheme, u0, v0, d0)
+        r.step(T)
+        assert L.or_smoke_recorded() == size
+    finally:
+        L.or_smoke_record(None, 0)
+    return buf

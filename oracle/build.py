@@ -7,7 +7,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["or_codec.c", "or_mpm.c", "or_scheme.c", "or_adjoint.c"]
+SOURCES = ["or_codec.c", "or_mpm.c", "or_scheme.c", "or_adjoint.c", "or_smoke.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 

@@ -150,6 +150,39 @@ int or_scheme_solve(const or_solve_in_t *in, or_solve_out_t *out);
  * memory mode (min error s.t. bits); returns the optimum's frac_h / bits */
 int or_scheme_bruteforce(const or_solve_in_t *in, int frac_lo, int frac_hi, or_solve_out_t *out);
 
+/* ---- 2D Eulerian smoke (Sec. 8.1: advection-reflection, quantized pressure and velocity) ---- */
+typedef struct {
+    int n;             /* n x n cells, h = 1/n */
+    int jacobi;        /* Jacobi sweeps per projection */
+    double dt;
+    double buoyancy;   /* v += dt * buoyancy * density */
+    double v_in;       /* inflow velocity inside the source box */
+    double src[4];     /* source box x0, y0, x1, y1 */
+    uint64_t seed;
+    int dither;
+} or_smoke_t;
+
+typedef struct {       /* type 0: velocity (u and v), type 1: pressure q */
+    int bits[2];
+    int frac[2];
+    int64_t offset[2];
+} or_smoke_scheme_t;
+
+/* One step in place; sch NULL for the unquantized step.  q receives the final pressure.
+ * Returns the number of saturated stores. */
+int64_t or_smoke_step(const or_smoke_t *sm, const or_smoke_scheme_t *sch, uint32_t step, double *u, double *v,
+                      double *d, double *q);
+double or_smoke_measure(const or_smoke_t *sm, const double *d);
+/* inject delta at the store (field 0 u, 1 v, 2 q; sample index; store counter) while active */
+void or_smoke_inject(int active, int field, uint32_t idx, uint32_t counter, double delta);
+/* follow a kernel's codes of every store in order (codes NULL: off); tau in quanta */
+void or_smoke_follow(const uint32_t *codes, int64_t n, double tau_v, double tau_p);
+/* record the oracle's own code of every store in order (buf NULL: off) */
+void or_smoke_record(uint32_t *buf, int64_t n);
+int64_t or_smoke_recorded(void);
+/* out = {stores seen, codes adopted at near-ties, violations}; largest adopted distance */
+void or_smoke_follow_report(int64_t out[3], double *max_dist);
+
 #ifdef __cplusplus
 }
 #endif

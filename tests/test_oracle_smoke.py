@@ -1,0 +1,265 @@
+"""Pins of the oracle's 2D advection-reflection smoke (Sec. 8.1) against what the
+mathematics fixes, CPU only:
+  - a state at rest with no source stays exactly at rest (the step adds nothing);
+  - a uniform flow translates a linear density exactly (RK-3 of a constant field is the
+    straight path and bilinear interpolation is exact for linear fields), and interior
+    velocities stay uniform (reflection of a divergence-free uniform field is itself);
+  - a solid rotation follows third-order paths in closed form (velocity advected by
+    itself, reflected, advected again; density advected by the projected half-step
+    velocity);
+  - with enough Jacobi sweeps the step's final velocity is discretely divergence-free up
+    to the one checkerboard mode that undamped Jacobi cannot remove (the sign and the h^2
+    scaling of the Poisson solve and of the gradient);
+  - a quantized store with a fine scheme lands within its quanta of the FP64 value;
+  - the store-event enumeration and injection hook: central differences over every
+    store, combined with the dither's rounding variance Delta^2 / 6 (Sec. 5), predict the
+    variance of z over dither seeds (Eq. 8's linear error propagation);
+  - follow mode: codes taken from the oracle itself are all accepted, a code moved by one
+    far from a tie is a violation."""
+import numpy as np
+import pytest
+
+
+def scene(**kw):
+    sc = dict(n=16, jacobi=16, dt=0.02, buoyancy=0.0, v_in=0.0, src=(1.0, 1.0, -1.0, -1.0), seed=5)
+    sc.update(kw)
+    return sc
+
+
+def divergence(u, v):
+    n = u.shape[0]
+    return (u[:, 1:] - u[:, :-1] + v[1:, :] - v[:-1, :]) * n
+
+
+def test_rest_stays_at_rest(oracle):
+    gen = np.random.default_rng(0)
+    n = 16
+    d0 = gen.uniform(0, 1, (n, n))
+    r = oracle.SmokeRollout(scene(), None, d0=d0)
+    r.step(3)
+    assert np.array_equal(r.d, d0)
+    assert not r.u.any() and not r.v.any() and not r.q.any()
+
+
+def test_uniform_flow_translates_linear_density(oracle):
+    n, cu, cv, dt = 32, 0.5, -0.3, 0.02
+    h = 1.0 / n
+    u0 = np.full((n, n + 1), cu)
+    v0 = np.full((n + 1, n), cv)
+    u0[:, 0] = u0[:, -1] = 0.0
+    v0[0, :] = v0[-1, :] = 0.0
+    xc = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(xc, xc)  # [row = y][col = x]
+    a, b, c = 0.2, 1.5, -0.7
+    d0 = a + b * X + c * Y
+    r = oracle.SmokeRollout(scene(n=n, jacobi=0, dt=dt), None, u0=u0, v0=v0, d0=d0)
+    r.step(1)
+    inner = slice(8, 24)
+    want = a + b * (X - cu * dt) + c * (Y - cv * dt)
+    assert np.abs(r.d[inner, inner] - want[inner, inner]).max() < 1e-12
+    assert np.abs(r.u[inner, inner] - cu).max() < 1e-12
+    assert np.abs(r.v[inner, inner] - cv).max() < 1e-12
+
+
+def p3(M):
+    """Third-order Taylor polynomial of exp(M): what any third-order Runge-Kutta method
+    (Ralston's included) computes for a linear autonomous ODE."""
+    I = np.eye(2)
+    return I + M + M @ M / 2 + M @ M @ M / 6
+
+
+def test_rotation_follows_third_order_paths(oracle):
+    """A solid rotation w = A (x - c) with no projection (0 sweeps): the backtrace of a
+    linear field is x_b - c = P3(-s A) (x - c), bilinear interpolation of linear fields is
+    exact, and the reflection of an unprojected field is the field itself.  So the step
+    makes u~ = u' = B (x - c) with B = A P3(-dt/2 A), the final velocity
+    B P3(-dt/2 B) (x - c), and moves the density along P3(-dt B) (the step advects it by
+    u', not by the final velocity)."""
+    n, dt, om = 32, 0.02, 1.3
+    h = 1.0 / n
+    A = om * np.array([[0.0, -1.0], [1.0, 0.0]])
+    c = np.array([0.5, 0.5])
+
+    def lin(M, x, y):  # field M (p - c) at points (x, y): returns its two components
+        return M[0, 0] * (x - c[0]) + M[0, 1] * (y - c[1]), M[1, 0] * (x - c[0]) + M[1, 1] * (y - c[1])
+
+    ux, uy = np.meshgrid(np.arange(n + 1) * h, (np.arange(n) + 0.5) * h)  # u faces
+    vx, vy = np.meshgrid((np.arange(n) + 0.5) * h, np.arange(n + 1) * h)  # v faces
+    cx, cy = np.meshgrid((np.arange(n) + 0.5) * h, (np.arange(n) + 0.5) * h)
+    u0 = lin(A, ux, uy)[0]
+    v0 = lin(A, vx, vy)[1]
+    u0[:, 0] = u0[:, -1] = 0.0
+    v0[0, :] = v0[-1, :] = 0.0
+    a, b, e = 0.3, 1.1, -0.6
+    d0 = a + b * cx + e * cy
+    r = oracle.SmokeRollout(scene(n=n, jacobi=0, dt=dt), None, u0=u0, v0=v0, d0=d0)
+    r.step(1)
+    B = A @ p3(-dt / 2 * A)
+    F = B @ p3(-dt / 2 * B)
+    inner = slice(8, 24)
+    assert np.abs(r.u[inner, inner] - lin(F, ux, uy)[0][inner, inner]).max() < 1e-12
+    assert np.abs(r.v[inner, inner] - lin(F, vx, vy)[1][inner, inner]).max() < 1e-12
+    xb, yb = lin(p3(-dt * B), cx, cy)
+    want = a + b * (xb + c[0]) + e * (yb + c[1])
+    assert np.abs(r.d[inner, inner] - want[inner, inner]).max() < 1e-12
+    # a second-order path (Taylor to dt^2) is off by far more than the tolerance
+    P2 = np.eye(2) - dt * B + (dt * B) @ (dt * B) / 2
+    xb2, yb2 = lin(P2, cx, cy)
+    off = a + b * (xb2 + c[0]) + e * (yb2 + c[1])
+    assert np.abs(off - want)[inner, inner].max() > 1e-8
+
+
+def checkerboard_residual(D):
+    """Divergence with its component along (-1)^(i+j) cnt_ij removed: undamped Jacobi on the
+    Neumann Laplacian (a cell divides by its cnt interior neighbours) has iteration
+    eigenvalue -1 on the bipartite grid, so that one mode of the divergence is never
+    removed; every other mode converges."""
+    n = D.shape[0]
+    cnt = np.full((n, n), 4.0)
+    cnt[0, :] -= 1
+    cnt[-1, :] -= 1
+    cnt[:, 0] -= 1
+    cnt[:, -1] -= 1
+    w = np.fromfunction(lambda j, i: (-1.0) ** (i + j), (n, n)) * cnt
+    return D - (D * w).sum() / (w * w).sum() * w
+
+
+def test_converged_projection_is_divergence_free(oracle):
+    gen = np.random.default_rng(1)
+    n = 12
+    u0 = gen.normal(0, 0.3, (n, n + 1))
+    v0 = gen.normal(0, 0.3, (n + 1, n))
+    u0[:, 0] = u0[:, -1] = 0.0
+    v0[0, :] = v0[-1, :] = 0.0
+    d_before = np.abs(divergence(u0, v0)).max()
+    r = oracle.SmokeRollout(scene(n=n, jacobi=3000, dt=0.01), None, u0=u0, v0=v0)
+    r.step(1)
+    d_after = np.abs(checkerboard_residual(divergence(r.u, r.v))).max()
+    assert d_before > 1.0
+    assert d_after < 1e-12 * d_before, (d_before, d_after)
+    assert not r.u[:, 0].any() and not r.u[:, -1].any()
+    assert not r.v[0, :].any() and not r.v[-1, :].any()
+    # thirty sweeps leave a visible residual: the iteration is what converges
+    r2 = oracle.SmokeRollout(scene(n=n, jacobi=30, dt=0.01), None, u0=u0, v0=v0)
+    r2.step(1)
+    assert np.abs(checkerboard_residual(divergence(r2.u, r2.v))).max() > 1e-4 * d_before
+
+
+def plume(n=16, jacobi=16, T=4, **kw):
+    return scene(n=n, jacobi=jacobi, dt=0.02, buoyancy=1.0, v_in=1.0, src=(0.35, 0.05, 0.65, 0.2), **kw), T
+
+
+def test_fine_scheme_tracks_fp64(oracle):
+    sc, T = plume()
+    ref = oracle.SmokeRollout(sc)
+    ref.step(1)
+    fine = {"v": dict(bits=32, frac=28, offset=-(1 << 31)), "p": dict(bits=32, frac=34, offset=-(1 << 31))}
+    q = oracle.SmokeRollout(sc, fine)
+    q.step(1)
+    assert q.saturations == 0
+    # each store is within one quantum; the pressure's error reaches the velocity through
+    # the gradient (n / Delta_p) and the Jacobi sweeps average, not grow, their errors
+    assert np.abs(q.u - ref.u).max() < 64 * 2.0 ** -28
+    assert np.abs(q.v - ref.v).max() < 64 * 2.0 ** -28
+    assert np.abs(q.d - ref.d).max() < 64 * 2.0 ** -28
+
+
+def generic_state(n, seed=7):
+    """A state with every interior value generic (nonzero velocities, spread density), so
+    that the stored values' fractions Y are spread and their rounding variances Y (1 - Y)
+    Delta^2 average to Delta^2 / 6."""
+    gen = np.random.default_rng(seed)
+    u0 = gen.normal(0, 0.3, (n, n + 1))
+    v0 = gen.normal(0, 0.3, (n + 1, n))
+    u0[:, 0] = u0[:, -1] = 0.0
+    v0[0, :] = v0[-1, :] = 0.0
+    return u0, v0, gen.uniform(0, 1, (n, n))
+
+
+def is_wall_face(n, field, idx):
+    """Wall faces store an exact zero: no rounding error is made there."""
+    if field == 0:
+        return idx % (n + 1) in (0, n)
+    if field == 1:
+        return idx // n in (0, n)
+    return False
+
+
+def fd_sensitivities(oracle, sc, T, state, step=1e-6):
+    """Sum over the stores of each type (0 velocity, 1 pressure) of (dz/d store)^2 by
+    central differences through the injection hook, on the unquantized run.  Left out: the
+    wall faces (an exact zero is stored) and the reflected velocity 2 u' - u~ (an integer
+    combination of two stored values of the same lattice is stored exactly)."""
+    n, J = sc["n"], sc["jacobi"]
+    G = np.zeros(2)
+    for (h, field, idx, ctr) in oracle.smoke_store_events(n, J, T):
+        if is_wall_face(n, field, idx) or (h == 0 and ctr % 1024 == J + 3):
+            continue
+        zs = []
+        for sgn in (1.0, -1.0):
+            oracle.smoke_inject(1, field, idx, ctr, sgn * step)
+            r = oracle.SmokeRollout(sc, None, *state)
+            r.step(T)
+            zs.append(r.measure())
+        oracle.smoke_inject(0)
+        G[h] += ((zs[0] - zs[1]) / (2 * step)) ** 2
+    return G
+
+
+def test_predicted_variance_matches_dither_runs(oracle):
+    # n = 12 (not a power of two) keeps the stored values off each other's lattices: with
+    # n = 2^k the gradient n (q_r - q_l) of stored pressures lands on the velocity lattice
+    # and some stores are then exact, which the linear prediction does not know
+    sc, T = plume(n=12, jacobi=8, T=2)
+    state = generic_state(12)
+    G = fd_sensitivities(oracle, sc, T, state)
+    sch = {"v": dict(bits=16, frac=8, offset=-(1 << 15)), "p": dict(bits=16, frac=11, offset=-(1 << 15))}
+    dv, dp = 2.0 ** -8, 2.0 ** -11
+    parts = np.array([G[0] * dv * dv, G[1] * dp * dp]) / 6.0
+    # both types carry a sizeable share, so a dropped store kind shows
+    assert parts.min() > 0.3 * parts.max(), parts
+    z = []
+    for s in range(800):
+        r = oracle.SmokeRollout(dict(sc, seed=1000 + s), sch, *state)
+        r.step(T)
+        assert r.saturations == 0
+        z.append(r.measure())
+    obs = float(np.var(z, ddof=1))
+    # 800 samples: the variance estimate's relative sd is 5%
+    assert 0.75 < obs / parts.sum() < 1.2, (obs, parts)
+
+
+def test_follow_accepts_own_codes_and_rejects_far_changes(oracle):
+    sc, T = plume(n=8, jacobi=4, T=2)
+    sch = {"v": dict(bits=16, frac=10, offset=-(1 << 15)), "p": dict(bits=16, frac=14, offset=-(1 << 15))}
+    ev = oracle.smoke_store_events(8, 4, T)
+    codes = oracle.smoke_codes(sc, sch, T)
+    assert codes.size == len(ev)
+    ref = oracle.SmokeRollout(sc, sch)
+    ref.step(T)
+    mine = oracle.SmokeRollout(sc, sch)
+    with oracle.smoke_follow(codes, 0.0, 0.0) as f:
+        mine.step(T)
+    assert f.report == (len(ev), 0, 0, 0.0)
+    assert np.array_equal(mine.u, ref.u) and np.array_equal(mine.d, ref.d)
+    # a code moved by one is adopted only within tau of its threshold: with tau = 0 it is
+    # a violation, and the run continues from it
+    bad = codes.copy()
+    k = len(bad) // 3
+    bad[k] += 1
+    other = oracle.SmokeRollout(sc, sch)
+    with oracle.smoke_follow(bad, 0.0, 0.0) as f:
+        other.step(T)
+    assert f.report[1] == 0 and f.report[2] >= 1
+    # with tau = 1 quantum every one-code difference is within reach and adopted
+    other = oracle.SmokeRollout(sc, sch)
+    with oracle.smoke_follow(bad, 1.0, 1.0) as f:
+        other.step(T)
+    assert f.report[1] >= 1 and f.report[2] == 0
+    # a code moved by two is never a near-tie
+    bad2 = codes.copy()
+    bad2[k] += 2
+    other = oracle.SmokeRollout(sc, sch)
+    with oracle.smoke_follow(bad2, 1.0, 1.0) as f:
+        other.step(T)
+    assert f.report[2] >= 1
