@@ -515,6 +515,8 @@ def _bind_smoke(L):
     L.or_smoke_inject.argtypes = [ct.c_int, ct.c_int, ct.c_uint32, ct.c_uint32, d]
     L.or_smoke_follow.argtypes = [P(ct.c_uint32), ct.c_int64, d, d]
     L.or_smoke_follow_report.argtypes = [P(ct.c_int64), P(d)]
+    L.or_smoke_follow_first.argtypes = [P(ct.c_int64), P(d), P(d)]
+    L.or_smoke_noise.argtypes = [ct.c_int, d, d, ct.c_uint64, d]
     L.or_smoke_record.argtypes = [P(ct.c_uint32), ct.c_int64]
     L.or_smoke_recorded.restype = ct.c_int64
 
@@ -584,6 +586,22 @@ def smoke_inject(active, field=0, idx=0, counter=0, delta=0.0):
     _smoke_lib().or_smoke_inject(int(active), int(field), int(idx), int(counter), float(delta))
 
 
+class smoke_noise:
+    """Context: every store of type h (but the reflection and the wall faces) gets
+    sign * sigma_h * (+-1), the signs drawn from Philox with key = seed."""
+
+    def __init__(self, sigma, seed, sign):
+        self.args = (float(sigma[0]), float(sigma[1]), int(seed) & 0xFFFFFFFFFFFFFFFF, float(sign))
+
+    def __enter__(self):
+        _smoke_lib().or_smoke_noise(1, *self.args)
+        return self
+
+    def __exit__(self, *exc):
+        _smoke_lib().or_smoke_noise(0, 0.0, 0.0, 0, 0.0)
+        return False
+
+
 class smoke_follow:
     """Context: the quantized smoke oracle follows the kernel's stored codes (every store in
     order, uint32) at near-ties within tau quanta; .report = (stores, adopted, violations,
@@ -603,8 +621,12 @@ class smoke_follow:
         out = (ct.c_int64 * 3)()
         md = ct.c_double()
         L.or_smoke_follow_report(out, ct.byref(md))
-        L.or_smoke_follow(None, 0, 0.0, 0.0)
         self.report = (int(out[0]), int(out[1]), int(out[2]), float(md.value))
+        fx, fd = ct.c_double(), ct.c_double()
+        L.or_smoke_follow_first(out, ct.byref(fx), ct.byref(fd))
+        self.first = {"pos": int(out[0]), "oracle": int(out[1]), "kernel": int(out[2]), "x": fx.value,
+                      "dist": fd.value} if self.report[2] else None
+        L.or_smoke_follow(None, 0, 0.0, 0.0)
         return False
 
 

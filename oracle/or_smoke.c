@@ -136,6 +136,32 @@ void or_smoke_inject(int active, int field, uint32_t idx, uint32_t counter, doub
 static double store_q(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int field, double x, uint32_t idx,
                       uint32_t counter, int64_t *sat);
 
+/* Noise at every store (sensitivity estimates by antithetic injection): sign * sigma_h * r
+ * with r = +-1 the top bit of the 16-bit lane of Philox4x32-10 (key = noise seed, counter
+ * (i / 8, store counter, field, 0), lane i % 8), at every store of type h except the
+ * reflected velocity and the wall faces (stores that make no rounding error). */
+static struct {
+    int active;
+    double sigma[2], sign;
+    uint64_t seed;
+} g_noise;
+
+void or_smoke_noise(int active, double sigma_v, double sigma_p, uint64_t seed, double sign)
+{
+    g_noise.active = active;
+    g_noise.sigma[0] = sigma_v;
+    g_noise.sigma[1] = sigma_p;
+    g_noise.seed = seed;
+    g_noise.sign = sign;
+}
+
+static int wall_face(int n, int field, uint32_t idx)
+{
+    if (field == 0) return idx % (uint32_t)(n + 1) == 0 || idx % (uint32_t)(n + 1) == (uint32_t)n;
+    if (field == 1) return idx / (uint32_t)n == 0 || idx / (uint32_t)n == (uint32_t)n;
+    return 0;
+}
+
 /* store of a value through the codec (quantized run) or as is, plus an injected error */
 static double store(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int field, double x, uint32_t idx,
                     uint32_t counter, int64_t *sat)
@@ -143,6 +169,12 @@ static double store(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int fiel
     double y = store_q(sm, sch, field, x, idx, counter, sat);
     if (g_inject.active && g_inject.field == field && g_inject.idx == idx && g_inject.counter == counter)
         y += g_inject.delta;
+    const int type = field == 2 ? 1 : 0;
+    if (g_noise.active && g_noise.sigma[type] != 0.0 && !wall_face(sm->n, field, idx) &&
+        !(field < 2 && counter % 1024u == (uint32_t)sm->jacobi + 3u)) {
+        const uint32_t q = or_dither_draw(g_noise.seed, idx >> 3, counter, 8 * field + (int)(idx & 7u)) >> 16;
+        y += g_noise.sign * g_noise.sigma[type] * ((q & 0x8000u) ? 1.0 : -1.0);
+    }
     return y;
 }
 
@@ -150,6 +182,8 @@ static struct {
     const uint32_t *codes;
     int64_t n, pos, adopted, violations;
     double tau[2], max_dist;
+    int64_t first[3];   /* first violation: store position, oracle code, kernel code */
+    double first_x, first_dist;
 } g_follow;
 
 void or_smoke_follow(const uint32_t *codes, int64_t n, double tau_v, double tau_p)
@@ -174,6 +208,15 @@ void or_smoke_record(uint32_t *buf, int64_t n)
 }
 
 int64_t or_smoke_recorded(void) { return g_record.pos; }
+
+void or_smoke_follow_first(int64_t out[3], double *x, double *dist)
+{
+    out[0] = g_follow.first[0];
+    out[1] = g_follow.first[1];
+    out[2] = g_follow.first[2];
+    *x = g_follow.first_x;
+    *dist = g_follow.first_dist;
+}
 
 void or_smoke_follow_report(int64_t out[3], double *max_dist)
 {
@@ -212,6 +255,13 @@ static double store_q(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int fi
                     g_follow.adopted += 1;
                     if (dist > g_follow.max_dist) g_follow.max_dist = dist;
                 } else {
+                    if (g_follow.violations == 0) {
+                        g_follow.first[0] = g_follow.pos;
+                        g_follow.first[1] = q;
+                        g_follow.first[2] = k;
+                        g_follow.first_x = x;
+                        g_follow.first_dist = dist;
+                    }
                     g_follow.violations += 1;
                 }
                 q = k;

@@ -160,6 +160,25 @@ class qmpm_engine_stats_t(ct.Structure):
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/qmpm.h
+class qmpm_smoke_config_t(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("jacobi", ct.c_int32), ("dt", ct.c_float), ("buoyancy", ct.c_float),
+                ("v_in", ct.c_float), ("src", ct.c_float * 4), ("dither", ct.c_int32)]
+
+
+class qmpm_smoke_scheme_t(ct.Structure):
+    _fields_ = [("bits", ct.c_int32 * 2), ("frac", ct.c_int32 * 2), ("offset", ct.c_int64 * 2)]
+
+
+class qmpm_smoke_info_t(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("jacobi", ct.c_int32), ("n_scenes", ct.c_int32), ("quantized", ct.c_int32),
+                ("steps", ct.c_int64), ("state_bytes", ct.c_int64), ("state_bytes_fp32", ct.c_int64),
+                ("device_bytes", ct.c_int64), ("kernel_launches", ct.c_int64), ("graph_launches", ct.c_int64),
+                ("launches_per_step", ct.c_int32), ("pad", ct.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 _P = ct.POINTER
 _SIGNATURES = [
     ("qmpm_scheme_layout", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t)]),
@@ -205,6 +224,19 @@ _SIGNATURES = [
                                  _P(qmpm_stats_t), ct.c_void_p]),
     ("qmpm_unpack_f32", ct.c_int, [ct.c_int32, ct.c_int32, _P(qmpm_scheme_t), ct.c_void_p,
                                    ct.c_int64, ct.c_int64, ct.c_void_p, ct.c_void_p]),
+]
+_SIGNATURES += [
+    ("qmpm_smoke_create", ct.c_int, [_P(qmpm_smoke_config_t), _P(qmpm_smoke_scheme_t), ct.c_int32,
+                                     _P(ct.c_uint64), ct.c_void_p, _P(ct.c_void_p)]),
+    ("qmpm_smoke_set_state", ct.c_int, [ct.c_void_p, ct.c_int32, _P(ct.c_float), _P(ct.c_float), _P(ct.c_float)]),
+    ("qmpm_smoke_set_noise", ct.c_int, [ct.c_void_p, _P(ct.c_float), _P(ct.c_uint64), _P(ct.c_float)]),
+    ("qmpm_smoke_step", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int64]),
+    ("qmpm_smoke_measure", ct.c_int, [ct.c_void_p, _P(ct.c_double)]),
+    ("qmpm_smoke_readback", ct.c_int, [ct.c_void_p, ct.c_int32, _P(ct.c_float), _P(ct.c_float), _P(ct.c_float),
+                                       _P(ct.c_float)]),
+    ("qmpm_smoke_ranges", ct.c_int, [ct.c_void_p, _P(ct.c_float), _P(ct.c_float), _P(ct.c_int64)]),
+    ("qmpm_smoke_info", ct.c_int, [ct.c_void_p, _P(qmpm_smoke_info_t)]),
+    ("qmpm_smoke_destroy", ct.c_int, [ct.c_void_p]),
 ]
 OPTIONAL_SIGNATURES = [
     ("qmpm_tile_order_static", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, _P(qmpm_scheme_t),

@@ -1,0 +1,192 @@
+"""Binding of the quantized 2D Eulerian smoke (``include/qmpm_smoke.h``) and the scheme
+workflow of the paper's second error-bounded experiment (Sec. 8.1) on top of it.
+
+Argument marshalling only: every step runs in libqmpm's CUDA kernels (there is no CPU
+fallback).  ``Smoke`` wraps a batch handle; ``sensitivities`` estimates Eq. 8's g_h for the
+two quantized types (velocity, pressure) by antithetic noise injection in FP32 runs, and
+``solve`` hands them with the recorded ranges to the library's Algorithm 1 solve.
+
+Array layouts (row = y index): u [n][n+1] x-faces, v [n+1][n] y-faces, d and q [n][n].
+"""
+import ctypes as ct
+
+import numpy as np
+
+from . import qmpm
+from .qmpm import _check, _dptr, lib
+
+TYPES = ("v", "p")
+
+
+def make_config(scene):
+    c = qmpm.qmpm_smoke_config_t()
+    c.n = int(scene["n"])
+    c.jacobi = int(scene.get("jacobi", 64))
+    c.dt = float(scene["dt"])
+    c.buoyancy = float(scene.get("buoyancy", 0.0))
+    c.v_in = float(scene.get("v_in", 0.0))
+    for k, x in enumerate(scene.get("src", (1.0, 1.0, -1.0, -1.0))):
+        c.src[k] = float(x)
+    c.dither = int(bool(scene.get("dither", True)))
+    return c
+
+
+def make_scheme(scheme):
+    if scheme is None:
+        return None
+    s = qmpm.qmpm_smoke_scheme_t()
+    for h, name in enumerate(TYPES):
+        s.bits[h] = int(scheme[name]["bits"])
+        s.frac[h] = int(scheme[name]["frac"])
+        s.offset[h] = int(scheme[name]["offset"])
+    return s
+
+
+def _f32(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    assert a.shape == shape, (a.shape, shape)
+    return a
+
+
+class Smoke:
+    """A batch of n_scenes smoke scenes sharing one configuration and scheme (None: FP32)."""
+
+    def __init__(self, scene, scheme=None, n_scenes=1, seeds=None, stream=0):
+        self.scene = dict(scene)
+        self.n = int(scene["n"])
+        self.S = int(n_scenes)
+        self.quantized = scheme is not None
+        self.h = ct.c_void_p()
+        cfg = make_config(scene)
+        sch = make_scheme(scheme)
+        sd = None
+        if seeds is not None:
+            sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+            assert sd.size == self.S
+        _check(lib().qmpm_smoke_create(ct.byref(cfg), ct.byref(sch) if sch is not None else None, self.S,
+                                       _dptr(sd, ct.c_uint64) if sd is not None else None, ct.c_void_p(stream),
+                                       ct.byref(self.h)))
+
+    def set_state(self, u=None, v=None, d=None, scene=-1):
+        n = self.n
+        u, v, d = _f32(u, (n, n + 1)), _f32(v, (n + 1, n)), _f32(d, (n, n))
+        p = lambda a: _dptr(a, ct.c_float) if a is not None else None  # noqa: E731
+        _check(lib().qmpm_smoke_set_state(self.h, int(scene), p(u), p(v), p(d)))
+
+    def set_noise(self, sigma, noise_seeds, signs):
+        sg = (ct.c_float * 2)(float(sigma[0]), float(sigma[1]))
+        ns = np.ascontiguousarray(np.asarray(noise_seeds, dtype=np.uint64))
+        si = np.ascontiguousarray(np.asarray(signs, dtype=np.float32))
+        assert ns.size == self.S and si.size == self.S
+        _check(lib().qmpm_smoke_set_noise(self.h, sg, _dptr(ns, ct.c_uint64), _dptr(si, ct.c_float)))
+
+    def trace_len(self, steps):
+        n, J = self.n, int(self.scene.get("jacobi", 64))
+        return steps * (10 * n * (n + 1) + 2 * J * n * n)
+
+    def step(self, steps=1, trace=None):
+        """trace: a CUDA int32 tensor of trace_len(steps) elements that receives scene 0's
+        store codes (plain launches), or None (CUDA graph replay)."""
+        if trace is None:
+            _check(lib().qmpm_smoke_step(self.h, int(steps), None, 0))
+        else:
+            _check(lib().qmpm_smoke_step(self.h, int(steps), ct.c_void_p(trace.data_ptr()), int(trace.numel())))
+
+    def measure(self):
+        z = np.zeros(self.S)
+        _check(lib().qmpm_smoke_measure(self.h, _dptr(z, ct.c_double)))
+        return z
+
+    def readback(self, scene=0):
+        n = self.n
+        out = {"u": np.zeros((n, n + 1), np.float32), "v": np.zeros((n + 1, n), np.float32),
+               "d": np.zeros((n, n), np.float32), "q": np.zeros((n, n), np.float32)}
+        _check(lib().qmpm_smoke_readback(self.h, int(scene), *[_dptr(out[k], ct.c_float) for k in "uvdq"]))
+        return out
+
+    def ranges(self):
+        lo = np.zeros((self.S, 2), np.float32)
+        hi = np.zeros((self.S, 2), np.float32)
+        sat = np.zeros((self.S, 2), np.int64)
+        _check(lib().qmpm_smoke_ranges(self.h, _dptr(lo, ct.c_float), _dptr(hi, ct.c_float), _dptr(sat, ct.c_int64)))
+        return lo, hi, sat
+
+    def info(self):
+        out = qmpm.qmpm_smoke_info_t()
+        _check(lib().qmpm_smoke_info(self.h, ct.byref(out)))
+        return out.as_dict()
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            _check(lib().qmpm_smoke_destroy(self.h))
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+def reference(scene, T, state=None):
+    """FP32 run of one scene: z, the per-type value ranges of every store, and the state."""
+    with Smoke(scene, None, 1) as s:
+        if state is not None:
+            s.set_state(*state)
+        s.step(T)
+        z = float(s.measure()[0])
+        lo, hi, _ = s.ranges()
+        return {"z": z, "lo": lo[0].astype(float), "hi": hi[0].astype(float), "state": s.readback(0)}
+
+
+def sensitivities(scene, T, pairs=32, sigma=(1e-4, 1e-6), seed=0, state=None):
+    """Eq. 8's g_h = sum over the stores of type h of (dz/dstore)^2, for h = velocity,
+    pressure, by antithetic noise injection: scenes 2k and 2k+1 of a batch get the same
+    +-sigma_h noise at every store of type h with opposite signs, and
+    E[((z+ - z-) / 2)^2] = sigma_h^2 g_h to second order.  Returns g, its standard error,
+    and the per-pair estimates."""
+    g, se, per = np.zeros(2), np.zeros(2), []
+    for h in range(2):
+        sg = [0.0, 0.0]
+        sg[h] = float(sigma[h])
+        S = 2 * pairs
+        ns = np.repeat(np.arange(pairs, dtype=np.uint64) + np.uint64(1 + 7919 * seed + 104729 * h), 2)
+        signs = np.tile(np.array([1.0, -1.0], np.float32), pairs)
+        with Smoke(scene, None, S) as s:
+            if state is not None:
+                s.set_state(*state)
+            s.set_noise(sg, ns, signs)
+            s.step(T)
+            z = s.measure()
+        est = ((z[0::2] - z[1::2]) / 2.0) ** 2 / sg[h] ** 2
+        g[h] = est.mean()
+        se[h] = est.std(ddof=1) / np.sqrt(pairs)
+        per.append(est)
+    return g, se, per
+
+
+def solve(scene, T, eps, pairs=32, sigma=(1e-4, 1e-6), kappa=2.0, state=None, max_bits=24):
+    """Scheme for the error bound eps on z (Algorithm 1 with the recorded ranges widened by
+    kappa about their midpoint, Sec. 3.1).  Returns (scheme dict, report)."""
+    n = int(scene["n"])
+    ref = reference(scene, T, state)
+    g, se, _ = sensitivities(scene, T, pairs, sigma, state=state)
+    P = [2.0 * n * (n + 1), float(n * n)]
+    res = qmpm.qmpm_scheme_solve(P, list(g), list(ref["lo"]), list(ref["hi"]), ref["z"], eps, kappa=kappa)
+    scheme, capped = {}, []
+    for h, name in enumerate(TYPES):
+        bits, frac, off = int(res["bits"][h]), int(res["frac"][h]), int(res["offset"][h])
+        if bits > max_bits:
+            drop = bits - max_bits
+            bits, frac, off = max_bits, frac - drop, off >> drop
+            capped.append(name)
+        scheme[name] = dict(bits=bits, frac=frac, offset=off)
+    bits_state = P[0] * scheme["v"]["bits"] + 32.0 * n * n
+    rep = {"z": ref["z"], "g": list(g), "g_se": list(se), "lo": list(ref["lo"]), "hi": list(ref["hi"]),
+           "solve": res, "capped": capped, "P": P,
+           "compression_state": (P[0] + n * n) * 32.0 / bits_state,
+           "compression_quantized": (P[0] + P[1]) * 32.0 / (P[0] * scheme["v"]["bits"] + P[1] * scheme["p"]["bits"])}
+    return scheme, rep

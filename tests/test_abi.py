@@ -10,12 +10,16 @@ import pytest
 
 from conftest import ROOT
 
-HEADER = os.path.join(ROOT, "include", "qmpm.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(qmpm_\w+)\s*\(", text, re.M)))
+    names = set()
+    for path in HEADERS:
+        text = open(path).read()
+        names |= set(re.findall(r"^\s*(?:int|const char \*)\s*(qmpm_\w+)\s*\(", text, re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
