@@ -49,7 +49,10 @@ typedef struct {
     float v_in;         /* inflow velocity inside the source box */
     float src[4];       /* source box x0, y0, x1, y1 in [0,1] */
     int32_t dither;     /* 1: dithered stores (Sec. 5), 0: round to nearest */
+    int32_t flags;      /* QMPM_SMOKE_RANGES: record the range of every type's stored values */
 } qmpm_smoke_config_t;
+
+#define QMPM_SMOKE_RANGES 1
 
 /* Type 0: velocity (u and v), type 1: pressure q.  value = (code + offset) * 2^-frac,
  * code in [0, 2^bits); bits 1 .. 24, |offset| < 2^24. */
@@ -75,7 +78,8 @@ typedef struct {
 
 /* Create a batch of n_scenes scenes (1 .. 4096) sharing config and scheme, all at rest
  * (u = v = d = 0).  scheme NULL: FP32 stores.  h_seeds: n_scenes dither seeds (host; NULL
- * = scene index).  stream: a cudaStream_t (NULL = legacy default stream).
+ * = scene index).  stream: a cudaStream_t (NULL: the handle creates its own, since a CUDA
+ * graph cannot capture the legacy stream).
  * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME, QMPM_ERR_OOM, QMPM_ERR_CUDA. */
 int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t *scheme, int32_t n_scenes,
                       const uint64_t *h_seeds, void *stream, qmpm_smoke_handle *out);
@@ -115,9 +119,10 @@ int qmpm_smoke_measure(qmpm_smoke_handle h, double *h_z);
  * QMPM_ERR_CUDA. */
 int qmpm_smoke_readback(qmpm_smoke_handle h, int32_t scene, float *h_u, float *h_v, float *h_d, float *h_q);
 
-/* Per scene and type, the smallest and largest value stored so far and the number of
- * saturated stores: h_lo, h_hi [n_scenes][2], h_sat [n_scenes][2] (any may be NULL).
- * Synchronises.  Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_CUDA. */
+/* Per scene and type, the smallest and largest value offered to a store so far (handles
+ * created with QMPM_SMOKE_RANGES; zeros otherwise) and the number of saturated stores:
+ * h_lo, h_hi [n_scenes][2], h_sat [n_scenes][2] (any may be NULL).  Synchronises.
+ * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_CUDA. */
 int qmpm_smoke_ranges(qmpm_smoke_handle h, float *h_lo, float *h_hi, int64_t *h_sat);
 
 int qmpm_smoke_info(qmpm_smoke_handle h, qmpm_smoke_info_t *out);

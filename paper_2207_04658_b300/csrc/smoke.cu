@@ -30,6 +30,7 @@ namespace qmpm {
 namespace smoke {
 
 constexpr int kT = 256;
+constexpr int kSlots = 64;   // range-recording slots per scene and type (spreads the atomics)
 
 struct Fld {
     uint32_t *p;   // scene 0's first word
@@ -40,7 +41,7 @@ struct Params {
     int n, J, su;              // su: padded row length of u (n + 32)
     float dt, buoy, v_in, inv_h, h, h2;
     double hd, src[4];
-    int quant, dither;
+    int quant, dither, ranges;
     CompCodec cc[2];           // 0 velocity, 1 pressure (word/shift unused)
     int bits[2];
     float sigma[2];
@@ -50,7 +51,7 @@ struct Params {
     const uint2 *seed, *nseed;
     const float *sign;
     unsigned long long *sat;   // [S][2]
-    unsigned int *lo, *hi;     // [S][2], order-preserving keys of floats
+    unsigned int *lo, *hi;     // [S][2][kSlots], order-preserving keys of floats
     double *z;
     uint32_t *ctr;             // steps done
 };
@@ -144,6 +145,18 @@ __device__ __forceinline__ void backtrace(const Params &P, const Lat &U, const L
     yb = y - s * (2.0f * k1y + 3.0f * k2y + 4.0f * k3y) / 9.0f;
 }
 
+// Warp-reduced range keys into one of the scene's slots (whole warp calls).
+__device__ __forceinline__ void record_range(const Params &P, int s, int type, unsigned kmin, unsigned kmax)
+{
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if ((threadIdx.x & 31) == 0) {
+        const int64_t slot = ((int64_t)s * 2 + type) * kSlots + ((blockIdx.x * (kT / 32) + (threadIdx.x >> 5)) & (kSlots - 1));
+        if (kmin != 0xffffffffu) atomicMin(P.lo + slot, kmin);
+        if (kmax != 0u) atomicMax(P.hi + slot, kmax);
+    }
+}
+
 // ---- the store ------------------------------------------------------------------------
 // Called by every lane of a warp (valid = the lane holds a real sample).  Quantized: encode
 // (dithered or nearest), count saturations, write the code to the packed stream and to the
@@ -182,12 +195,7 @@ __device__ __forceinline__ float store(const Params &P, int s, int type, int fie
         }
         if (valid) out[pidx] = __float_as_uint(y);
     }
-    const unsigned kmin = __reduce_min_sync(full, valid ? fkey(x) : 0xffffffffu);
-    const unsigned kmax = __reduce_max_sync(full, valid ? fkey(x) : 0u);
-    if ((threadIdx.x & 31) == 0) {
-        if (kmin != 0xffffffffu) atomicMin(P.lo + 2 * s + type, kmin);
-        if (kmax != 0u) atomicMax(P.hi + 2 * s + type, kmax);
-    }
+    if (P.ranges) record_range(P, s, type, valid ? fkey(x) : 0xffffffffu, valid ? fkey(x) : 0u);
     return y;
 }
 
@@ -287,31 +295,120 @@ __global__ void __launch_bounds__(kT) divergence_kernel(Params P, int which)  //
 }
 
 // Sweep it (1-based) of a projection: reads q[(it - 1) & 1] (zero for it = 1), writes
-// q[it & 1]; store counter base + it.
+// q[it & 1]; store counter base + it.  A thread takes an octet, 8 consecutive cells of a
+// row (n is a multiple of 32, so an octet never crosses a row), and draws one Philox block
+// for all 8 (their dither counter is (cell / 8, counter, 2, 0), lanes cell % 8).  The warp's 256 codes are
+// staged in shared memory and packed into its 8 * bits words by the lanes in turn.
 template <bool Q>
-__global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it, uint32_t cbase, uint32_t *trace)
+__global__ void __launch_bounds__(kT) jacobi8_kernel(Params P, int it, uint32_t cbase, uint32_t *trace)
 {
-    const int s = blockIdx.y, n = P.n;
-    const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
-    if (t - (threadIdx.x & 31) >= (int64_t)n * n) return;
-    const bool valid = t < (int64_t)n * n;
-    const int i = valid ? (int)(t % n) : 0, j = valid ? (int)(t / n) : 0;
+    __shared__ uint32_t stage[kT * 8];
+    const int s = blockIdx.y, n = P.n, lane = threadIdx.x & 31;
+    const int64_t nc = (int64_t)n * n;
+    const int64_t o = (int64_t)blockIdx.x * kT + threadIdx.x;
+    const int64_t t0 = o * 8;
+    if (t0 - (int64_t)lane * 8 >= nc) return;  // whole warps (n^2 / 8 is a multiple of 32)
+    const int i0 = (int)(t0 % n), j = (int)(t0 / n);
     const uint32_t *qi = P.q[(it - 1) & 1].p + s * P.q[0].ss;
     const CompCodec &c = P.cc[1];
     const int b = P.bits[1];
-    float acc = 0.0f;
-    int cnt = 0;
+    const float4 *dv4 = reinterpret_cast<const float4 *>(P.div + s * P.ncell_s + t0);
+    const float4 da = dv4[0], db = dv4[1];
+    const float dv[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
+    float x[8];
     if (it > 1) {
-        if (i > 0) { acc += ld<Q>(qi, (int64_t)j * n + i - 1, c, b); ++cnt; }
-        if (i < n - 1) { acc += ld<Q>(qi, (int64_t)j * n + i + 1, c, b); ++cnt; }
-        if (j > 0) { acc += ld<Q>(qi, (int64_t)(j - 1) * n + i, c, b); ++cnt; }
-        if (j < n - 1) { acc += ld<Q>(qi, (int64_t)(j + 1) * n + i, c, b); ++cnt; }
+        float row[10], dn[8], up[8];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            const int ii = i0 - 1 + k;
+            row[k] = (ii >= 0 && ii < n) ? ld<Q>(qi, (int64_t)j * n + ii, c, b) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            dn[k] = j > 0 ? ld<Q>(qi, (int64_t)(j - 1) * n + i0 + k, c, b) : 0.0f;
+            up[k] = j < n - 1 ? ld<Q>(qi, (int64_t)(j + 1) * n + i0 + k, c, b) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k;
+            float acc = 0.0f;
+            int cnt = 0;
+            if (i > 0) { acc += row[k]; ++cnt; }
+            if (i < n - 1) { acc += row[k + 2]; ++cnt; }
+            if (j > 0) { acc += dn[k]; ++cnt; }
+            if (j < n - 1) { acc += up[k]; ++cnt; }
+            x[k] = (acc - P.h2 * dv[k]) / (float)cnt;
+        }
     } else {
-        cnt = (i > 0) + (i < n - 1) + (j > 0) + (j < n - 1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k;
+            const int cnt = (i > 0) + (i < n - 1) + (j > 0) + (j < n - 1);
+            x[k] = (0.0f - P.h2 * dv[k]) / (float)cnt;
+        }
     }
-    const float x = valid ? (acc - P.h2 * P.div[s * P.ncell_s + t]) / (float)cnt : 0.0f;
     const uint32_t counter = 1024u * step_index(P) + cbase + (uint32_t)it;
-    store<Q>(P, s, 1, 2, x, (uint32_t)t, counter, valid, false, true, P.q[it & 1].p + s * P.q[0].ss, t, trace);
+    uint32_t *qo = P.q[it & 1].p + s * P.q[0].ss;
+    if (P.ranges) {
+        unsigned kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            kmin = min(kmin, fkey(x[k]));
+            kmax = max(kmax, fkey(x[k]));
+        }
+        record_range(P, s, 1, kmin, kmax);
+    }
+    if (Q) {
+        uint4 blk = make_uint4(0u, 0u, 0u, 0u);
+        if (P.dither) {
+            const uint2 key = P.seed[s];
+            blk = philox4x32_10(make_uint4((uint32_t)o, counter, 2u, 0u), key.x, key.y);
+        }
+        uint32_t code[8];
+        int nsat = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int flags = 0;
+            code[k] = encode_f32(x[k], c, P.dither != 0, P.dither ? dither_threshold(blk, k) : 0u, flags);
+            nsat += flags & 1;
+        }
+        nsat = __reduce_add_sync(0xffffffffu, nsat);
+        if (nsat && lane == 0) atomicAdd(P.sat + 2 * s + 1, (unsigned long long)nsat);
+        if (trace && s == 0) {
+            uint4 *tw = reinterpret_cast<uint4 *>(trace + t0);
+            tw[0] = make_uint4(code[0], code[1], code[2], code[3]);
+            tw[1] = make_uint4(code[4], code[5], code[6], code[7]);
+        }
+        uint32_t *st = stage + (threadIdx.x >> 5) * 256;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) st[lane * 8 + k] = code[k];
+        __syncwarp();
+        uint32_t *ow = qo + (t0 - (int64_t)lane * 8) / 32 * b;
+        for (int w = lane; w < 8 * b; w += 32) {
+            const int b0 = 32 * w, m1 = min((b0 + 31) / b, 255);
+            uint32_t word = 0u;
+            for (int m = b0 / b; m <= m1; ++m) {
+                const int sh = m * b - b0;
+                word |= sh >= 0 ? (st[m] << sh) : (st[m] >> -sh);
+            }
+            ow[w] = word;
+        }
+    } else {
+        if (P.sigma[1] != 0.0f) {
+            const uint2 key = P.nseed[s];
+            const uint4 blk = philox4x32_10(make_uint4((uint32_t)o, counter, 2u, 0u), key.x, key.y);
+            const float amp = P.sign[s] * P.sigma[1];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t w = uint4_at(blk, (k >> 1) & 3);
+                const uint32_t q16 = (k & 1) ? (w >> 16) : (w & 0xFFFFu);
+                x[k] += amp * ((q16 & 0x8000u) ? 1.0f : -1.0f);
+            }
+        }
+        float4 *qw = reinterpret_cast<float4 *>(qo + t0);
+        qw[0] = make_float4(x[0], x[1], x[2], x[3]);
+        qw[1] = make_float4(x[4], x[5], x[6], x[7]);
+    }
 }
 
 // out = in - grad q on interior faces (q = the last sweep's iterate; none when J = 0), then
@@ -532,19 +629,20 @@ int enqueue_step(qmpm_smoke *h, uint32_t *trace)
     const int64_t nfaces = (int64_t)n * P.su + (int64_t)(n + 1) * n;
     const dim3 gf((unsigned)((nfaces + kT - 1) / kT), S);
     const dim3 gc((unsigned)(((int64_t)n * n + kT - 1) / kT), S);
+    const dim3 g8((unsigned)(((int64_t)n * n / 8 + kT - 1) / kT), S);
     const dim3 gv((unsigned)(((int64_t)(n + 1) * n + kT - 1) / kT), S);
     const int64_t V = 2 * (int64_t)n * (n + 1), Pq = (int64_t)n * n;
     auto tr = [&](int64_t off) { return trace ? trace + off : nullptr; };
     forces_kernel<Q><<<gv, kT, 0, h->st>>>(P);
     advect_vel_kernel<Q, 1><<<gf, kT, 0, h->st>>>(P, tr(0));
     divergence_kernel<Q><<<gc, kT, 0, h->st>>>(P, 0);
-    for (int it = 1; it <= J; ++it) jacobi_kernel<Q><<<gc, kT, 0, h->st>>>(P, it, 1u, tr(V + (it - 1) * Pq));
+    for (int it = 1; it <= J; ++it) jacobi8_kernel<Q><<<g8, kT, 0, h->st>>>(P, it, 1u, tr(V + (it - 1) * Pq));
     gradsub_kernel<Q, 2><<<gf, kT, 0, h->st>>>(P, tr(V + J * Pq));
     reflect_kernel<Q><<<gf, kT, 0, h->st>>>(P, tr(2 * V + J * Pq));
     advect_vel_kernel<Q, 4><<<gf, kT, 0, h->st>>>(P, tr(3 * V + J * Pq));
     divergence_kernel<Q><<<gc, kT, 0, h->st>>>(P, 1);
     for (int it = 1; it <= J; ++it)
-        jacobi_kernel<Q><<<gc, kT, 0, h->st>>>(P, it, (uint32_t)J + 4u, tr(4 * V + (J + it - 1) * Pq));
+        jacobi8_kernel<Q><<<g8, kT, 0, h->st>>>(P, it, (uint32_t)J + 4u, tr(4 * V + (J + it - 1) * Pq));
     gradsub_kernel<Q, 5><<<gf, kT, 0, h->st>>>(P, tr(4 * V + 2 * J * Pq));
     advect_d_kernel<Q><<<gc, kT, 0, h->st>>>(P);
     advance_kernel<<<1, 1, 0, h->st>>>(P.ctr);
@@ -604,6 +702,7 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
     for (int k = 0; k < 4; ++k) P.src[k] = cfg->src[k];
     P.quant = h->quant;
     P.dither = h->quant && cfg->dither;
+    P.ranges = (cfg->flags & QMPM_SMOKE_RANGES) != 0;
     P.bits[0] = P.bits[1] = 32;
     if (h->quant) {
         for (int t = 0; t < 2; ++t) {
@@ -650,8 +749,8 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
     uint2 *nseeds = (uint2 *)alloc(sizeof(uint2) * S);
     float *signs = (float *)alloc(sizeof(float) * S);
     P.sat = (unsigned long long *)alloc(sizeof(unsigned long long) * 2 * S);
-    P.lo = (unsigned int *)alloc(sizeof(unsigned int) * 2 * S);
-    P.hi = (unsigned int *)alloc(sizeof(unsigned int) * 2 * S);
+    P.lo = (unsigned int *)alloc(sizeof(unsigned int) * 2 * kSlots * S);
+    P.hi = (unsigned int *)alloc(sizeof(unsigned int) * 2 * kSlots * S);
     P.z = (double *)alloc(sizeof(double) * S);
     P.ctr = (uint32_t *)alloc(sizeof(uint32_t));
     h->stage_floats = 2 * nv + 2 * nc + 64;
@@ -668,13 +767,14 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
         const uint64_t v = h_seeds ? h_seeds[s] : (uint64_t)s;
         hs[s] = make_uint2((uint32_t)v, (uint32_t)(v >> 32));
     }
-    std::vector<unsigned int> lo(2 * S, 0xffffffffu);
+    std::vector<unsigned int> lo(2 * kSlots * S, 0xffffffffu);
     cudaError_t e = cudaMemcpyAsync(seeds, hs.data(), sizeof(uint2) * S, cudaMemcpyHostToDevice, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(nseeds, 0, sizeof(uint2) * S, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(signs, 0, sizeof(float) * S, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P.sat, 0, sizeof(unsigned long long) * 2 * S, h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(P.lo, lo.data(), sizeof(unsigned int) * 2 * S, cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P.hi, 0, sizeof(unsigned int) * 2 * S, h->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P.lo, lo.data(), sizeof(unsigned int) * 2 * kSlots * S, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.hi, 0, sizeof(unsigned int) * 2 * kSlots * S, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P.ctr, 0, sizeof(uint32_t), h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
@@ -830,10 +930,12 @@ int qmpm_smoke_ranges(qmpm_smoke_handle h, float *h_lo, float *h_hi, int64_t *h_
 {
     if (!h) return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_ranges: NULL handle");
     const int S = h->S;
-    std::vector<unsigned int> lo(2 * S), hi(2 * S);
+    std::vector<unsigned int> lo(2 * kSlots * S), hi(2 * kSlots * S);
     std::vector<unsigned long long> sat(2 * S);
-    cudaError_t e = cudaMemcpyAsync(lo.data(), h->p.lo, sizeof(unsigned) * 2 * S, cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hi.data(), h->p.hi, sizeof(unsigned) * 2 * S, cudaMemcpyDeviceToHost, h->st);
+    cudaError_t e =
+        cudaMemcpyAsync(lo.data(), h->p.lo, sizeof(unsigned) * 2 * kSlots * S, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hi.data(), h->p.hi, sizeof(unsigned) * 2 * kSlots * S, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sat.data(), h->p.sat, sizeof(unsigned long long) * 2 * S, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -845,8 +947,13 @@ int qmpm_smoke_ranges(qmpm_smoke_handle h, float *h_lo, float *h_hi, int64_t *h_
         return f;
     };
     for (int i = 0; i < 2 * S; ++i) {
-        if (h_lo) h_lo[i] = lo[i] == 0xffffffffu ? 0.0f : unkey(lo[i]);
-        if (h_hi) h_hi[i] = hi[i] == 0u ? 0.0f : unkey(hi[i]);
+        unsigned kl = 0xffffffffu, kh = 0u;
+        for (int k = 0; k < kSlots; ++k) {
+            kl = std::min(kl, lo[(int64_t)i * kSlots + k]);
+            kh = std::max(kh, hi[(int64_t)i * kSlots + k]);
+        }
+        if (h_lo) h_lo[i] = kl == 0xffffffffu ? 0.0f : unkey(kl);
+        if (h_hi) h_hi[i] = kh == 0u ? 0.0f : unkey(kh);
         if (h_sat) h_sat[i] = (int64_t)sat[i];
     }
     return QMPM_OK;

@@ -230,3 +230,14 @@ def serving_requests(rate=20.0, duration=15.0, seed=5, n_min=1e4, n_max=4e6):
         eps = SERVING_EPS[int(gen.integers(0, len(SERVING_EPS)))]
         out.append(dict(t=t, dim=dim, material=material, n=n, grid_log2=grids[gi], eps=eps,
                         seed=int(gen.integers(1, 2 ** 31))))
+
+
+# ------------------------------------------------------------------------------ smoke
+def smoke_scene(n=256, jacobi=64, steps=100, seed=7):
+    """The 2D smoke plume of the error-bounded experiment (Sec. 8.1: 256^2 grid, dt 0.01,
+    RK-3 advection, 64 Jacobi sweeps, z = sum of squared density): a source box at the
+    bottom centre (density 1, inflow 1) with buoyancy 1, run for `steps` steps from rest.
+    The paper prints neither the source nor the step count; this plume reaches the top of
+    the box within the run and gives z of the order of the paper's (about 2e4)."""
+    return dict(n=n, jacobi=jacobi, dt=0.01, buoyancy=1.0, v_in=1.0, src=(0.35, 0.05, 0.65, 0.12), seed=seed,
+                steps=steps)

@@ -16,6 +16,7 @@ from . import qmpm
 from .qmpm import _check, _dptr, lib
 
 TYPES = ("v", "p")
+RANGES = 1  # QMPM_SMOKE_RANGES
 
 
 def make_config(scene):
@@ -28,6 +29,7 @@ def make_config(scene):
     for k, x in enumerate(scene.get("src", (1.0, 1.0, -1.0, -1.0))):
         c.src[k] = float(x)
     c.dither = int(bool(scene.get("dither", True)))
+    c.flags = RANGES if scene.get("ranges", False) else 0
     return c
 
 
@@ -133,7 +135,7 @@ class Smoke:
 
 def reference(scene, T, state=None):
     """FP32 run of one scene: z, the per-type value ranges of every store, and the state."""
-    with Smoke(scene, None, 1) as s:
+    with Smoke(dict(scene, ranges=True), None, 1) as s:
         if state is not None:
             s.set_state(*state)
         s.step(T)
@@ -142,7 +144,7 @@ def reference(scene, T, state=None):
         return {"z": z, "lo": lo[0].astype(float), "hi": hi[0].astype(float), "state": s.readback(0)}
 
 
-def sensitivities(scene, T, pairs=32, sigma=(1e-4, 1e-6), seed=0, state=None):
+def sensitivities(scene, T, pairs=32, sigma=(3e-3, 3e-5), seed=0, state=None):
     """Eq. 8's g_h = sum over the stores of type h of (dz/dstore)^2, for h = velocity,
     pressure, by antithetic noise injection: scenes 2k and 2k+1 of a batch get the same
     +-sigma_h noise at every store of type h with opposite signs, and
@@ -168,7 +170,7 @@ def sensitivities(scene, T, pairs=32, sigma=(1e-4, 1e-6), seed=0, state=None):
     return g, se, per
 
 
-def solve(scene, T, eps, pairs=32, sigma=(1e-4, 1e-6), kappa=2.0, state=None, max_bits=24):
+def solve(scene, T, eps, pairs=32, sigma=(3e-3, 3e-5), kappa=2.0, state=None, max_bits=24):
     """Scheme for the error bound eps on z (Algorithm 1 with the recorded ranges widened by
     kappa about their midpoint, Sec. 3.1).  Returns (scheme dict, report)."""
     n = int(scene["n"])
@@ -190,3 +192,40 @@ def solve(scene, T, eps, pairs=32, sigma=(1e-4, 1e-6), kappa=2.0, state=None, ma
            "compression_state": (P[0] + n * n) * 32.0 / bits_state,
            "compression_quantized": (P[0] + P[1]) * 32.0 / (P[0] * scheme["v"]["bits"] + P[1] * scheme["p"]["bits"])}
     return scheme, rep
+
+
+def error_bound_protocol(scene, T, eps_list, runs=20, z_ref=None, pairs=32, seed0=1000):
+    """The error-bounded experiment of Sec. 8.1 on the smoke: per eps, the scheme Algorithm 1
+    solves from the noise-injection sensitivities and the FP32 run's ranges, then `runs`
+    quantized runs (one batch, dither seeds seed0 + r); success = |z~ - z| <= 3 eps z."""
+    n = int(scene["n"])
+    ref = reference(scene, T)
+    z0 = ref["z"] if z_ref is None else z_ref
+    g, se, _ = sensitivities(scene, T, pairs)
+    P = [2.0 * n * (n + 1), float(n * n)]
+    out = []
+    for eps in eps_list:
+        res = qmpm.qmpm_scheme_solve(P, list(g), list(ref["lo"]), list(ref["hi"]), ref["z"], eps, kappa=2.0)
+        scheme = {name: dict(bits=min(int(res["bits"][h]), 24), frac=int(res["frac"][h]) - max(0, int(res["bits"][h]) - 24),
+                             offset=int(res["offset"][h]) >> max(0, int(res["bits"][h]) - 24))
+                  for h, name in enumerate(TYPES)}
+        with Smoke(scene, scheme, runs, seeds=[seed0 + r for r in range(runs)]) as s:
+            s.step(T)
+            zs = s.measure()
+            _, _, sat = s.ranges()
+        dev = zs - z0
+        bits = [scheme["v"]["bits"], scheme["p"]["bits"]]
+        pred12 = float(sum(2.0 ** (-2 * scheme[t]["frac"]) * g[h] for h, t in enumerate(TYPES)) / 12.0)
+        out.append({
+            "eps": eps, "bits": bits, "frac": [scheme["v"]["frac"], scheme["p"]["frac"]],
+            "bits_paper": [int(b) for b in res["bits_paper"]],
+            "pred_sigma": float(np.sqrt(pred12)), "pred_sigma_dither": float(np.sqrt(2 * pred12)),
+            "obs_rms": float(np.sqrt(np.mean(dev ** 2))), "bias": float(dev.mean()),
+            "z_ref": z0, "z_mean": float(zs.mean()), "z_std": float(zs.std(ddof=1)) if runs > 1 else 0.0,
+            "success_3eps": float(np.mean(np.abs(dev) <= 3 * eps * abs(z0))),
+            "success_eps": float(np.mean(np.abs(dev) <= eps * abs(z0))),
+            "saturations": int(sat.sum()),
+            "compression": 3 * 32.0 / (2 * bits[0] + bits[1]), "runs": runs,
+        })
+    return {"z_ref": z0, "g": list(g), "g_se": list(se), "lo": list(ref["lo"]), "hi": list(ref["hi"]),
+            "results": out}

@@ -13,7 +13,7 @@ Everything runs through the library (adjoint, solve, rollouts).  The reference z
 supplied by the caller (the FP64 oracle in the tests); the command line uses the FP32 run
 of the same kernels.
 
-    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300]
+    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300] [--smoke]
 """
 import argparse
 import json
@@ -69,7 +69,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", type=int, default=20)
     ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--smoke", action="store_true", help="the 2D smoke plume instead of the MPM block")
     args = ap.parse_args()
+    if args.smoke:
+        from . import smoke
+        sc = scenes.smoke_scene()
+        res = smoke.error_bound_protocol(sc, sc["steps"], [0.1, 0.01, 1e-3, 1e-4], args.runs)
+        print(json.dumps({"scene": "2D smoke plume, 256^2, 64 Jacobi sweeps, 100 steps",
+                          "reference": "FP32 run of the same kernels", **res}))
+        return
     sc, s0 = impact_block()
     g = qmpm.Scene(sc, None, s0)
     g.step(args.steps)

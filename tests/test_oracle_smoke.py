@@ -263,3 +263,26 @@ def test_follow_accepts_own_codes_and_rejects_far_changes(oracle):
     with oracle.smoke_follow(bad2, 1.0, 1.0) as f:
         other.step(T)
     assert f.report[2] >= 1
+
+
+def test_antithetic_noise_estimates_the_sensitivities(oracle):
+    """E[((z+ - z-) / 2)^2] / sigma_h^2 over random +-sigma_h injections at every store of
+    type h is g_h (the FD sum over the same stores): the estimator the kernels use."""
+    sc, T = plume(n=12, jacobi=8, T=2)
+    state = generic_state(12)
+    G = fd_sensitivities(oracle, sc, T, state)
+    pairs = 300
+    for h, sigma in ((0, (1e-5, 0.0)), (1, (0.0, 1e-5))):
+        est = []
+        for k in range(pairs):
+            zs = []
+            for sign in (1.0, -1.0):
+                with oracle.smoke_noise(sigma, 1 + k, sign):
+                    r = oracle.SmokeRollout(sc, None, *state)
+                    r.step(T)
+                zs.append(r.measure())
+            est.append(((zs[0] - zs[1]) / 2) ** 2 / sigma[h] ** 2)
+        est = np.array(est)
+        se = est.std(ddof=1) / np.sqrt(pairs)
+        assert abs(est.mean() - G[h]) < 4 * se, (h, est.mean(), G[h], se)
+        assert se < 0.15 * G[h]
