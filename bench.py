@@ -38,7 +38,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cubes3d", choices=["cubes3d", "dambreak3d", "block2d"])
+    ap.add_argument("--workload", default="cubes3d", choices=["cubes3d", "dambreak3d", "block2d", "smoke"],
+                    help="smoke: the quantized 2D smoke batch alone (its own JSON line)")
+    ap.add_argument("--no-smoke", action="store_true", help="leave the smoke section out of the MPM line")
+    ap.add_argument("--smoke-scenes", type=int, default=64)
+    ap.add_argument("--smoke-fixed-scheme", action="store_true",
+                    help="the smoke's eps 1e-3 scheme as written down instead of solved in the run")
+    ap.add_argument("--no-smoke-validation", action="store_true", help="skip the smoke error-bound protocol")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -328,6 +334,159 @@ def cpu_baseline(name, sample_steps=2):
             "sample": sample}
 
 
+# ------------------------------------------------------------------------------ smoke
+SMOKE_METRIC = "quantized 2D smoke cell-steps/s (advection-reflection, 64 Jacobi sweeps per projection)"
+SMOKE_UNIT = "cell-steps/s"
+SMOKE_FIXED_SCHEME = {"v": dict(bits=10, frac=7, offset=-512), "p": dict(bits=9, frac=13, offset=-256)}
+
+
+def smoke_counters():
+    """Warp instructions and DRAM bytes per Jacobi launch from the committed ncu summary,
+    or (None, None) when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "smoke_jacobi_counters.json")
+    if not os.path.exists(path):
+        return None, None, None
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_2207_04658_b300", "csrc", "smoke.cu"), "rb").read()
+        if rec.get("smoke_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None, None, None
+        return rec["warp_instructions_per_launch"], rec["dram_bytes_per_launch"], rec
+    except Exception:
+        return None, None, None
+
+
+def smoke_section(args, peaks, dc, torch):
+    """The quantized smoke batch (Sec. 8.1's 2D advection-reflection workload): S scenes of
+    the 256^2 plume stepped together by one CUDA graph per step; the scheme Algorithm 1
+    solves at eps 1e-3 from noise-injection sensitivities.  Device-timed throughput
+    (quantized and FP32), the Jacobi kernel against the issue peak, an end-to-end rollout
+    from host state, and the error-bound protocol at eps 1e-2 and 1e-3 (20 dither seeds)."""
+    from paper_2207_04658_b300 import scenes, smoke
+    sc = scenes.smoke_scene()
+    T = sc["steps"]
+    S = args.smoke_scenes
+    n = sc["n"]
+    if args.smoke_fixed_scheme:
+        scheme = SMOKE_FIXED_SCHEME
+        source = "written down: the solve's eps 1e-3 result on this scene (bits 10/9, frac 7/13)"
+    else:
+        scheme, rep = smoke.solve(sc, T, 1e-3)
+        source = ("qmpm_scheme_solve at eps 1e-3 on z = sum d^2 after 100 steps, noise-injection "
+                  "sensitivities (32 antithetic pairs per type)")
+    steps = max(10, min(args.steps, 200))
+    warm = max(3, args.warmup)
+    st = torch.cuda.Stream()
+    out = {"config": {"workload": "2D smoke plume batch", "scenes": S, "grid": f"{n}^2", "jacobi": sc["jacobi"],
+                      "dt": sc["dt"], "rollout_steps": T, "scheme": scheme,
+                      "scheme_source": source,
+                      "l2": "L2-resident working set (packed state "
+                            f"{S * (2 * n * (n + 1) * scheme['v']['bits'] / 8 + 4 * n * n) / 1e6:.0f} MB)"}}
+    for name, sch in (("quant", scheme), ("fp32", None)):
+        with smoke.Smoke(sc, sch, S, seeds=list(range(S)), stream=st.cuda_stream) as g:
+            g.step(warm)
+            torch.cuda.synchronize()
+            dc.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            g.step(steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = dc.max(torch, e0.elapsed_time(e1))
+            info = g.info()
+        out[name] = {"value": dc.world * S * n * n * steps / (ms / 1e3), "unit": SMOKE_UNIT,
+                     "ms_per_step": ms / steps, "state_bytes_per_scene": info["state_bytes"],
+                     "launches_per_step": info["launches_per_step"]}
+    out["value"] = out["quant"]["value"]
+    out["quantized_over_fp32"] = round(out["quant"]["value"] / out["fp32"]["value"], 4)
+    out["gpu_launches"] = out["quant"]["launches_per_step"] * steps
+    # the Jacobi sweeps, timed by events around their launches
+    with smoke.Smoke(dict(sc, profile=True), scheme, S, seeds=list(range(S)), stream=st.cuda_stream) as g:
+        g.step(warm)
+        g.profile()
+        g.step(steps)
+        prof = g.profile()
+    jac_ms = prof["jacobi_ms"] / max(1, prof["jacobi_launches"])
+    winst, dram, rec = smoke_counters()
+    ipk = issue_peak(peaks)
+    roof = {"kernel": "jacobi_kernel (4 dithered pressure sweeps per launch, shared-memory tiles)",
+            "avg_launch_ms": round(jac_ms, 5), "share_of_step": round(prof["jacobi_ms"] / prof["step_ms"], 3),
+            "bound": "alu", "peak": round(ipk / 1e9, 2), "unit": "G warp-instructions/s",
+            "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clk x max SM clock"}
+    if winst is not None:
+        f = S / rec["scenes"] if rec.get("n") == n else None
+        if f is not None:
+            ach = winst * f / (jac_ms / 1e3)
+            roof.update({"achieved": round(ach / 1e9, 2), "frac": round(ach / ipk, 4), "traffic": dram * f,
+                         "warp_instructions_per_launch": winst * f})
+    if "achieved" not in roof:
+        roof.update({"achieved": None, "frac": None, "traffic": None})
+    out["roofline"] = roof
+    # end to end: state from host memory, a full rollout, z back to the host
+    u0 = np.zeros((n, n + 1), np.float32)
+    v0 = np.zeros((n + 1, n), np.float32)
+    d0 = np.zeros((n, n), np.float32)
+    with smoke.Smoke(sc, scheme, S, seeds=list(range(S)), stream=st.cuda_stream) as g:
+        g.set_state(u0, v0, d0)
+        g.step(warm)
+        g.measure()
+        t = time.perf_counter()
+        g.set_state(u0, v0, d0)
+        g.step(T)
+        z = g.measure()
+        el = dc.max(torch, time.perf_counter() - t)
+    out["e2e"] = {"value": dc.world * S * n * n * T / el, "unit": SMOKE_UNIT,
+                  "h2d_bytes_per_step": (u0.nbytes + v0.nbytes + d0.nbytes) / T, "d2h_bytes_per_step": 8 * S / T,
+                  "path": "qmpm_smoke_set_state from host arrays, 100-step rollout of the batch, z to the host"}
+    if dc.rank == 0 and not args.no_smoke_validation:
+        res = smoke.error_bound_protocol(sc, T, [1e-2, 1e-3], runs=20)
+        out["error_bound"] = [{k: r[k] for k in ("eps", "bits", "frac", "pred_sigma_dither", "obs_rms", "bias",
+                                                 "z_std", "success_3eps", "compression")} for r in res["results"]]
+        out["error_bound_z_ref"] = res["z_ref"]
+    return out
+
+
+def smoke_cpu_baseline(steps=3):
+    """The smoke oracle (single-threaded FP64 C, quantized stores) on one 256^2 scene."""
+    import oracle
+    from paper_2207_04658_b300 import scenes
+    sc = scenes.smoke_scene()
+    sch = {"v": dict(bits=16, frac=12, offset=-(1 << 15)), "p": dict(bits=16, frac=18, offset=-(1 << 15))}
+    ro = oracle.SmokeRollout(sc, sch)
+    t = time.perf_counter()
+    ro.step(steps)
+    el = time.perf_counter() - t
+    return {"value": sc["n"] ** 2 * steps / el, "unit": SMOKE_UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one 256^2 scene of the batch, {steps} quantized steps"}
+
+
+def run_smoke(args):
+    import torch
+    from paper_2207_04658_b300 import build
+    build.build()
+    dc = DistCtx()
+    dc.init(torch)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    clocks = ClockSampler(dc.local)
+    clocks.start()
+    sm = smoke_section(args, peaks, dc, torch)
+    clk = clocks.stop()
+    line = {"metric": SMOKE_METRIC, "value": sm["value"], "unit": SMOKE_UNIT, "n_gpus": dc.world,
+            "steps": max(10, min(args.steps, 200)), "warmup": max(3, args.warmup),
+            "ms_per_step": sm["quant"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "gpu_launches": sm["gpu_launches"],
+            "config": dict(sm["config"], parallelism=f"replicas{dc.world}"), "roofline": sm["roofline"],
+            "clocks": clk, "e2e": sm["e2e"], "fp32": sm["fp32"], "quantized_over_fp32": sm["quantized_over_fp32"]}
+    if "error_bound" in sm:
+        line["error_bound"] = sm["error_bound"]
+    if dc.rank == 0 and dc.world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = smoke_cpu_baseline()
+    if dc.rank == 0:
+        print(json.dumps(line), flush=True)
+    dc.close()
+
+
 def DistCtx():
     from paper_2207_04658_b300.replicas import Replicas
     return Replicas()
@@ -444,6 +603,8 @@ def run_ours(args):
         line["accuracy"] = accuracy(qmpm, sc, s0, sch)
     if args.serving_duration > 0:
         line["serving"] = serving(qmpm, args.serving_duration, dc=dc)
+    if not args.no_smoke:
+        line["smoke"] = smoke_section(args, peaks, dc, torch)
     if dc.rank == 0 and dc.world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if dc.rank == 0:
@@ -456,6 +617,17 @@ def run_reference(args):
     bounded sample of the same workload, each step one quantized oracle step."""
     dc = DistCtx()
     if dc.rank != 0:
+        return
+    if args.workload == "smoke":
+        b = smoke_cpu_baseline(max(1, min(args.steps, 20)))
+        line = {"impl": "reference", "metric": SMOKE_METRIC, "value": b["value"], "unit": SMOKE_UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 256 * 256 / b["value"] * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "2D smoke plume batch", "grid": "256^2", "jacobi": 64},
+                "cpu_baseline": b, "e2e": {"value": b["value"], "unit": SMOKE_UNIT, "h2d_bytes_per_step": 0,
+                                           "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     import oracle
     sc, s0, sch, desc = workload(args.workload, args.scale)
@@ -480,5 +652,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "smoke":
+        run_smoke(a)
     else:
         run_ours(a)

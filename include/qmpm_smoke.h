@@ -49,10 +49,12 @@ typedef struct {
     float v_in;         /* inflow velocity inside the source box */
     float src[4];       /* source box x0, y0, x1, y1 in [0,1] */
     int32_t dither;     /* 1: dithered stores (Sec. 5), 0: round to nearest */
-    int32_t flags;      /* QMPM_SMOKE_RANGES: record the range of every type's stored values */
+    int32_t flags;      /* QMPM_SMOKE_RANGES: record the range of every type's stored values;
+                           QMPM_SMOKE_PROFILE: time the Jacobi sweeps (qmpm_smoke_profile) */
 } qmpm_smoke_config_t;
 
 #define QMPM_SMOKE_RANGES 1
+#define QMPM_SMOKE_PROFILE 2  /* plain launches with CUDA events around the Jacobi sweeps */
 
 /* Type 0: velocity (u and v), type 1: pressure q.  value = (code + offset) * 2^-frac,
  * code in [0, 2^bits); bits 1 .. 24, |offset| < 2^24. */
@@ -126,6 +128,12 @@ int qmpm_smoke_readback(qmpm_smoke_handle h, int32_t scene, float *h_u, float *h
 int qmpm_smoke_ranges(qmpm_smoke_handle h, float *h_lo, float *h_hi, int64_t *h_sat);
 
 int qmpm_smoke_info(qmpm_smoke_handle h, qmpm_smoke_info_t *out);
+
+/* Handles created with QMPM_SMOKE_PROFILE: device time of the steps run since the last
+ * call (h_step_ms), of their Jacobi sweep launches (h_jacobi_ms) and the number of those
+ * launches; resets.  Synchronises.  Errors: QMPM_ERR_INVALID_ARG (no profile flag),
+ * QMPM_ERR_CUDA. */
+int qmpm_smoke_profile(qmpm_smoke_handle h, double *h_step_ms, double *h_jacobi_ms, int64_t *h_jacobi_launches);
 
 /* Free everything the handle holds (synchronises its stream).  NULL is a no-op. */
 int qmpm_smoke_destroy(qmpm_smoke_handle h);

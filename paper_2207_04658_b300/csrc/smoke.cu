@@ -31,6 +31,7 @@ namespace smoke {
 
 constexpr int kT = 256;
 constexpr int kSlots = 64;   // range-recording slots per scene and type (spreads the atomics)
+constexpr int kMeasureBlocks = 64;  // blocks per scene of the z reduction
 
 struct Fld {
     uint32_t *p;   // scene 0's first word
@@ -39,8 +40,9 @@ struct Fld {
 
 struct Params {
     int n, J, su;              // su: padded row length of u (n + 32)
+    int qfin;                  // buffer holding a projection's last iterate
     float dt, buoy, v_in, inv_h, h, h2;
-    double hd, src[4];
+    int box[6];                // source box as index ranges (inclusive): cell x, cell y, v-face y
     int quant, dither, ranges;
     CompCodec cc[2];           // 0 velocity, 1 pressure (word/shift unused)
     int bits[2];
@@ -52,7 +54,7 @@ struct Params {
     const float *sign;
     unsigned long long *sat;   // [S][2]
     unsigned int *lo, *hi;     // [S][2][kSlots], order-preserving keys of floats
-    double *z;
+    double *z;                 // [S][kMeasureBlocks] partial sums of d^2
     uint32_t *ctr;             // steps done
 };
 
@@ -93,6 +95,41 @@ __device__ __forceinline__ float ld(const uint32_t *f, int64_t pidx, const CompC
 {
     if (PK) return decode_u(get_code(f, pidx, bits, c.mask), c);
     return __uint_as_float(f[pidx]);
+}
+
+// Eight consecutive values from index p0 (a multiple of 8): packed codes read once through a
+// 64-bit shift register (every refill brings 32 bits, so a code of at most 24 bits is
+// always whole), or two float4 loads.
+template <bool PK>
+__device__ __forceinline__ void ld_run8(const uint32_t *f, int64_t p0, const CompCodec &c, int bits, float *out)
+{
+    if (PK) {
+        const int64_t b0 = p0 * bits;
+        const uint32_t *w = f + (b0 >> 5);
+        uint64_t acc = (uint64_t)(w[0] >> (b0 & 31));
+        int have = 32 - (int)(b0 & 31), next = 1;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            if (have < bits) {
+                acc |= (uint64_t)w[next++] << have;
+                have += 32;
+            }
+            out[m] = decode_u((uint32_t)acc & c.mask, c);
+            acc >>= bits;
+            have -= bits;
+        }
+    } else {
+        const float4 *f4 = reinterpret_cast<const float4 *>(f + p0);
+        const float4 a = f4[0], e = f4[1];
+        out[0] = a.x, out[1] = a.y, out[2] = a.z, out[3] = a.w;
+        out[4] = e.x, out[5] = e.y, out[6] = e.z, out[7] = e.w;
+    }
+}
+
+// 1 / (number of interior neighbours): exact for 4 and 2, within one rounding for 3.
+__device__ __forceinline__ float inv_count(int cnt)
+{
+    return cnt == 4 ? 0.25f : cnt == 3 ? (1.0f / 3.0f) : cnt == 2 ? 0.5f : 1.0f;
 }
 
 // A lattice of nx x ny samples, row stride ld.
@@ -199,9 +236,16 @@ __device__ __forceinline__ float store(const Params &P, int s, int type, int fie
     return y;
 }
 
-__device__ __forceinline__ bool in_box(const Params &P, double x, double y)
+// Cell (i, j) inside the source box.
+__device__ __forceinline__ bool cell_in_box(const Params &P, int i, int j)
 {
-    return x >= P.src[0] && x <= P.src[2] && y >= P.src[1] && y <= P.src[3];
+    return i >= P.box[0] && i <= P.box[1] && j >= P.box[2] && j <= P.box[3];
+}
+
+// y-face (i, j) inside the source box.
+__device__ __forceinline__ bool vface_in_box(const Params &P, int i, int j)
+{
+    return i >= P.box[0] && i <= P.box[1] && j >= P.box[4] && j <= P.box[5];
 }
 
 __device__ __forceinline__ uint32_t step_index(const Params &P) { return *P.ctr + 1u; }
@@ -216,17 +260,17 @@ __global__ void __launch_bounds__(kT) forces_kernel(Params P)
     float *d = P.d[par] + s * P.ncell_s;
     if (t < (int64_t)n * n) {
         const int i = (int)(t % n), j = (int)(t / n);
-        if (in_box(P, (i + 0.5) * P.hd, (j + 0.5) * P.hd)) d[t] = 1.0f;
+        if (cell_in_box(P, i, j)) d[t] = 1.0f;
     }
     if (t < (int64_t)(n + 1) * n) {
         const int i = (int)(t % n), j = (int)(t / n);
         float vv = 0.0f;
         if (j > 0 && j < n) {
             vv = ld<Q>(P.v.p + s * P.v.ss, t, P.cc[0], P.bits[0]);
-            const float d1 = in_box(P, (i + 0.5) * P.hd, (j + 0.5) * P.hd) ? 1.0f : d[(int64_t)j * n + i];
-            const float d0 = in_box(P, (i + 0.5) * P.hd, (j - 0.5) * P.hd) ? 1.0f : d[(int64_t)(j - 1) * n + i];
+            const float d1 = cell_in_box(P, i, j) ? 1.0f : d[(int64_t)j * n + i];
+            const float d0 = cell_in_box(P, i, j - 1) ? 1.0f : d[(int64_t)(j - 1) * n + i];
             vv += P.dt * P.buoy * 0.5f * (d1 + d0);
-            if (in_box(P, (i + 0.5) * P.hd, j * P.hd)) vv = P.v_in;
+            if (vface_in_box(P, i, j)) vv = P.v_in;
         }
         P.vf[s * P.nvf_s + t] = vv;
     }
@@ -294,121 +338,179 @@ __global__ void __launch_bounds__(kT) divergence_kernel(Params P, int which)  //
     P.div[s * P.ncell_s + t] = (ur - ul + vt - vb) * P.inv_h;
 }
 
-// Sweep it (1-based) of a projection: reads q[(it - 1) & 1] (zero for it = 1), writes
-// q[it & 1]; store counter base + it.  A thread takes an octet, 8 consecutive cells of a
-// row (n is a multiple of 32, so an octet never crosses a row), and draws one Philox block
-// for all 8 (their dither counter is (cell / 8, counter, 2, 0), lanes cell % 8).  The warp's 256 codes are
-// staged in shared memory and packed into its 8 * bits words by the lanes in turn.
+// Jacobi sweeps it0 .. it0 + nsweep - 1 (1-based, nsweep <= kK) of a projection, blocked in
+// time: a CTA loads a tile of kTY x kTX cells with a halo (kHX columns, kK rows) of the
+// previous iterate (q[src]; zero when it0 = 1) and of div into shared memory, runs the
+// sweeps there (every sweep's values stored through the codec: encode, then the decoded
+// value is what the next sweep reads) and writes the tile's last iterate to q[src ^ 1].
+// The halo's values go wrong by one cell per sweep from the region's edge inward, so
+// after kK sweeps the tile itself is still exact; halo cells are recomputed bit for bit
+// as their own tile computes them (same inputs, same arithmetic, same dither draw).  A
+// thread takes octets, 8 consecutive cells of a row aligned to 8 (one Philox block serves
+// all 8: their dither counter is (cell / 8, counter, 2, 0), lanes cell % 8).  Only tile
+// cells count saturations, record ranges and write the trace (sweep k of the launch to
+// trace + k n^2).
+constexpr int kTX = 128, kTY = 32, kK = 4, kHX = 8;
+constexpr int kRW = kTX + 2 * kHX, kRH = kTY + 2 * kK, kRO = kRW / 8;
+constexpr size_t kJacobiSmem = sizeof(float) * 3 * kRW * kRH;
+
 template <bool Q>
-__global__ void __launch_bounds__(kT) jacobi8_kernel(Params P, int it, uint32_t cbase, uint32_t *trace)
+__global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nsweep, uint32_t cbase, int src,
+                                                    uint32_t *trace)
 {
-    __shared__ uint32_t stage[kT * 8];
-    const int s = blockIdx.y, n = P.n, lane = threadIdx.x & 31;
-    const int64_t nc = (int64_t)n * n;
-    const int64_t o = (int64_t)blockIdx.x * kT + threadIdx.x;
-    const int64_t t0 = o * 8;
-    if (t0 - (int64_t)lane * 8 >= nc) return;  // whole warps (n^2 / 8 is a multiple of 32)
-    const int i0 = (int)(t0 % n), j = (int)(t0 / n);
-    const uint32_t *qi = P.q[(it - 1) & 1].p + s * P.q[0].ss;
+    extern __shared__ float4 smem4[];
+    float *qa = reinterpret_cast<float *>(smem4), *qb = qa + kRW * kRH, *dvs = qb + kRW * kRH;
+    const int s = blockIdx.y, n = P.n;
+    const int tiles_x = (n + kTX - 1) / kTX;
+    const int x0 = (int)(blockIdx.x % tiles_x) * kTX, y0 = (int)(blockIdx.x / tiles_x) * kTY;
+    const int w = min(kTX, n - x0);  // a multiple of 32
+    const int gx0 = x0 - kHX, gy0 = y0 - kK;
     const CompCodec &c = P.cc[1];
     const int b = P.bits[1];
-    const float4 *dv4 = reinterpret_cast<const float4 *>(P.div + s * P.ncell_s + t0);
-    const float4 da = dv4[0], db = dv4[1];
-    const float dv[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
-    float x[8];
-    if (it > 1) {
-        float row[10], dn[8], up[8];
-#pragma unroll
-        for (int k = 0; k < 10; ++k) {
-            const int ii = i0 - 1 + k;
-            row[k] = (ii >= 0 && ii < n) ? ld<Q>(qi, (int64_t)j * n + ii, c, b) : 0.0f;
+    const uint32_t *qin = P.q[src].p + s * P.q[0].ss;
+    const uint32_t *div = reinterpret_cast<const uint32_t *>(P.div + s * P.ncell_s);
+    for (int e = threadIdx.x; e < kRO * kRH; e += kT) {
+        const int ry = e / kRO, ro = e % kRO;
+        const int gy = gy0 + ry, gx = gx0 + ro * 8;
+        float q8[8] = {0, 0, 0, 0, 0, 0, 0, 0}, d8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (gy >= 0 && gy < n && gx >= 0 && gx < n) {  // octets lie wholly inside or outside
+            if (it0 > 1) ld_run8<Q>(qin, (int64_t)gy * n + gx, c, b, q8);
+            ld_run8<false>(div, (int64_t)gy * n + gx, c, b, d8);
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            dn[k] = j > 0 ? ld<Q>(qi, (int64_t)(j - 1) * n + i0 + k, c, b) : 0.0f;
-            up[k] = j < n - 1 ? ld<Q>(qi, (int64_t)(j + 1) * n + i0 + k, c, b) : 0.0f;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = i0 + k;
-            float acc = 0.0f;
-            int cnt = 0;
-            if (i > 0) { acc += row[k]; ++cnt; }
-            if (i < n - 1) { acc += row[k + 2]; ++cnt; }
-            if (j > 0) { acc += dn[k]; ++cnt; }
-            if (j < n - 1) { acc += up[k]; ++cnt; }
-            x[k] = (acc - P.h2 * dv[k]) / (float)cnt;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = i0 + k;
-            const int cnt = (i > 0) + (i < n - 1) + (j > 0) + (j < n - 1);
-            x[k] = (0.0f - P.h2 * dv[k]) / (float)cnt;
-        }
+        float4 *qa4 = reinterpret_cast<float4 *>(qa + ry * kRW + ro * 8);
+        float4 *dv4 = reinterpret_cast<float4 *>(dvs + ry * kRW + ro * 8);
+        qa4[0] = make_float4(q8[0], q8[1], q8[2], q8[3]);
+        qa4[1] = make_float4(q8[4], q8[5], q8[6], q8[7]);
+        dv4[0] = make_float4(d8[0], d8[1], d8[2], d8[3]);
+        dv4[1] = make_float4(d8[4], d8[5], d8[6], d8[7]);
     }
-    const uint32_t counter = 1024u * step_index(P) + cbase + (uint32_t)it;
-    uint32_t *qo = P.q[it & 1].p + s * P.q[0].ss;
-    if (P.ranges) {
-        unsigned kmin = 0xffffffffu, kmax = 0u;
+    __syncthreads();
+    float *cur = qa, *nxt = qb;
+    unsigned nsat = 0;
+    unsigned kmin = 0xffffffffu, kmax = 0u;
+    const uint32_t step_base = 1024u * step_index(P) + cbase;
+    for (int k = 0; k < nsweep; ++k) {
+        const int it = it0 + k;
+        const uint32_t counter = step_base + (uint32_t)it;
+        const bool last = k == nsweep - 1;
+        for (int e = threadIdx.x; e < kRO * (kRH - 2); e += kT) {
+            const int ry = 1 + e / kRO, ro = e % kRO;
+            const int gy = gy0 + ry, gx = gx0 + ro * 8;
+            if (gy < 0 || gy >= n || gx < 0 || gx >= n) continue;
+            const float *rc = cur + ry * kRW + ro * 8;
+            const float4 c0 = reinterpret_cast<const float4 *>(rc)[0], c1 = reinterpret_cast<const float4 *>(rc)[1];
+            const float4 d0 = reinterpret_cast<const float4 *>(rc - kRW)[0], d1 = reinterpret_cast<const float4 *>(rc - kRW)[1];
+            const float4 u0 = reinterpret_cast<const float4 *>(rc + kRW)[0], u1 = reinterpret_cast<const float4 *>(rc + kRW)[1];
+            const float4 v0 = reinterpret_cast<const float4 *>(dvs + ry * kRW + ro * 8)[0];
+            const float4 v1 = reinterpret_cast<const float4 *>(dvs + ry * kRW + ro * 8)[1];
+            const float row[10] = {ro > 0 ? rc[-1] : 0.0f, c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w,
+                                   ro < kRO - 1 ? rc[8] : 0.0f};
+            const float dn[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+            const float up[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            const float dv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            float x[8];
+            if (gx > 0 && gx + 8 < n && gy > 0 && gy < n - 1) {  // away from the walls: 4 neighbours
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            kmin = min(kmin, fkey(x[k]));
-            kmax = max(kmax, fkey(x[k]));
+                for (int m = 0; m < 8; ++m) {
+                    const float acc = it > 1 ? row[m] + row[m + 2] + dn[m] + up[m] : 0.0f;
+                    x[m] = (acc - P.h2 * dv[m]) * 0.25f;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int i = gx + m;
+                    float acc = 0.0f;
+                    int cnt = 0;
+                    if (it > 1) {
+                        if (i > 0) { acc += row[m]; ++cnt; }
+                        if (i < n - 1) { acc += row[m + 2]; ++cnt; }
+                        if (gy > 0) { acc += dn[m]; ++cnt; }
+                        if (gy < n - 1) { acc += up[m]; ++cnt; }
+                    } else {
+                        cnt = (i > 0) + (i < n - 1) + (gy > 0) + (gy < n - 1);
+                    }
+                    x[m] = (acc - P.h2 * dv[m]) * inv_count(cnt);
+                }
+            }
+            const bool inner = ry >= kK && ry < kK + kTY && ro >= 1 && (ro - 1) * 8 < w;
+            const uint32_t oct = (uint32_t)(((int64_t)gy * n + gx) >> 3);
+            if (inner && P.ranges) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    kmin = min(kmin, fkey(x[m]));
+                    kmax = max(kmax, fkey(x[m]));
+                }
+            }
+            if (Q) {
+                uint4 blk = make_uint4(0u, 0u, 0u, 0u);
+                if (P.dither) {
+                    const uint2 key = P.seed[s];
+                    blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), key.x, key.y);
+                }
+                uint32_t code[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    int flags = 0;
+                    code[m] = encode_f32(x[m], c, P.dither != 0, P.dither ? dither_threshold(blk, m) : 0u, flags);
+                    if (inner) nsat += (unsigned)(flags & 1);
+                    x[m] = decode_u(code[m], c);
+                }
+                if (inner) {
+                    if (trace && s == 0) {
+                        uint4 *tw = reinterpret_cast<uint4 *>(trace + (int64_t)k * n * n + (int64_t)gy * n + gx);
+                        tw[0] = make_uint4(code[0], code[1], code[2], code[3]);
+                        tw[1] = make_uint4(code[4], code[5], code[6], code[7]);
+                    }
+                }
+                if (last) {  // nobody reads the last sweep's values here: keep its codes instead
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) x[m] = __uint_as_float(code[m]);
+                }
+            } else if (P.sigma[1] != 0.0f) {
+                const uint2 key = P.nseed[s];
+                const uint4 blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), key.x, key.y);
+                const float amp = P.sign[s] * P.sigma[1];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const uint32_t wd = uint4_at(blk, (m >> 1) & 3);
+                    const uint32_t q16 = (m & 1) ? (wd >> 16) : (wd & 0xFFFFu);
+                    x[m] += amp * ((q16 & 0x8000u) ? 1.0f : -1.0f);
+                }
+            }
+            float4 *nw = reinterpret_cast<float4 *>(nxt + ry * kRW + ro * 8);
+            nw[0] = make_float4(x[0], x[1], x[2], x[3]);
+            nw[1] = make_float4(x[4], x[5], x[6], x[7]);
+            if (!Q && last && inner) {
+                float4 *gw = reinterpret_cast<float4 *>(P.q[src ^ 1].p + s * P.q[0].ss + (int64_t)gy * n + gx);
+                gw[0] = nw[0];
+                gw[1] = nw[1];
+            }
         }
-        record_range(P, s, 1, kmin, kmax);
+        __syncthreads();
+        float *t = cur;
+        cur = nxt;
+        nxt = t;
     }
     if (Q) {
-        uint4 blk = make_uint4(0u, 0u, 0u, 0u);
-        if (P.dither) {
-            const uint2 key = P.seed[s];
-            blk = philox4x32_10(make_uint4((uint32_t)o, counter, 2u, 0u), key.x, key.y);
-        }
-        uint32_t code[8];
-        int nsat = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int flags = 0;
-            code[k] = encode_f32(x[k], c, P.dither != 0, P.dither ? dither_threshold(blk, k) : 0u, flags);
-            nsat += flags & 1;
-        }
-        nsat = __reduce_add_sync(0xffffffffu, nsat);
-        if (nsat && lane == 0) atomicAdd(P.sat + 2 * s + 1, (unsigned long long)nsat);
-        if (trace && s == 0) {
-            uint4 *tw = reinterpret_cast<uint4 *>(trace + t0);
-            tw[0] = make_uint4(code[0], code[1], code[2], code[3]);
-            tw[1] = make_uint4(code[4], code[5], code[6], code[7]);
-        }
-        uint32_t *st = stage + (threadIdx.x >> 5) * 256;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) st[lane * 8 + k] = code[k];
-        __syncwarp();
-        uint32_t *ow = qo + (t0 - (int64_t)lane * 8) / 32 * b;
-        for (int w = lane; w < 8 * b; w += 32) {
-            const int b0 = 32 * w, m1 = min((b0 + 31) / b, 255);
+        // the tile's last codes (in cur after the swap), row segments of w cells = w b / 32
+        // whole words each
+        const uint32_t *cs = reinterpret_cast<const uint32_t *>(cur) + kK * kRW + kHX;
+        const int wpr = w / 32 * b;
+        uint32_t *qout = P.q[src ^ 1].p + s * P.q[0].ss;
+        for (int e = threadIdx.x; e < kTY * wpr; e += kT) {
+            const int r = e / wpr, wr = e % wpr;
+            const int b0 = 32 * wr, m1 = min((b0 + 31) / b, w - 1);
             uint32_t word = 0u;
             for (int m = b0 / b; m <= m1; ++m) {
                 const int sh = m * b - b0;
-                word |= sh >= 0 ? (st[m] << sh) : (st[m] >> -sh);
+                word |= sh >= 0 ? (cs[r * kRW + m] << sh) : (cs[r * kRW + m] >> -sh);
             }
-            ow[w] = word;
+            qout[((int64_t)(y0 + r) * n + x0) / 32 * b + wr] = word;
         }
-    } else {
-        if (P.sigma[1] != 0.0f) {
-            const uint2 key = P.nseed[s];
-            const uint4 blk = philox4x32_10(make_uint4((uint32_t)o, counter, 2u, 0u), key.x, key.y);
-            const float amp = P.sign[s] * P.sigma[1];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t w = uint4_at(blk, (k >> 1) & 3);
-                const uint32_t q16 = (k & 1) ? (w >> 16) : (w & 0xFFFFu);
-                x[k] += amp * ((q16 & 0x8000u) ? 1.0f : -1.0f);
-            }
-        }
-        float4 *qw = reinterpret_cast<float4 *>(qo + t0);
-        qw[0] = make_float4(x[0], x[1], x[2], x[3]);
-        qw[1] = make_float4(x[4], x[5], x[6], x[7]);
+        nsat = __reduce_add_sync(0xffffffffu, nsat);
+        if (nsat && (threadIdx.x & 31) == 0) atomicAdd(P.sat + 2 * s + 1, (unsigned long long)nsat);
     }
+    if (P.ranges) record_range(P, s, 1, kmin, kmax);
 }
 
 // out = in - grad q on interior faces (q = the last sweep's iterate; none when J = 0), then
@@ -421,7 +523,7 @@ __global__ void __launch_bounds__(kT) gradsub_kernel(Params P, uint32_t *trace)
     const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (t - (threadIdx.x & 31) >= nu + nv) return;
     const uint32_t counter = 1024u * step_index(P) + (STAGE == 2 ? (uint32_t)P.J + 2u : 2u * (uint32_t)P.J + 5u);
-    const uint32_t *q = P.q[P.J & 1].p + s * P.q[0].ss;
+    const uint32_t *q = P.q[P.qfin].p + s * P.q[0].ss;
     const CompCodec &cq = P.cc[1];
     const int bq = P.bits[1];
     const Fld fin_u = STAGE == 2 ? P.ut : P.u, fin_v = STAGE == 2 ? P.vt : P.v;
@@ -510,7 +612,7 @@ __global__ void __launch_bounds__(kT) measure_kernel(Params P)
     if (threadIdx.x == 0) {
         double a = 0.0;
         for (int w = 0; w < kT / 32; ++w) a += part[w];
-        atomicAdd(P.z + s, a);
+        P.z[(int64_t)s * kMeasureBlocks + blockIdx.x] = a;  // summed in order on the host
     }
 }
 
@@ -566,7 +668,7 @@ __global__ void __launch_bounds__(kT) readback_kernel(Params P, int s, float *u,
     }
     if (t < (int64_t)n * n) {
         d[t] = P.d[*P.ctr & 1u][s * P.ncell_s + t];
-        q[t] = P.J > 0 ? ld<Q>(P.q[P.J & 1].p + s * P.q[0].ss, t, P.cc[1], P.bits[1]) : 0.0f;
+        q[t] = P.J > 0 ? ld<Q>(P.q[P.qfin].p + s * P.q[0].ss, t, P.cc[1], P.bits[1]) : 0.0f;
     }
 }
 
@@ -587,6 +689,9 @@ struct qmpm_smoke {
     int64_t stage_floats = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t steps = 0, launches = 0, graph_launches = 0, device_bytes = 0;
+    bool profile = false;
+    std::vector<cudaEvent_t> ev;   // per profiled step: start, sweeps 1 begin/end, sweeps 2 begin/end, end
+    int64_t prof_jacobi_launches = 0;
 };
 
 namespace {
@@ -619,7 +724,7 @@ int make_codec(int bits, int frac, int64_t offset, CompCodec &c)
     return 0;
 }
 
-unsigned launches_per_step(int J) { return 11u + 2u * (unsigned)J; }
+unsigned launches_per_step(int J) { return 11u + 2u * (unsigned)((J + kK - 1) / kK); }
 
 template <bool Q>
 int enqueue_step(qmpm_smoke *h, uint32_t *trace)
@@ -629,23 +734,45 @@ int enqueue_step(qmpm_smoke *h, uint32_t *trace)
     const int64_t nfaces = (int64_t)n * P.su + (int64_t)(n + 1) * n;
     const dim3 gf((unsigned)((nfaces + kT - 1) / kT), S);
     const dim3 gc((unsigned)(((int64_t)n * n + kT - 1) / kT), S);
-    const dim3 g8((unsigned)(((int64_t)n * n / 8 + kT - 1) / kT), S);
     const dim3 gv((unsigned)(((int64_t)(n + 1) * n + kT - 1) / kT), S);
     const int64_t V = 2 * (int64_t)n * (n + 1), Pq = (int64_t)n * n;
     auto tr = [&](int64_t off) { return trace ? trace + off : nullptr; };
+    cudaEvent_t ev[6] = {};
+    if (h->profile) {
+        for (auto &e : ev) {
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(QMPM_ERR_CUDA, "qmpm_smoke_step: event creation");
+            h->ev.push_back(e);
+        }
+        h->prof_jacobi_launches += 2 * ((J + kK - 1) / kK);
+    }
+    auto mark = [&](int k) {
+        if (h->profile) cudaEventRecord(ev[k], h->st);
+    };
+    mark(0);
     forces_kernel<Q><<<gv, kT, 0, h->st>>>(P);
     advect_vel_kernel<Q, 1><<<gf, kT, 0, h->st>>>(P, tr(0));
     divergence_kernel<Q><<<gc, kT, 0, h->st>>>(P, 0);
-    for (int it = 1; it <= J; ++it) jacobi8_kernel<Q><<<g8, kT, 0, h->st>>>(P, it, 1u, tr(V + (it - 1) * Pq));
+    const dim3 gj((unsigned)(((n + kTX - 1) / kTX) * (n / kTY)), S);
+    auto sweeps = [&](uint32_t cbase, int64_t toff) {
+        for (int l = 0; l * kK < J; ++l) {
+            const int it0 = l * kK + 1, ns = std::min(kK, J - l * kK);
+            jacobi_kernel<Q><<<gj, kT, kJacobiSmem, h->st>>>(P, it0, ns, cbase, l & 1, tr(toff + (int64_t)(it0 - 1) * Pq));
+        }
+    };
+    mark(1);
+    sweeps(1u, V);
+    mark(2);
     gradsub_kernel<Q, 2><<<gf, kT, 0, h->st>>>(P, tr(V + J * Pq));
     reflect_kernel<Q><<<gf, kT, 0, h->st>>>(P, tr(2 * V + J * Pq));
     advect_vel_kernel<Q, 4><<<gf, kT, 0, h->st>>>(P, tr(3 * V + J * Pq));
     divergence_kernel<Q><<<gc, kT, 0, h->st>>>(P, 1);
-    for (int it = 1; it <= J; ++it)
-        jacobi8_kernel<Q><<<g8, kT, 0, h->st>>>(P, it, (uint32_t)J + 4u, tr(4 * V + (J + it - 1) * Pq));
+    mark(3);
+    sweeps((uint32_t)J + 4u, 4 * V + J * Pq);
+    mark(4);
     gradsub_kernel<Q, 5><<<gf, kT, 0, h->st>>>(P, tr(4 * V + 2 * J * Pq));
     advect_d_kernel<Q><<<gc, kT, 0, h->st>>>(P);
     advance_kernel<<<1, 1, 0, h->st>>>(P.ctr);
+    mark(5);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("qmpm_smoke_step", e);
     h->launches += launches_per_step(J);
@@ -698,11 +825,40 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
     P.inv_h = (float)n;
     P.h = 1.0f / (float)n;
     P.h2 = 1.0f / ((float)n * (float)n);
-    P.hd = 1.0 / n;
-    for (int k = 0; k < 4; ++k) P.src[k] = cfg->src[k];
+    // the box as index ranges: the samples whose position (cell centre (i + 1/2) h, y-face
+    // j h) lies in [src0, src2] x [src1, src3], decided in FP64 on the host
+    {
+        const double hd = 1.0 / n;
+        auto range = [&](double lo, double hi, double off, int count, int &a, int &b) {
+            a = 1;
+            b = 0;
+            bool any = false;
+            for (int i = 0; i < count; ++i) {
+                const double x = (i + off) * hd;
+                if (x >= lo && x <= hi) {
+                    if (!any) a = i;
+                    b = i;
+                    any = true;
+                }
+            }
+        };
+        range(cfg->src[0], cfg->src[2], 0.5, n, P.box[0], P.box[1]);
+        range(cfg->src[1], cfg->src[3], 0.5, n, P.box[2], P.box[3]);
+        range(cfg->src[1], cfg->src[3], 0.0, n + 1, P.box[4], P.box[5]);
+    }
     P.quant = h->quant;
     P.dither = h->quant && cfg->dither;
     P.ranges = (cfg->flags & QMPM_SMOKE_RANGES) != 0;
+    h->profile = (cfg->flags & QMPM_SMOKE_PROFILE) != 0;
+    P.qfin = ((P.J + kK - 1) / kK) & 1;
+    if (cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmem) !=
+            cudaSuccess) {
+        if (h->own_stream) cudaStreamDestroy(h->st);
+        delete h;
+        return fail(QMPM_ERR_CUDA, "qmpm_smoke_create: shared memory opt-in failed");
+    }
     P.bits[0] = P.bits[1] = 32;
     if (h->quant) {
         for (int t = 0; t < 2; ++t) {
@@ -751,7 +907,7 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
     P.sat = (unsigned long long *)alloc(sizeof(unsigned long long) * 2 * S);
     P.lo = (unsigned int *)alloc(sizeof(unsigned int) * 2 * kSlots * S);
     P.hi = (unsigned int *)alloc(sizeof(unsigned int) * 2 * kSlots * S);
-    P.z = (double *)alloc(sizeof(double) * S);
+    P.z = (double *)alloc(sizeof(double) * kMeasureBlocks * S);
     P.ctr = (uint32_t *)alloc(sizeof(uint32_t));
     h->stage_floats = 2 * nv + 2 * nc + 64;
     h->stage = (uint32_t *)alloc(sizeof(float) * h->stage_floats);
@@ -852,6 +1008,14 @@ int qmpm_smoke_step(qmpm_smoke_handle h, int32_t steps, uint32_t *d_trace, int64
     if (!h || steps < 0) return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_step: bad handle or steps");
     const int n = h->p.n, J = h->p.J;
     const int64_t per = 10 * (int64_t)n * (n + 1) + 2 * (int64_t)J * n * n;
+    if (h->profile && !d_trace) {
+        for (int t = 0; t < steps; ++t) {
+            const int r = enqueue(h, nullptr);
+            if (r != QMPM_OK) return r;
+            ++h->steps;
+        }
+        return QMPM_OK;
+    }
     if (d_trace) {
         if (!h->quant || trace_len < per * steps)
             return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_step: trace needs a quantized handle and steps x "
@@ -893,15 +1057,18 @@ int qmpm_smoke_step(qmpm_smoke_handle h, int32_t steps, uint32_t *d_trace, int64
 int qmpm_smoke_measure(qmpm_smoke_handle h, double *h_z)
 {
     if (!h || !h_z) return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_measure: NULL argument");
-    cudaError_t e = cudaMemsetAsync(h->p.z, 0, sizeof(double) * h->S, h->st);
-    if (e != cudaSuccess) return cuda_fail("qmpm_smoke_measure", e);
-    const int n = h->p.n;
-    const unsigned gx = (unsigned)std::min<int64_t>(((int64_t)n * n + kT - 1) / kT, 64);
-    measure_kernel<<<dim3(gx, h->S), kT, 0, h->st>>>(h->p);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_z, h->p.z, sizeof(double) * h->S, cudaMemcpyDeviceToHost, h->st);
+    measure_kernel<<<dim3(kMeasureBlocks, h->S), kT, 0, h->st>>>(h->p);
+    std::vector<double> part((size_t)kMeasureBlocks * h->S);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(part.data(), h->p.z, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail("qmpm_smoke_measure", e);
+    for (int s = 0; s < h->S; ++s) {  // a fixed order: the same z for the same state
+        double a = 0.0;
+        for (int b = 0; b < kMeasureBlocks; ++b) a += part[(size_t)s * kMeasureBlocks + b];
+        h_z[s] = a;
+    }
     return QMPM_OK;
 }
 
@@ -979,11 +1146,35 @@ int qmpm_smoke_info(qmpm_smoke_handle h, qmpm_smoke_info_t *out)
     return QMPM_OK;
 }
 
+int qmpm_smoke_profile(qmpm_smoke_handle h, double *h_step_ms, double *h_jacobi_ms, int64_t *h_jacobi_launches)
+{
+    if (!h || !h->profile) return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_profile: handle created without QMPM_SMOKE_PROFILE");
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail("qmpm_smoke_profile", e);
+    double step = 0.0, jac = 0.0;
+    for (size_t k = 0; k + 6 <= h->ev.size(); k += 6) {
+        float a = 0.0f, b = 0.0f, c = 0.0f;
+        cudaEventElapsedTime(&a, h->ev[k], h->ev[k + 5]);
+        cudaEventElapsedTime(&b, h->ev[k + 1], h->ev[k + 2]);
+        cudaEventElapsedTime(&c, h->ev[k + 3], h->ev[k + 4]);
+        step += a;
+        jac += (double)b + c;
+    }
+    for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
+    h->ev.clear();
+    if (h_step_ms) *h_step_ms = step;
+    if (h_jacobi_ms) *h_jacobi_ms = jac;
+    if (h_jacobi_launches) *h_jacobi_launches = h->prof_jacobi_launches;
+    h->prof_jacobi_launches = 0;
+    return QMPM_OK;
+}
+
 int qmpm_smoke_destroy(qmpm_smoke_handle h)
 {
     if (!h) return QMPM_OK;
     cudaStreamSynchronize(h->st);
     drop_graph(h);
+    for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
     for (void *p : h->allocs) cudaFree(p);
     if (h->own_stream) cudaStreamDestroy(h->st);
     delete h;

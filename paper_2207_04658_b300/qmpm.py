@@ -236,6 +236,7 @@ _SIGNATURES += [
                                        _P(ct.c_float)]),
     ("qmpm_smoke_ranges", ct.c_int, [ct.c_void_p, _P(ct.c_float), _P(ct.c_float), _P(ct.c_int64)]),
     ("qmpm_smoke_info", ct.c_int, [ct.c_void_p, _P(qmpm_smoke_info_t)]),
+    ("qmpm_smoke_profile", ct.c_int, [ct.c_void_p, _P(ct.c_double), _P(ct.c_double), _P(ct.c_int64)]),
     ("qmpm_smoke_destroy", ct.c_int, [ct.c_void_p]),
 ]
 OPTIONAL_SIGNATURES = [

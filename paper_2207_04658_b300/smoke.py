@@ -17,6 +17,7 @@ from .qmpm import _check, _dptr, lib
 
 TYPES = ("v", "p")
 RANGES = 1  # QMPM_SMOKE_RANGES
+PROFILE = 2  # QMPM_SMOKE_PROFILE
 
 
 def make_config(scene):
@@ -29,7 +30,7 @@ def make_config(scene):
     for k, x in enumerate(scene.get("src", (1.0, 1.0, -1.0, -1.0))):
         c.src[k] = float(x)
     c.dither = int(bool(scene.get("dither", True)))
-    c.flags = RANGES if scene.get("ranges", False) else 0
+    c.flags = (RANGES if scene.get("ranges", False) else 0) | (PROFILE if scene.get("profile", False) else 0)
     return c
 
 
@@ -119,6 +120,13 @@ class Smoke:
         out = qmpm.qmpm_smoke_info_t()
         _check(lib().qmpm_smoke_info(self.h, ct.byref(out)))
         return out.as_dict()
+
+    def profile(self):
+        """Device ms of the steps since the last call, of their Jacobi launches, and the
+        number of those launches (handles created with scene["profile"] = True)."""
+        a, b, k = ct.c_double(), ct.c_double(), ct.c_int64()
+        _check(lib().qmpm_smoke_profile(self.h, ct.byref(a), ct.byref(b), ct.byref(k)))
+        return {"step_ms": a.value, "jacobi_ms": b.value, "jacobi_launches": k.value}
 
     def close(self):
         if self.h is not None and self.h.value:
