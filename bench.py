@@ -337,7 +337,7 @@ def cpu_baseline(name, sample_steps=2):
 # ------------------------------------------------------------------------------ smoke
 SMOKE_METRIC = "quantized 2D smoke cell-steps/s (advection-reflection, 64 Jacobi sweeps per projection)"
 SMOKE_UNIT = "cell-steps/s"
-SMOKE_FIXED_SCHEME = {"v": dict(bits=10, frac=7, offset=-512), "p": dict(bits=9, frac=13, offset=-256)}
+SMOKE_FIXED_SCHEME = {"v": dict(bits=12, frac=9, offset=-1808), "p": dict(bits=14, frac=18, offset=-4288)}
 
 
 def smoke_counters():
@@ -369,11 +369,11 @@ def smoke_section(args, peaks, dc, torch):
     n = sc["n"]
     if args.smoke_fixed_scheme:
         scheme = SMOKE_FIXED_SCHEME
-        source = "written down: the solve's eps 1e-3 result on this scene (bits 10/9, frac 7/13)"
+        source = "written down: the bias-aware solve's eps 1e-3 result on this scene (bits 12/14, frac 9/18)"
     else:
-        scheme, rep = smoke.solve(sc, T, 1e-3)
+        scheme, rep = smoke.solve(sc, T, 1e-3, bias_aware=True)
         source = ("qmpm_scheme_solve at eps 1e-3 on z = sum d^2 after 100 steps, noise-injection "
-                  "sensitivities (32 antithetic pairs per type)")
+                  "sensitivities (32 antithetic pairs per type), bits added for the second-order bias")
     steps = max(10, min(args.steps, 200))
     warm = max(3, args.warmup)
     st = torch.cuda.Stream()
@@ -440,8 +440,9 @@ def smoke_section(args, peaks, dc, torch):
                   "path": "qmpm_smoke_set_state from host arrays, 100-step rollout of the batch, z to the host"}
     if dc.rank == 0 and not args.no_smoke_validation:
         res = smoke.error_bound_protocol(sc, T, [1e-2, 1e-3], runs=20)
-        out["error_bound"] = [{k: r[k] for k in ("eps", "bits", "frac", "pred_sigma_dither", "obs_rms", "bias",
-                                                 "z_std", "success_3eps", "compression")} for r in res["results"]]
+        out["error_bound"] = [{k: r[k] for k in ("eps", "solve", "bits", "frac", "pred_sigma_dither", "pred_bias",
+                                                 "obs_rms", "bias", "z_std", "success_3eps", "compression")}
+                              for r in res["results"]]
         out["error_bound_z_ref"] = res["z_ref"]
     return out
 

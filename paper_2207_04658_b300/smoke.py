@@ -152,13 +152,17 @@ def reference(scene, T, state=None):
         return {"z": z, "lo": lo[0].astype(float), "hi": hi[0].astype(float), "state": s.readback(0)}
 
 
-def sensitivities(scene, T, pairs=32, sigma=(3e-3, 3e-5), seed=0, state=None):
+def sensitivities(scene, T, pairs=32, sigma=(3e-3, 3e-5), seed=0, state=None, z0=None):
     """Eq. 8's g_h = sum over the stores of type h of (dz/dstore)^2, for h = velocity,
     pressure, by antithetic noise injection: scenes 2k and 2k+1 of a batch get the same
     +-sigma_h noise at every store of type h with opposite signs, and
-    E[((z+ - z-) / 2)^2] = sigma_h^2 g_h to second order.  Returns g, its standard error,
-    and the per-pair estimates."""
-    g, se, per = np.zeros(2), np.zeros(2), []
+    E[((z+ - z-) / 2)^2] = sigma_h^2 g_h to second order.  The pairs' means give the
+    second-order term as well: E[(z+ + z-) / 2] - z0 = sigma_h^2 beta_h with
+    beta_h = (1/2) sum over the stores of d^2 z / dstore^2 (z0: the noise-free run).
+    Returns a dict with g, beta, their standard errors, and the per-pair estimates."""
+    if z0 is None:
+        z0 = reference(scene, T, state)["z"]
+    g, se, beta, beta_se, per = np.zeros(2), np.zeros(2), np.zeros(2), np.zeros(2), []
     for h in range(2):
         sg = [0.0, 0.0]
         sg[h] = float(sigma[h])
@@ -172,18 +176,79 @@ def sensitivities(scene, T, pairs=32, sigma=(3e-3, 3e-5), seed=0, state=None):
             s.step(T)
             z = s.measure()
         est = ((z[0::2] - z[1::2]) / 2.0) ** 2 / sg[h] ** 2
-        g[h] = est.mean()
-        se[h] = est.std(ddof=1) / np.sqrt(pairs)
+        mid = ((z[0::2] + z[1::2]) / 2.0 - z0) / sg[h] ** 2
+        g[h], se[h] = est.mean(), est.std(ddof=1) / np.sqrt(pairs)
+        beta[h], beta_se[h] = mid.mean(), mid.std(ddof=1) / np.sqrt(pairs)
         per.append(est)
-    return g, se, per
+    return {"g": g, "g_se": se, "beta": beta, "beta_se": beta_se, "per_pair": per, "z0": z0,
+            "sigma": list(sigma)}
 
 
-def solve(scene, T, eps, pairs=32, sigma=(3e-3, 3e-5), kappa=2.0, state=None, max_bits=24):
+def predicted_moments(frac, g, beta):
+    """Predicted bias and variance of z under dithered stores (rounding error of variance
+    Delta_h^2 / 6 per store, Sec. 5): bias = sum_h beta_h Delta_h^2 / 6 and
+    var = sum_h g_h Delta_h^2 / 6 (Eq. 8's linear term with the dither's variance)."""
+    d2 = np.array([2.0 ** (-2 * f) for f in frac])
+    return float(np.dot(beta, d2) / 6.0), float(np.dot(g, d2) / 6.0)
+
+
+def refine_for_bias(scheme, g, beta, P, z, eps, max_bits=24):
+    """Add fraction bits (one at a time, to the type with the largest drop of the predicted
+    second moment bias^2 + var per stored bit) until bias^2 + var <= (eps z)^2: the error
+    bound of Eq. 6 on the second moment, with the second-order term that the linear model
+    of Eq. 8 leaves out.  Ranges stay: each added bit doubles the code range."""
+    sch = {k: dict(v) for k, v in scheme.items()}
+    target = (eps * z) ** 2
+    for _ in range(64):
+        frac = [sch[t]["frac"] for t in TYPES]
+        b, v = predicted_moments(frac, g, beta)
+        if b * b + v <= target:
+            break
+        best, gain = None, 0.0
+        for h, t in enumerate(TYPES):
+            if sch[t]["bits"] >= max_bits:
+                continue
+            f2 = list(frac)
+            f2[h] += 1
+            b2, v2 = predicted_moments(f2, g, beta)
+            r = (b * b + v - b2 * b2 - v2) / P[h]
+            if r > gain:
+                best, gain = h, r
+        if best is None:
+            break
+        t = TYPES[best]
+        sch[t] = dict(bits=sch[t]["bits"] + 1, frac=sch[t]["frac"] + 1, offset=sch[t]["offset"] * 2)
+    return sch
+
+
+def bias_aware_scheme(scene, T, eps, paper, g, beta, P, z, pairs=32, iters=3, state=None, max_bits=24):
+    """refine_for_bias, with the second-order term re-estimated at the refined scheme's own
+    noise scale (sigma_h = Delta_h / sqrt(6), the dither's spread): the shift of z is not
+    quadratic in the noise scale (the advection samples piecewise-bilinearly), so the
+    estimate taken at the sensitivity run's scale is only a start.  Stops when the scheme
+    repeats; where the last two differ, keeps the finer fraction per type.  Returns the
+    scheme and the last beta."""
+    sch = refine_for_bias(paper, g, beta, P, z, eps, max_bits)
+    prev = None
+    for _ in range(iters):
+        sig = tuple(2.0 ** -sch[t]["frac"] / 6 ** 0.5 for t in TYPES)
+        beta = sensitivities(scene, T, pairs, sig, state=state, z0=z)["beta"]
+        prev, sch = sch, refine_for_bias(paper, g, beta, P, z, eps, max_bits)
+        if sch == prev:
+            break
+    if prev is not None and sch != prev:
+        sch = {t: (sch[t] if sch[t]["frac"] >= prev[t]["frac"] else prev[t]) for t in TYPES}
+    return sch, beta
+
+
+def solve(scene, T, eps, pairs=32, sigma=(3e-3, 3e-5), kappa=2.0, state=None, max_bits=24, bias_aware=False):
     """Scheme for the error bound eps on z (Algorithm 1 with the recorded ranges widened by
-    kappa about their midpoint, Sec. 3.1).  Returns (scheme dict, report)."""
+    kappa about their midpoint, Sec. 3.1); bias_aware adds the bits refine_for_bias asks
+    for.  Returns (scheme dict, report)."""
     n = int(scene["n"])
     ref = reference(scene, T, state)
-    g, se, _ = sensitivities(scene, T, pairs, sigma, state=state)
+    sens = sensitivities(scene, T, pairs, sigma, state=state, z0=ref["z"])
+    g = sens["g"]
     P = [2.0 * n * (n + 1), float(n * n)]
     res = qmpm.qmpm_scheme_solve(P, list(g), list(ref["lo"]), list(ref["hi"]), ref["z"], eps, kappa=kappa)
     scheme, capped = {}, []
@@ -194,46 +259,63 @@ def solve(scene, T, eps, pairs=32, sigma=(3e-3, 3e-5), kappa=2.0, state=None, ma
             bits, frac, off = max_bits, frac - drop, off >> drop
             capped.append(name)
         scheme[name] = dict(bits=bits, frac=frac, offset=off)
+    beta = sens["beta"]
+    if bias_aware:
+        scheme, beta = bias_aware_scheme(scene, T, eps, scheme, g, beta, P, ref["z"], pairs, state=state,
+                                         max_bits=max_bits)
+    frac = [scheme[t]["frac"] for t in TYPES]
+    bias, var = predicted_moments(frac, g, beta)
     bits_state = P[0] * scheme["v"]["bits"] + 32.0 * n * n
-    rep = {"z": ref["z"], "g": list(g), "g_se": list(se), "lo": list(ref["lo"]), "hi": list(ref["hi"]),
-           "solve": res, "capped": capped, "P": P,
+    rep = {"z": ref["z"], "g": list(g), "g_se": list(sens["g_se"]), "beta": list(beta),
+           "beta_se": list(sens["beta_se"]), "lo": list(ref["lo"]), "hi": list(ref["hi"]),
+           "solve": res, "capped": capped, "P": P, "pred_bias": bias, "pred_sigma": var ** 0.5,
            "compression_state": (P[0] + n * n) * 32.0 / bits_state,
            "compression_quantized": (P[0] + P[1]) * 32.0 / (P[0] * scheme["v"]["bits"] + P[1] * scheme["p"]["bits"])}
     return scheme, rep
 
 
-def error_bound_protocol(scene, T, eps_list, runs=20, z_ref=None, pairs=32, seed0=1000):
+def error_bound_protocol(scene, T, eps_list, runs=20, z_ref=None, pairs=32, seed0=1000, variants=(False, True)):
     """The error-bounded experiment of Sec. 8.1 on the smoke: per eps, the scheme Algorithm 1
-    solves from the noise-injection sensitivities and the FP32 run's ranges, then `runs`
-    quantized runs (one batch, dither seeds seed0 + r); success = |z~ - z| <= 3 eps z."""
+    solves from the noise-injection sensitivities and the FP32 run's ranges (and, for the
+    bias-aware variant, the bits bias_aware_scheme adds), then `runs` quantized runs (one batch,
+    dither seeds seed0 + r); success = |z~ - z| <= 3 eps z."""
     n = int(scene["n"])
     ref = reference(scene, T)
     z0 = ref["z"] if z_ref is None else z_ref
-    g, se, _ = sensitivities(scene, T, pairs)
+    sens = sensitivities(scene, T, pairs, z0=ref["z"])
+    g = sens["g"]
     P = [2.0 * n * (n + 1), float(n * n)]
     out = []
     for eps in eps_list:
         res = qmpm.qmpm_scheme_solve(P, list(g), list(ref["lo"]), list(ref["hi"]), ref["z"], eps, kappa=2.0)
-        scheme = {name: dict(bits=min(int(res["bits"][h]), 24), frac=int(res["frac"][h]) - max(0, int(res["bits"][h]) - 24),
-                             offset=int(res["offset"][h]) >> max(0, int(res["bits"][h]) - 24))
-                  for h, name in enumerate(TYPES)}
-        with Smoke(scene, scheme, runs, seeds=[seed0 + r for r in range(runs)]) as s:
-            s.step(T)
-            zs = s.measure()
-            _, _, sat = s.ranges()
-        dev = zs - z0
-        bits = [scheme["v"]["bits"], scheme["p"]["bits"]]
-        pred12 = float(sum(2.0 ** (-2 * scheme[t]["frac"]) * g[h] for h, t in enumerate(TYPES)) / 12.0)
-        out.append({
-            "eps": eps, "bits": bits, "frac": [scheme["v"]["frac"], scheme["p"]["frac"]],
-            "bits_paper": [int(b) for b in res["bits_paper"]],
-            "pred_sigma": float(np.sqrt(pred12)), "pred_sigma_dither": float(np.sqrt(2 * pred12)),
-            "obs_rms": float(np.sqrt(np.mean(dev ** 2))), "bias": float(dev.mean()),
-            "z_ref": z0, "z_mean": float(zs.mean()), "z_std": float(zs.std(ddof=1)) if runs > 1 else 0.0,
-            "success_3eps": float(np.mean(np.abs(dev) <= 3 * eps * abs(z0))),
-            "success_eps": float(np.mean(np.abs(dev) <= eps * abs(z0))),
-            "saturations": int(sat.sum()),
-            "compression": 3 * 32.0 / (2 * bits[0] + bits[1]), "runs": runs,
-        })
-    return {"z_ref": z0, "g": list(g), "g_se": list(se), "lo": list(ref["lo"]), "hi": list(ref["hi"]),
-            "results": out}
+        paper = {}
+        for h, name in enumerate(TYPES):
+            drop = max(0, int(res["bits"][h]) - 24)
+            paper[name] = dict(bits=int(res["bits"][h]) - drop, frac=int(res["frac"][h]) - drop,
+                               offset=int(res["offset"][h]) >> drop)
+        for aware in variants:
+            beta = sens["beta"]
+            scheme = paper
+            if aware:
+                scheme, beta = bias_aware_scheme(scene, T, eps, paper, g, beta, P, ref["z"], pairs)
+            with Smoke(scene, scheme, runs, seeds=[seed0 + r for r in range(runs)]) as s:
+                s.step(T)
+                zs = s.measure()
+                _, _, sat = s.ranges()
+            dev = zs - z0
+            bits = [scheme["v"]["bits"], scheme["p"]["bits"]]
+            frac = [scheme["v"]["frac"], scheme["p"]["frac"]]
+            pb, pv = predicted_moments(frac, g, beta)
+            out.append({
+                "eps": eps, "solve": "bias-aware" if aware else "Algorithm 1", "bits": bits, "frac": frac,
+                "bits_paper": [int(b) for b in res["bits_paper"]],
+                "pred_sigma": float(np.sqrt(pv / 2.0)), "pred_sigma_dither": float(np.sqrt(pv)),
+                "pred_bias": pb, "obs_rms": float(np.sqrt(np.mean(dev ** 2))), "bias": float(dev.mean()),
+                "z_ref": z0, "z_mean": float(zs.mean()), "z_std": float(zs.std(ddof=1)) if runs > 1 else 0.0,
+                "success_3eps": float(np.mean(np.abs(dev) <= 3 * eps * abs(z0))),
+                "success_eps": float(np.mean(np.abs(dev) <= eps * abs(z0))),
+                "saturations": int(sat.sum()),
+                "compression": 3 * 32.0 / (2 * bits[0] + bits[1]), "runs": runs,
+            })
+    return {"z_ref": z0, "g": list(g), "g_se": list(sens["g_se"]), "beta": list(sens["beta"]),
+            "beta_se": list(sens["beta_se"]), "lo": list(ref["lo"]), "hi": list(ref["hi"]), "results": out}

@@ -15,7 +15,9 @@ mathematics fixes, CPU only:
     store, combined with the dither's rounding variance Delta^2 / 6 (Sec. 5), predict the
     variance of z over dither seeds (Eq. 8's linear error propagation);
   - follow mode: codes taken from the oracle itself are all accepted, a code moved by one
-    far from a tie is a violation."""
+    far from a tie is a violation;
+  - antithetic noise injection estimates the FD sensitivities g_h, and the mean shift of
+    z under dithered stores equals that under noise of the same variance."""
 import numpy as np
 import pytest
 
@@ -266,8 +268,9 @@ def test_follow_accepts_own_codes_and_rejects_far_changes(oracle):
 
 
 def test_antithetic_noise_estimates_the_sensitivities(oracle):
-    """E[((z+ - z-) / 2)^2] / sigma_h^2 over random +-sigma_h injections at every store of
-    type h is g_h (the FD sum over the same stores): the estimator the kernels use."""
+    """Over random +-sigma_h injections at every store of type h, E[((z+ - z-) / 2)^2] is
+    sigma_h^2 g_h (the FD sum over the same stores): the estimator the kernels use for
+    Eq. 8's linear term."""
     sc, T = plume(n=12, jacobi=8, T=2)
     state = generic_state(12)
     G = fd_sensitivities(oracle, sc, T, state)
@@ -286,3 +289,37 @@ def test_antithetic_noise_estimates_the_sensitivities(oracle):
         se = est.std(ddof=1) / np.sqrt(pairs)
         assert abs(est.mean() - G[h]) < 4 * se, (h, est.mean(), G[h], se)
         assert se < 0.15 * G[h]
+
+
+def test_dither_bias_has_the_sign_and_size_of_equal_variance_noise(oracle):
+    """The premise of the second-order term: a dithered store errs by zero-mean noise of
+    variance Delta^2 / 6 on average (Sec. 5), so the mean shift of z under dithered stores
+    has the sign and the order of magnitude of the shift under +-Delta/sqrt(6) noise at the
+    same stores.  Only that: where a stored value's fraction is not uniform (values on a
+    coarser lattice, exact zeros) the dither errs less than the noise, and the advection's
+    piecewise-bilinear sampling makes the shift depend on the noise scale, which is why the
+    kernels estimate it at each scheme's own scale."""
+    sc, T = plume(n=24, jacobi=8, T=8)
+    state = generic_state(24)
+    r0 = oracle.SmokeRollout(sc, None, *state)
+    r0.step(T)
+    z0 = r0.measure()
+    fv, fp = 5, 8
+    sch = {"v": dict(bits=16, frac=fv, offset=-(1 << 15)), "p": dict(bits=16, frac=fp, offset=-(1 << 15))}
+    sig = (2.0 ** -fv / 6 ** 0.5, 2.0 ** -fp / 6 ** 0.5)
+    K = 300
+    zq, zn = [], []
+    for k in range(K):
+        r = oracle.SmokeRollout(dict(sc, seed=5000 + k), sch, *state)
+        r.step(T)
+        assert r.saturations == 0
+        zq.append(r.measure() - z0)
+        with oracle.smoke_noise(sig, 9000 + k, 1.0):
+            r = oracle.SmokeRollout(sc, None, *state)
+            r.step(T)
+        zn.append(r.measure() - z0)
+    zq, zn = np.array(zq), np.array(zn)
+    se_q, se_n = zq.std(ddof=1) / np.sqrt(K), zn.std(ddof=1) / np.sqrt(K)
+    assert zq.mean() < -5 * se_q and zn.mean() < -5 * se_n, (zq.mean(), zn.mean(), se_q, se_n)
+    assert 0.5 < zq.mean() / zn.mean() < 2.0, (zq.mean(), zn.mean())
+    assert 0.6 < zq.std() / zn.std() < 1.25
