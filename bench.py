@@ -337,7 +337,7 @@ def cpu_baseline(name, sample_steps=2):
 # ------------------------------------------------------------------------------ smoke
 SMOKE_METRIC = "quantized 2D smoke cell-steps/s (advection-reflection, 64 Jacobi sweeps per projection)"
 SMOKE_UNIT = "cell-steps/s"
-SMOKE_FIXED_SCHEME = {"v": dict(bits=12, frac=9, offset=-1808), "p": dict(bits=14, frac=18, offset=-4288)}
+SMOKE_FIXED_SCHEME = {"v": dict(bits=13, frac=10, offset=-3616), "p": dict(bits=14, frac=18, offset=-4288)}
 
 
 def smoke_counters():
@@ -369,7 +369,7 @@ def smoke_section(args, peaks, dc, torch):
     n = sc["n"]
     if args.smoke_fixed_scheme:
         scheme = SMOKE_FIXED_SCHEME
-        source = "written down: the bias-aware solve's eps 1e-3 result on this scene (bits 12/14, frac 9/18)"
+        source = "written down: the bias-aware solve's eps 1e-3 result on this scene (bits 13/14, frac 10/18)"
     else:
         scheme, rep = smoke.solve(sc, T, 1e-3, bias_aware=True)
         source = ("qmpm_scheme_solve at eps 1e-3 on z = sum d^2 after 100 steps, noise-injection "
