@@ -218,7 +218,7 @@ struct Sizes {
     size_t bytes() const
     {
         return 2 * (words * 4 + ids * 8 + grid * 16 + touched + keys * 4 * 2) + digit_counts * 4 +
-               scan_partials * 4 + 3 * seg * 4 + 2 * key_chunks * 4 + chunks * sizeof(qmpm::Chunk) + 16 * 8 + 8;
+               scan_partials * 4 + 3 * seg * 4 + 2 * key_chunks * 4 + chunks * sizeof(qmpm::Chunk) + 17 * 8 + 8;
     }
 };
 
@@ -306,7 +306,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
     ok = ok && dalloc(&c->chunks, z.chunks, st) == cudaSuccess;
     ok = ok && dalloc(&c->tile_idx, z.key_chunks, st) == cudaSuccess;
     ok = ok && dalloc(&c->tile_first, z.seg, st) == cudaSuccess;
-    ok = ok && dalloc(&c->d_stats, 16, st) == cudaSuccess;
+    ok = ok && dalloc(&c->d_stats, 17, st) == cudaSuccess;  // 16 statistics + the step kernels' tile queue
     ok = ok && dalloc(&c->d_z, 1, st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -328,7 +328,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
             return cuda_fail(e, "grid clear");
         }
     }
-    e = cudaMemsetAsync(c->d_stats, 0, 16 * sizeof(unsigned long long), c->stream);
+    e = cudaMemsetAsync(c->d_stats, 0, 17 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) {
         release(c);
         return cuda_fail(e, "stats clear");

@@ -66,6 +66,7 @@ struct StepParams {
     uint8_t *touched_out;       // blocks of grid_out that received mass
     unsigned long long *stats;  // QMPM_FLAG_STATS counters (13) or null
     const uint32_t *step_ctr;   // multi-scene launches: steps done so far (the store uses + 1)
+    uint32_t *work;             // [0] next tile to take, [1] CTAs finished; both 0 between launches
 };
 
 // Grid buffer of one member of a multi-scene clear.
@@ -135,7 +136,7 @@ struct Ctx {
 
     qmpm_batch *batch;          // the batch the scene steps in, or null
 
-    unsigned long long *d_stats; // 16 counters
+    unsigned long long *d_stats; // 16 counters, then the step kernels' tile queue (2 x u32)
     double *d_z;
     int64_t steps;
     CompCodec cc[kMaxComp];
