@@ -334,7 +334,7 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
                     const CompCodec &cc = P.comp[c];
                     const uint32_t u = encode_f32(val[c], cc, P.dither != 0, dither_threshold(rnd, c), fl);
                     atomicOr(my + cc.word * kThreads, u << cc.shift);
-                    atomicOr(my + (cc.word + 1) * kThreads, __funnelshift_l(u, 0u, cc.shift));
+                    if (cc.straddle) atomicOr(my + (cc.word + 1) * kThreads, __funnelshift_l(u, 0u, cc.shift));
                     val[c] = decode_u(u, cc);  // the stored (quantized) value
                     if (STATS) {
                         // the field of component c (x, v, C, F/J), folded at compile time
@@ -506,20 +506,20 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
 // stride: tiles hold from one to sixteen chunks, and a fixed stride left the average SM
 // idle for 6 % of the launch.  The last CTA to finish puts both words back to zero for the
 // next launch (every CTA has taken its last ticket before it counts itself finished).
-__device__ __forceinline__ uint32_t take_tile(const StepParams &P, uint32_t *slot)
+__device__ __forceinline__ uint32_t take_tile(uint32_t *work, uint32_t *slot)
 {
-    if (threadIdx.x == 0) *slot = atomicAdd(P.work, 1u);
+    if (threadIdx.x == 0) *slot = atomicAdd(work, 1u);
     __syncthreads();
     return *slot;
 }
 
-__device__ __forceinline__ void finish_launch(const StepParams &P)
+__device__ __forceinline__ void finish_launch(uint32_t *work)
 {
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(P.work + 1, 1u) == gridDim.x - 1) {
-            P.work[0] = 0u;
-            P.work[1] = 0u;
+        if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
+            work[0] = 0u;
+            work[1] = 0u;
             __threadfence();
         }
     }
@@ -536,12 +536,12 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>()) step
     for (;;) {
         // run_chunk ends with a barrier, so every thread has read the ticket before thread 0
         // takes the next one
-        const uint32_t ti = take_tile(P, &ticket);
+        const uint32_t ti = take_tile(P.work, &ticket);
         if (ti >= n_tiles) break;
         run_chunk<DIM, MAT, QUANT, STATS, DO_G2P>(P, P.tile_first[ti], 0u, cnt, tid, pj);
     }
     if (STATS) flush_counters(cnt, P.stats);
-    finish_launch(P);
+    finish_launch(P.work);
 }
 
 // One scene of a batch stepped by its own launch (parameters in the constant bank, as the
@@ -558,17 +558,17 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>())
     const uint32_t n_tiles = *P.n_tiles;
     __shared__ uint32_t ticket;
     for (;;) {
-        const uint32_t ti = take_tile(P, &ticket);
+        const uint32_t ti = take_tile(P.work, &ticket);
         if (ti >= n_tiles) break;
         run_chunk<DIM, MAT, QUANT, STATS, true, true>(P, P.tile_first[ti], step, cnt, tid, pj);
     }
     if (STATS) flush_counters(cnt, P.stats);
-    finish_launch(P);
+    finish_launch(P.work);
 }
 
 // Multi-scene launch: the work queue is the concatenation of the members' tile lists
-// (member-major); each CTA strides over it, copying a member's parameters into shared
-// memory when its items move on to the next member.  The members share the template
+// (member-major); the CTAs take its items in turn, copying a member's parameters into
+// shared memory when their items move on to the next member.  The members share the template
 // class (dimension, material, quantized or not); everything else (grid size, scheme,
 // physics, buffers, step index) is per member.
 // (Two CTAs per SM: with the parameters in shared memory, 80 registers would spill.)
@@ -591,7 +591,13 @@ __global__ void __launch_bounds__(kThreads, 2)
     StepCounters cnt;
     int cur = -1;
     uint32_t step = 0;
-    for (uint32_t item = blockIdx.x; item < total; item += gridDim.x) {
+    // the launch's queue of items lives in the first member's queue words (a member is in
+    // one launch at a time)
+    uint32_t *queue = tab[0].work;
+    __shared__ uint32_t ticket;
+    for (;;) {
+        const uint32_t item = take_tile(queue, &ticket);
+        if (item >= total) break;
         int lo = 0, hi = n_members;  // first[lo] <= item < first[hi]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -611,6 +617,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         run_chunk<DIM, MAT, QUANT, STATS, true, true>(Ps, Ps.tile_first[item - first[lo]], step, cnt, tid, pj);
     }
     if (STATS && cur >= 0) flush_counters(cnt, Ps.stats);
+    finish_launch(queue);
 }
 
 // ------------------------------------------------------------------------------ grid clear
