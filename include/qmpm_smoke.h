@@ -47,7 +47,9 @@ typedef struct {
     float dt;
     float buoyancy;     /* v += dt * buoyancy * density */
     float v_in;         /* inflow velocity inside the source box */
-    float src[4];       /* source box x0, y0, x1, y1 in [0,1] */
+    double src[4];      /* source box x0, y0, x1, y1 in [0,1]; a sample is inside when its
+                           position ((i + 1/2) h for cells, j h for y-faces) lies in the box,
+                           compared in FP64 */
     int32_t dither;     /* 1: dithered stores (Sec. 5), 0: round to nearest */
     int32_t flags;      /* QMPM_SMOKE_RANGES: record the range of every type's stored values;
                            QMPM_SMOKE_PROFILE: time the Jacobi sweeps (qmpm_smoke_profile) */

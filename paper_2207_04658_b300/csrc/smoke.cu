@@ -41,7 +41,7 @@ struct Fld {
 struct Params {
     int n, J, su;              // su: padded row length of u (n + 32)
     int qfin;                  // buffer holding a projection's last iterate
-    float dt, buoy, v_in, inv_h, h, h2;
+    float dt, buoy, v_in, inv_h, h2;
     int box[6];                // source box as index ranges (inclusive): cell x, cell y, v-face y
     int quant, dither, ranges;
     CompCodec cc[2];           // 0 velocity, 1 pressure (word/shift unused)
@@ -144,42 +144,66 @@ __device__ __forceinline__ float lat_at(const Lat &L, int i, int j, const CompCo
     return ld<PK>(L.f, (int64_t)j * L.ld + i, c, bits);
 }
 
-// Bilinear sample at lattice coordinates (gx, gy), clamped into the lattice.
-template <bool PK>
-__device__ __forceinline__ float sample(const Lat &L, float gx, float gy, const CompCodec &c, int bits)
+// A point in cell units, (ci + fx, cj + fy): an integer part and a float offset that stays
+// within a few cells of the sample point a backtrace starts from, so the position keeps
+// its precision on any grid size (a single FP32 coordinate of a 4096-cell grid carries only
+// 2^-11 cells).
+struct Pt {
+    int ci, cj;
+    float fx, fy;
+};
+
+// One axis of a lattice coordinate gi + gf clamped into [0, n - 1]: the base index (at
+// most n - 2) and the weight of the next sample.
+__device__ __forceinline__ void lattice_axis(int gi, float gf, int n, int &i, float &f)
 {
-    gx = fminf(fmaxf(gx, 0.0f), (float)(L.nx - 1));
-    gy = fminf(fmaxf(gy, 0.0f), (float)(L.ny - 1));
-    int i = (int)floorf(gx), j = (int)floorf(gy);
-    i = min(max(i, 0), L.nx - 2);
-    j = min(max(j, 0), L.ny - 2);
-    const float fx = gx - (float)i, fy = gy - (float)j;
+    const float fl = floorf(gf);
+    i = gi + (int)fl;
+    f = gf - fl;
+    if (i < 0) {
+        i = 0;
+        f = 0.0f;
+    } else if (i >= n - 1) {
+        i = n - 2;
+        f = 1.0f;
+    }
+}
+
+// Bilinear sample at the point p of a lattice whose sample (0, 0) sits at cell coordinates
+// (ox, oy), clamped into the lattice.
+template <bool PK>
+__device__ __forceinline__ float sample(const Lat &L, const Pt &p, float ox, float oy, const CompCodec &c, int bits)
+{
+    int i, j;
+    float fx, fy;
+    lattice_axis(p.ci, p.fx - ox, L.nx, i, fx);
+    lattice_axis(p.cj, p.fy - oy, L.ny, j, fy);
     const float a = lat_at<PK>(L, i, j, c, bits), b = lat_at<PK>(L, i + 1, j, c, bits);
     const float e = lat_at<PK>(L, i, j + 1, c, bits), g = lat_at<PK>(L, i + 1, j + 1, c, bits);
     return (1.0f - fy) * ((1.0f - fx) * a + fx * b) + fy * ((1.0f - fx) * e + fx * g);
 }
 
-// Velocity (u lattice PU, v lattice PV) at a point in domain units.
+// Velocity (u lattice PU, v lattice PV) at p: u samples sit at (i, j + 1/2), v samples at
+// (i + 1/2, j) in cell units.
 template <bool PU, bool PV>
-__device__ __forceinline__ void vel_at(const Params &P, const Lat &U, const Lat &V, float x, float y, float &ux,
-                                       float &vy)
+__device__ __forceinline__ void vel_at(const Params &P, const Lat &U, const Lat &V, const Pt &p, float &ux, float &vy)
 {
-    const float n = P.inv_h;
-    ux = sample<PU>(U, x * n, y * n - 0.5f, P.cc[0], P.bits[0]);
-    vy = sample<PV>(V, x * n - 0.5f, y * n, P.cc[0], P.bits[0]);
+    ux = sample<PU>(U, p, 0.0f, 0.5f, P.cc[0], P.bits[0]);
+    vy = sample<PV>(V, p, 0.5f, 0.0f, P.cc[0], P.bits[0]);
 }
 
-// Ralston's RK-3 backtrace over s.
+// Ralston's RK-3 backtrace over s from p (velocities in domain units per second; one domain
+// unit is n cells).
 template <bool PU, bool PV>
-__device__ __forceinline__ void backtrace(const Params &P, const Lat &U, const Lat &V, float s, float x, float y,
-                                          float &xb, float &yb)
+__device__ __forceinline__ Pt backtrace(const Params &P, const Lat &U, const Lat &V, float s, const Pt &p)
 {
+    const float sn = s * P.inv_h;
     float k1x, k1y, k2x, k2y, k3x, k3y;
-    vel_at<PU, PV>(P, U, V, x, y, k1x, k1y);
-    vel_at<PU, PV>(P, U, V, x - 0.5f * s * k1x, y - 0.5f * s * k1y, k2x, k2y);
-    vel_at<PU, PV>(P, U, V, x - 0.75f * s * k2x, y - 0.75f * s * k2y, k3x, k3y);
-    xb = x - s * (2.0f * k1x + 3.0f * k2x + 4.0f * k3x) / 9.0f;
-    yb = y - s * (2.0f * k1y + 3.0f * k2y + 4.0f * k3y) / 9.0f;
+    vel_at<PU, PV>(P, U, V, p, k1x, k1y);
+    vel_at<PU, PV>(P, U, V, Pt{p.ci, p.cj, p.fx - 0.5f * sn * k1x, p.fy - 0.5f * sn * k1y}, k2x, k2y);
+    vel_at<PU, PV>(P, U, V, Pt{p.ci, p.cj, p.fx - 0.75f * sn * k2x, p.fy - 0.75f * sn * k2y}, k3x, k3y);
+    return Pt{p.ci, p.cj, p.fx - sn * (2.0f * k1x + 3.0f * k2x + 4.0f * k3x) / 9.0f,
+              p.fy - sn * (2.0f * k1y + 3.0f * k2y + 4.0f * k3y) / 9.0f};
 }
 
 // Warp-reduced range keys into one of the scene's slots (whole warp calls).
@@ -298,9 +322,8 @@ __global__ void __launch_bounds__(kT) advect_vel_kernel(Params P, uint32_t *trac
         const bool valid = i <= n, wall = i == 0 || i == n;
         float x = 0.0f;
         if (valid && !wall) {
-            float xb, yb;
-            backtrace<Q, PV>(P, WU, WV, half, (float)i * P.h, ((float)j + 0.5f) * P.h, xb, yb);
-            x = sample<Q>(FU, xb * P.inv_h, yb * P.inv_h - 0.5f, P.cc[0], P.bits[0]);
+            const Pt pb = backtrace<Q, PV>(P, WU, WV, half, Pt{i, j, 0.0f, 0.5f});
+            x = sample<Q>(FU, pb, 0.0f, 0.5f, P.cc[0], P.bits[0]);
         }
         const uint32_t k = (uint32_t)(j * (n + 1) + i);
         Fld o = STAGE == 1 ? P.ut : P.u;
@@ -311,9 +334,8 @@ __global__ void __launch_bounds__(kT) advect_vel_kernel(Params P, uint32_t *trac
         const bool wall = j == 0 || j == n;
         float x = 0.0f;
         if (!wall) {
-            float xb, yb;
-            backtrace<Q, PV>(P, WU, WV, half, ((float)i + 0.5f) * P.h, (float)j * P.h, xb, yb);
-            x = sample<PV>(FV, xb * P.inv_h - 0.5f, yb * P.inv_h, P.cc[0], P.bits[0]);
+            const Pt pb = backtrace<Q, PV>(P, WU, WV, half, Pt{i, j, 0.5f, 0.0f});
+            x = sample<PV>(FV, pb, 0.5f, 0.0f, P.cc[0], P.bits[0]);
         }
         const uint32_t k = (uint32_t)tv;
         Fld o = STAGE == 1 ? P.vt : P.v;
@@ -591,9 +613,8 @@ __global__ void __launch_bounds__(kT) advect_d_kernel(Params P)
     const Lat WU{P.up.p + s * P.up.ss, P.su, n + 1, n};
     const Lat WV{P.vp.p + s * P.vp.ss, n, n, n + 1};
     const Lat D{reinterpret_cast<const uint32_t *>(P.d[par] + s * P.ncell_s), n, n, n};
-    float xb, yb;
-    backtrace<Q, Q>(P, WU, WV, P.dt, ((float)i + 0.5f) * P.h, ((float)j + 0.5f) * P.h, xb, yb);
-    P.d[par ^ 1u][s * P.ncell_s + t] = sample<false>(D, xb * P.inv_h - 0.5f, yb * P.inv_h - 0.5f, P.cc[0], 0);
+    const Pt pb = backtrace<Q, Q>(P, WU, WV, P.dt, Pt{i, j, 0.5f, 0.5f});
+    P.d[par ^ 1u][s * P.ncell_s + t] = sample<false>(D, pb, 0.5f, 0.5f, P.cc[0], 0);
 }
 
 __global__ void advance_kernel(uint32_t *ctr) { *ctr += 1u; }
@@ -823,7 +844,6 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
     P.buoy = cfg->buoyancy;
     P.v_in = cfg->v_in;
     P.inv_h = (float)n;
-    P.h = 1.0f / (float)n;
     P.h2 = 1.0f / ((float)n * (float)n);
     // the box as index ranges: the samples whose position (cell centre (i + 1/2) h, y-face
     // j h) lies in [src0, src2] x [src1, src3], decided in FP64 on the host
@@ -842,7 +862,7 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
                 }
             }
         };
-        range(cfg->src[0], cfg->src[2], 0.5, n, P.box[0], P.box[1]);
+        range(cfg->src[0], cfg->src[2], 0.5, n, P.box[0], P.box[1]);  // the oracle's comparisons, in FP64
         range(cfg->src[1], cfg->src[3], 0.5, n, P.box[2], P.box[3]);
         range(cfg->src[1], cfg->src[3], 0.0, n + 1, P.box[4], P.box[5]);
     }

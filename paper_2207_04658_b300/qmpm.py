@@ -162,7 +162,7 @@ _lib = None
 # (name, restype, argtypes) of every entry point declared in include/qmpm.h
 class qmpm_smoke_config_t(ct.Structure):
     _fields_ = [("n", ct.c_int32), ("jacobi", ct.c_int32), ("dt", ct.c_float), ("buoyancy", ct.c_float),
-                ("v_in", ct.c_float), ("src", ct.c_float * 4), ("dither", ct.c_int32), ("flags", ct.c_int32)]
+                ("v_in", ct.c_float), ("src", ct.c_double * 4), ("dither", ct.c_int32), ("flags", ct.c_int32)]
 
 
 class qmpm_smoke_scheme_t(ct.Structure):

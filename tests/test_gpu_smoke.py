@@ -249,3 +249,32 @@ def test_bias_aware_schemes_meet_the_error_bound(sm):
         assert 0.3 < r["z_std"] / r["pred_sigma_dither"] < 3.0, r
         # the scheme still compresses the quantized fields
         assert r["compression"] > 1.5, r
+
+
+def test_largest_grid_fp32_matches_fp64(sm, oracle):
+    """The largest grid the C ABI accepts (4096^2, 16.8 M cells), one step against the FP64
+    oracle: the tiles, the packed-row padding and the index arithmetic at full size."""
+    sc = plume(n=4096, jacobi=8)
+    with sm.Smoke(sc) as g:
+        g.step(1)
+        st = g.readback(0)
+    o = oracle_run(oracle, sc, 1)
+    for k, ref in (("u", o.u), ("v", o.v), ("d", o.d), ("q", o.q)):
+        err = np.abs(st[k] - ref).max() / scale(ref)
+        assert err < 2e-5, (k, err)
+
+
+@pytest.mark.parametrize("n", [160, 1024])
+def test_quantized_codes_match_oracle_ragged_and_large(sm, oracle, n):
+    """A grid whose width is not a multiple of the 128-cell tile (160: one full and one
+    32-cell tile per row) and a 1024^2 grid, every store of one step against the oracle."""
+    sc = plume(n=n, jacobi=8)
+    codes, st, sat = trace_run(sm, sc, SCHEME, 1)
+    o = oracle.SmokeRollout(sc, SCHEME)
+    with oracle.smoke_follow(codes, *taus(oracle, sc, SCHEME, 1)) as f:
+        o.step(1)
+    assert f.report[0] == codes.size and f.report[2] == 0, (f.report, f.first)
+    assert f.report[1] <= 1e-4 * f.report[0]
+    assert np.array_equal(st["u"].astype(np.float64), o.u)
+    assert np.array_equal(st["v"].astype(np.float64), o.v)
+    assert np.abs(st["d"] - o.d).max() < 1e-5
