@@ -9,8 +9,8 @@
 //   advect_vel  u~ = A(u; u, dt/2) or u~2 = A(u^; u', dt/2), then the velocity store
 //   divergence  FP32 div of a stored velocity
 //   jacobi      one Jacobi sweep of the pressure Poisson equation, then the pressure store
-//   gradsub     u - grad q on the interior faces, then the velocity store
-//   reflect     u^ = 2 u' - u~, then the velocity store
+//   gradsub     u - grad q on the interior faces, then the velocity store (after the first
+//               projection also the reflection u^ = 2 u' - u~ and its store)
 //   advect_d    d = A(d; u', dt) (FP32)
 //   advance     steps done += 1 (the kernels take the step index and the density buffer
 //               parity from that device counter, so one captured step replays as is)
@@ -536,9 +536,11 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
 }
 
 // out = in - grad q on interior faces (q = the last sweep's iterate; none when J = 0), then
-// the velocity store.  STAGE 2: (ut, vt) -> (up, vp); STAGE 5: (u, v) in place.
+// the velocity store.  STAGE 2: (ut, vt) -> (up, vp), followed by the reflection
+// u^ = 2 u' - u~ stored over (ut, vt) (store J + 3, no noise: an integer combination of two
+// stored values of one lattice is itself on it); STAGE 5: (u, v) in place.
 template <bool Q, int STAGE>
-__global__ void __launch_bounds__(kT) gradsub_kernel(Params P, uint32_t *trace)
+__global__ void __launch_bounds__(kT) gradsub_kernel(Params P, uint32_t *trace, uint32_t *trace3)
 {
     const int s = blockIdx.y, n = P.n;
     const int64_t nu = (int64_t)n * P.su, nv = (int64_t)(n + 1) * n;
@@ -553,52 +555,32 @@ __global__ void __launch_bounds__(kT) gradsub_kernel(Params P, uint32_t *trace)
     if (t < nu) {
         const int i = (int)(t % P.su), j = (int)(t / P.su);
         const bool valid = i <= n, wall = i == 0 || i >= n;
-        float x = 0.0f;
+        const uint32_t k = (uint32_t)(j * (n + 1) + i);
+        float xin = 0.0f, x = 0.0f;
         if (valid && !wall) {
-            x = ld<Q>(fin_u.p + s * fin_u.ss, t, P.cc[0], P.bits[0]);
+            xin = ld<Q>(fin_u.p + s * fin_u.ss, t, P.cc[0], P.bits[0]);
+            x = xin;
             if (P.J > 0) x -= (ld<Q>(q, (int64_t)j * n + i, cq, bq) - ld<Q>(q, (int64_t)j * n + i - 1, cq, bq)) * P.inv_h;
         }
-        store<Q>(P, s, 0, 0, x, (uint32_t)(j * (n + 1) + i), counter, valid, wall, true, fo_u.p + s * fo_u.ss, t,
-                 trace);
+        const float y = store<Q>(P, s, 0, 0, x, k, counter, valid, wall, true, fo_u.p + s * fo_u.ss, t, trace);
+        if (STAGE == 2)  // u^ = 2 u' - u~ over u~ (store J + 3)
+            store<Q>(P, s, 0, 0, 2.0f * y - xin, k, counter + 1u, valid, wall, false, P.ut.p + s * P.ut.ss, t, trace3);
     } else {
         const int64_t tv = t - nu;
         const int i = (int)(tv % n), j = (int)(tv / n);
         const bool wall = j == 0 || j == n;
-        float x = 0.0f;
+        float xin = 0.0f, x = 0.0f;
         if (!wall) {
-            x = ld<Q>(fin_v.p + s * fin_v.ss, tv, P.cc[0], P.bits[0]);
+            xin = ld<Q>(fin_v.p + s * fin_v.ss, tv, P.cc[0], P.bits[0]);
+            x = xin;
             if (P.J > 0) x -= (ld<Q>(q, (int64_t)j * n + i, cq, bq) - ld<Q>(q, (int64_t)(j - 1) * n + i, cq, bq)) * P.inv_h;
         }
-        store<Q>(P, s, 0, 1, x, (uint32_t)tv, counter, true, wall, true, fo_v.p + s * fo_v.ss, tv,
-                 trace ? trace + (int64_t)(n + 1) * n : nullptr);
-    }
-}
-
-// u^ = 2 u' - u~ into (ut, vt), store J + 3 (no noise: the value of two stored values of
-// one lattice is itself on it).
-template <bool Q>
-__global__ void __launch_bounds__(kT) reflect_kernel(Params P, uint32_t *trace)
-{
-    const int s = blockIdx.y, n = P.n;
-    const int64_t nu = (int64_t)n * P.su, nv = (int64_t)(n + 1) * n;
-    const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
-    if (t - (threadIdx.x & 31) >= nu + nv) return;
-    const uint32_t counter = 1024u * step_index(P) + (uint32_t)P.J + 3u;
-    const CompCodec &c = P.cc[0];
-    const int b = P.bits[0];
-    if (t < nu) {
-        const int i = (int)(t % P.su), j = (int)(t / P.su);
-        const bool valid = i <= n;
-        float x = 0.0f;
-        if (valid) x = 2.0f * ld<Q>(P.up.p + s * P.up.ss, t, c, b) - ld<Q>(P.ut.p + s * P.ut.ss, t, c, b);
-        store<Q>(P, s, 0, 0, x, (uint32_t)(j * (n + 1) + i), counter, valid, i == 0 || i == n, false,
-                 P.ut.p + s * P.ut.ss, t, trace);
-    } else {
-        const int64_t tv = t - nu;
-        const int j = (int)(tv / n);
-        const float x = 2.0f * ld<Q>(P.vp.p + s * P.vp.ss, tv, c, b) - ld<Q>(P.vt.p + s * P.vt.ss, tv, c, b);
-        store<Q>(P, s, 0, 1, x, (uint32_t)tv, counter, true, j == 0 || j == n, false, P.vt.p + s * P.vt.ss, tv,
-                 trace ? trace + (int64_t)(n + 1) * n : nullptr);
+        const int64_t tvo = (int64_t)(n + 1) * n;
+        const float y = store<Q>(P, s, 0, 1, x, (uint32_t)tv, counter, true, wall, true, fo_v.p + s * fo_v.ss, tv,
+                                 trace ? trace + tvo : nullptr);
+        if (STAGE == 2)
+            store<Q>(P, s, 0, 1, 2.0f * y - xin, (uint32_t)tv, counter + 1u, true, wall, false, P.vt.p + s * P.vt.ss, tv,
+                     trace3 ? trace3 + tvo : nullptr);
     }
 }
 
@@ -745,7 +727,7 @@ int make_codec(int bits, int frac, int64_t offset, CompCodec &c)
     return 0;
 }
 
-unsigned launches_per_step(int J) { return 11u + 2u * (unsigned)((J + kK - 1) / kK); }
+unsigned launches_per_step(int J) { return 10u + 2u * (unsigned)((J + kK - 1) / kK); }
 
 template <bool Q>
 int enqueue_step(qmpm_smoke *h, uint32_t *trace)
@@ -783,14 +765,13 @@ int enqueue_step(qmpm_smoke *h, uint32_t *trace)
     mark(1);
     sweeps(1u, V);
     mark(2);
-    gradsub_kernel<Q, 2><<<gf, kT, 0, h->st>>>(P, tr(V + J * Pq));
-    reflect_kernel<Q><<<gf, kT, 0, h->st>>>(P, tr(2 * V + J * Pq));
+    gradsub_kernel<Q, 2><<<gf, kT, 0, h->st>>>(P, tr(V + J * Pq), tr(2 * V + J * Pq));
     advect_vel_kernel<Q, 4><<<gf, kT, 0, h->st>>>(P, tr(3 * V + J * Pq));
     divergence_kernel<Q><<<gc, kT, 0, h->st>>>(P, 1);
     mark(3);
     sweeps((uint32_t)J + 4u, 4 * V + J * Pq);
     mark(4);
-    gradsub_kernel<Q, 5><<<gf, kT, 0, h->st>>>(P, tr(4 * V + 2 * J * Pq));
+    gradsub_kernel<Q, 5><<<gf, kT, 0, h->st>>>(P, tr(4 * V + 2 * J * Pq), nullptr);
     advect_d_kernel<Q><<<gc, kT, 0, h->st>>>(P);
     advance_kernel<<<1, 1, 0, h->st>>>(P.ctr);
     mark(5);

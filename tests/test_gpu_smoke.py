@@ -194,7 +194,7 @@ def test_batch_invariance_and_graph_replay(sm):
         info = g.info()
     for k in "uvdq":
         assert np.array_equal(st[k], ss[k])
-    assert info["steps"] == 4 and info["launches_per_step"] == 11 + 2 * 2
+    assert info["steps"] == 4 and info["launches_per_step"] == 10 + 2 * 2
 
 
 def test_edge_cases(sm, oracle):
