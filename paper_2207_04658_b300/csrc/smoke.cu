@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -806,7 +807,8 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
         n_scenes > 4096 || !(cfg->dt > 0.0f))
         return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_create: n must be a multiple of 32 in 32..4096, jacobi "
                                           "0..500, n_scenes 1..4096, dt > 0");
-    auto *h = new qmpm_smoke();
+    auto *h = new (std::nothrow) qmpm_smoke();
+    if (!h) return fail(QMPM_ERR_OOM, "qmpm_smoke_create: host allocation failed");
     h->st = (cudaStream_t)stream;
     if (!h->st) {
         if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -856,15 +858,14 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
             cudaSuccess ||
         cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmem) !=
             cudaSuccess) {
-        if (h->own_stream) cudaStreamDestroy(h->st);
-        delete h;
+        qmpm_smoke_destroy(h);
         return fail(QMPM_ERR_CUDA, "qmpm_smoke_create: shared memory opt-in failed");
     }
     P.bits[0] = P.bits[1] = 32;
     if (h->quant) {
         for (int t = 0; t < 2; ++t) {
             if (make_codec(scheme->bits[t], scheme->frac[t], scheme->offset[t], P.cc[t])) {
-                delete h;
+                qmpm_smoke_destroy(h);  // nothing allocated yet but the stream
                 return fail(QMPM_ERR_SCHEME, "qmpm_smoke_create: bits outside 1..24 or |offset| >= 2^24");
             }
             P.bits[t] = scheme->bits[t];
