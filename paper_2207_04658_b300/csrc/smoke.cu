@@ -68,27 +68,33 @@ __device__ __forceinline__ unsigned int fkey(float x)
 // ---- packed bit streams --------------------------------------------------------------
 __device__ __forceinline__ uint32_t get_code(const uint32_t *f, int64_t pidx, int bits, uint32_t mask)
 {
-    const int64_t b = pidx * bits;
+    const uint32_t b = (uint32_t)pidx * (uint32_t)bits;  // a scene's stream holds < 2^32 bits
     const uint32_t *w = f + (b >> 5);
-    const int sh = (int)(b & 31);
+    const int sh = (int)(b & 31u);
     const uint64_t two = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
     return (uint32_t)(two >> sh) & mask;
 }
 
-// All 32 lanes of the warp call this with pidx = 32 g + lane.
+// All 32 lanes of the warp call this with pidx = 32 g + lane: the codes go through the
+// warp's 32 shared slots, and lane w < bits assembles word w of the group from the (at most
+// 32 / bits + 2) codes that overlap it.
 __device__ __forceinline__ void put_codes(uint32_t *f, int64_t pidx, uint32_t code, int bits)
 {
+    __shared__ uint32_t slots[kT];
     const int lane = threadIdx.x & 31;
-    const int bo = lane * bits, w0 = bo >> 5, sh = bo & 31;
-    const uint32_t lo = code << sh;
-    const uint32_t hi = (sh + bits > 32) ? (code >> (32 - sh)) : 0u;
-    uint32_t mine = 0u;
-    for (int w = 0; w < bits; ++w) {
-        const uint32_t part = (w == w0 ? lo : 0u) | (w == w0 + 1 ? hi : 0u);
-        const uint32_t word = __reduce_or_sync(0xffffffffu, part);
-        if (lane == w) mine = word;
+    uint32_t *sl = slots + (threadIdx.x & ~31);
+    __syncwarp();  // the previous call's reads are done
+    sl[lane] = code;
+    __syncwarp();
+    if (lane < bits) {
+        const int b0 = 32 * lane, m1 = min((b0 + 31) / bits, 31);
+        uint32_t word = 0u;
+        for (int m = b0 / bits; m <= m1; ++m) {
+            const int sh = m * bits - b0;
+            word |= sh >= 0 ? (sl[m] << sh) : (sl[m] >> -sh);
+        }
+        f[(pidx >> 5) * bits + lane] = word;
     }
-    if (lane < bits) f[(pidx >> 5) * bits + lane] = mine;
 }
 
 template <bool PK>
@@ -284,11 +290,11 @@ __global__ void __launch_bounds__(kT) forces_kernel(Params P)
     const uint32_t par = *P.ctr & 1u;
     float *d = P.d[par] + s * P.ncell_s;
     if (t < (int64_t)n * n) {
-        const int i = (int)(t % n), j = (int)(t / n);
+        const int i = (int)((uint32_t)t % (uint32_t)n), j = (int)((uint32_t)t / (uint32_t)n);
         if (cell_in_box(P, i, j)) d[t] = 1.0f;
     }
     if (t < (int64_t)(n + 1) * n) {
-        const int i = (int)(t % n), j = (int)(t / n);
+        const int i = (int)((uint32_t)t % (uint32_t)n), j = (int)((uint32_t)t / (uint32_t)n);
         float vv = 0.0f;
         if (j > 0 && j < n) {
             vv = ld<Q>(P.v.p + s * P.v.ss, t, P.cc[0], P.bits[0]);
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(kT) advect_vel_kernel(Params P, uint32_t *trac
     const Lat FV{vsrc, n, n, n + 1};
     const float half = 0.5f * P.dt;
     if (t < nu) {
-        const int i = (int)(t % P.su), j = (int)(t / P.su);
+        const int i = (int)((uint32_t)t % (uint32_t)P.su), j = (int)((uint32_t)t / (uint32_t)P.su);
         const bool valid = i <= n, wall = i == 0 || i == n;
         float x = 0.0f;
         if (valid && !wall) {
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(kT) advect_vel_kernel(Params P, uint32_t *trac
         store<Q>(P, s, 0, 0, x, k, counter, valid, wall, true, o.p + s * o.ss, t, trace);
     } else {
         const int64_t tv = t - nu;
-        const int i = (int)(tv % n), j = (int)(tv / n);
+        const int i = (int)((uint32_t)tv % (uint32_t)n), j = (int)((uint32_t)tv / (uint32_t)n);
         const bool wall = j == 0 || j == n;
         float x = 0.0f;
         if (!wall) {
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(kT) divergence_kernel(Params P, int which)  //
     const int s = blockIdx.y, n = P.n;
     const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (t >= (int64_t)n * n) return;
-    const int i = (int)(t % n), j = (int)(t / n);
+    const int i = (int)((uint32_t)t % (uint32_t)n), j = (int)((uint32_t)t / (uint32_t)n);
     const Fld fu = which == 0 ? P.ut : P.u, fv = which == 0 ? P.vt : P.v;
     const uint32_t *u = fu.p + s * fu.ss, *v = fv.p + s * fv.ss;
     const CompCodec &c = P.cc[0];
@@ -554,7 +560,7 @@ __global__ void __launch_bounds__(kT) gradsub_kernel(Params P, uint32_t *trace, 
     const Fld fin_u = STAGE == 2 ? P.ut : P.u, fin_v = STAGE == 2 ? P.vt : P.v;
     const Fld fo_u = STAGE == 2 ? P.up : P.u, fo_v = STAGE == 2 ? P.vp : P.v;
     if (t < nu) {
-        const int i = (int)(t % P.su), j = (int)(t / P.su);
+        const int i = (int)((uint32_t)t % (uint32_t)P.su), j = (int)((uint32_t)t / (uint32_t)P.su);
         const bool valid = i <= n, wall = i == 0 || i >= n;
         const uint32_t k = (uint32_t)(j * (n + 1) + i);
         float xin = 0.0f, x = 0.0f;
@@ -568,7 +574,7 @@ __global__ void __launch_bounds__(kT) gradsub_kernel(Params P, uint32_t *trace, 
             store<Q>(P, s, 0, 0, 2.0f * y - xin, k, counter + 1u, valid, wall, false, P.ut.p + s * P.ut.ss, t, trace3);
     } else {
         const int64_t tv = t - nu;
-        const int i = (int)(tv % n), j = (int)(tv / n);
+        const int i = (int)((uint32_t)tv % (uint32_t)n), j = (int)((uint32_t)tv / (uint32_t)n);
         const bool wall = j == 0 || j == n;
         float xin = 0.0f, x = 0.0f;
         if (!wall) {
@@ -591,7 +597,7 @@ __global__ void __launch_bounds__(kT) advect_d_kernel(Params P)
     const int s = blockIdx.y, n = P.n;
     const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (t >= (int64_t)n * n) return;
-    const int i = (int)(t % n), j = (int)(t / n);
+    const int i = (int)((uint32_t)t % (uint32_t)n), j = (int)((uint32_t)t / (uint32_t)n);
     const uint32_t par = *P.ctr & 1u;
     const Lat WU{P.up.p + s * P.up.ss, P.su, n + 1, n};
     const Lat WV{P.vp.p + s * P.vp.ss, n, n, n + 1};
@@ -636,14 +642,14 @@ __global__ void __launch_bounds__(kT) set_state_kernel(Params P, int s, const fl
     float x = 0.0f;
     bool valid = true;
     if (t < nu) {
-        const int i = (int)(t % P.su), j = (int)(t / P.su);
+        const int i = (int)((uint32_t)t % (uint32_t)P.su), j = (int)((uint32_t)t / (uint32_t)P.su);
         valid = i <= n;
         if (valid && i > 0 && i < n && u) x = u[(int64_t)j * (n + 1) + i];
         out = P.u.p + s * P.u.ss;
         pidx = t;
     } else {
         const int64_t tv = t - nu;
-        const int j = (int)(tv / n);
+        const int j = (int)((uint32_t)tv / (uint32_t)n);
         if (j > 0 && j < n && v) x = v[tv];
         out = P.v.p + s * P.v.ss;
         pidx = tv;
