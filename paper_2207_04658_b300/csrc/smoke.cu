@@ -373,8 +373,9 @@ __global__ void __launch_bounds__(kT) divergence_kernel(Params P, int which)  //
 // sweeps there (every sweep's values stored through the codec: encode, then the decoded
 // value is what the next sweep reads) and writes the tile's last iterate to q[src ^ 1].
 // The halo's values go wrong by one cell per sweep from the region's edge inward, so
-// after kK sweeps the tile itself is still exact; halo cells are recomputed bit for bit
-// as their own tile computes them (same inputs, same arithmetic, same dither draw).  A
+// after kK sweeps the tile itself is still exact (each sweep computes only the cells within
+// the remaining sweeps' reach of the tile); halo cells are recomputed bit for bit as their
+// own tile computes them (same inputs, same arithmetic, same dither draw).  A
 // thread takes octets, 8 consecutive cells of a row aligned to 8 (one Philox block serves
 // all 8: their dither counter is (cell / 8, counter, 2, 0), lanes cell % 8).  Only tile
 // cells count saturations, record ranges and write the trace (sweep k of the launch to
@@ -422,8 +423,12 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
         const int it = it0 + k;
         const uint32_t counter = step_base + (uint32_t)it;
         const bool last = k == nsweep - 1;
-        for (int e = threadIdx.x; e < kRO * (kRH - 2); e += kT) {
-            const int ry = 1 + e / kRO, ro = e % kRO;
+        // only what the tile's last sweep still depends on: r more rows and cells on each
+        // side of the tile, r = the sweeps left after this one
+        const int r = nsweep - 1 - k;
+        const int ro_lo = (kHX - r) / 8, ro_hi = (kHX + w - 1 + r) / 8, ncol = ro_hi - ro_lo + 1;
+        for (int e = threadIdx.x; e < (kTY + 2 * r) * ncol; e += kT) {
+            const int ry = kK - r + e / ncol, ro = ro_lo + e % ncol;
             const int gy = gy0 + ry, gx = gx0 + ro * 8;
             if (gy < 0 || gy >= n || gx < 0 || gx >= n) continue;
             const float *rc = cur + ry * kRW + ro * 8;
