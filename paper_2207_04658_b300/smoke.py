@@ -95,6 +95,10 @@ class Smoke:
         if trace is None:
             _check(lib().qmpm_smoke_step(self.h, int(steps), None, 0))
         else:
+            import torch
+            # the tensor's allocation and fill are ordered on torch's stream, the handle's
+            # kernels on its own: let the former finish first
+            torch.cuda.current_stream(trace.device).synchronize()
             _check(lib().qmpm_smoke_step(self.h, int(steps), ct.c_void_p(trace.data_ptr()), int(trace.numel())))
 
     def measure(self):
