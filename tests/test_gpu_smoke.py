@@ -278,3 +278,37 @@ def test_quantized_codes_match_oracle_ragged_and_large(sm, oracle, n):
     assert np.array_equal(st["u"].astype(np.float64), o.u)
     assert np.array_equal(st["v"].astype(np.float64), o.v)
     assert np.abs(st["d"] - o.d).max() < 1e-5
+
+
+def test_bench_configuration_against_oracle(sm, oracle):
+    """The benchmark's configuration (the 256^2 plume, 64 sweeps, the bias-aware eps 1e-3
+    scheme: v 13 bits, p 14 bits) in a batch of scenes: every store of scene 0's first two
+    steps against the oracle, and another scene's state after two steps against the oracle
+    with that scene's seed (the batch stores what single runs store)."""
+    import torch
+    from paper_2207_04658_b300 import scenes
+    sc = scenes.smoke_scene()
+    sch = {"v": dict(bits=13, frac=10, offset=-3616), "p": dict(bits=14, frac=18, offset=-4288)}
+    T = 2
+    seeds = [sc["seed"], 1234, 99]
+    with sm.Smoke(sc, sch, len(seeds), seeds=seeds) as g:
+        tr = torch.zeros(g.trace_len(T), dtype=torch.int32, device="cuda")
+        g.step(T, trace=tr)
+        st0, st2 = g.readback(0), g.readback(2)
+        _, _, sat = g.ranges()
+    codes = tr.cpu().numpy().view(np.uint32)
+    o = oracle.SmokeRollout(sc, sch)
+    with oracle.smoke_follow(codes, *taus(oracle, sc, sch, T)) as f:
+        o.step(T)
+    assert f.report[0] == codes.size and f.report[2] == 0, (f.report, f.first)
+    assert f.report[1] <= 1e-4 * f.report[0]
+    assert o.saturations == int(sat[0].sum()) == 0
+    assert np.array_equal(st0["u"].astype(np.float64), o.u)
+    assert np.array_equal(st0["v"].astype(np.float64), o.v)
+    assert np.abs(st0["d"] - o.d).max() < 1e-5
+    # scene 2 (no trace): same dither rule with its own seed; near-ties may flip a code, so
+    # compare in quanta
+    o2 = oracle.SmokeRollout(dict(sc, seed=99), sch)
+    o2.step(T)
+    dq = np.abs(st2["u"] - o2.u).max() / 2.0 ** -10
+    assert dq <= 2.0 and np.abs(st2["d"] - o2.d).max() < 1e-3, dq
