@@ -7,13 +7,17 @@ rollouts that differ only in their dither seed, and compare
   * the mean deviation (bias; dithering makes the store unbiased, Sec. 5);
   * the success rate: runs within the paper's band |z~ - z| <= 3 eps z (Sec. 8.1), and
     within eps z;
-  * the memory of the scheme (bits per particle vs FP32).
+  * the memory of the scheme (bits per particle vs FP32);
+
+and, with --optimality, the optimality check (bits taken from all or half of the fields,
+bits moved between fields) and the dithering experiment (with and without dithered stores,
+round-up / round-down ratios).
 
 Everything runs through the library (adjoint, solve, rollouts).  The reference z is
 supplied by the caller (the FP64 oracle in the tests); the command line uses the FP32 run
 of the same kernels.
 
-    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300] [--smoke]
+    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300] [--smoke | --optimality]
 """
 import argparse
 import json
@@ -65,11 +69,81 @@ def error_bound_protocol(scene, state0, T, eps_list, runs, z_ref, ckpt_every=25,
     return out
 
 
+def _rollouts(scene, state0, T, scheme, runs, seed0, dither=True, stats=False):
+    """z of `runs` quantized rollouts differing only in their dither seed, and the summed
+    round-up / round-down counters per field when `stats`."""
+    zs, ups, dns = [], np.zeros(4, np.int64), np.zeros(4, np.int64)
+    for r in range(runs):
+        g = qmpm.Scene(dict(scene, seed=seed0 + r, dither=dither), scheme, state0, stats=stats)
+        g.step(T)
+        rb = g.readback(state=True, ids=False)
+        zs.append(kinetic_energy(scene, rb["state"]))
+        if stats:
+            ups += np.asarray(rb["stats"]["round_ups"], np.int64)
+            dns += np.asarray(rb["stats"]["round_downs"], np.int64)
+        g.close()
+    return np.asarray(zs), ups, dns
+
+
+def shift_bits(field, k):
+    """A field's scheme with k fewer bits (k < 0: more) over the same window: the resolution
+    doubles per bit taken."""
+    f = dict(field)
+    f["bits"], f["frac"] = f["bits"] - k, f["frac"] - k
+    f["offset"] = f["offset"] >> k if k >= 0 else f["offset"] << -k
+    return f
+
+
+def optimality_check(scene, state0, T, z_ref, eps=0.01, runs=20, takes=(1, 2, 3), move_runs=10, seed=7,
+                     ckpt_every=25, seed0=3000):
+    """The optimality check of Sec. 8.1 on the scheme Algorithm 1 solves at eps: take k bits
+    from every field, or from a random half of the fields, and move one bit between fields
+    (x <-> v, C <-> F); success = |z~ - z| <= 3 eps z over repeated dithered rollouts."""
+    info = qmpm.sensitivities(scene, state0, T, ckpt_every, qmpm.MEASURE_KINETIC_ENERGY)
+    base, res = qmpm.solve_scheme(info, eps, material=scene["material"])
+    names = [k for k in ("x", "v", "C", "F", "J") if k in base]
+    gen = np.random.default_rng(seed)
+
+    def trial(scheme, n):
+        zs, _, _ = _rollouts(scene, state0, T, scheme, n, seed0)
+        dev = zs - z_ref
+        return {"bits": [scheme[k]["bits"] for k in names], "success_3eps": float(np.mean(np.abs(dev) <= 3 * eps * abs(z_ref))),
+                "z_mean": float(zs.mean()), "z_std": float(zs.std(ddof=1)) if n > 1 else 0.0,
+                "obs_rms": float(np.sqrt(np.mean(dev ** 2)))}
+
+    out = {"eps": eps, "fields": names, "base": trial(base, runs), "reduce_all": {}, "reduce_half": {}, "move": {}}
+    for k in takes:
+        out["reduce_all"][k] = trial({f: shift_bits(base[f], k) if base[f]["bits"] > k else base[f] for f in names}, runs)
+        half = set(gen.choice(names, size=len(names) // 2, replace=False).tolist())
+        red = {f: shift_bits(base[f], k) if f in half and base[f]["bits"] > k else base[f] for f in names}
+        out["reduce_half"][k] = dict(trial(red, runs), fields_reduced=sorted(half))
+    pairs = [(names[0], names[1]), (names[1], names[0]), (names[2], names[3]), (names[3], names[2])]
+    for a, b in pairs:
+        moved = dict(base)
+        moved[a], moved[b] = shift_bits(base[a], 1), shift_bits(base[b], -1)
+        out["move"][f"{a}->{b}"] = trial(moved, move_runs)
+    return out
+
+
+def dithering_effectiveness(scene, state0, T, z_ref, scheme, runs=5, seed0=5000):
+    """Sec. 8.1's dithering experiment: the same scheme with and without dithered stores;
+    z against the reference and the ratio of round-ups to round-downs per field (about 1
+    when dithered; skewed by the rounding of systematically placed values otherwise)."""
+    out = {}
+    for name, dither in (("dithered", True), ("nearest", False)):
+        zs, ups, dns = _rollouts(scene, state0, T, scheme, runs if dither else 1, seed0, dither=dither, stats=True)
+        out[name] = {"z_mean": float(zs.mean()), "rel_err": float(abs(zs.mean() - z_ref) / abs(z_ref)),
+                     "up_down_ratio": [float(u) / max(float(d), 1.0) for u, d in zip(ups, dns)]}
+    out["z_ref"] = z_ref
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", type=int, default=20)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--smoke", action="store_true", help="the 2D smoke plume instead of the MPM block")
+    ap.add_argument("--optimality", action="store_true", help="the optimality check and the dithering experiment")
     args = ap.parse_args()
     if args.smoke:
         from . import smoke
@@ -83,6 +157,15 @@ def main():
     g.step(args.steps)
     z_ref = kinetic_energy(sc, g.readback(state=True, ids=False)["state"])
     g.close()
+    if args.optimality:
+        opt = optimality_check(sc, s0, args.steps, z_ref, runs=args.runs)
+        info = qmpm.sensitivities(sc, s0, args.steps, 25, qmpm.MEASURE_KINETIC_ENERGY)
+        bold, _ = qmpm.solve_scheme(info, 0.1, material=sc["material"])
+        dith = dithering_effectiveness(sc, s0, args.steps, z_ref, bold)
+        print(json.dumps({"scene": "2D neo-Hookean impact block, 2,048 particles, 128^2",
+                          "reference": "FP32 run of the same kernels", "optimality": opt,
+                          "dithering": dict(dith, scheme=bold)}, default=str))
+        return
     res = error_bound_protocol(sc, s0, args.steps, [0.1, 0.01, 1e-3, 1e-4], args.runs, z_ref)
     print(json.dumps({"scene": "2D neo-Hookean impact block, 2048 particles, 128^2",
                       "reference": "FP32 run of the same kernels", "results": res}))

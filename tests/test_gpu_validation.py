@@ -27,3 +27,32 @@ def test_error_bound_protocol(oracle):
         assert abs(r["bias"]) <= 4 * r["bias_stderr"] + 1e-12 * abs(z_ref), r
     assert sum(res[1]["bits"]) > sum(res[0]["bits"])
     assert res[1]["obs_rms"] < res[0]["obs_rms"]
+
+
+def test_optimality_check_and_dithering():
+    """Sec. 8.1's optimality check on the eps = 0.01 scheme of the impact block: taking bits
+    away from every field quickly breaks the bound (the scheme sits near the critical
+    point), and the error grows with the bits taken.  The dithering experiment on the
+    eps = 0.1 scheme: dithered stores round up as often as down in every field, while
+    round-to-nearest stores of the slowly changing velocity are skewed to one side."""
+    import torch
+    from paper_2207_04658_b300 import qmpm, validation
+    assert torch.cuda.is_available()
+    qmpm.lib()
+    sc, s0 = validation.impact_block()
+    T = 300
+    g = qmpm.Scene(sc, None, s0)
+    g.step(T)
+    z_ref = validation.kinetic_energy(sc, g.readback(state=True, ids=False)["state"])
+    g.close()
+    opt = validation.optimality_check(sc, s0, T, z_ref, runs=12, takes=(1, 2), move_runs=6)
+    assert opt["base"]["success_3eps"] >= 0.8, opt["base"]
+    assert opt["reduce_all"][2]["success_3eps"] <= 0.5, opt["reduce_all"]
+    assert opt["base"]["obs_rms"] < opt["reduce_all"][1]["obs_rms"] < opt["reduce_all"][2]["obs_rms"], opt
+    assert set(opt["move"]) == {"x->v", "v->x", "C->F", "F->C"}
+    info = qmpm.sensitivities(sc, s0, T, 25, qmpm.MEASURE_KINETIC_ENERGY)
+    bold, _ = qmpm.solve_scheme(info, 0.1, material=sc["material"])
+    dith = validation.dithering_effectiveness(sc, s0, T, z_ref, bold, runs=3)
+    assert all(0.9 < r < 1.1 for r in dith["dithered"]["up_down_ratio"]), dith
+    v_ratio = dith["nearest"]["up_down_ratio"][1]
+    assert v_ratio > 2.0 or v_ratio < 0.5, dith
