@@ -241,3 +241,21 @@ def smoke_scene(n=256, jacobi=64, steps=100, seed=7):
     the box within the run and gives z of the order of the paper's (about 2e4)."""
     return dict(n=n, jacobi=jacobi, dt=0.01, buoyancy=1.0, v_in=1.0, src=(0.35, 0.05, 0.65, 0.12), seed=seed,
                 steps=steps)
+
+
+# ------------------------------------------------------------------------ memory bound
+def dambreak2d_scene(n_particles=10_000, grid_log2=7, steps=16_384, seed=9):
+    """The 2D fluid dam break of the memory-bounded experiment (Sec. 8.1: 10,000 particles,
+    128^2 grid, 16,384 steps of 2e-4 s, J tracked instead of F, kinetic energy at the final
+    step): a jittered column of 100 x 100 strata over [0.05, 0.45]^2 at the low corner,
+    K = 100 (wave speed 10 m/s: 0.26 dx per step), rho 1, gravity -9.8.  The paper prints
+    neither the column nor K."""
+    n = 1 << grid_log2
+    k = int(round(n_particles ** 0.5))
+    gen = rng(seed)
+    x = jitter_box(gen, np.array([0.05, 0.05]), np.array([0.4, 0.4]), (k, k))
+    s0 = initial_state(2, "fluid", x)
+    scene = dict(name="dambreak2d", dim=2, material="fluid", grid_log2=grid_log2, bound=3, dt=2e-4, E=0.0, nu=0.0,
+                 bulk=100.0, rho=1.0, p_vol=0.16 / x.shape[0], gravity=(0.0, -9.8, 0.0), seed=seed, dither=True,
+                 steps=steps, resort_every=8)
+    return scene, s0

@@ -11,13 +11,14 @@ rollouts that differ only in their dither seed, and compare
 
 and, with --optimality, the optimality check (bits taken from all or half of the fields,
 bits moved between fields) and the dithering experiment (with and without dithered stores,
-round-up / round-down ratios).
+round-up / round-down ratios); with --memory, the memory-bounded experiment (a 2D fluid dam
+break at target fractions of the FP32 bits).
 
 Everything runs through the library (adjoint, solve, rollouts).  The reference z is
 supplied by the caller (the FP64 oracle in the tests); the command line uses the FP32 run
 of the same kernels.
 
-    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300] [--smoke | --optimality]
+    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300] [--smoke | --optimality | --memory]
 """
 import argparse
 import json
@@ -138,13 +139,52 @@ def dithering_effectiveness(scene, state0, T, z_ref, scheme, runs=5, seed0=5000)
     return out
 
 
+def memory_bound_protocol(scene, state0, T, eps_list, z_ref, runs=10, ckpt_every=0, seed0=7000):
+    """The memory-bounded experiment of Sec. 8.1: per target fraction eps_mem of the FP32
+    bits, the scheme of the memory-bound solve (Eq. 7), its real compression, and z over
+    `runs` dithered rollouts: mean, spread and e_mem = sqrt(sigma^2 + (mu - z)^2) / z."""
+    info = qmpm.sensitivities(scene, state0, T, ckpt_every, qmpm.MEASURE_KINETIC_ENERGY)
+    # the floor: FP32 rollouts differ from one another through the order of the grid's
+    # floating-point atomic sums, and a long fluid run amplifies that like any other noise
+    z32, _, _ = _rollouts(scene, state0, T, None, runs, seed0)
+    out = [{"eps_mem": 1.0, "bits": [32] * 4, "real_fraction": 1.0, "compression": 1.0, "z_mean": float(z32.mean()),
+            "z_std": float(z32.std(ddof=1)) if runs > 1 else 0.0,
+            "e_mem": float(np.sqrt(z32.var(ddof=1) + (z32.mean() - z_ref) ** 2) / abs(z_ref)) if runs > 1 else 0.0,
+            "z_ref": z_ref, "runs": runs, "fp32": True}]
+    for eps in eps_list:
+        scheme, res = qmpm.solve_scheme(info, eps, mode="memory", material=scene["material"])
+        zs, _, _ = _rollouts(scene, state0, T, scheme, runs, seed0)
+        names = [k for k in ("x", "v", "C", "F", "J") if k in scheme]
+        d = scene["dim"]
+        n_comp = {"x": d, "v": d, "C": d * d, "F": d * d, "J": 1}
+        bits = sum(scheme[f]["bits"] * n_comp[f] for f in names)
+        fp32 = 32 * sum(n_comp[f] for f in names)
+        mu, sd = float(zs.mean()), float(zs.std(ddof=1)) if runs > 1 else 0.0
+        out.append({"eps_mem": eps, "bits": [scheme[f]["bits"] for f in names], "real_fraction": bits / fp32,
+                    "compression": fp32 / bits, "z_mean": mu, "z_std": sd,
+                    "e_mem": float(np.sqrt(sd ** 2 + (mu - z_ref) ** 2) / abs(z_ref)), "z_ref": z_ref, "runs": runs})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", type=int, default=20)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--smoke", action="store_true", help="the 2D smoke plume instead of the MPM block")
     ap.add_argument("--optimality", action="store_true", help="the optimality check and the dithering experiment")
+    ap.add_argument("--memory", action="store_true", help="the memory-bounded 2D fluid dam break")
     args = ap.parse_args()
+    if args.memory:
+        sc, s0 = scenes.dambreak2d_scene()
+        T = sc["steps"]
+        g = qmpm.Scene(sc, None, s0)
+        g.step(T)
+        z_ref = kinetic_energy(sc, g.readback(state=True, ids=False)["state"])
+        g.close()
+        res = memory_bound_protocol(sc, s0, T, [0.6, 0.5, 0.4], z_ref, runs=min(args.runs, 10))
+        print(json.dumps({"scene": "2D fluid dam break, 10,000 particles, 128^2, 16,384 steps",
+                          "reference": "FP32 run of the same kernels", "results": res}))
+        return
     if args.smoke:
         from . import smoke
         sc = scenes.smoke_scene()

@@ -56,3 +56,26 @@ def test_optimality_check_and_dithering():
     assert all(0.9 < r < 1.1 for r in dith["dithered"]["up_down_ratio"]), dith
     v_ratio = dith["nearest"]["up_down_ratio"][1]
     assert v_ratio > 2.0 or v_ratio < 0.5, dith
+
+
+def test_memory_bound_protocol():
+    """Sec. 8.1's memory-bounded experiment on the 2D fluid dam break (shortened to 2048
+    steps): the memory-bound solve meets each target fraction of the FP32 bits, and the
+    error metric e_mem stays within a few times the FP32 runs' own run-to-run spread (the
+    grid's atomic sums make FP32 rollouts differ, and the sloshing fluid amplifies that)."""
+    import torch
+    from paper_2207_04658_b300 import qmpm, scenes, validation
+    assert torch.cuda.is_available()
+    qmpm.lib()
+    sc, s0 = scenes.dambreak2d_scene(steps=2048)
+    T = sc["steps"]
+    g = qmpm.Scene(sc, None, s0)
+    g.step(T)
+    z_ref = validation.kinetic_energy(sc, g.readback(state=True, ids=False)["state"])
+    g.close()
+    res = validation.memory_bound_protocol(sc, s0, T, [0.6, 0.5, 0.4], z_ref, runs=5)
+    floor = res[0]
+    assert floor.get("fp32") and floor["real_fraction"] == 1.0
+    for r in res[1:]:
+        assert r["eps_mem"] - 0.12 <= r["real_fraction"] <= r["eps_mem"] + 1e-9, r
+        assert r["e_mem"] <= max(4 * floor["e_mem"], 0.05), (r, floor)
