@@ -12,13 +12,15 @@ rollouts that differ only in their dither seed, and compare
 and, with --optimality, the optimality check (bits taken from all or half of the fields,
 bits moved between fields) and the dithering experiment (with and without dithered stores,
 round-up / round-down ratios); with --memory, the memory-bounded experiment (a 2D fluid dam
-break at target fractions of the FP32 bits).
+break at target fractions of the FP32 bits); with --checkpointing, the adjoint's memory and
+time with every state kept, uniform and bisection checkpoints.
 
 Everything runs through the library (adjoint, solve, rollouts).  The reference z is
 supplied by the caller (the FP64 oracle in the tests); the command line uses the FP32 run
 of the same kernels.
 
-    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300] [--smoke | --optimality | --memory]
+    python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300]
+        [--smoke | --optimality | --memory | --checkpointing]
 """
 import argparse
 import json
@@ -166,6 +168,32 @@ def memory_bound_protocol(scene, state0, T, eps_list, z_ref, runs=10, ckpt_every
     return out
 
 
+def checkpointing_cost(scene, state0, Ts=(256, 1024, 4096)):
+    """The cost of the adjoint's checkpointing (Sec. 6; the paper's comparison of bisection
+    with the unfolded tape): per horizon T, the states held, the forward steps run and the
+    wall time of one adjoint pass with every state kept (ckpt_every 1), uniform checkpoints
+    every sqrt(T) steps, and bisection checkpoints."""
+    import time
+    import torch
+    N, nc = state0.shape
+    out = []
+    for T in Ts:
+        row = {"T": T}
+        for name, every in (("unfolded", 1), ("uniform", int(round(T ** 0.5))), ("bisection", qmpm.CKPT_BISECTION)):
+            g = qmpm.Scene(dict(scene, resort_every=0), None, state0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = qmpm.qmpm_adjoint(g.h, T, every, qmpm.MEASURE_KINETIC_ENERGY)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            g.close()
+            row[name] = {"ckpt_every": every, "state_buffers": info["state_buffers"],
+                         "state_mb": info["state_buffers"] * N * nc * 4 / 1e6,
+                         "forward_steps": info["forward_steps"], "seconds": el, "g": info["g"]}
+        out.append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", type=int, default=20)
@@ -173,7 +201,13 @@ def main():
     ap.add_argument("--smoke", action="store_true", help="the 2D smoke plume instead of the MPM block")
     ap.add_argument("--optimality", action="store_true", help="the optimality check and the dithering experiment")
     ap.add_argument("--memory", action="store_true", help="the memory-bounded 2D fluid dam break")
+    ap.add_argument("--checkpointing", action="store_true", help="adjoint memory and time by checkpointing")
     args = ap.parse_args()
+    if args.checkpointing:
+        sc, s0 = impact_block()
+        print(json.dumps({"scene": "2D neo-Hookean impact block, 2,048 particles, 128^2",
+                          "results": checkpointing_cost(sc, s0)}))
+        return
     if args.memory:
         sc, s0 = scenes.dambreak2d_scene()
         T = sc["steps"]
