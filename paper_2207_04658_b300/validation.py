@@ -13,14 +13,15 @@ and, with --optimality, the optimality check (bits taken from all or half of the
 bits moved between fields) and the dithering experiment (with and without dithered stores,
 round-up / round-down ratios); with --memory, the memory-bounded experiment (a 2D fluid dam
 break at target fractions of the FP32 bits); with --checkpointing, the adjoint's memory and
-time with every state kept, uniform and bisection checkpoints.
+time with every state kept, uniform and bisection checkpoints; with --layouts, the step
+time of bit-packed against bit-struct records.
 
 Everything runs through the library (adjoint, solve, rollouts).  The reference z is
 supplied by the caller (the FP64 oracle in the tests); the command line uses the FP32 run
 of the same kernels.
 
     python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300]
-        [--smoke | --optimality | --memory | --checkpointing]
+        [--smoke | --optimality | --memory | --checkpointing | --layouts]
 """
 import argparse
 import json
@@ -194,6 +195,34 @@ def checkpointing_cost(scene, state0, Ts=(256, 1024, 4096)):
     return out
 
 
+def layout_cost(widths=(16, 20, 24), steps=20, warmup=3):
+    """The layout experiment of Sec. 8.2 (bit pack vs bit struct): the 3D elastic cubes
+    (8,192,000 particles) with every component stored in w bits, packed across word
+    boundaries (components straddle words when 32 is not a multiple of w) or in 64-bit
+    containers (whole components per container, the rest of a container unused); words per
+    particle and the step kernel's device time per step."""
+    import torch
+    sc, s0 = scenes.cubes3d_scene()
+    out = []
+    for w in widths:
+        row = {"bits": w}
+        for name, cont in (("bit_pack", 0), ("bit_struct", 64)):
+            sch = scenes.fixed_scheme_3d("corotated", x_bits=w, v=(w, -8.0, 8.0), C=(w, -512.0, 512.0),
+                                         F=(w, -0.5, 1.5), x_container=cont)
+            for f in sch.values():
+                f["container"] = cont
+            g = qmpm.Scene(dict(sc, resort_every=8), sch, s0, profile=True)
+            g.step(warmup)
+            torch.cuda.synchronize()
+            g.profile(reset=True)
+            g.step(steps)
+            prof = g.profile(reset=True)
+            row[name] = {"words": g.n_words, "step_kernel_ms": prof["step_ms"] / max(1, prof["step_launches"])}
+            g.close()
+        out.append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", type=int, default=20)
@@ -202,7 +231,11 @@ def main():
     ap.add_argument("--optimality", action="store_true", help="the optimality check and the dithering experiment")
     ap.add_argument("--memory", action="store_true", help="the memory-bounded 2D fluid dam break")
     ap.add_argument("--checkpointing", action="store_true", help="adjoint memory and time by checkpointing")
+    ap.add_argument("--layouts", action="store_true", help="bit pack vs bit struct step time")
     args = ap.parse_args()
+    if args.layouts:
+        print(json.dumps({"scene": "3D fixed-corotated cubes, 8,192,000 particles, 256^3", "results": layout_cost()}))
+        return
     if args.checkpointing:
         sc, s0 = impact_block()
         print(json.dumps({"scene": "2D neo-Hookean impact block, 2,048 particles, 128^2",
