@@ -95,6 +95,16 @@ int qmpm_smoke_create(const qmpm_smoke_config_t *cfg, const qmpm_smoke_scheme_t 
 int qmpm_smoke_set_state(qmpm_smoke_handle h, int32_t scene, const float *h_u, const float *h_v,
                          const float *h_d);
 
+/* Every scene's state at once: host FP32 arrays of n_scenes consecutive scenes in the
+ * layout above (u [n_scenes][n][n+1], v [n_scenes][n+1][n], d [n_scenes][n][n]; any may be
+ * NULL = zero), set as qmpm_smoke_set_state sets one (get: decoded, NULL = not copied).
+ * One copy each way and one kernel over the batch; pinned host arrays copy fastest.  The
+ * first call allocates device staging for the whole batch (4 (2 n (n+1) + 2 n^2) bytes per
+ * scene), held until qmpm_smoke_destroy.  Synchronise the stream.
+ * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_OOM, QMPM_ERR_CUDA. */
+int qmpm_smoke_set_states(qmpm_smoke_handle h, const float *h_u, const float *h_v, const float *h_d);
+int qmpm_smoke_get_states(qmpm_smoke_handle h, float *h_u, float *h_v, float *h_d);
+
 /* Noise injection for sensitivity estimates (FP32 handles only): every velocity store
  * except the reflection u^ and every pressure store gets sign_s * sigma_h * r added, r = +-1
  * from Philox4x32-10 with key = h_noise_seeds[s] and the store's dither counter (the top bit

@@ -633,8 +633,14 @@ __global__ void __launch_bounds__(kT) measure_kernel(Params P)
 
 // Host FP32 state (oracle layout) -> stored fields; nearest rounding, walls zero.
 template <bool Q>
-__global__ void __launch_bounds__(kT) set_state_kernel(Params P, int s, const float *u, const float *v, const float *d)
+__global__ void __launch_bounds__(kT) set_state_kernel(Params P, int s0, const float *u, const float *v, const float *d,
+                                                       int64_t stride_uv, int64_t stride_d)
 {
+    // scene s0 + blockIdx.y, its arrays blockIdx.y strides into the staged ones
+    const int s = s0 + (int)blockIdx.y;
+    if (u) u += blockIdx.y * stride_uv;
+    if (v) v += blockIdx.y * stride_uv;
+    if (d) d += blockIdx.y * stride_d;
     const int n = P.n;
     const int64_t nu = (int64_t)n * P.su, nv = (int64_t)(n + 1) * n;
     const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
@@ -671,8 +677,14 @@ __global__ void __launch_bounds__(kT) set_state_kernel(Params P, int s, const fl
 
 // Stored fields of scene s -> FP32 arrays in the oracle layout (q: the final iterate).
 template <bool Q>
-__global__ void __launch_bounds__(kT) readback_kernel(Params P, int s, float *u, float *v, float *d, float *q)
+__global__ void __launch_bounds__(kT) readback_kernel(Params P, int s0, float *u, float *v, float *d, float *q,
+                                                      int64_t stride_uv, int64_t stride_d)
 {
+    const int s = s0 + (int)blockIdx.y;
+    u += blockIdx.y * stride_uv;
+    v += blockIdx.y * stride_uv;
+    d += blockIdx.y * stride_d;
+    q += blockIdx.y * stride_d;
     const int n = P.n;
     const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
     const int64_t nu = (int64_t)n * (n + 1);
@@ -701,6 +713,7 @@ struct qmpm_smoke {
     bool quant = false;
     std::vector<void *> allocs;
     uint32_t *stage = nullptr;     // device staging for set_state / readback (FP32)
+    float *stage_all = nullptr;    // every scene's u, v, d, q for the batch transfers (on first use)
     int64_t stage_floats = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t steps = 0, launches = 0, graph_launches = 0, device_bytes = 0;
@@ -989,13 +1002,81 @@ int qmpm_smoke_set_state(qmpm_smoke_handle h, int32_t scene, const float *h_u, c
     const dim3 g((unsigned)((nfaces + kT - 1) / kT));
     for (int s = (scene < 0 ? 0 : scene); s < (scene < 0 ? h->S : scene + 1); ++s) {
         if (h->quant)
-            set_state_kernel<true><<<g, kT, 0, h->st>>>(P, s, h_u ? du : nullptr, h_v ? dv : nullptr, h_d ? dd : nullptr);
+            set_state_kernel<true><<<g, kT, 0, h->st>>>(P, s, h_u ? du : nullptr, h_v ? dv : nullptr, h_d ? dd : nullptr,
+                                                        0, 0);
         else
-            set_state_kernel<false><<<g, kT, 0, h->st>>>(P, s, h_u ? du : nullptr, h_v ? dv : nullptr, h_d ? dd : nullptr);
+            set_state_kernel<false><<<g, kT, 0, h->st>>>(P, s, h_u ? du : nullptr, h_v ? dv : nullptr, h_d ? dd : nullptr,
+                                                         0, 0);
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail("qmpm_smoke_set_state", e);
+    return QMPM_OK;
+}
+
+// Device staging of every scene's u, v, d (and q) for the batch transfers, made on first use.
+static int ensure_stage_all(qmpm_smoke *h)
+{
+    if (h->stage_all) return QMPM_OK;
+    const int64_t n = h->p.n, nu = n * (n + 1), nc = n * n;
+    const size_t bytes = sizeof(float) * (size_t)h->S * (size_t)(2 * nu + 2 * nc);
+    if (cudaMalloc(&h->stage_all, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h->stage_all = nullptr;
+        return fail(QMPM_ERR_OOM, "smoke batch staging: device allocation failed");
+    }
+    h->allocs.push_back(h->stage_all);
+    h->device_bytes += (int64_t)bytes;
+    return QMPM_OK;
+}
+
+int qmpm_smoke_set_states(qmpm_smoke_handle h, const float *h_u, const float *h_v, const float *h_d)
+{
+    if (!h) return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_set_states: NULL handle");
+    int r = ensure_stage_all(h);
+    if (r != QMPM_OK) return r;
+    const Params &P = h->p;
+    const int n = P.n, S = h->S;
+    const int64_t nu = (int64_t)n * (n + 1), nc = (int64_t)n * n;
+    float *du = h->stage_all, *dv = du + S * nu, *dd = dv + S * nu;
+    cudaError_t e = cudaSuccess;
+    if (h_u) e = cudaMemcpyAsync(du, h_u, sizeof(float) * S * nu, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess && h_v) e = cudaMemcpyAsync(dv, h_v, sizeof(float) * S * nu, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess && h_d) e = cudaMemcpyAsync(dd, h_d, sizeof(float) * S * nc, cudaMemcpyHostToDevice, h->st);
+    if (e != cudaSuccess) return cuda_fail("qmpm_smoke_set_states", e);
+    const int64_t nfaces = (int64_t)n * P.su + (int64_t)(n + 1) * n;
+    const dim3 g((unsigned)((nfaces + kT - 1) / kT), S);
+    if (h->quant)
+        set_state_kernel<true><<<g, kT, 0, h->st>>>(P, 0, h_u ? du : nullptr, h_v ? dv : nullptr, h_d ? dd : nullptr,
+                                                    nu, nc);
+    else
+        set_state_kernel<false><<<g, kT, 0, h->st>>>(P, 0, h_u ? du : nullptr, h_v ? dv : nullptr, h_d ? dd : nullptr,
+                                                     nu, nc);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail("qmpm_smoke_set_states", e);
+    return QMPM_OK;
+}
+
+int qmpm_smoke_get_states(qmpm_smoke_handle h, float *h_u, float *h_v, float *h_d)
+{
+    if (!h) return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_get_states: NULL handle");
+    int r = ensure_stage_all(h);
+    if (r != QMPM_OK) return r;
+    const int n = h->p.n, S = h->S;
+    const int64_t nu = (int64_t)n * (n + 1), nc = (int64_t)n * n;
+    float *du = h->stage_all, *dv = du + S * nu, *dd = dv + S * nu, *dq = dd + S * nc;
+    const dim3 g((unsigned)((nu + kT - 1) / kT), S);
+    if (h->quant)
+        readback_kernel<true><<<g, kT, 0, h->st>>>(h->p, 0, du, dv, dd, dq, nu, nc);
+    else
+        readback_kernel<false><<<g, kT, 0, h->st>>>(h->p, 0, du, dv, dd, dq, nu, nc);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && h_u) e = cudaMemcpyAsync(h_u, du, sizeof(float) * S * nu, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h_v) e = cudaMemcpyAsync(h_v, dv, sizeof(float) * S * nu, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h_d) e = cudaMemcpyAsync(h_d, dd, sizeof(float) * S * nc, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail("qmpm_smoke_get_states", e);
     return QMPM_OK;
 }
 
@@ -1093,9 +1174,9 @@ int qmpm_smoke_readback(qmpm_smoke_handle h, int32_t scene, float *h_u, float *h
     float *du = (float *)h->stage, *dv = du + nu, *dd = dv + nu, *dq = dd + nc;
     const unsigned g = (unsigned)((nu + kT - 1) / kT);
     if (h->quant)
-        readback_kernel<true><<<g, kT, 0, h->st>>>(h->p, scene, du, dv, dd, dq);
+        readback_kernel<true><<<g, kT, 0, h->st>>>(h->p, scene, du, dv, dd, dq, 0, 0);
     else
-        readback_kernel<false><<<g, kT, 0, h->st>>>(h->p, scene, du, dv, dd, dq);
+        readback_kernel<false><<<g, kT, 0, h->st>>>(h->p, scene, du, dv, dd, dq, 0, 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && h_u) e = cudaMemcpyAsync(h_u, du, sizeof(float) * nu, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess && h_v) e = cudaMemcpyAsync(h_v, dv, sizeof(float) * nu, cudaMemcpyDeviceToHost, h->st);

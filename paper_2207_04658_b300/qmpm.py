@@ -229,6 +229,8 @@ _SIGNATURES += [
     ("qmpm_smoke_create", ct.c_int, [_P(qmpm_smoke_config_t), _P(qmpm_smoke_scheme_t), ct.c_int32,
                                      _P(ct.c_uint64), ct.c_void_p, _P(ct.c_void_p)]),
     ("qmpm_smoke_set_state", ct.c_int, [ct.c_void_p, ct.c_int32, _P(ct.c_float), _P(ct.c_float), _P(ct.c_float)]),
+    ("qmpm_smoke_set_states", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    ("qmpm_smoke_get_states", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     ("qmpm_smoke_set_noise", ct.c_int, [ct.c_void_p, _P(ct.c_float), _P(ct.c_uint64), _P(ct.c_float)]),
     ("qmpm_smoke_step", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int64]),
     ("qmpm_smoke_measure", ct.c_int, [ct.c_void_p, _P(ct.c_double)]),

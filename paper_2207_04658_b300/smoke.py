@@ -78,6 +78,30 @@ class Smoke:
         p = lambda a: _dptr(a, ct.c_float) if a is not None else None  # noqa: E731
         _check(lib().qmpm_smoke_set_state(self.h, int(scene), p(u), p(v), p(d)))
 
+    def _host_ptr(self, a, shape, out=False):
+        """Pointer of a host array of every scene (a CPU torch tensor, pinned or not, or a
+        numpy array), checked for shape and float32."""
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            assert tuple(a.shape) == shape and str(a.dtype) == "torch.float32" and a.is_contiguous()
+            assert a.device.type == "cpu"
+            return ct.c_void_p(a.data_ptr())
+        assert a.shape == shape and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+        return ct.c_void_p(a.ctypes.data)
+
+    def set_states(self, u=None, v=None, d=None):
+        """Every scene's state from host arrays u [S][n][n+1], v [S][n+1][n], d [S][n][n]."""
+        n, S = self.n, self.S
+        _check(lib().qmpm_smoke_set_states(self.h, self._host_ptr(u, (S, n, n + 1)), self._host_ptr(v, (S, n + 1, n)),
+                                           self._host_ptr(d, (S, n, n))))
+
+    def get_states(self, u=None, v=None, d=None):
+        """Every scene's decoded state into host arrays shaped as in set_states."""
+        n, S = self.n, self.S
+        _check(lib().qmpm_smoke_get_states(self.h, self._host_ptr(u, (S, n, n + 1)), self._host_ptr(v, (S, n + 1, n)),
+                                           self._host_ptr(d, (S, n, n))))
+
     def set_noise(self, sigma, noise_seeds, signs):
         sg = (ct.c_float * 2)(float(sigma[0]), float(sigma[1]))
         ns = np.ascontiguousarray(np.asarray(noise_seeds, dtype=np.uint64))
