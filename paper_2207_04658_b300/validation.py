@@ -14,14 +14,15 @@ bits moved between fields) and the dithering experiment (with and without dither
 round-up / round-down ratios); with --memory, the memory-bounded experiment (a 2D fluid dam
 break at target fractions of the FP32 bits); with --checkpointing, the adjoint's memory and
 time with every state kept, uniform and bisection checkpoints; with --layouts, the step
-time of bit-packed against bit-struct records.
+time of bit-packed against bit-struct records; with --scaling, the scaling procedure (one
+scheme from the smallest of four 3D fluid configurations applied up to 5M particles).
 
 Everything runs through the library (adjoint, solve, rollouts).  The reference z is
 supplied by the caller (the FP64 oracle in the tests); the command line uses the FP32 run
 of the same kernels.
 
     python -m paper_2207_04658_b300.validation [--runs 20] [--steps 300]
-        [--smoke | --optimality | --memory | --checkpointing | --layouts]
+        [--smoke | --optimality | --memory | --checkpointing | --layouts | --scaling]
 """
 import argparse
 import json
@@ -223,6 +224,67 @@ def layout_cost(widths=(16, 20, 24), steps=20, warmup=3):
     return out
 
 
+def mean_height(state):
+    return float(state[:, 1].mean())
+
+
+def scaling_protocol(configs=None, eps_mem=0.5, runs=3, range_every=1024, seed0=9000):
+    """The scaling procedure of Sec. 8.3 on a 3D fluid column: g_h from the adjoint of the
+    smallest configuration (mean height as z, bisection checkpoints), ranges recorded from
+    the FP32 run of the largest one (the state read back every `range_every` steps), one
+    memory-bound scheme (eps_mem of the FP32 bits) applied unchanged to every
+    configuration; per configuration the FP32 z and the quantized z over `runs` dither
+    seeds."""
+    import torch
+    configs = configs or scenes.SCALING_CONFIGS
+    sc0, s00 = scenes.fluid3d_column_scene(*configs[0])
+    N0, nc = s00.shape
+    seed = torch.zeros((N0, nc), dtype=torch.float32, device="cuda")
+    seed[:, 1] = 1.0 / N0  # dz/dy of the mean height
+    g = qmpm.Scene(dict(sc0, resort_every=0), None, s00)
+    info = qmpm.qmpm_adjoint(g.h, configs[0][3], qmpm.CKPT_BISECTION, qmpm.MEASURE_USER, seed.data_ptr())
+    g.close()
+    # ranges from the largest configuration's FP32 run
+    scL, sL = scenes.fluid3d_column_scene(*configs[-1])
+    comps = [[0, 1, 2], [3, 4, 5], list(range(6, 15)), [15]]
+    lo, hi = np.full(4, np.inf), np.full(4, -np.inf)
+    g = qmpm.Scene(scL, None, sL)
+    fp32_last = None
+    for t0 in range(0, configs[-1][3] + 1, range_every):
+        if t0 > 0:
+            g.step(range_every)
+        st = g.readback(state=True, ids=False)["state"]
+        for h in range(4):
+            lo[h] = min(lo[h], float(st[:, comps[h]].min()))
+            hi[h] = max(hi[h], float(st[:, comps[h]].max()))
+        fp32_last = st
+    g.close()
+    info = dict(info, lo=list(lo), hi=list(hi))
+    scheme, res = qmpm.solve_scheme(info, eps_mem, mode="memory", material="fluid")
+    out = {"scheme": scheme, "g": info["g"], "lo": list(lo), "hi": list(hi), "configs": []}
+    for k, cfg in enumerate(configs):
+        sc, s0 = scenes.fluid3d_column_scene(*cfg)
+        if k == len(configs) - 1:
+            z32 = mean_height(fp32_last)
+        else:
+            g = qmpm.Scene(sc, None, s0)
+            g.step(cfg[3])
+            z32 = mean_height(g.readback(state=True, ids=False)["state"])
+            g.close()
+        zq = []
+        for r in range(runs):
+            g = qmpm.Scene(dict(sc, seed=seed0 + r), scheme, s0)
+            g.step(cfg[3])
+            zq.append(mean_height(g.readback(state=True, ids=False)["state"]))
+            g.close()
+        zq = np.asarray(zq)
+        out["configs"].append({"particles": s0.shape[0], "grid": f"{1 << cfg[1]}^3", "dt": cfg[2], "steps": cfg[3],
+                               "z_fp32": z32, "z_quant_mean": float(zq.mean()),
+                               "z_quant_std": float(zq.std(ddof=1)) if runs > 1 else 0.0,
+                               "rel_err": float(abs(zq.mean() - z32) / abs(z32))})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", type=int, default=20)
@@ -232,7 +294,12 @@ def main():
     ap.add_argument("--memory", action="store_true", help="the memory-bounded 2D fluid dam break")
     ap.add_argument("--checkpointing", action="store_true", help="adjoint memory and time by checkpointing")
     ap.add_argument("--layouts", action="store_true", help="bit pack vs bit struct step time")
+    ap.add_argument("--scaling", action="store_true", help="one scheme from 0.2M particles applied up to 5M")
     args = ap.parse_args()
+    if args.scaling:
+        print(json.dumps({"scene": "3D fluid column (K 200), mean height", "reference": "FP32 runs",
+                          **scaling_protocol()}, default=float))
+        return
     if args.layouts:
         print(json.dumps({"scene": "3D fixed-corotated cubes, 8,192,000 particles, 256^3", "results": layout_cost()}))
         return

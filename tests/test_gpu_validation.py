@@ -79,3 +79,20 @@ def test_memory_bound_protocol():
     for r in res[1:]:
         assert r["eps_mem"] - 0.12 <= r["real_fraction"] <= r["eps_mem"] + 1e-9, r
         assert r["e_mem"] <= max(4 * floor["e_mem"], 0.05), (r, floor)
+
+
+def test_scaling_procedure_small():
+    """The scaling procedure of Sec. 8.3 at small sizes: a memory-bound scheme (half the FP32
+    bits) from the gradients of a 20,000-particle 3D fluid column on 32^3, with ranges
+    recorded on the 160,000-particle configuration, applied unchanged to both: the mean
+    height stays within 1 % of the FP32 run's."""
+    import torch
+    from paper_2207_04658_b300 import qmpm, validation
+    assert torch.cuda.is_available()
+    qmpm.lib()
+    res = validation.scaling_protocol(configs=[(20_000, 5, 4e-4, 512), (160_000, 6, 2e-4, 1024)], runs=2,
+                                      range_every=256)
+    bits = {k: v["bits"] for k, v in res["scheme"].items()}
+    assert 3 * bits["x"] + 3 * bits["v"] + 9 * bits["C"] + bits["J"] <= 0.5 * 32 * 16
+    for c in res["configs"]:
+        assert c["rel_err"] < 1e-2, c
