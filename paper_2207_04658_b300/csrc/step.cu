@@ -124,14 +124,22 @@ __device__ __forceinline__ void g2p_gather(const StepParams &P, const float *tvx
 }
 
 
-// Thread t works on the particle at position (t % 32) * 8 + t / 32 of its chunk: the
-// chunk is sorted by cell, so the 32 lanes of a warp land on different cells and the
-// shared-memory atomics of P2G rarely collide.
-__device__ __forceinline__ int spread(int t) { return (t & 31) * 8 + (t >> 5); }
+// The particle a thread works on in a chunk of `count` particles: the chunk takes
+// nw = ceil(count / 32) warps, and lane l of warp w < nw the particle l * nw + w.  The chunk
+// is sorted by cell, so a warp's lanes land on different cells and the shared-memory
+// atomics of P2G rarely collide; a short chunk (the last of a tile: most tiles hold a few
+// particles more than a multiple of the chunk size) occupies only the warps it needs, and
+// the others skip the per-particle work.  Threads without a particle get kThreads.
+__device__ __forceinline__ int chunk_particle(int t, int count)
+{
+    const int nw = min(kThreads / 32, (count + 31) >> 5), w = t >> 5;
+    return w < nw ? (t & 31) * nw + w : kThreads;
+}
 
 // Shared column of particle p's record words: p's row of 32 rotated by p / 32, which keeps
-// both the coalesced staging (lane l of warp w touches particle 32 w + l) and the spread
-// compute mapping (lane l of warp w touches particle 8 l + w) free of bank conflicts.
+// both the coalesced staging (lane l of warp w touches particle 32 w + l) and the compute
+// mapping of a full chunk (lane l of warp w touches particle 8 l + w) free of bank
+// conflicts.
 __device__ __forceinline__ int column_of(int p) { return (p & ~31) | ((p + (p >> 5)) & 31); }
 
 // ------------------------------------------------------------------------------ step kernel
@@ -181,7 +189,7 @@ constexpr size_t step_smem_fixed() { return (size_t)7 * (DIM == 2 ? 64 : 512) * 
 // together (it synchronises).
 template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P, bool MULTI = false>
 __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci0, uint32_t step, StepCounters &cnt,
-                                          const int tid, const int pj)
+                                          const int tid)
 {
     using Tr = Traits<DIM, MAT>;
     constexpr int NC = Tr::NC, TN = Tr::TN;
@@ -192,7 +200,6 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
     int *tpx = tpm + TN, *tpy = tpx + TN, *tpz = tpy + TN;
     float *red = reinterpret_cast<float *>(tpz + TN);   // per-warp maxima (kThreads / 32)
     uint32_t *sw = reinterpret_cast<uint32_t *>(red + kThreads / 32);  // record words, column per particle
-    uint32_t *my = sw + column_of(pj);  // its column of record words, stride kThreads
 
     const Chunk ch0 = P.chunks[ci0];
     const uint32_t key = ch0.key;
@@ -246,7 +253,9 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
         for (int j = 0; j < P.n_words; ++j) sw[j * kThreads + mycol] = P.words[j * P.ld + ch.start + tid];
     __syncthreads();
 
+    const int pj = chunk_particle(tid, (int)ch.count);
     const bool active = pj < (int)ch.count;
+    uint32_t *my = sw + column_of(min(pj, kThreads - 1));  // its column of record words, stride kThreads
     const int64_t slot = (int64_t)ch.start + pj;
     // P2G payload, kept across the barrier that fixes the chunk's fixed-point scale
     int pbase[3] = {0, 0, 0};
@@ -531,14 +540,13 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>()) step
     __shared__ uint32_t ticket;
     StepCounters cnt;
     const int tid = threadIdx.x;
-    const int pj = spread(tid);  // this thread's particle within each chunk
     const uint32_t n_tiles = *P.n_tiles;
     for (;;) {
         // run_chunk ends with a barrier, so every thread has read the ticket before thread 0
         // takes the next one
         const uint32_t ti = take_tile(P.work, &ticket);
         if (ti >= n_tiles) break;
-        run_chunk<DIM, MAT, QUANT, STATS, DO_G2P>(P, P.tile_first[ti], 0u, cnt, tid, pj);
+        run_chunk<DIM, MAT, QUANT, STATS, DO_G2P>(P, P.tile_first[ti], 0u, cnt, tid);
     }
     if (STATS) flush_counters(cnt, P.stats);
     finish_launch(P.work);
@@ -553,14 +561,13 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>())
 {
     StepCounters cnt;
     const int tid = threadIdx.x;
-    const int pj = spread(tid);
     const uint32_t step = *P.step_ctr + 1u;
     const uint32_t n_tiles = *P.n_tiles;
     __shared__ uint32_t ticket;
     for (;;) {
         const uint32_t ti = take_tile(P.work, &ticket);
         if (ti >= n_tiles) break;
-        run_chunk<DIM, MAT, QUANT, STATS, true, true>(P, P.tile_first[ti], step, cnt, tid, pj);
+        run_chunk<DIM, MAT, QUANT, STATS, true, true>(P, P.tile_first[ti], step, cnt, tid);
     }
     if (STATS) flush_counters(cnt, P.stats);
     finish_launch(P.work);
@@ -580,7 +587,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ __align__(16) StepParams Ps;
     static_assert(sizeof(StepParams) % 4 == 0, "StepParams is copied as 32-bit words");
     const int tid = threadIdx.x;
-    const int pj = spread(tid);
     if (tid < n_members) first[tid + 1] = *tab[tid].n_tiles;
     if (tid == 0) first[0] = 0;
     __syncthreads();
@@ -614,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             cur = lo;
             step = *Ps.step_ctr + 1u;
         }
-        run_chunk<DIM, MAT, QUANT, STATS, true, true>(Ps, Ps.tile_first[item - first[lo]], step, cnt, tid, pj);
+        run_chunk<DIM, MAT, QUANT, STATS, true, true>(Ps, Ps.tile_first[item - first[lo]], step, cnt, tid);
     }
     if (STATS && cur >= 0) flush_counters(cnt, Ps.stats);
     finish_launch(queue);
