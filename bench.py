@@ -192,25 +192,26 @@ def e2e_scene(qmpm, torch, g, steps, warmup):
 
 
 def kernel_counters(desc, n_particles, words=None):
-    """DRAM bytes and warp instructions per launch of the step kernel from the committed
-    ncu summary (a smaller case of the same workload), scaled by the particle count to
-    this workload; (None, None) when the kernel source changed since the capture."""
+    """DRAM bytes, warp instructions and thread instructions per launch of the step kernel
+    from the committed ncu summary, scaled by the particle count to this workload; Nones
+    when the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
-        return None, None
+        return None, None, None
     try:
         rec = json.load(open(path))
         src = open(os.path.join(ROOT, "paper_2207_04658_b300", "csrc", "step.cu"), "rb").read()
         if rec.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
-            return None, None
+            return None, None, None
         if rec.get("workload") != desc["workload"]:
-            return None, None
+            return None, None, None
         if words is not None and rec.get("words_per_particle") not in (None, words):
-            return None, None
+            return None, None, None
         f = n_particles / rec["particles"]
-        return rec["dram_bytes_per_launch"] * f, rec["warp_instructions_per_launch"] * f
+        return (rec["dram_bytes_per_launch"] * f, rec["warp_instructions_per_launch"] * f,
+                rec.get("thread_instructions_per_launch", 0) * f or None)
     except Exception:
-        return None, None
+        return None, None, None
 
 
 def issue_peak(peaks):
@@ -218,6 +219,31 @@ def issue_peak(peaks):
     at the maximum SM clock."""
     mhz = peaks.get("sm_max_mhz", 2032.0)
     return 148 * 4 * mhz * 1e6
+
+
+LANE_PEAK_SOURCE = "148 SMs x 4 schedulers x 32 lanes x 1 instruction/clk x max SM clock"
+
+
+def alu_roofline(kernel, avg_ms, winst, tinst, peaks, **extra):
+    """The issue-bound roofline of a kernel: the thread instructions it executes (the work
+    its active lanes do) per second against 32 lanes x the warp-issue peak; the warp-issue
+    rate (idle lanes of a warp count as issued) is reported beside it."""
+    ipk = issue_peak(peaks)
+    out = {"bound": "alu", "kernel": kernel, "avg_launch_ms": round(avg_ms, 5), "unit": "T lane-instructions/s",
+           "peak": round(32 * ipk / 1e12, 3), "peak_source": LANE_PEAK_SOURCE}
+    if tinst:
+        ach = tinst / (avg_ms / 1e3)
+        out.update({"achieved": round(ach / 1e12, 3), "frac": round(ach / (32 * ipk), 4),
+                    "thread_instructions_per_launch": tinst})
+    else:
+        out.update({"achieved": None, "frac": None})
+    if winst:
+        w = winst / (avg_ms / 1e3)
+        out["warp_issue"] = {"achieved": round(w / 1e9, 2), "peak": round(ipk / 1e9, 2),
+                             "unit": "G warp-instructions/s", "frac": round(w / ipk, 4),
+                             "warp_instructions_per_launch": winst}
+    out.update(extra)
+    return out
 
 
 def accuracy(qmpm, sc, s0, sch):
@@ -408,20 +434,12 @@ def smoke_section(args, peaks, dc, torch):
         prof = g.profile()
     jac_ms = prof["jacobi_ms"] / max(1, prof["jacobi_launches"])
     winst, dram, rec = smoke_counters()
-    ipk = issue_peak(peaks)
-    roof = {"kernel": "jacobi_kernel (4 dithered pressure sweeps per launch, shared-memory tiles)",
-            "avg_launch_ms": round(jac_ms, 5), "share_of_step": round(prof["jacobi_ms"] / prof["step_ms"], 3),
-            "bound": "alu", "peak": round(ipk / 1e9, 2), "unit": "G warp-instructions/s",
-            "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clk x max SM clock"}
-    if winst is not None:
-        f = S / rec["scenes"] if rec.get("n") == n else None
-        if f is not None:
-            ach = winst * f / (jac_ms / 1e3)
-            roof.update({"achieved": round(ach / 1e9, 2), "frac": round(ach / ipk, 4), "traffic": dram * f,
-                         "warp_instructions_per_launch": winst * f})
-    if "achieved" not in roof:
-        roof.update({"achieved": None, "frac": None, "traffic": None})
-    out["roofline"] = roof
+    f = S / rec["scenes"] if (winst is not None and rec.get("n") == n) else None
+    out["roofline"] = alu_roofline("jacobi_kernel (4 dithered pressure sweeps per launch, shared-memory tiles)",
+                                   jac_ms, winst * f if f else None,
+                                   rec.get("thread_instructions_per_launch", 0) * f if f else None, peaks,
+                                   share_of_step=round(prof["jacobi_ms"] / prof["step_ms"], 3),
+                                   traffic=dram * f if f else None)
     # end to end: every step the whole batch's state from pinned host arrays, one step, the
     # state and z back to the host (the batch transfer calls; FP32 arrays both ways)
     pin = lambda *shape: torch.zeros(shape, dtype=torch.float32).pin_memory()  # noqa: E731
@@ -544,20 +562,14 @@ def run_ours(args):
     nodes = st["active_blocks"] * (64 if sc["dim"] == 3 else 16)
     alg_bytes = N * 2 * 4 * W + nodes * 2 * node_bytes
     achieved = alg_bytes / (step_avg_ms / 1e3) / 1e9
-    traffic, winst = kernel_counters(desc, N, W)
+    traffic, winst, tinst = kernel_counters(desc, N, W)
     hbm = {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
            "frac": round(achieved / hbm_peak, 4), "peak_source": peak_note,
            "alg_bytes_per_launch": alg_bytes}
     if winst is not None:
         # the step kernel is issue bound (see profiles/): report against the issue peak
-        ipk = issue_peak(peaks)
-        ach = winst / (step_avg_ms / 1e3)
-        roofline = {"bound": "alu", "achieved": round(ach / 1e9, 2), "peak": round(ipk / 1e9, 2),
-                    "unit": "G warp-instructions/s", "frac": round(ach / ipk, 4),
-                    "traffic": traffic, "warp_instructions_per_launch": winst,
-                    "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clk x max SM clock",
-                    "kernel": "step_kernel (G2P -> dithered store -> P2G)",
-                    "avg_launch_ms": round(step_avg_ms, 4), "hbm": hbm}
+        roofline = alu_roofline("step_kernel (G2P -> dithered store -> P2G)", step_avg_ms, winst, tinst, peaks,
+                                traffic=traffic, hbm=hbm)
     else:
         roofline = dict({"bound": "hbm", "traffic": None,
                          "kernel": "step_kernel (G2P -> dithered store -> P2G)",
