@@ -15,7 +15,6 @@ collective on the data path): weak scaling, value = all particle-steps / max ran
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess

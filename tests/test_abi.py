@@ -102,7 +102,6 @@ def test_scheme_solve_rejects_bad_input(q):
 
 
 def test_missing_library_fails_loudly(monkeypatch, q):
-    import importlib
     from paper_2207_04658_b300 import qmpm as qm
     monkeypatch.setattr(qm, "_lib", None)
     monkeypatch.setattr(qm, "LIB_PATH", "/nonexistent/libqmpm.so")

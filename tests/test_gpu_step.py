@@ -7,7 +7,6 @@ Bars (floating point, FP32 device vs FP64 oracle):
     rounding or dither threshold);
   - FP32 state, one step: |gpu - oracle| <= 1e-5 (|oracle| + scale of the field);
   - rollouts: the position measurement z within the error bound of the oracle's."""
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ within the paper's 3 eps band in at least 80 % of cases (the paper reports 19/20
 20/20), the observed spread of z is within a factor 3 of the prediction of Eq. 8 (the
 linearisation holds), the mean deviation is within 4 standard errors of zero (the
 dithered store is unbiased), and tighter bounds cost more bits."""
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

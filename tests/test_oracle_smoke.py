@@ -19,7 +19,6 @@ mathematics fixes, CPU only:
   - antithetic noise injection estimates the FD sensitivities g_h, and the mean shift of
     z under dithered stores equals that under noise of the same variance."""
 import numpy as np
-import pytest
 
 
 def scene(**kw):

@@ -4,7 +4,6 @@ the serving stream -- on world_size 2 with the gloo backend on the CPU."""
 import os
 import socket
 
-import pytest
 
 
 def _free_port():
