@@ -425,12 +425,14 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
         const bool last = k == nsweep - 1;
         // only what the tile's last sweep still depends on: r more rows and cells on each
         // side of the tile, r = the sweeps left after this one
+        // (and inside the domain: the loop hands out no octet outside it)
         const int r = nsweep - 1 - k;
-        const int ro_lo = (kHX - r) / 8, ro_hi = (kHX + w - 1 + r) / 8, ncol = ro_hi - ro_lo + 1;
-        for (int e = threadIdx.x; e < (kTY + 2 * r) * ncol; e += kT) {
-            const int ry = kK - r + e / ncol, ro = ro_lo + e % ncol;
+        const int ro_lo = max((kHX - r) / 8, -gx0 / 8), ro_hi = min((kHX + w - 1 + r) / 8, (n - 1 - gx0) / 8);
+        const int ry_lo = max(kK - r, -gy0), ry_hi = min(kK + kTY - 1 + r, n - 1 - gy0);
+        const int ncol = ro_hi - ro_lo + 1, nrow = ry_hi - ry_lo + 1;
+        for (int e = threadIdx.x; e < nrow * ncol; e += kT) {
+            const int ry = ry_lo + e / ncol, ro = ro_lo + e % ncol;
             const int gy = gy0 + ry, gx = gx0 + ro * 8;
-            if (gy < 0 || gy >= n || gx < 0 || gx >= n) continue;
             const float *rc = cur + ry * kRW + ro * 8;
             const float4 c0 = reinterpret_cast<const float4 *>(rc)[0], c1 = reinterpret_cast<const float4 *>(rc)[1];
             const float4 d0 = reinterpret_cast<const float4 *>(rc - kRW)[0], d1 = reinterpret_cast<const float4 *>(rc - kRW)[1];
@@ -442,29 +444,20 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
             const float dn[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
             const float up[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
             const float dv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            // neighbours outside the domain enter as zeros and are not counted: the same sums,
+            // in the same order, as adding only the interior ones, without branches that
+            // would split a warp at the walls
             float x[8];
-            if (gx > 0 && gx + 8 < n && gy > 0 && gy < n - 1) {  // away from the walls: 4 neighbours
+            const bool has_d = gy > 0, has_u = gy < n - 1;
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const float acc = it > 1 ? row[m] + row[m + 2] + dn[m] + up[m] : 0.0f;
-                    x[m] = (acc - P.h2 * dv[m]) * 0.25f;
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const int i = gx + m;
-                    float acc = 0.0f;
-                    int cnt = 0;
-                    if (it > 1) {
-                        if (i > 0) { acc += row[m]; ++cnt; }
-                        if (i < n - 1) { acc += row[m + 2]; ++cnt; }
-                        if (gy > 0) { acc += dn[m]; ++cnt; }
-                        if (gy < n - 1) { acc += up[m]; ++cnt; }
-                    } else {
-                        cnt = (i > 0) + (i < n - 1) + (gy > 0) + (gy < n - 1);
-                    }
-                    x[m] = (acc - P.h2 * dv[m]) * inv_count(cnt);
-                }
+            for (int m = 0; m < 8; ++m) {
+                const int i = gx + m;
+                const bool has_l = i > 0, has_r = i < n - 1;
+                const int cnt = has_l + has_r + has_d + has_u;
+                const float acc = it > 1 ? (((has_l ? row[m] : 0.0f) + (has_r ? row[m + 2] : 0.0f)) +
+                                            (has_d ? dn[m] : 0.0f)) + (has_u ? up[m] : 0.0f)
+                                         : 0.0f;
+                x[m] = (acc - P.h2 * dv[m]) * inv_count(cnt);
             }
             const bool inner = ry >= kK && ry < kK + kTY && ro >= 1 && (ro - 1) * 8 < w;
             const uint32_t oct = (uint32_t)(((int64_t)gy * n + gx) >> 3);
