@@ -228,7 +228,7 @@ def mean_height(state):
     return float(state[:, 1].mean())
 
 
-def scaling_protocol(configs=None, eps_mem=0.5, runs=3, range_every=1024, seed0=9000):
+def scaling_protocol(sizes=None, eps_mem=0.5, runs=3, range_every=1024, seed0=9000):
     """The scaling procedure of Sec. 8.3 on a 3D fluid column: g_h from the adjoint of the
     smallest configuration (mean height as z, bisection checkpoints), ranges recorded from
     the FP32 run of the largest one (the state read back every `range_every` steps), one
@@ -236,21 +236,21 @@ def scaling_protocol(configs=None, eps_mem=0.5, runs=3, range_every=1024, seed0=
     configuration; per configuration the FP32 z and the quantized z over `runs` dither
     seeds."""
     import torch
-    configs = configs or scenes.SCALING_CONFIGS
-    sc0, s00 = scenes.fluid3d_column_scene(*configs[0])
+    sizes = sizes or scenes.SCALING_CONFIGS
+    sc0, s00 = scenes.fluid3d_column_scene(*sizes[0])
     N0, nc = s00.shape
     seed = torch.zeros((N0, nc), dtype=torch.float32, device="cuda")
     seed[:, 1] = 1.0 / N0  # dz/dy of the mean height
     g = qmpm.Scene(dict(sc0, resort_every=0), None, s00)
-    info = qmpm.qmpm_adjoint(g.h, configs[0][3], qmpm.CKPT_BISECTION, qmpm.MEASURE_USER, seed.data_ptr())
+    info = qmpm.qmpm_adjoint(g.h, sizes[0][3], qmpm.CKPT_BISECTION, qmpm.MEASURE_USER, seed.data_ptr())
     g.close()
     # ranges from the largest configuration's FP32 run
-    scL, sL = scenes.fluid3d_column_scene(*configs[-1])
+    scL, sL = scenes.fluid3d_column_scene(*sizes[-1])
     comps = [[0, 1, 2], [3, 4, 5], list(range(6, 15)), [15]]
     lo, hi = np.full(4, np.inf), np.full(4, -np.inf)
     g = qmpm.Scene(scL, None, sL)
     fp32_last = None
-    for t0 in range(0, configs[-1][3] + 1, range_every):
+    for t0 in range(0, sizes[-1][3] + 1, range_every):
         if t0 > 0:
             g.step(range_every)
         st = g.readback(state=True, ids=False)["state"]
@@ -262,9 +262,9 @@ def scaling_protocol(configs=None, eps_mem=0.5, runs=3, range_every=1024, seed0=
     info = dict(info, lo=list(lo), hi=list(hi))
     scheme, res = qmpm.solve_scheme(info, eps_mem, mode="memory", material="fluid")
     out = {"scheme": scheme, "g": info["g"], "lo": list(lo), "hi": list(hi), "configs": []}
-    for k, cfg in enumerate(configs):
+    for k, cfg in enumerate(sizes):
         sc, s0 = scenes.fluid3d_column_scene(*cfg)
-        if k == len(configs) - 1:
+        if k == len(sizes) - 1:
             z32 = mean_height(fp32_last)
         else:
             g = qmpm.Scene(sc, None, s0)

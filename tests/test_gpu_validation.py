@@ -89,7 +89,7 @@ def test_scaling_procedure_small():
     from paper_2207_04658_b300 import qmpm, validation
     assert torch.cuda.is_available()
     qmpm.lib()
-    res = validation.scaling_protocol(configs=[(20_000, 5, 4e-4, 512), (160_000, 6, 2e-4, 1024)], runs=2,
+    res = validation.scaling_protocol(sizes=[(20_000, 5, 4e-4, 512), (160_000, 6, 2e-4, 1024)], runs=2,
                                       range_every=256)
     bits = {k: v["bits"] for k, v in res["scheme"].items()}
     assert 3 * bits["x"] + 3 * bits["v"] + 9 * bits["C"] + bits["J"] <= 0.5 * 32 * 16
