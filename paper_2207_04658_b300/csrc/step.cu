@@ -173,11 +173,13 @@ __device__ __forceinline__ void flush_counters(StepCounters &cnt, unsigned long 
     cnt = StepCounters();
 }
 
-// Three 256-thread CTAs per SM (80 registers a thread): 24 resident warps hide the
-// shared-memory and L2 latencies of the chunk loop better than 16 (measured 11 % faster).
-// The 3D instantiations with saturation counters keep two, which they need to avoid spills.
+// Four 256-thread CTAs per SM (64 registers a thread): 32 resident warps hide the
+// shared-memory and L2 latencies of the chunk loop better than 24 at 80 registers, although
+// the 3D kernels then spill ~170 bytes a thread to L1 (3D cubes, 8.2 M particles: 1.196 ->
+// 1.127 ms quantized, 0.878 -> 0.812 ms FP32; 16 warps were 11 % slower than 24).  The 3D
+// instantiations with saturation counters keep two, which they need to avoid spills.
 template <int DIM, bool STATS>
-constexpr int step_ctas_per_sm() { return DIM == 3 && STATS ? 2 : 3; }
+constexpr int step_ctas_per_sm() { return DIM == 3 && STATS ? 2 : 4; }
 
 // Shared memory of the step kernels: G2P velocity tile (3 x TN floats), P2G fixed-point
 // tile (4 x TN ints), per-warp maxima, then the chunk's record words (W + 1 columns).
@@ -268,14 +270,14 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
             // independent per-component extraction: words k and k+1 through a funnel shift
             // (the column carries one padding word after the record)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
+            for (int c = 0; c < (DO_G2P ? DIM : NC); ++c) {
                 const CompCodec &cc = P.comp[c];
                 const uint32_t lo = my[cc.word * kThreads], hi = my[(cc.word + 1) * kThreads];
                 val[c] = decode_u(__funnelshift_r(lo, hi, cc.shift) & cc.mask, cc);
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) val[c] = __uint_as_float(my[c * kThreads]);
+            for (int c = 0; c < (DO_G2P ? DIM : NC); ++c) val[c] = __uint_as_float(my[c * kThreads]);
         }
         float *x = val, *v = val + DIM, *C = val + 2 * DIM, *FJ = val + 2 * DIM + DIM * DIM;
 
@@ -307,6 +309,17 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
                 x[a] += P.dt * vn[a];
 #pragma unroll
                 for (int b = 0; b < DIM; ++b) C[a * DIM + b] = P.Dinv * B[a * DIM + b];
+            }
+            // the deformation gradient (or J) is read only now, after the gather
+#pragma unroll
+            for (int c = 2 * DIM + DIM * DIM; c < NC; ++c) {
+                if (QUANT) {
+                    const CompCodec &cc = P.comp[c];
+                    const uint32_t lo = my[cc.word * kThreads], hi = my[(cc.word + 1) * kThreads];
+                    val[c] = decode_u(__funnelshift_r(lo, hi, cc.shift) & cc.mask, cc);
+                } else {
+                    val[c] = __uint_as_float(my[c * kThreads]);
+                }
             }
             if (MAT == QMPM_FLUID) {
                 float tr = 0.0f;
@@ -578,9 +591,10 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>())
 // shared memory when their items move on to the next member.  The members share the template
 // class (dimension, material, quantized or not); everything else (grid size, scheme,
 // physics, buffers, step index) is per member.
-// (Two CTAs per SM: with the parameters in shared memory, 80 registers would spill.)
+// CTAs per SM as for the single-scene kernel (a 32-scene batch of 3D serving scenes:
+// 1.86 ms per step with two, 1.73 with three, 1.68 with four).
 template <int DIM, int MAT, bool QUANT, bool STATS>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>())
     step_kernel_multi(const StepParams *__restrict__ tab, int n_members)
 {
     __shared__ uint32_t first[kMaxMembers + 1];  // prefix sums of the members' chunk counts
