@@ -407,10 +407,13 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
             if (it0 > 1) ld_run8<Q>(qin, (int64_t)gy * n + gx, c, b, q8);
             ld_run8<false>(div, (int64_t)gy * n + gx, c, b, d8);
         }
+        // both iterate buffers: the sweeps write only octets inside the domain, so the cells
+        // outside it keep these zeros in either buffer for the whole launch
         float4 *qa4 = reinterpret_cast<float4 *>(qa + ry * kRW + ro * 8);
+        float4 *qb4 = reinterpret_cast<float4 *>(qb + ry * kRW + ro * 8);
         float4 *dv4 = reinterpret_cast<float4 *>(dvs + ry * kRW + ro * 8);
-        qa4[0] = make_float4(q8[0], q8[1], q8[2], q8[3]);
-        qa4[1] = make_float4(q8[4], q8[5], q8[6], q8[7]);
+        qa4[0] = qb4[0] = make_float4(q8[0], q8[1], q8[2], q8[3]);
+        qa4[1] = qb4[1] = make_float4(q8[4], q8[5], q8[6], q8[7]);
         dv4[0] = make_float4(d8[0], d8[1], d8[2], d8[3]);
         dv4[1] = make_float4(d8[4], d8[5], d8[6], d8[7]);
     }
@@ -444,20 +447,19 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
             const float dn[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
             const float up[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
             const float dv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-            // neighbours outside the domain enter as zeros and are not counted: the same sums,
-            // in the same order, as adding only the interior ones, without branches that
-            // would split a warp at the walls
+            // neighbours outside the domain are the zeros of the tile's halo: the same sums, in
+            // the same order, as adding only the interior ones, with no per-cell tests.  The
+            // neighbour count differs only at the walls: rows 0 and n - 1 for the whole
+            // octet, and the octet's first (last) cell when it starts (ends) at x = 0 (n - 1)
+            // -- an octet lies wholly inside the domain
             float x[8];
-            const bool has_d = gy > 0, has_u = gy < n - 1;
+            const int cnt_mid = 2 + (gy > 0) + (gy < n - 1);
+            const float inv_mid = inv_count(cnt_mid);
+            const float inv_first = inv_count(cnt_mid - (gx == 0)), inv_last = inv_count(cnt_mid - (gx + 8 == n));
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const int i = gx + m;
-                const bool has_l = i > 0, has_r = i < n - 1;
-                const int cnt = has_l + has_r + has_d + has_u;
-                const float acc = it > 1 ? (((has_l ? row[m] : 0.0f) + (has_r ? row[m + 2] : 0.0f)) +
-                                            (has_d ? dn[m] : 0.0f)) + (has_u ? up[m] : 0.0f)
-                                         : 0.0f;
-                x[m] = (acc - P.h2 * dv[m]) * inv_count(cnt);
+                const float acc = it > 1 ? ((row[m] + row[m + 2]) + dn[m]) + up[m] : 0.0f;
+                x[m] = (acc - P.h2 * dv[m]) * (m == 0 ? inv_first : m == 7 ? inv_last : inv_mid);
             }
             const bool inner = ry >= kK && ry < kK + kTY && ro >= 1 && (ro - 1) * 8 < w;
             const uint32_t oct = (uint32_t)(((int64_t)gy * n + gx) >> 3);
