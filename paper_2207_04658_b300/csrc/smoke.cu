@@ -422,6 +422,12 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
     unsigned nsat = 0;
     unsigned kmin = 0xffffffffu, kmax = 0u;
     const uint32_t step_base = 1024u * step_index(P) + cbase;
+    // the scene's Philox keys, read once: inside the sweeps the compiler could not keep them
+    // in registers across the trace stores
+    const uint2 dkey = Q && P.dither ? P.seed[s] : make_uint2(0u, 0u);
+    const bool noise = !Q && P.sigma[1] != 0.0f;
+    const uint2 nkey = noise ? P.nseed[s] : make_uint2(0u, 0u);
+    const float namp = noise ? P.sign[s] * P.sigma[1] : 0.0f;
     for (int k = 0; k < nsweep; ++k) {
         const int it = it0 + k;
         const uint32_t counter = step_base + (uint32_t)it;
@@ -472,10 +478,7 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
             }
             if (Q) {
                 uint4 blk = make_uint4(0u, 0u, 0u, 0u);
-                if (P.dither) {
-                    const uint2 key = P.seed[s];
-                    blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), key.x, key.y);
-                }
+                if (P.dither) blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), dkey.x, dkey.y);
                 uint32_t code[8];
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
@@ -495,15 +498,13 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
 #pragma unroll
                     for (int m = 0; m < 8; ++m) x[m] = __uint_as_float(code[m]);
                 }
-            } else if (P.sigma[1] != 0.0f) {
-                const uint2 key = P.nseed[s];
-                const uint4 blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), key.x, key.y);
-                const float amp = P.sign[s] * P.sigma[1];
+            } else if (noise) {
+                const uint4 blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), nkey.x, nkey.y);
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
                     const uint32_t wd = uint4_at(blk, (m >> 1) & 3);
                     const uint32_t q16 = (m & 1) ? (wd >> 16) : (wd & 0xFFFFu);
-                    x[m] += amp * ((q16 & 0x8000u) ? 1.0f : -1.0f);
+                    x[m] += namp * ((q16 & 0x8000u) ? 1.0f : -1.0f);
                 }
             }
             float4 *nw = reinterpret_cast<float4 *>(nxt + ry * kRW + ro * 8);

@@ -53,7 +53,7 @@ def one_step_parity(q, oracle, sc, s0, sch, block=1 << 24):
 
 def test_cubes_full_size_one_step(q, oracle):
     from paper_2207_04658_b300 import autoquant, scenes
-    sc, s0 = scenes.cubes3d_scene()
+    sc, s0 = scenes.cubes3d_scene(resort_every=16)  # as bench.py runs it
     assert s0.shape[0] == 8_192_000
     scheme, _ = autoquant.cubes3d_scheme(0.01)
     dmax, frac = one_step_parity(q, oracle, sc, s0, scheme)
