@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(kT) divergence_kernel(Params P, int which)  //
 
 // Jacobi sweeps it0 .. it0 + nsweep - 1 (1-based, nsweep <= kK) of a projection, blocked in
 // time: a CTA loads a tile of kTY x kTX cells with a halo (kHX columns, kK rows) of the
-// previous iterate (q[src]; zero when it0 = 1) and of div into shared memory, runs the
+// previous iterate (q[src]; zero when it0 = 1) into shared memory (div is read through the
+// read-only cache as the sweeps need it), runs the
 // sweeps there (every sweep's values stored through the codec: encode, then the decoded
 // value is what the next sweep reads) and writes the tile's last iterate to q[src ^ 1].
 // The halo's values go wrong by one cell per sweep from the region's edge inward, so
@@ -382,14 +383,14 @@ __global__ void __launch_bounds__(kT) divergence_kernel(Params P, int which)  //
 // trace + k n^2).
 constexpr int kTX = 128, kTY = 32, kK = 4, kHX = 8;
 constexpr int kRW = kTX + 2 * kHX, kRH = kTY + 2 * kK, kRO = kRW / 8;
-constexpr size_t kJacobiSmem = sizeof(float) * 3 * kRW * kRH;
+constexpr size_t kJacobiSmem = sizeof(float) * 2 * kRW * kRH;
 
 template <bool Q>
-__global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nsweep, uint32_t cbase, int src,
+__global__ void __launch_bounds__(kT, 4) jacobi_kernel(Params P, int it0, int nsweep, uint32_t cbase, int src,
                                                     uint32_t *trace)
 {
     extern __shared__ float4 smem4[];
-    float *qa = reinterpret_cast<float *>(smem4), *qb = qa + kRW * kRH, *dvs = qb + kRW * kRH;
+    float *qa = reinterpret_cast<float *>(smem4), *qb = qa + kRW * kRH;
     const int s = blockIdx.y, n = P.n;
     const int tiles_x = (n + kTX - 1) / kTX;
     const int x0 = (int)(blockIdx.x % tiles_x) * kTX, y0 = (int)(blockIdx.x / tiles_x) * kTY;
@@ -402,20 +403,15 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
     for (int e = threadIdx.x; e < kRO * kRH; e += kT) {
         const int ry = e / kRO, ro = e % kRO;
         const int gy = gy0 + ry, gx = gx0 + ro * 8;
-        float q8[8] = {0, 0, 0, 0, 0, 0, 0, 0}, d8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (gy >= 0 && gy < n && gx >= 0 && gx < n) {  // octets lie wholly inside or outside
-            if (it0 > 1) ld_run8<Q>(qin, (int64_t)gy * n + gx, c, b, q8);
-            ld_run8<false>(div, (int64_t)gy * n + gx, c, b, d8);
-        }
+        float q8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (it0 > 1 && gy >= 0 && gy < n && gx >= 0 && gx < n)  // octets lie wholly inside or outside
+            ld_run8<Q>(qin, (int64_t)gy * n + gx, c, b, q8);
         // both iterate buffers: the sweeps write only octets inside the domain, so the cells
         // outside it keep these zeros in either buffer for the whole launch
         float4 *qa4 = reinterpret_cast<float4 *>(qa + ry * kRW + ro * 8);
         float4 *qb4 = reinterpret_cast<float4 *>(qb + ry * kRW + ro * 8);
-        float4 *dv4 = reinterpret_cast<float4 *>(dvs + ry * kRW + ro * 8);
         qa4[0] = qb4[0] = make_float4(q8[0], q8[1], q8[2], q8[3]);
         qa4[1] = qb4[1] = make_float4(q8[4], q8[5], q8[6], q8[7]);
-        dv4[0] = make_float4(d8[0], d8[1], d8[2], d8[3]);
-        dv4[1] = make_float4(d8[4], d8[5], d8[6], d8[7]);
     }
     __syncthreads();
     float *cur = qa, *nxt = qb;
@@ -446,8 +442,10 @@ __global__ void __launch_bounds__(kT) jacobi_kernel(Params P, int it0, int nswee
             const float4 c0 = reinterpret_cast<const float4 *>(rc)[0], c1 = reinterpret_cast<const float4 *>(rc)[1];
             const float4 d0 = reinterpret_cast<const float4 *>(rc - kRW)[0], d1 = reinterpret_cast<const float4 *>(rc - kRW)[1];
             const float4 u0 = reinterpret_cast<const float4 *>(rc + kRW)[0], u1 = reinterpret_cast<const float4 *>(rc + kRW)[1];
-            const float4 v0 = reinterpret_cast<const float4 *>(dvs + ry * kRW + ro * 8)[0];
-            const float4 v1 = reinterpret_cast<const float4 *>(dvs + ry * kRW + ro * 8)[1];
+            // the divergence through the read-only cache: kept out of shared memory, the
+            // tile's two iterate buffers (46 KB) let four CTAs share an SM
+            const float4 *dv4 = reinterpret_cast<const float4 *>(div + (int64_t)gy * n + gx);
+            const float4 v0 = __ldg(dv4), v1 = __ldg(dv4 + 1);
             const float row[10] = {ro > 0 ? rc[-1] : 0.0f, c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w,
                                    ro < kRO - 1 ? rc[8] : 0.0f};
             const float dn[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
