@@ -468,15 +468,24 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
                 }
             }
         } else {
-            // slow path: FP32 global atomics straight into the grid
+            // slow path: FP32 global atomics straight into the grid (rolled loops over local
+            // copies: rarely taken, and unrolled it would raise the hot path's register need)
+            float spw[3][3], sdx[3], sdy[3];
 #pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                sdx[a] = dpx[a];
+                sdy[a] = dpy[a];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) spw[a][b] = pw[a][b];
+            }
+#pragma unroll 1
             for (int i = 0; i < 3; ++i)
-#pragma unroll
+#pragma unroll 1
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int k = 0; k < (DIM == 3 ? 3 : 1); ++k) {
-                        const float wt = pw[0][i] * pw[1][j] * (DIM == 3 ? pw[2][k] : 1.0f);
-                        const float dp[3] = {dpx[i], dpy[j], dpz[k]};
+                        const float wt = spw[0][i] * spw[1][j] * (DIM == 3 ? spw[2][k] : 1.0f);
+                        const float dp[3] = {sdx[i], sdy[j], dpz[k]};
                         float mom[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                         for (int a = 0; a < DIM; ++a) {
