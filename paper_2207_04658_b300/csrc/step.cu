@@ -174,9 +174,9 @@ __device__ __forceinline__ void flush_counters(StepCounters &cnt, unsigned long 
 }
 
 // Four 256-thread CTAs per SM (64 registers a thread): 32 resident warps hide the
-// shared-memory and L2 latencies of the chunk loop better than 24 at 80 registers, although
-// the 3D kernels then spill ~170 bytes a thread to L1 (3D cubes, 8.2 M particles: 1.196 ->
-// 1.127 ms quantized, 0.878 -> 0.812 ms FP32; 16 warps were 11 % slower than 24).  The 3D
+// shared-memory and L2 latencies of the chunk loop better than 24 at 80 registers (3D
+// cubes, 8.2 M particles: 1.196 -> 1.127 ms quantized, 0.878 -> 0.812 ms FP32, then with
+// the fallback P2G rolled 1.094 and 0.788 ms; 16 warps were 11 % slower than 24).  The 3D
 // instantiations with saturation counters keep two, which they need to avoid spills.
 template <int DIM, bool STATS>
 constexpr int step_ctas_per_sm() { return DIM == 3 && STATS ? 2 : 4; }
