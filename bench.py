@@ -193,6 +193,20 @@ def e2e_scene(qmpm, torch, g, steps, warmup):
     return el, int(words.nbytes)
 
 
+STEP_SOURCES = ("step.cu", "device_common.cuh", "mpm_device.cuh", "qmpm_internal.h")
+SMOKE_SOURCES = ("smoke.cu", "device_common.cuh", "qmpm_internal.h")
+
+
+def sources_sha256(names):
+    """SHA-256 over the named csrc files in order: a committed counter record is used only
+    while the kernel and every header it compiles from are unchanged since its capture."""
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2207_04658_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def kernel_counters(desc, n_particles, words=None):
     """DRAM bytes, warp instructions and thread instructions per launch of the step kernel
     from the committed ncu summary, scaled by the particle count to this workload; Nones
@@ -202,8 +216,7 @@ def kernel_counters(desc, n_particles, words=None):
         return None, None, None
     try:
         rec = json.load(open(path))
-        src = open(os.path.join(ROOT, "paper_2207_04658_b300", "csrc", "step.cu"), "rb").read()
-        if rec.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("sources_sha256") != sources_sha256(STEP_SOURCES):
             return None, None, None
         if rec.get("workload") != desc["workload"]:
             return None, None, None
@@ -376,8 +389,7 @@ def smoke_counters():
         return None, None, None
     try:
         rec = json.load(open(path))
-        src = open(os.path.join(ROOT, "paper_2207_04658_b300", "csrc", "smoke.cu"), "rb").read()
-        if rec.get("smoke_cu_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("sources_sha256") != sources_sha256(SMOKE_SOURCES):
             return None, None, None
         return rec["warp_instructions_per_launch"], rec["dram_bytes_per_launch"], rec
     except Exception:

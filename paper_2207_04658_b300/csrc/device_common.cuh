@@ -30,6 +30,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same generator with its ten round keys given (round r: seed_lo + r 0x9E3779B9,
+// seed_hi + r 0xBB67AE85, precomputed on the host): read from the kernel's parameters, each
+// key is an operand of the round's XOR instead of two additions per round.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk)[2][10])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[0][r], lo1, hi0 ^ c.w ^ rk[1][r], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint32_t uint4_at(const uint4 &v, int i)
 {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;

@@ -52,6 +52,7 @@ struct StepParams {
     int32_t n_words;
     int32_t dither;
     uint32_t seed_lo, seed_hi;
+    uint32_t round_key[2][10];  // Philox round keys: seed + r x Weyl constant (host-filled)
     uint32_t step;              // dither step index of this step's store
     CompCodec comp[kMaxComp];
     // data

@@ -189,7 +189,7 @@ constexpr size_t step_smem_fixed() { return (size_t)7 * (DIM == 2 ? 64 : 512) * 
 // One work item: the chunk ch of the scene described by P.  Its dithered stores use step
 // index P.step, or `step` in a multi-scene launch (MULTI).  All threads of the CTA call it
 // together (it synchronises).
-template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P, bool MULTI = false>
+template <int DIM, int MAT, bool QUANT, bool STATS, bool DO_G2P, bool MULTI = false, bool ROUND_KEYS = !MULTI>
 __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci0, uint32_t step, StepCounters &cnt,
                                           const int tid)
 {
@@ -349,9 +349,16 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
                 uint4 rnd = make_uint4(0, 0, 0, 0);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    if (P.dither && (c & 7) == 0)
-                        rnd = philox4x32_10(make_uint4((uint32_t)slot, MULTI ? step : P.step, (uint32_t)(c >> 3), 0u),
-                                            P.seed_lo, P.seed_hi);
+                    if (P.dither && (c & 7) == 0) {
+                        // the round keys are operands where P sits in the parameter space; the
+                        // multi-scene kernel reads P from shared memory, and there the two
+                        // additions per round are cheaper than loading the keys
+                        const uint4 ctr = make_uint4((uint32_t)slot, MULTI ? step : P.step, (uint32_t)(c >> 3), 0u);
+                        if (ROUND_KEYS)
+                            rnd = philox4x32_10_rk(ctr, P.round_key);
+                        else
+                            rnd = philox4x32_10(ctr, P.seed_lo, P.seed_hi);
+                    }
                     int fl;
                     const CompCodec &cc = P.comp[c];
                     const uint32_t u = encode_f32(val[c], cc, P.dither != 0, dither_threshold(rnd, c), fl);
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, step_ctas_per_sm<DIM, STATS>())
     for (;;) {
         const uint32_t ti = take_tile(P.work, &ticket);
         if (ti >= n_tiles) break;
-        run_chunk<DIM, MAT, QUANT, STATS, true, true>(P, P.tile_first[ti], step, cnt, tid);
+        run_chunk<DIM, MAT, QUANT, STATS, true, true, true>(P, P.tile_first[ti], step, cnt, tid);
     }
     if (STATS) flush_counters(cnt, P.stats);
     finish_launch(P.work);
@@ -872,6 +879,10 @@ void fill_params(const Ctx &c, StepParams &p)
     p.dither = s.dither;
     p.seed_lo = (uint32_t)s.seed;
     p.seed_hi = (uint32_t)(s.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.round_key[0][r] = p.seed_lo + (uint32_t)r * 0x9E3779B9u;
+        p.round_key[1][r] = p.seed_hi + (uint32_t)r * 0xBB67AE85u;
+    }
     for (int q = 0; q < c.n_comp; ++q) p.comp[q] = c.cc[q];
     p.words = c.words[c.cur];
     p.ld = c.ld;
