@@ -159,16 +159,27 @@ __global__ void radix_hist_kernel(const uint32_t *keys, int64_t N, int shift, ui
     counts[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// Scatter of one pass.  A CTA ranks its 4096 keys stably by digit (warp match masks, then
+// a prefix over warps), places them in shared memory in digit order, and writes each
+// digit's run out with consecutive threads on consecutive addresses: the destinations are
+// those of a direct scatter, but the stores coalesce instead of landing one 4-byte word
+// per digit run and warp.
 __global__ void radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                                      uint32_t *vals_out, int64_t N, int shift, const uint32_t *offsets,
                                      int64_t n_tiles)
 {
     constexpr int kWarps = kSortThreads / 32;
+    static_assert(kSortThreads == 256, "one thread per digit in the digit prefix");
     __shared__ uint32_t wcount[kWarps][257];
+    __shared__ uint32_t dstart[256];       // first local position of each digit
+    __shared__ uint32_t dglobal[256];      // its global destination minus dstart
+    __shared__ uint32_t wsum[kWarps];
+    __shared__ uint32_t skey[kSortTile], sval[kSortTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kWarps * 257; i += kSortThreads) (&wcount[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (kSortItems * 32);
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)warp * (kSortItems * 32);
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
     int dg[kSortItems];
@@ -188,22 +199,44 @@ __global__ void radix_scatter_kernel(const uint32_t *keys_in, const uint32_t *va
         dg[r] = d;
     }
     __syncthreads();
-    if (threadIdx.x < 256) {
+    // digit d = threadIdx.x: prefix over warps, then the exclusive prefix over digits
+    {
+        const int d = threadIdx.x;
         uint32_t run = 0;
         for (int w = 0; w < kWarps; ++w) {
-            const uint32_t t = wcount[w][threadIdx.x];
-            wcount[w][threadIdx.x] = run;
+            const uint32_t t = wcount[w][d];
+            wcount[w][d] = run;
             run += t;
         }
+        uint32_t incl = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t before_warp = 0;
+        for (int w = 0; w < warp; ++w) before_warp += wsum[w];
+        const uint32_t start = before_warp + incl - run;
+        dstart[d] = start;
+        dglobal[d] = offsets[(int64_t)d * n_tiles + blockIdx.x] - start;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (dg[r] < 256) {
-            const uint32_t dst = offsets[(int64_t)dg[r] * n_tiles + blockIdx.x] + wcount[warp][dg[r]] + rank[r];
-            keys_out[dst] = k[r];
-            vals_out[dst] = v[r];
+            const uint32_t lp = dstart[dg[r]] + wcount[warp][dg[r]] + rank[r];
+            skey[lp] = k[r];
+            sval[lp] = v[r];
         }
+    }
+    __syncthreads();
+    const int n_here = (int)min((int64_t)kSortTile, N - tile0);
+    for (int i = threadIdx.x; i < n_here; i += kSortThreads) {
+        const uint32_t key = skey[i];
+        const uint32_t dst = dglobal[(key >> shift) & 255u] + (uint32_t)i;
+        keys_out[dst] = key;
+        vals_out[dst] = sval[i];
     }
 }
 
