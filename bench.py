@@ -196,6 +196,7 @@ def e2e_scene(qmpm, torch, g, steps, warmup):
     return el, int(words.nbytes)
 
 
+L2_BYTES = 126 * 2 ** 20  # B300 L2
 STEP_SOURCES = ("step.cu", "device_common.cuh", "mpm_device.cuh", "qmpm_internal.h")
 SMOKE_SOURCES = ("smoke.cu", "device_common.cuh", "qmpm_internal.h")
 
@@ -600,8 +601,10 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "gpu_launches": int(prof["kernel_launches"]),
-            "config": dict(desc, replicas=dc.world, l2="inputs larger than L2 (packed state "
-                           f"{N * 4 * W / 1e6:.0f} MB per replica)",
+            "config": dict(desc, replicas=dc.world, l2=(f"inputs larger than L2 (packed state {N * 4 * W / 1e6:.0f} MB "
+                           "per replica, two buffers plus the grid)" if 2 * N * 4 * W > L2_BYTES else
+                           f"L2-resident, not flushed (packed state {N * 4 * W / 1e6:.1f} MB): a latency "
+                           "measurement, not a bandwidth one"),
                            bytes_per_particle_quantized=4 * W, bytes_per_particle_fp32=4 * g.n_comp,
                            compression=round(g.n_comp / W, 3), parallelism=f"replicas{dc.world}"),
             "roofline": roofline, "breakdown": breakdown, "clocks": clk,
