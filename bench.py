@@ -215,22 +215,22 @@ def kernel_counters(desc, n_particles, words=None):
     """DRAM bytes, warp instructions and thread instructions per launch of the step kernel
     from the committed ncu summary, scaled by the particle count to this workload; Nones
     when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    if not os.path.exists(path):
-        return None, None, None
-    try:
-        rec = json.load(open(path))
-        if rec.get("sources_sha256") != sources_sha256(STEP_SOURCES):
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "step_kernel_traffic*.json"))):
+        try:
+            rec = json.load(open(path))
+            if rec.get("workload") != desc["workload"]:
+                continue
+            if rec.get("sources_sha256") != sources_sha256(STEP_SOURCES):
+                return None, None, None
+            if words is not None and rec.get("words_per_particle") not in (None, words):
+                return None, None, None
+            f = n_particles / rec["particles"]
+            return (rec["dram_bytes_per_launch"] * f, rec["warp_instructions_per_launch"] * f,
+                    rec.get("thread_instructions_per_launch", 0) * f or None)
+        except Exception:
             return None, None, None
-        if rec.get("workload") != desc["workload"]:
-            return None, None, None
-        if words is not None and rec.get("words_per_particle") not in (None, words):
-            return None, None, None
-        f = n_particles / rec["particles"]
-        return (rec["dram_bytes_per_launch"] * f, rec["warp_instructions_per_launch"] * f,
-                rec.get("thread_instructions_per_launch", 0) * f or None)
-    except Exception:
-        return None, None, None
+    return None, None, None
 
 
 def issue_peak(peaks):
