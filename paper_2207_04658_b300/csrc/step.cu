@@ -40,9 +40,10 @@ __device__ __forceinline__ float4 node_velocity(float4 mm, int gx, int gy, int g
     bool wall = gx < P.bound || gx > hi || gy < P.bound || gy > hi;
     if (DIM == 3) wall = wall || gz < P.bound || gz > hi;
     if (mm.x > 0.0f && !wall) {
-        v.x = mm.y / mm.x + P.dt * P.gravity[0];
-        v.y = mm.z / mm.x + P.dt * P.gravity[1];
-        if (DIM == 3) v.z = mm.w / mm.x + P.dt * P.gravity[2];
+        const float inv_m = 1.0f / mm.x;  // one division for the d components
+        v.x = mm.y * inv_m + P.dt * P.gravity[0];
+        v.y = mm.z * inv_m + P.dt * P.gravity[1];
+        if (DIM == 3) v.z = mm.w * inv_m + P.dt * P.gravity[2];
     }
     return v;
 }
@@ -517,15 +518,16 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
     }  // chunks of the tile
 
     // 7. the P2G tile flush: one vector atomic per node that received mass
+    const float mm = P.p_mass / (scale > 0.0f ? scale : 1.0f);  // momentum units -> m v
+    const float mmass = P.p_mass / kfix;                        // mass units -> m
     for (int t = tid; t < TN; t += kThreads) {
         const int i = DIM == 2 ? (t >> 3) : (t >> 6), j = DIM == 2 ? (t & 7) : ((t >> 3) & 7);
         const int k = DIM == 2 ? 0 : (t & 7);
         const int q = tile_index<DIM>(i, j, k);
         const int im = tpm[q];
         if (im != 0) {
-            const float mm = P.p_mass / (scale > 0.0f ? scale : 1.0f);  // momentum units -> m v
             atomicAdd(P.grid_out + node_addr<DIM>(P.nb, o0 + i, o1 + j, o2 + k),
-                      make_float4((float)im * (P.p_mass / kfix), (float)tpx[q] * mm, (float)tpy[q] * mm,
+                      make_float4((float)im * mmass, (float)tpx[q] * mm, (float)tpy[q] * mm,
                                   DIM == 3 ? (float)tpz[q] * mm : 0.0f));
         }
     }
