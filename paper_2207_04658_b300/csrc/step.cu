@@ -417,7 +417,10 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
     for (int w8 = 0; w8 < kThreads / 32; ++w8) bmax = fmaxf(bmax, red[w8]);
     // the largest power of two that maps this chunk's largest contribution inside kfix; a
     // chunk that needs a smaller one than the tile's sums so far shifts those sums down first
-    const float want = bmax > 0.0f ? exp2f(floorf(log2f(kfix / bmax))) : 0.0f;
+    // (kfix / bmax with its mantissa bits cleared, clamped so that a vanishing bmax cannot
+    // make it infinite; the division's rounding stays inside the 64 units kfix keeps free)
+    const float want =
+        bmax > 0.0f ? __uint_as_float(__float_as_uint(fminf(kfix / bmax, 1.7e38f)) & 0xFF800000u) : 0.0f;
     if (want > 0.0f && scale == 0.0f) {
         scale = want;
     } else if (want > 0.0f && want < scale) {

