@@ -354,29 +354,81 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
                    "[1e4, 4e6]; eps uniform {0.1, 0.01}; 200 steps; schemes from Algorithm 1 per class and grid"}
 
 
-def cpu_baseline(name, sample_steps=2):
-    """The oracle (single-threaded FP64 C) on a bounded sample of the same workload: the
-    first cube (or a slice of the column) on the full grid, `sample_steps` quantized steps.
-    It takes the hand-written scheme (its inputs never come from the CUDA path; its cost
-    does not depend on the bit widths)."""
+def host_cpu():
+    """The host's CPU model, its logical cores (those this process may run on) and memory."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    try:
+        mem = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        mem = 0
+    return {"model": model, "cores": cores, "logical_cpus": os.cpu_count(), "mem_available_gb": round(mem / 2 ** 30, 1)}
+
+
+def _oracle_slice(job):
+    """One oracle process of the aggregate: its slice of the workload's initial state (read
+    from the shared .npy file), `steps` quantized steps on the full grid."""
+    sc, sch, path, lo, hi, steps = job
     import oracle
-    sc, s0, sch, desc = workload(name)
-    if name == "cubes3d":
-        n = 512_000
-        sample = f"first cube of 16 ({n} particles) on the full 256^3 grid, {sample_steps} steps, hand-written scheme"
-    elif name == "dambreak3d":
-        n = 256_000
-        sample = f"first {n} particles of the column on the full 512^3 grid, {sample_steps} steps"
-    else:
-        n = s0.shape[0]
-        sample = f"whole scene, {sample_steps} steps"
-    s0 = s0[:n]
+    s0 = np.array(np.load(path, mmap_mode="r")[lo:hi])
     ro = oracle.QuantRollout(sc, sch, s0)
+    t = time.perf_counter()
+    ro.step(steps)
+    return (hi - lo) * steps, time.perf_counter() - t
+
+
+def cpu_baseline(name, scheme=None, sample_steps=2):
+    """The oracle (single-threaded FP64 C, as it stands) on bounded samples of the same
+    workload and scheme.  Single core: the first cube (or a slice of the column) on the full
+    grid, `sample_steps` quantized steps.  Aggregate: one oracle process per host core (capped
+    by the memory each needs: the full FP64 grid plus its slice), each stepping a disjoint
+    slice of the whole scene; value = the particle-steps of all processes over the slowest
+    one's time."""
+    import multiprocessing as mp
+    import oracle
+    sc, s0, sch, desc = workload(name, scheme=scheme)
+    n = {"cubes3d": 512_000, "dambreak3d": 256_000}.get(name, s0.shape[0])
+    what = {"cubes3d": "first cube of 16", "dambreak3d": "first particles of the column"}.get(name, "whole scene")
+    ro = oracle.QuantRollout(sc, sch, s0[:n])
     t = time.perf_counter()
     ro.step(sample_steps)
     el = time.perf_counter() - t
-    return {"value": n * sample_steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample}
+    one = n * sample_steps / el
+    host = host_cpu()
+    grid_bytes = oracle.n_nodes(ro.ph) * (1 + ro.ph.dim) * 8
+    del ro
+    per_proc = 2 * grid_bytes + 3 * 8 * s0.shape[1] * (s0.shape[0] // max(1, host["cores"]))
+    P = max(1, min(host["cores"], 256, int(0.6 * host["mem_available_gb"] * 2 ** 30 // max(1, per_proc))))
+    out = {"value": one, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{what} ({n} particles) on the full grid, {sample_steps} steps, the bench's scheme",
+           "host": host, "single_core": one}
+    N = s0.shape[0]
+    if P > 1:
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "s0.npy")
+            np.save(path, s0)
+            del s0
+            bounds = [N * i // P for i in range(P + 1)]
+            jobs = [(sc, sch, path, bounds[i], bounds[i + 1], 1) for i in range(P)]
+            with mp.get_context("spawn").Pool(P) as pool:
+                res = pool.map(_oracle_slice, jobs, chunksize=1)
+        work = sum(r[0] for r in res)
+        out.update(value=work / max(r[1] for r in res), cores=P,
+                   sample=f"{P} oracle processes (one per core, memory permitting), each a disjoint "
+                          f"1/{P} of the whole {N}-particle scene on the full grid for one quantized step, "
+                          "the bench's scheme; value = all particle-steps over the slowest process's time")
+    return out
 
 
 # ------------------------------------------------------------------------------ smoke
@@ -646,7 +698,7 @@ def run_ours(args):
     if not args.no_smoke:
         line["smoke"] = smoke_section(args, peaks, dc, torch)
     if dc.rank == 0 and dc.world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, scheme=scheme)
     if dc.rank == 0:
         print(json.dumps(line), flush=True)
     dc.close()

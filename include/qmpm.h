@@ -32,8 +32,9 @@ extern "C" {
 #define QMPM_ERR_OOM (-2)
 #define QMPM_ERR_SCHEME (-3)   /* field wider than 24 bits, |offset| >= 2^24, bad layout */
 #define QMPM_ERR_CUDA (-4)
-#define QMPM_ERR_TIMEOUT (-5)  /* a bounded device wait expired */
+#define QMPM_ERR_TIMEOUT (-5)  /* a bounded wait expired (qmpm_engine_wait) */
 #define QMPM_ERR_OVERFLOW (-6) /* strict mode: a store saturated */
+#define QMPM_ERR_QUEUE_FULL (-7) /* the serving queue holds max_queued requests */
 
 #define QMPM_MAX_COMP 24
 #define QMPM_MAX_FIELD_BITS 24
@@ -359,7 +360,7 @@ typedef struct {
     int32_t resort_every;  /* the batch's re-sort interval; also the longest iteration */
     int32_t max_active;    /* scenes stepping at once, 1 .. 256 */
     int32_t flags;         /* QMPM_BATCH_GRAPHS */
-    int32_t pad;
+    int32_t max_queued;    /* requests waiting for admission at most (0: no limit) */
 } qmpm_engine_config_t;
 
 typedef struct {
@@ -389,8 +390,10 @@ typedef struct {
  * step together in one batch (see qmpm_batch_*); each iteration runs up to resort_every
  * steps, and scenes join and leave between iterations while the others keep running.  A
  * new scene's upload, encode and sort run on a second stream, overlapping the batch.
- * Finished scenes are measured, optionally read back, and freed.  Errors:
- * QMPM_ERR_INVALID_ARG, QMPM_ERR_CUDA. */
+ * Finished scenes are measured, optionally read back, and freed.  Creation is host only;
+ * the engine's streams, events and batch are made by the first iteration (an iteration on
+ * a host without a usable device fails with QMPM_ERR_CUDA after admission has run).
+ * Errors: QMPM_ERR_INVALID_ARG. */
 int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out);
 
 #define QMPM_SUBMIT_KEEP_STATE 1 /* keep the final state for qmpm_engine_result */
@@ -398,9 +401,12 @@ int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out)
                                     caller keeps it unchanged until the request is polled */
 
 /* Queue a request; the engine copies h_state (host, as for qmpm_init) unless flags has
- * QMPM_SUBMIT_BORROW.  Thread-safe.  Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME.  A
- * request larger than the budget fails with QMPM_ERR_OOM when it reaches the head of the
- * queue. */
+ * QMPM_SUBMIT_BORROW.  The request is checked before it is queued: the scene (as
+ * qmpm_init), the scheme (as qmpm_scheme_layout), steps >= 0 and every initial value
+ * finite (a corrupted request is refused, not simulated).  Thread-safe.  Errors:
+ * QMPM_ERR_INVALID_ARG, QMPM_ERR_SCHEME, QMPM_ERR_QUEUE_FULL (max_queued requests wait
+ * already), QMPM_ERR_OOM (host allocation).  A request larger than the budget fails with
+ * QMPM_ERR_OOM when it reaches the head of the queue. */
 int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qmpm_scheme_t *scheme,
                        const double *h_state, int32_t steps, int32_t flags, int64_t *id);
 
@@ -410,8 +416,16 @@ int qmpm_engine_start(qmpm_engine_handle e);
 int qmpm_engine_stop(qmpm_engine_handle e, int32_t drain);
 
 /* Or run `iterations` iterations in the calling thread (not while the thread runs);
- * *busy = 0 once nothing is queued, running or finishing. */
+ * *busy = 0 once nothing is queued, running or finishing.  Errors: QMPM_ERR_INVALID_ARG,
+ * QMPM_ERR_CUDA (the engine's device setup failed). */
 int qmpm_engine_run(qmpm_engine_handle e, int32_t iterations, int32_t *busy);
+
+/* Wait at most timeout_s seconds (host clock) for the engine to become idle: nothing
+ * queued, admitted, running or finishing.  The waiting is done by the engine's thread
+ * (qmpm_engine_start); without it the queue does not move and the wait expires unless the
+ * engine is idle already.  *busy (may be NULL) = 1 if work remains.  Errors:
+ * QMPM_ERR_INVALID_ARG, QMPM_ERR_TIMEOUT (the deadline passed with work remaining). */
+int qmpm_engine_wait(qmpm_engine_handle e, double timeout_s, int32_t *busy);
 
 /* Take up to max finished requests (oldest first).  Thread-safe. */
 int qmpm_engine_poll(qmpm_engine_handle e, qmpm_request_t *out, int32_t max, int32_t *n_out);
@@ -440,6 +454,24 @@ int qmpm_pack_f32(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, ui
 int qmpm_unpack_f32(int32_t dim, int32_t material, const qmpm_scheme_t *scheme,
                     const uint32_t *d_words, int64_t N, int64_t ld, float *d_vals, void *stream);
 
+/* ---- host-side fault injection ------------------------------------------------- */
+
+/* Kinds of injected faults.  None touches a GPU: the library reports the failure where the
+ * real one would be detected, so that callers' recovery paths can be tested. */
+#define QMPM_FAULT_DEVICE_ALLOC 0 /* a device allocation of qmpm_init fails: QMPM_ERR_OOM */
+#define QMPM_FAULT_HOST_ALLOC 1   /* the host allocation of a request in qmpm_engine_submit
+                                     fails: QMPM_ERR_OOM */
+#define QMPM_FAULT_WAIT 2         /* qmpm_engine_wait expires at once: QMPM_ERR_TIMEOUT */
+#define QMPM_FAULT_KINDS 3
+
+/* Arm `kind`: the next `after` occurrences pass, the `count` after them fail (count 0
+ * disarms).  Process-wide and thread-safe.  Errors: QMPM_ERR_INVALID_ARG. */
+int qmpm_fault_inject(int32_t kind, int64_t after, int64_t count);
+/* How many faults of `kind` were injected since the last qmpm_fault_clear. */
+int qmpm_fault_hits(int32_t kind, int64_t *hits);
+/* Disarm every kind and reset the counts. */
+int qmpm_fault_clear(void);
+
 /* ---- ordering without device allocation ----------------------------------------- */
 
 /* Largest N accepted by qmpm_tile_order_static. */
@@ -461,8 +493,12 @@ int qmpm_unpack_f32(int32_t dim, int32_t material, const qmpm_scheme_t *scheme,
  * call's contents; every word a call reads is written earlier in the same call, so
  * nothing has to be cleared.  Calls whose work overlaps on the GPU (other streams or
  * threads) race on the array: order them.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Asynchronous on `stream` after the lookup.
+ * array's device address (cudaGetSymbolAddress) with that device current; with lazy module
+ * loading (the CUDA default) that lookup may load the library's device code, which can
+ * synchronise the device, so make that first call early: before any stream capture and
+ * outside the code that must not allocate.  The address is kept for the life of the
+ * process; a cudaDeviceReset between calls is not supported.  Asynchronous on `stream`
+ * after the lookup.
  * Errors: QMPM_ERR_INVALID_ARG (N > QMPM_STATIC_SORT_MAX, bad dim/material/grid/buffers),
  * QMPM_ERR_SCHEME, QMPM_ERR_CUDA. */
 int qmpm_tile_order_static(int32_t dim, int32_t material, int32_t grid_log2, const qmpm_scheme_t *scheme,

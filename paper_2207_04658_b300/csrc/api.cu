@@ -35,6 +35,7 @@ cudaError_t dalloc(T **p, size_t count, cudaStream_t s)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (qmpm::fault_hit(QMPM_FAULT_DEVICE_ALLOC)) return cudaErrorMemoryAllocation;
     return cudaMallocAsync(reinterpret_cast<void **>(p), count * sizeof(T), s);
 }
 
@@ -144,7 +145,7 @@ int do_clear(qmpm::Ctx &c, int buf)
     return QMPM_OK;
 }
 
-int validate_scene(const qmpm_scene_t *s)
+int check_scene(const qmpm_scene_t *s)
 {
     if (!s) return fail(QMPM_ERR_INVALID_ARG, "scene is NULL");
     if (s->dim != 2 && s->dim != 3) return fail(QMPM_ERR_INVALID_ARG, "dim must be 2 or 3");
@@ -165,6 +166,7 @@ int validate_scene(const qmpm_scene_t *s)
 
 namespace qmpm {
 void set_last_error(const std::string &msg) { g_err = msg; }
+int validate_scene(const qmpm_scene_t *s) { return check_scene(s); }
 
 // Free a handle's device memory in order on its stream, without waiting for the stream.
 void destroy_nosync(qmpm_ctx *c)
@@ -269,7 +271,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
 {
     if (!out) return fail(QMPM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    int rc = validate_scene(scene);
+    int rc = check_scene(scene);
     if (rc != QMPM_OK) return rc;
     if (scene->n_particles > 0 && !h_state) return fail(QMPM_ERR_INVALID_ARG, "h_state is NULL");
     qmpm_ctx *c = new (std::nothrow) qmpm_ctx();
@@ -290,28 +292,34 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
     const Sizes z = sizes_of(*c);
     const cudaStream_t st = c->stream;
     bool ok = true;
+    cudaError_t ae = cudaSuccess;  // the first failed allocation's error
+    auto okd = [&ae](cudaError_t r) {
+        if (r != cudaSuccess && ae == cudaSuccess) ae = r;
+        return r == cudaSuccess;
+    };
     for (int i = 0; i < 2 && ok; ++i) {
-        ok = ok && dalloc(&c->words[i], z.words, st) == cudaSuccess;
-        ok = ok && dalloc(&c->ids[i], z.ids, st) == cudaSuccess;
-        ok = ok && dalloc(&c->grid[i], z.grid, st) == cudaSuccess;
-        ok = ok && dalloc(&c->touched[i], z.touched, st) == cudaSuccess;
-        ok = ok && dalloc(&c->keys[i], z.keys, st) == cudaSuccess;
-        ok = ok && dalloc(&c->vals[i], z.keys, st) == cudaSuccess;
+        ok = ok && okd(dalloc(&c->words[i], z.words, st));
+        ok = ok && okd(dalloc(&c->ids[i], z.ids, st));
+        ok = ok && okd(dalloc(&c->grid[i], z.grid, st));
+        ok = ok && okd(dalloc(&c->touched[i], z.touched, st));
+        ok = ok && okd(dalloc(&c->keys[i], z.keys, st));
+        ok = ok && okd(dalloc(&c->vals[i], z.keys, st));
     }
-    ok = ok && dalloc(&c->digit_counts, z.digit_counts, st) == cudaSuccess;
-    ok = ok && dalloc(&c->scan_partials, z.scan_partials, st) == cudaSuccess;
-    ok = ok && dalloc(&c->seg_begin, z.seg, st) == cudaSuccess;
-    ok = ok && dalloc(&c->seg_end, z.seg, st) == cudaSuccess;
-    ok = ok && dalloc(&c->key_chunks, z.key_chunks, st) == cudaSuccess;
-    ok = ok && dalloc(&c->chunks, z.chunks, st) == cudaSuccess;
-    ok = ok && dalloc(&c->tile_idx, z.key_chunks, st) == cudaSuccess;
-    ok = ok && dalloc(&c->tile_first, z.seg, st) == cudaSuccess;
-    ok = ok && dalloc(&c->d_stats, 17, st) == cudaSuccess;  // 16 statistics + the step kernels' tile queue
-    ok = ok && dalloc(&c->d_z, 1, st) == cudaSuccess;
+    ok = ok && okd(dalloc(&c->digit_counts, z.digit_counts, st));
+    ok = ok && okd(dalloc(&c->scan_partials, z.scan_partials, st));
+    ok = ok && okd(dalloc(&c->seg_begin, z.seg, st));
+    ok = ok && okd(dalloc(&c->seg_end, z.seg, st));
+    ok = ok && okd(dalloc(&c->key_chunks, z.key_chunks, st));
+    ok = ok && okd(dalloc(&c->chunks, z.chunks, st));
+    ok = ok && okd(dalloc(&c->tile_idx, z.key_chunks, st));
+    ok = ok && okd(dalloc(&c->tile_first, z.seg, st));
+    ok = ok && okd(dalloc(&c->d_stats, 17, st));  // 16 statistics + the step kernels' tile queue
+    ok = ok && okd(dalloc(&c->d_z, 1, st));
     if (!ok) {
         cudaGetLastError();
         release(c);
-        return fail(QMPM_ERR_OOM, "device allocation failed");
+        if (ae == cudaErrorMemoryAllocation) return fail(QMPM_ERR_OOM, "device allocation failed");
+        return cuda_fail(ae, "device allocation");
     }
     c->n_chunks = c->key_chunks + c->n_blocks;
     c->n_tiles = c->tile_idx + c->n_blocks;
@@ -373,7 +381,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
 int qmpm_footprint(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, int64_t *resident_bytes,
                    int64_t *init_peak_bytes)
 {
-    int rc = validate_scene(scene);
+    int rc = check_scene(scene);
     if (rc != QMPM_OK) return rc;
     qmpm_ctx *c = new (std::nothrow) qmpm_ctx();
     if (!c) return fail(QMPM_ERR_OOM, "host allocation failed");

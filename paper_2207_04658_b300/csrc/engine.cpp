@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -56,6 +57,7 @@ struct Request {
 struct qmpm_engine {
     qmpm_engine_config_t cfg;
     int dev = 0;
+    bool device_ready = false;  // streams, events, pinned slots and batch made (first iteration)
     cudaStream_t step_stream = nullptr;
     qmpm_batch_handle batch = nullptr;
     double *pinned = nullptr;  // one z slot per request id modulo kSlots
@@ -73,6 +75,7 @@ struct qmpm_engine {
     std::vector<Request *> done;
     std::map<int64_t, Request *> kept;
     int64_t next_id = 1;
+    int64_t pending = 0;             // submitted requests not yet finished (idle when 0)
     int64_t snap_active = 0, snap_bytes = 0, snap_particle_steps = 0, snap_iterations = 0;  // for stats
     int64_t snap_launches = 0, snap_graph_launches = 0;
 
@@ -123,6 +126,7 @@ void finish(qmpm_engine &e, Request *r, int32_t status)
     std::lock_guard<std::mutex> lk(e.mu);
     e.done.push_back(r);
     e.n_done += 1;
+    e.pending -= 1;
 }
 
 // Requests whose measurement has reached the host.
@@ -227,6 +231,7 @@ void join_ready(qmpm_engine &e)
         e.in_init -= (int)rd.size();
     }
     for (Request *r : rd) {
+        r->h_z = e.pinned + (r->id % qmpm_engine::kSlots);
         int rc = r->error ? r->error : QMPM_OK;
         if (rc == QMPM_OK && r->steps > 0) rc = qmpm_batch_add(e.batch, r->h);
         if (rc != QMPM_OK) {
@@ -247,12 +252,48 @@ void join_ready(qmpm_engine &e)
     }
 }
 
+// The engine's device resources, made on the first iteration (creation stays host only).
+int setup_device(qmpm_engine &e)
+{
+    cudaSetDevice(e.dev);
+    // keep freed scene memory in the pool between requests instead of returning it to the
+    // driver at every synchronisation (a setting of this process's pool only)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, e.dev) == cudaSuccess) {
+        uint64_t keep = ~uint64_t(0);
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaError_t ce = cudaSuccess;
+    if (!e.step_stream) ce = cudaStreamCreateWithFlags(&e.step_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess && !e.iter_ev[0]) ce = cudaEventCreateWithFlags(&e.iter_ev[0], cudaEventDisableTiming);
+    if (ce == cudaSuccess && !e.iter_ev[1]) ce = cudaEventCreateWithFlags(&e.iter_ev[1], cudaEventDisableTiming);
+    if (ce == cudaSuccess && !e.pinned)
+        ce = cudaMallocHost(reinterpret_cast<void **>(&e.pinned), sizeof(double) * qmpm_engine::kSlots);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return efail(QMPM_ERR_CUDA, std::string("engine device setup: ") + cudaGetErrorString(ce));
+    }
+    if (!e.batch) {
+        const int rc = qmpm_batch_create(e.step_stream, e.cfg.resort_every, e.cfg.flags, &e.batch);
+        if (rc != QMPM_OK) return rc;
+    }
+    e.device_ready = true;
+    return QMPM_OK;
+}
+
 // One iteration: completions, admissions, then up to resort_every steps of every member.
 // Returns the number of members stepped.
-int iterate(qmpm_engine &e)
+int iterate(qmpm_engine &e, int *rc_out = nullptr)
 {
     collect(e);
     admit(e);
+    if (!e.device_ready) {
+        const int rc = setup_device(e);
+        if (rc != QMPM_OK) {
+            if (rc_out) *rc_out = rc;
+            return 0;
+        }
+    }
     join_ready(e);
     if (e.active.empty()) return 0;
     int32_t L = e.cfg.resort_every > 0 ? e.cfg.resort_every : 8;
@@ -319,7 +360,9 @@ void loop(qmpm_engine *e)
     cudaSetDevice(e->dev);
     while (true) {
         if (e->stop_req.load() && (!e->drain.load() || idle(*e))) break;
-        const int stepped = iterate(*e);
+        int rc = QMPM_OK;
+        const int stepped = iterate(*e, &rc);
+        if (rc != QMPM_OK) break;  // no device: nothing can run
         if (stepped == 0) {
             std::unique_lock<std::mutex> lk(e->mu);
             e->cv.wait_for(lk, std::chrono::microseconds(e->finishing.empty() ? 1000 : 50),
@@ -336,33 +379,17 @@ extern "C" {
 int qmpm_engine_create(const qmpm_engine_config_t *cfg, qmpm_engine_handle *out)
 {
     if (!cfg || !out) return efail(QMPM_ERR_INVALID_ARG, "cfg or out is NULL");
-    if (cfg->budget_bytes <= 0 || cfg->max_active <= 0 || cfg->max_active > 256 || cfg->resort_every < 0)
+    if (cfg->budget_bytes <= 0 || cfg->max_active <= 0 || cfg->max_active > 256 || cfg->resort_every < 0 ||
+        cfg->max_queued < 0)
         return efail(QMPM_ERR_INVALID_ARG, "bad engine configuration");
     *out = nullptr;
     qmpm_engine *e = new (std::nothrow) qmpm_engine();
     if (!e) return efail(QMPM_ERR_OOM, "host allocation failed");
     e->cfg = *cfg;
     e->t0 = Clock::now();
-    cudaGetDevice(&e->dev);
-    // keep freed scene memory in the pool between requests instead of returning it to the
-    // driver at every synchronisation (a setting of this process's pool only)
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, e->dev) == cudaSuccess) {
-        uint64_t keep = ~uint64_t(0);
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    }
-    cudaError_t ce = cudaStreamCreateWithFlags(&e->step_stream, cudaStreamNonBlocking);
-    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->iter_ev[0], cudaEventDisableTiming);
-    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->iter_ev[1], cudaEventDisableTiming);
-    if (ce == cudaSuccess) ce = cudaMallocHost(reinterpret_cast<void **>(&e->pinned), sizeof(double) * qmpm_engine::kSlots);
-    if (ce != cudaSuccess) {
-        qmpm_engine_destroy(e);
-        return efail(QMPM_ERR_CUDA, std::string("engine setup: ") + cudaGetErrorString(ce));
-    }
-    const int rc = qmpm_batch_create(e->step_stream, cfg->resort_every, cfg->flags, &e->batch);
-    if (rc != QMPM_OK) {
-        qmpm_engine_destroy(e);
-        return rc;
+    if (cudaGetDevice(&e->dev) != cudaSuccess) {
+        cudaGetLastError();
+        e->dev = 0;
     }
     e->init_worker = std::thread(init_loop, e);
     *out = e;
@@ -374,7 +401,24 @@ int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qm
 {
     if (!e || !scene || steps < 0 || (scene->n_particles > 0 && !h_state))
         return efail(QMPM_ERR_INVALID_ARG, "bad request");
-    Request *r = new (std::nothrow) Request();
+    int vrc = qmpm::validate_scene(scene);
+    if (vrc != QMPM_OK) return vrc;
+    if (scheme && scheme->quantized) {
+        qmpm_scheme_t chk = *scheme;
+        vrc = qmpm_scheme_layout(scene->dim, scene->material, &chk);
+        if (vrc != QMPM_OK) return vrc;
+    }
+    {
+        // a corrupted initial state (NaN or infinite values) is refused before it is queued
+        const int nc0 = 2 * scene->dim + scene->dim * scene->dim +
+                        (scene->material == QMPM_FLUID ? 1 : scene->dim * scene->dim);
+        const size_t nv = (size_t)scene->n_particles * (size_t)nc0;
+        for (size_t i = 0; i < nv; ++i)
+            if (!std::isfinite(h_state[i]))
+                return efail(QMPM_ERR_INVALID_ARG, "request state holds a non-finite value at index " +
+                                                       std::to_string(i));
+    }
+    Request *r = qmpm::fault_hit(QMPM_FAULT_HOST_ALLOC) ? nullptr : new (std::nothrow) Request();
     if (!r) return efail(QMPM_ERR_OOM, "host allocation failed");
     r->scene = *scene;
     r->has_scheme = scheme && scheme->quantized;
@@ -395,8 +439,12 @@ int qmpm_engine_submit(qmpm_engine_handle e, const qmpm_scene_t *scene, const qm
     r->t_submit = e->now();
     {
         std::lock_guard<std::mutex> lk(e->mu);
+        if (e->cfg.max_queued > 0 && (int64_t)e->queue.size() >= e->cfg.max_queued) {
+            delete r;
+            return efail(QMPM_ERR_QUEUE_FULL, "the request queue is full (max_queued)");
+        }
         r->id = e->next_id++;
-        r->h_z = e->pinned + (r->id % qmpm_engine::kSlots);
+        e->pending += 1;
         e->queue.push_back(r);
     }
     e->cv.notify_one();
@@ -408,9 +456,34 @@ int qmpm_engine_run(qmpm_engine_handle e, int32_t iterations, int32_t *busy)
 {
     if (!e || iterations < 0) return efail(QMPM_ERR_INVALID_ARG, "bad engine or iterations");
     if (e->running.load()) return efail(QMPM_ERR_INVALID_ARG, "the engine's thread is running");
-    for (int i = 0; i < iterations; ++i) iterate(*e);
+    int rc = QMPM_OK;
+    for (int i = 0; i < iterations && rc == QMPM_OK; ++i) iterate(*e, &rc);
     if (busy) *busy = idle(*e) ? 0 : 1;
-    return QMPM_OK;
+    return rc;
+}
+
+int qmpm_engine_wait(qmpm_engine_handle e, double timeout_s, int32_t *busy)
+{
+    if (!e || !(timeout_s >= 0.0)) return efail(QMPM_ERR_INVALID_ARG, "bad engine or timeout");
+    if (qmpm::fault_hit(QMPM_FAULT_WAIT)) {
+        if (busy) *busy = 1;
+        return efail(QMPM_ERR_TIMEOUT, "qmpm_engine_wait: deadline passed (injected)");
+    }
+    const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(e->mu);
+            if (e->pending == 0) {  // every submitted request has finished
+                if (busy) *busy = 0;
+                return QMPM_OK;
+            }
+        }
+        if (Clock::now() >= deadline) {
+            if (busy) *busy = 1;
+            return efail(QMPM_ERR_TIMEOUT, "qmpm_engine_wait: deadline passed with work remaining");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(500));
+    }
 }
 
 int qmpm_engine_start(qmpm_engine_handle e)

@@ -21,7 +21,9 @@ constexpr int64_t kScratchWords = 4 * kMaxN + kCounts + kPartials;
 __device__ __align__(256) uint32_t g_static_sort_scratch[kScratchWords];
 
 // The host-side name of the array is not a device address; each device's address comes
-// from cudaGetSymbolAddress, looked up once per device with that device current.
+// from cudaGetSymbolAddress, looked up once per device with that device current and kept
+// for the life of the process (a cudaDeviceReset, after which the module may be reloaded
+// elsewhere, is not supported).
 std::mutex g_mutex;
 uint32_t *g_scratch_addr[256] = {nullptr};
 

@@ -149,6 +149,10 @@ inline int64_t resort_launches(int key_bits) { return 14 + 5 * (int64_t)(key_bit
 
 // api.cu: message returned by qmpm_last_error() on this thread
 void set_last_error(const std::string &msg);
+// True if an armed fault of this kind (QMPM_FAULT_*) fires now (qmpm_fault_inject).
+bool fault_hit(int kind);
+// The scene checks of qmpm_init (sets the last error on failure).
+int validate_scene(const qmpm_scene_t *s);
 
 // scheme.cpp
 int layout(int dim, int material, qmpm_scheme_t *scheme, std::string &err);

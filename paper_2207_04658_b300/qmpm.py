@@ -19,7 +19,9 @@ MAX_COMP = 24
 MATERIALS = {"neohookean": 0, "corotated": 1, "fluid": 2}
 FLAG_STATS, FLAG_STRICT, FLAG_PROFILE = 1, 2, 4
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "SCHEME", -4: "CUDA", -5: "TIMEOUT",
-          -6: "OVERFLOW"}
+          -6: "OVERFLOW", -7: "QUEUE_FULL"}
+ERR_INVALID_ARG, ERR_OOM, ERR_SCHEME, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_QUEUE_FULL = -1, -2, -3, -4, -5, -6, -7
+FAULT_DEVICE_ALLOC, FAULT_HOST_ALLOC, FAULT_WAIT = 0, 1, 2
 
 
 class QmpmError(RuntimeError):
@@ -136,7 +138,7 @@ class qmpm_tune_t(ct.Structure):
 
 class qmpm_engine_config_t(ct.Structure):
     _fields_ = [("budget_bytes", ct.c_int64), ("resort_every", ct.c_int32), ("max_active", ct.c_int32),
-                ("flags", ct.c_int32), ("pad", ct.c_int32)]
+                ("flags", ct.c_int32), ("max_queued", ct.c_int32)]
 
 
 class qmpm_request_t(ct.Structure):
@@ -214,6 +216,10 @@ _SIGNATURES = [
     ("qmpm_engine_start", ct.c_int, [ct.c_void_p]),
     ("qmpm_engine_stop", ct.c_int, [ct.c_void_p, ct.c_int32]),
     ("qmpm_engine_run", ct.c_int, [ct.c_void_p, ct.c_int32, _P(ct.c_int32)]),
+    ("qmpm_engine_wait", ct.c_int, [ct.c_void_p, ct.c_double, _P(ct.c_int32)]),
+    ("qmpm_fault_inject", ct.c_int, [ct.c_int32, ct.c_int64, ct.c_int64]),
+    ("qmpm_fault_hits", ct.c_int, [ct.c_int32, _P(ct.c_int64)]),
+    ("qmpm_fault_clear", ct.c_int, []),
     ("qmpm_engine_poll", ct.c_int, [ct.c_void_p, _P(qmpm_request_t), ct.c_int32, _P(ct.c_int32)]),
     ("qmpm_engine_result", ct.c_int, [ct.c_void_p, ct.c_int64, _P(ct.c_double), _P(ct.c_int64)]),
     ("qmpm_engine_release", ct.c_int, [ct.c_void_p, ct.c_int64]),
@@ -422,6 +428,21 @@ def qmpm_tile_order_static(dim, material, scheme_struct, grid_log2, d_words_ptr,
                                         ct.byref(scheme_struct) if scheme_struct is not None else None,
                                         ct.c_void_p(d_words_ptr), int(N), int(ld),
                                         ct.c_void_p(d_order_ptr), ct.c_void_p(stream)))
+
+
+def qmpm_fault_inject(kind, after=0, count=1):
+    """Arm a host-side fault (FAULT_*): `after` occurrences pass, then `count` fail."""
+    _check(lib().qmpm_fault_inject(int(kind), int(after), int(count)))
+
+
+def qmpm_fault_hits(kind):
+    out = ct.c_int64()
+    _check(lib().qmpm_fault_hits(int(kind), ct.byref(out)))
+    return out.value
+
+
+def qmpm_fault_clear():
+    _check(lib().qmpm_fault_clear())
 
 
 def qmpm_footprint(scene_struct, scheme_struct):
@@ -652,12 +673,13 @@ class Batch:
 class Engine:
     """The serving loop (qmpm_engine_*): submit scenes, poll finished requests."""
 
-    def __init__(self, budget_bytes=120 * 2 ** 30, resort_every=8, max_active=64, graphs=True):
+    def __init__(self, budget_bytes=120 * 2 ** 30, resort_every=8, max_active=64, graphs=True, max_queued=0):
         cfg = qmpm_engine_config_t()
         cfg.budget_bytes = int(budget_bytes)
         cfg.resort_every = int(resort_every)
         cfg.max_active = int(max_active)
         cfg.flags = BATCH_GRAPHS if graphs else 0
+        cfg.max_queued = int(max_queued)
         self.h = ct.c_void_p()
         self._borrowed = {}
         _check(lib().qmpm_engine_create(ct.byref(cfg), ct.byref(self.h)))
@@ -685,6 +707,13 @@ class Engine:
     def run(self, iterations=1):
         busy = ct.c_int32()
         _check(lib().qmpm_engine_run(self.h, int(iterations), ct.byref(busy)))
+        return bool(busy.value)
+
+    def wait(self, timeout_s):
+        """Wait (host clock, bounded) until every submitted request has finished; raises
+        QmpmError(QMPM_ERR_TIMEOUT) if the deadline passes first."""
+        busy = ct.c_int32()
+        _check(lib().qmpm_engine_wait(self.h, float(timeout_s), ct.byref(busy)))
         return bool(busy.value)
 
     def poll(self, max_n=256):
