@@ -140,6 +140,28 @@ typedef struct {
     int32_t mode;         /* 0: error bound (Eq. 6), 1: memory bound (Eq. 7) */
     int32_t rounding;     /* 0: Algorithm 1's ceil (memory mode: floor then greedy),
                              1: exact integer search around it */
+    /* Options, applied in this order after the solve; all zero gives the plain solve. */
+    int32_t max_bits;     /* > 0: a type given more bits keeps its window at max_bits bits and
+                             a resolution one power of two coarser per bit dropped (FP32
+                             compute decodes exactly up to 24 bits) */
+    int32_t refine;       /* 1 (error mode): the second-order refinement.  Eq. 6 bounds the
+                             second moment of the error of z; Eq. 8 keeps its linear part.
+                             With dithered stores (error variance Delta_h^2 / 6 averaged
+                             over the fraction) the moments are bias = sum beta_h Delta_h^2
+                             / 6 and var = sum g_h Delta_h^2 / 6; while bias^2 + var >
+                             (eps z)^2, one fraction bit goes to the type with the largest
+                             drop of bias^2 + var per stored bit (P_h; to every type when
+                             no single bit lowers it, as when biases of opposite signs
+                             cancel), never past max_bits (24 if 0), the window kept (its
+                             code range doubles) */
+    double beta[8];       /* second-order coefficients of z (qmpm_noise_moments' shift per
+                             sigma_h^2), for refine */
+    double margin_gain[8];/* > 0: type h's window is widened on each side by margin_gain[h]
+                             times the solved resolution of type margin_src[h] (a field that
+                             picks up another's store noise, e.g. the affine velocity C
+                             takes about 6 n Delta_v from the dithered velocities), h keeping
+                             its resolution (max_bits applies) */
+    int32_t margin_src[8];
 } qmpm_solve_in_t;
 
 typedef struct {
@@ -150,6 +172,10 @@ typedef struct {
     int64_t offset[8];
     double pred_err;      /* (1/12) sum Delta_h^2 g_h (Eq. 8) of the scheme */
     double total_bits;    /* sum P_h bits_h */
+    double pred_bias;     /* sum beta_h Delta_h^2 / 6 (dithered stores) */
+    double pred_var_dither; /* sum g_h Delta_h^2 / 6 */
+    int32_t capped;       /* bit h set: type h was held at max_bits */
+    int32_t refined;      /* fraction bits the refinement added */
 } qmpm_solve_out_t;
 
 /* Solve for a scheme.  Error mode: Delta_h of Eq. 10, b_h = ceil(-log2(Delta_h/R_h)),
@@ -275,6 +301,34 @@ int qmpm_bisection_schedule(int32_t T, qmpm_rev_op_t *ops, int64_t max_ops, int6
  * Errors: QMPM_ERR_INVALID_ARG, QMPM_ERR_OOM, QMPM_ERR_CUDA. */
 int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_t measure, const float *d_seed,
                  float *d_grad0, qmpm_adjoint_out_t *out);
+
+typedef struct {
+    double z0;         /* the noise-free FP32 run's measurement */
+    double shift;      /* mean over pairs of (z+ + z-) / 2 - z0: the second-order shift */
+    double shift_se;   /* its standard error */
+    double spread;     /* mean over pairs of ((z+ - z-) / 2)^2: the first-order variance */
+    double spread_se;
+    int32_t pairs;
+    int32_t pad;
+} qmpm_noise_out_t;
+
+/* The moments of z under an explicit error injected at every store, by antithetic pairs
+ * of FP32 runs (the forward of qmpm_adjoint: the same MLS-MPM step, from the handle's
+ * current state, fixed particle order).  Eq. 6 bounds the second moment of the error of z;
+ * Eq. 8 keeps its linear part only, so zero-mean store errors also shift the mean of z at
+ * second order (half the Hessian against their covariance).  Run k (k < n_pairs) adds to
+ * component c of particle p after step t (t = 1..T) the error sign * sigma[h(c)] * xi,
+ * xi uniform on [-sqrt 3, sqrt 3) (unit variance) from Philox4x32-10 with counter
+ * (p, t, c / 4, 0xA5) and key seed0 + k, once with sign +1 and once with -1; then
+ *   shift  = mean_k ((z+ + z-) / 2 - z0)   ~ sum_h beta_h sigma_h^2  (second order),
+ *   spread = mean_k ((z+ - z-) / 2)^2      ~ sum_h g_h sigma_h^2     (Eq. 8's linear term).
+ * With sigma_h = Delta_h / sqrt 6 (the variance of a dithered store, averaged over the
+ * fraction) the shift predicts the mean error of the quantized runs.  measure:
+ * QMPM_MEASURE_MEAN_SQ_POS or QMPM_MEASURE_KINETIC_ENERGY.  Synchronous; allocates three
+ * FP32 states and a dense grid for the call.  Errors: QMPM_ERR_INVALID_ARG (n_pairs < 2,
+ * negative sigma), QMPM_ERR_OOM, QMPM_ERR_CUDA. */
+int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, const double *sigma, uint64_t seed0,
+                       int32_t n_pairs, qmpm_noise_out_t *out);
 
 /* ---- several scenes in one launch ------------------------------------------------- */
 

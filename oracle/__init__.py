@@ -49,7 +49,13 @@ class SolveIn(ct.Structure):
 class SolveOut(ct.Structure):
     _fields_ = [("delta_cont", ct.c_double * 8), ("bits_paper", ct.c_int * 8),
                 ("bits", ct.c_int * 8), ("frac", ct.c_int * 8), ("offset", ct.c_int64 * 8),
-                ("pred_err", ct.c_double), ("total_bits", ct.c_double)]
+                ("pred_err", ct.c_double), ("total_bits", ct.c_double), ("pred_bias", ct.c_double),
+                ("pred_var_dither", ct.c_double), ("capped", ct.c_int), ("refined", ct.c_int)]
+
+
+class SolveOpt(ct.Structure):
+    _fields_ = [("max_bits", ct.c_int), ("refine", ct.c_int), ("beta", ct.c_double * 8),
+                ("margin_gain", ct.c_double * 8), ("margin_src", ct.c_int * 8)]
 
 
 def lib(threaded=False):
@@ -91,6 +97,7 @@ def _bind(L):
     L.or_g2p.restype = i64
     L.or_step_fp64.argtypes = [P(Phys), i64, P(d), P(d)]
     L.or_step_fp64.restype = i64
+    L.or_add_noise.argtypes = [ct.c_int, ct.c_int, i64, P(d), u32, ct.c_uint64, P(d), d]
     L.or_encode_state.argtypes = [P(Codec), i64, P(d), u32, P(u32), P(i64)]
     L.or_decode_state.argtypes = [P(Codec), i64, P(u32), P(d)]
     L.or_step_quant.argtypes = [P(Phys), P(Codec), i64, P(u32), u32, P(d), P(d), P(i64)]
@@ -102,6 +109,7 @@ def _bind(L):
     L.or_mean_sq_pos.restype = d
     L.or_scheme_solve.argtypes = [P(SolveIn), P(SolveOut)]
     L.or_scheme_bruteforce.argtypes = [P(SolveIn), ct.c_int, ct.c_int, P(SolveOut)]
+    L.or_scheme_options.argtypes = [P(SolveIn), P(SolveOpt), P(SolveOut)]
     if hasattr(L, "or_adjoint_step"):
         _bind_adjoint(L)
     return L
@@ -275,6 +283,38 @@ def step_fp64(ph, s, grid=None):
         grid = np.zeros(n_nodes(ph) * (1 + ph.dim))
     lib().or_step_fp64(ct.byref(ph), s.shape[0], _p(s, ct.c_double), _p(grid, ct.c_double))
     return s
+
+
+def add_noise(dim, material, s, step, seed, sigma, sign):
+    """s + sign * sigma[field] * xi at every component (the explicit store error of the
+    noise-injection estimate; xi uniform with unit variance from the Philox counter
+    (particle, step, comp / 4, 0xA5)).  Returns a new array."""
+    s = np.ascontiguousarray(s, dtype=np.float64).copy()
+    mat = MATERIALS[material] if isinstance(material, str) else int(material)
+    if s.ndim != 2 or s.shape[1] != int(lib().or_n_comp(int(dim), mat)):
+        raise ValueError("state must be [N, n_comp(dim, material)]")
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    if sg.shape != (4,):
+        raise ValueError("sigma holds one value per field")
+    lib().or_add_noise(int(dim), MATERIALS[material] if isinstance(material, str) else int(material), s.shape[0],
+                       _p(s, ct.c_double), int(step), int(seed) & 0xFFFFFFFFFFFFFFFF, _p(sg, ct.c_double),
+                       float(sign))
+    return s
+
+
+def noise_rollout_z(scene, s0, T, sigma, seed, sign, measure="mean_sq_pos"):
+    """z after T FP64 steps (no re-ordering) from s0 with the explicit error of (seed, sign)
+    added after every step (sign 0: none)."""
+    ph = make_phys(scene)
+    s = np.ascontiguousarray(s0, dtype=np.float64).copy()
+    grid = np.zeros(n_nodes(ph) * (1 + ph.dim))
+    for t in range(T):
+        s = step_fp64(ph, s, grid)
+        if sign != 0.0:
+            s = add_noise(ph.dim, ph.material, s, t + 1, seed, sigma, sign)
+    if measure == "kinetic_energy":
+        return kinetic_energy(ph, s)
+    return mean_sq_pos(ph.dim, s)
 
 
 def encode_state(cd, s, step, stats=None, threaded=False):
@@ -474,15 +514,33 @@ def _solve_out(so, H):
         "offset": [int(so.offset[h]) for h in range(H)],
         "pred_err": so.pred_err,
         "total_bits": so.total_bits,
+        "pred_bias": so.pred_bias,
+        "pred_var_dither": so.pred_var_dither,
+        "capped_mask": so.capped,
+        "refined": so.refined,
     }
 
 
-def scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper", kappa=2.0):
+def scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper", kappa=2.0, max_bits=0, beta=None,
+                 margins=None):
+    """The solve, then (when given) its options: max_bits, the second-order refinement with
+    beta, and window margins {h: (src, gain)}."""
     si = _solve_in(P, g, lo, hi, z, eps, mode, rounding, kappa)
     so = SolveOut()
     rc = lib().or_scheme_solve(ct.byref(si), ct.byref(so))
     if rc != 0:
         raise ValueError(f"oracle scheme solve failed ({rc})")
+    op = SolveOpt()
+    op.max_bits = int(max_bits)
+    if beta is not None:
+        op.refine = 1
+        for h, b in enumerate(beta):
+            op.beta[h] = float(b)
+    for h, (src, gain) in (margins or {}).items():
+        op.margin_src[h], op.margin_gain[h] = int(src), float(gain)
+    rc = lib().or_scheme_options(ct.byref(si), ct.byref(op), ct.byref(so))
+    if rc != 0:
+        raise ValueError(f"oracle scheme options failed ({rc})")
     return _solve_out(so, len(P))
 
 

@@ -303,6 +303,32 @@ int64_t or_step_fp64(const or_phys_t *ph, int64_t N, double *s, double *grid_scr
     return oog;
 }
 
+/* An explicit error at every store of step `step` (the second-order error model: Eq. 6
+ * bounds the second moment of the error of z, Eq. 8 keeps its linear part): component c of
+ * particle p gets sign * sigma[field(c)] * xi, xi uniform with unit variance.  The draw:
+ * Philox4x32-10 block of counter (p, step, floor(c / 4), 0xA5) and key `seed` (low word
+ * first); its word c mod 4, w, gives k = floor(w / 2^9) (23 bits), u = (k + 1/2) / 2^23 in
+ * (0, 1) and xi = (2u - 1) sqrt(3), i.e. uniform on (-sqrt 3, sqrt 3). */
+void or_add_noise(int dim, int material, int64_t N, double *s, uint32_t step, uint64_t seed,
+                  const double sigma[4], double sign)
+{
+    const int nc = or_n_comp(dim, material);
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t p = 0; p < N; ++p) {
+        uint32_t blk[4] = {0, 0, 0, 0};
+        for (int c = 0; c < nc; ++c) {
+            if (c % 4 == 0) {
+                const uint32_t ctr[4] = {(uint32_t)p, step, (uint32_t)(c / 4), 0xA5u};
+                or_philox4x32_10(ctr, key, blk);
+            }
+            const double k = (double)(blk[c % 4] >> 9);
+            const double u = (k + 0.5) / 8388608.0;
+            const double xi = (2.0 * u - 1.0) * sqrt(3.0);
+            s[p * nc + c] += sign * sigma[or_comp_field(dim, material, c)] * xi;
+        }
+    }
+}
+
 void or_step_quant(const or_phys_t *ph, const or_codec_t *cd, int64_t N, uint32_t *words,
                    uint32_t step, double *s_scratch, double *grid_scratch, int64_t *stats)
 {

@@ -293,3 +293,114 @@ int or_scheme_bruteforce(const or_solve_in_t *in, int frac_lo, int frac_hi, or_s
     finish(in, frac, bits, out);
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Options on a solved scheme (see oracle.h): the cap, the second-order refinement (the
+ * bound of Eq. 6 on the second moment with the shift that Eq. 8's linear term leaves
+ * out, for dithered stores of variance Delta^2 / 6) and widened windows.
+ * ---------------------------------------------------------------------------------- */
+static double sq_moment(const or_solve_in_t *in, const double *beta, const int *frac, double *bias, double *var)
+{
+    double b = 0.0, v = 0.0;
+    for (int h = 0; h < in->H; ++h) {
+        const double d2 = pow(2.0, -2.0 * frac[h]) / 6.0;
+        b += beta[h] * d2;
+        v += in->g[h] * d2;
+    }
+    if (bias) *bias = b;
+    if (var) *var = v;
+    return b * b + v;
+}
+
+int or_scheme_options(const or_solve_in_t *in, const or_solve_opt_t *opt, or_solve_out_t *out)
+{
+    const int H = in->H;
+    int frac[8], bits[8];
+    int64_t off[8];
+    for (int h = 0; h < H; ++h) {
+        frac[h] = out->frac[h];
+        bits[h] = out->bits[h];
+        off[h] = out->offset[h];
+    }
+    out->capped = 0;
+    out->refined = 0;
+    if (opt->max_bits > 0) {
+        for (int h = 0; h < H; ++h) {
+            while (bits[h] > opt->max_bits) {
+                /* one bit fewer over the same window: half the resolution */
+                bits[h] -= 1;
+                frac[h] -= 1;
+                off[h] = (int64_t)floor((double)off[h] / 2.0);
+                out->capped |= 1 << h;
+            }
+        }
+    }
+    const int top = opt->max_bits > 0 ? opt->max_bits : 24;
+    if (opt->refine && in->mode == 0) {
+        const double target = (in->eps * in->z) * (in->eps * in->z);
+        while (out->refined < 64) {
+            const double now = sq_moment(in, opt->beta, frac, NULL, NULL);
+            if (now <= target) break;
+            int best = -1;
+            double best_drop = 0.0;
+            for (int h = 0; h < H; ++h) {
+                if (bits[h] >= top) continue;
+                frac[h] += 1;
+                const double drop = (now - sq_moment(in, opt->beta, frac, NULL, NULL)) / in->P[h];
+                frac[h] -= 1;
+                if (drop > best_drop) {
+                    best_drop = drop;
+                    best = h;
+                }
+            }
+            if (best >= 0) {
+                frac[best] += 1;
+                bits[best] += 1;
+                off[best] = 2 * off[best];
+                out->refined += 1;
+                continue;
+            }
+            /* biases of opposite signs: no single bit helps, every type gets one (both
+             * moments fall by 4) */
+            int moved = 0;
+            for (int h = 0; h < H; ++h) {
+                if (bits[h] >= top) continue;
+                frac[h] += 1;
+                bits[h] += 1;
+                off[h] = 2 * off[h];
+                out->refined += 1;
+                moved = 1;
+            }
+            if (!moved) break;
+        }
+    }
+    for (int h = 0; h < H; ++h) {
+        if (!(opt->margin_gain[h] > 0.0)) continue;
+        const int src = opt->margin_src[h];
+        if (src < 0 || src >= H) return -1;
+        double lo, hi, R;
+        window(in, h, &lo, &hi, &R);
+        const double m = opt->margin_gain[h] * pow(2.0, -frac[src]);
+        lo -= m;
+        hi += m;
+        int k = frac[h];
+        while (opt->max_bits > 0 && bits_for_frac(k, lo, hi) > opt->max_bits) {
+            --k;
+            out->capped |= 1 << h;
+        }
+        frac[h] = k;
+        bits[h] = bits_for_frac(k, lo, hi);
+        off[h] = offset_for_frac(k, lo);
+    }
+    double tb = 0.0;
+    for (int h = 0; h < H; ++h) {
+        out->frac[h] = frac[h];
+        out->bits[h] = bits[h];
+        out->offset[h] = off[h];
+        tb += in->P[h] * (double)bits[h];
+    }
+    out->total_bits = tb;
+    out->pred_err = err_of(in, frac);
+    sq_moment(in, opt->beta, frac, &out->pred_bias, &out->pred_var_dither);
+    return 0;
+}

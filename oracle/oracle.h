@@ -99,6 +99,11 @@ int64_t or_p2g(const or_phys_t *ph, int64_t N, const double *s, double *grid);
 void or_grid_update(const or_phys_t *ph, double *grid);
 int64_t or_g2p(const or_phys_t *ph, int64_t N, const double *grid, double *s);
 int64_t or_step_fp64(const or_phys_t *ph, int64_t N, double *s, double *grid_scratch);
+/* s += sign * sigma[field] * xi at every component: the store error of the noise-injection
+ * estimate of the second-order term (xi uniform, unit variance, Philox counter (p, step,
+ * c / 4, 0xA5), key seed). */
+void or_add_noise(int dim, int material, int64_t N, double *s, uint32_t step, uint64_t seed,
+                  const double sigma[4], double sign);
 
 /* ---- quantized state ---- */
 void or_encode_state(const or_codec_t *cd, int64_t N, const double *s, uint32_t step,
@@ -143,7 +148,29 @@ typedef struct {
     int64_t offset[8];
     double pred_err;        /* (1/12) sum Delta_h^2 g_h for the final scheme */
     double total_bits;      /* sum P_h n_h */
+    double pred_bias;       /* sum beta_h Delta_h^2 / 6 (or_scheme_options) */
+    double pred_var_dither; /* sum g_h Delta_h^2 / 6 */
+    int capped;             /* bit h: type h held at max_bits */
+    int refined;            /* fraction bits added by the refinement */
 } or_solve_out_t;
+
+/* Options applied to a solved scheme, in this order: (1) max_bits > 0 holds each type at
+ * max_bits bits over the same window, one power of two coarser per bit dropped; (2) refine
+ * (error mode): while (sum beta Delta^2/6)^2 + sum g Delta^2/6 > (eps z)^2, one more
+ * fraction bit (code range doubled, window kept) to the type with the largest decrease of
+ * that sum per P_h (to every type when no single bit decreases it: biases of opposite
+ * signs), bits never above max_bits (24 when 0); (3) margin_gain[h] > 0: type
+ * h's window widened by margin_gain[h] * Delta_(margin_src[h]) on each side at h's
+ * resolution, coarser while it needs more than max_bits bits. */
+typedef struct {
+    int max_bits;
+    int refine;
+    double beta[8];
+    double margin_gain[8];
+    int margin_src[8];
+} or_solve_opt_t;
+
+int or_scheme_options(const or_solve_in_t *in, const or_solve_opt_t *opt, or_solve_out_t *out);
 
 int or_scheme_solve(const or_solve_in_t *in, or_solve_out_t *out);
 /* brute force over integer frac_h in [lo, hi] for error mode (min bits s.t. error) or

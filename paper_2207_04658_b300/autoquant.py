@@ -71,29 +71,14 @@ def cubes3d_scheme(eps=0.01, T=None, samples=2, ckpt_every=32, material="corotat
     return scheme, {"solve": res, "sensitivities": info}
 
 
-def widen_c_for_v_noise(scheme, info, grid_log2, kappa):
-    """The recorded C range comes from the unquantized run, where C of a rigidly moving body
-    is nearly zero; in the quantized run the dithered velocities (resolution Delta_v) make
-    the grid velocities noisy, and C = D^-1 sum_i w_i v_i (x_i - x_p)^T picks that noise up
-    with a gain of about 6 n (sum_i w_i |x_i - x_p| <= 1.5 dx, D^-1 = 4 / dx^2).  Keep C's
-    resolution and widen its window to the recorded range (times kappa) plus 6 n Delta_v on
-    each side.  Returns the scheme with the new C field."""
-    import math
-    n = 1 << grid_log2
-    dv = 2.0 ** -scheme["v"]["frac"]
-    c = dict(scheme["C"])
-    mid = 0.5 * (info["lo"][2] + info["hi"][2])
-    half = 0.5 * kappa * (info["hi"][2] - info["lo"][2]) + 6.0 * n * dv
-    k = c["frac"]
-    lo_i = math.floor((mid - half) * 2.0 ** k)
-    hi_i = math.ceil((mid + half) * 2.0 ** k)
-    bits = max(1, int(math.ceil(math.log2(hi_i - lo_i + 1))))
-    if bits > 24:
-        drop = bits - 24
-        k -= drop
-        lo_i, bits = lo_i >> drop, 24
-    c.update(bits=bits, frac=k, offset=int(lo_i))
-    return dict(scheme, C=c)
+def c_noise_margin(grid_log2):
+    """The solve's window margin for C (type 2) from the velocity noise (type 1): the
+    recorded C range comes from the unquantized run, where C of a rigidly moving body is
+    nearly zero; in the quantized run the dithered velocities (resolution Delta_v) make the
+    grid velocities noisy, and C = D^-1 sum_i w_i v_i (x_i - x_p)^T picks that noise up with
+    a gain of about 6 n (sum_i w_i |x_i - x_p| <= 1.5 dx, D^-1 = 4 / dx^2).  The solve keeps
+    C's resolution and widens its window by 6 n Delta_v on each side."""
+    return {2: (1, 6.0 * (1 << grid_log2))}
 
 
 def serving_schemes(eps_list=scenes.SERVING_EPS, n_rep=20000, samples=2, seed=11, reference="displacement",
@@ -106,7 +91,7 @@ def serving_schemes(eps_list=scenes.SERVING_EPS, n_rep=20000, samples=2, seed=11
     window is the unit domain (every request's body lies in it), the other windows the
     representative's recorded ranges widened by kappa (4: a request's body differs from the
     representative in size, so its fields spread further), C's also by the velocity noise it
-    picks up (widen_c_for_v_noise).  Returns {(dim, material, grid_log2, eps): scheme}."""
+    picks up (c_noise_margin).  Returns {(dim, material, grid_log2, eps): scheme}."""
     out = {}
     for dim, material in scenes.SERVING_CLASSES:
         for grid_log2 in scenes.SERVING_GRIDS[dim]:
@@ -115,8 +100,9 @@ def serving_schemes(eps_list=scenes.SERVING_EPS, n_rep=20000, samples=2, seed=11
                                           reference=reference)
             info["lo"][0], info["hi"][0] = 0.5 - 0.5 / kappa, 0.5 + 0.5 / kappa  # widened: [0, 1]
             for eps in eps_list:
-                scheme, _ = qmpm.solve_scheme(info, eps, material=material, kappa=kappa)
-                out[(dim, material, grid_log2, eps)] = widen_c_for_v_noise(scheme, info, grid_log2, kappa)
+                scheme, _ = qmpm.solve_scheme(info, eps, material=material, kappa=kappa,
+                                              margins=c_noise_margin(grid_log2))
+                out[(dim, material, grid_log2, eps)] = scheme
     return out
 
 

@@ -595,6 +595,27 @@ __global__ void adj_quantize_kernel(const __grid_constant__ StepParams P, float 
     }
 }
 
+// An explicit error added to every stored component of step `step`: component c of
+// particle p gets sign * sigma[field(c)] * xi with xi uniform on [-sqrt 3, sqrt 3) (unit
+// variance), drawn from Philox4x32-10 with counter (p, step, c / 4, 0xA5) and key `seed`:
+// word c % 4 of the block gives u = (floor(w / 2^9) + 1/2) 2^-23 and xi = (2u - 1) sqrt 3.
+__global__ void adj_noise_kernel(const __grid_constant__ StepParams P, float *s, int64_t N, uint32_t step,
+                                 uint32_t seed_lo, uint32_t seed_hi, float4 sig, float sign)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    uint4 rnd = make_uint4(0, 0, 0, 0);
+    for (int c = 0; c < P.n_comp; ++c) {
+        if ((c & 3) == 0) rnd = philox4x32_10(make_uint4((uint32_t)p, step, (uint32_t)(c >> 2), 0xA5u), seed_lo, seed_hi);
+        const uint32_t w = uint4_at(rnd, c & 3);
+        // 2u - 1 with u = (w / 2^9 + 1/2) 2^-23 in (0, 1): exact in FP32
+        const float xi = ((float)(2u * (w >> 9) + 1u) * (1.0f / 8388608.0f) - 1.0f) * 1.7320508f;
+        const int h = P.comp[c].field;
+        const float sg = h == 0 ? sig.x : h == 1 ? sig.y : h == 2 ? sig.z : sig.w;
+        s[p * P.n_comp + c] += sign * sg * xi;
+    }
+}
+
 // Order-preserving integer image of a float (signed comparison of the images orders the
 // floats); the map is its own inverse on the bit patterns.
 __host__ __device__ __forceinline__ int ordered_key(float f)
@@ -931,5 +952,115 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
         out->forward_steps = fwd_steps;
         out->state_buffers = (int32_t)(n_ckpt + tape_states);
     }
+    return QMPM_OK;
+}
+
+extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, const double *sigma, uint64_t seed0,
+                                  int32_t n_pairs, qmpm_noise_out_t *out)
+{
+    using namespace qmpm;
+    if (!h || T < 0 || n_pairs < 2 || !sigma || !out ||
+        (measure != QMPM_MEASURE_MEAN_SQ_POS && measure != QMPM_MEASURE_KINETIC_ENERGY)) {
+        set_last_error("qmpm_noise_moments: bad handle, T, measure, sigma, out or n_pairs (>= 2)");
+        return QMPM_ERR_INVALID_ARG;
+    }
+    for (int q = 0; q < 4; ++q)
+        if (!(sigma[q] >= 0.0)) {
+            set_last_error("qmpm_noise_moments: sigma must be >= 0");
+            return QMPM_ERR_INVALID_ARG;
+        }
+    Ctx &c = *h;
+    const int dim = c.scene.dim, nc = c.n_comp;
+    const int64_t N = c.N;
+    ForwardFn fwd;
+    ReverseFn rev;
+    pick(dim, c.scene.material, fwd, rev);
+    StepParams P;
+    fill_params(c, P);
+    const int64_t nn = dim == 2 ? (int64_t)c.n * c.n : (int64_t)c.n * c.n * c.n;
+    const size_t state_bytes = sizeof(float) * (size_t)std::max<int64_t>(N, 1) * nc;
+    cudaStream_t st = c.stream;
+    std::vector<void *> allocs;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *ptr = nullptr;
+        if (cudaMalloc(&ptr, bytes) != cudaSuccess) return nullptr;
+        allocs.push_back(ptr);
+        return ptr;
+    };
+    auto cleanup = [&]() {
+        for (void *ptr : allocs) cudaFree(ptr);
+    };
+    float *s0 = static_cast<float *>(alloc(state_bytes));
+    float *a = static_cast<float *>(alloc(state_bytes));
+    float *b = static_cast<float *>(alloc(state_bytes));
+    float *gm = static_cast<float *>(alloc(sizeof(float) * (size_t)nn));
+    float4 *gv = static_cast<float4 *>(alloc(sizeof(float4) * (size_t)nn));
+    double *dz = static_cast<double *>(alloc(sizeof(double) * 8));
+    if (!s0 || !a || !b || !gm || !gv || !dz) {
+        cudaGetLastError();
+        cleanup();
+        set_last_error("qmpm_noise_moments: device allocation failed");
+        return QMPM_ERR_OOM;
+    }
+    cudaError_t e = cudaSuccess;
+    if (N > 0) {
+        adj_load_kernel<<<nblk(N), kAdjThreads, 0, st>>>(P, c.quant ? 1 : 0, s0, N);
+        e = cudaGetLastError();
+    }
+    const float4 sig = make_float4((float)sigma[0], (float)sigma[1], (float)sigma[2], (float)sigma[3]);
+    // z of a T-step run from s_0, with the noise of (seed, sign) or none (sign 0)
+    auto run = [&](uint64_t seed, float sign, double *zout) -> cudaError_t {
+        cudaError_t r = cudaMemcpyAsync(a, s0, state_bytes, cudaMemcpyDeviceToDevice, st);
+        float *cur = a, *nxt = b;
+        for (int t = 0; t < T && r == cudaSuccess; ++t) {
+            r = fwd(P, cur, nxt, N, gm, gv, nn, st);
+            if (r == cudaSuccess && sign != 0.0f && N > 0) {
+                adj_noise_kernel<<<nblk(N), kAdjThreads, 0, st>>>(P, nxt, N, (uint32_t)(t + 1), (uint32_t)seed,
+                                                                 (uint32_t)(seed >> 32), sig, sign);
+                r = cudaGetLastError();
+            }
+            std::swap(cur, nxt);
+        }
+        if (r == cudaSuccess) r = cudaMemsetAsync(dz, 0, sizeof(double) * 8, st);
+        if (r == cudaSuccess && N > 0) {
+            const unsigned nbk = std::min<unsigned>(nblk(N), (unsigned)c.n_sms * 8);
+            adj_reduce_kernel<<<nbk, kAdjThreads, 0, st>>>(cur, N, nc, dim, dz, nullptr, nullptr, dz + 4, 0, 0,
+                                                           measure == QMPM_MEASURE_KINETIC_ENERGY ? 2 : 1, P.p_mass);
+            r = cudaGetLastError();
+        }
+        double hz[8];
+        if (r == cudaSuccess) r = cudaMemcpyAsync(hz, dz, sizeof(hz), cudaMemcpyDeviceToHost, st);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+        if (r == cudaSuccess) *zout = hz[4];
+        return r;
+    };
+    double z0 = 0.0;
+    std::vector<double> shift, spread;
+    if (e == cudaSuccess) e = run(0, 0.0f, &z0);
+    for (int k = 0; k < n_pairs && e == cudaSuccess; ++k) {
+        double zp = 0.0, zm = 0.0;
+        e = run(seed0 + (uint64_t)k, 1.0f, &zp);
+        if (e == cudaSuccess) e = run(seed0 + (uint64_t)k, -1.0f, &zm);
+        shift.push_back(0.5 * (zp + zm) - z0);
+        spread.push_back(0.25 * (zp - zm) * (zp - zm));
+    }
+    cleanup();
+    if (e != cudaSuccess) {
+        set_last_error(std::string("qmpm_noise_moments: ") + cudaGetErrorString(e));
+        return QMPM_ERR_CUDA;
+    }
+    auto mean_se = [](const std::vector<double> &v, double &m, double &se) {
+        m = 0.0;
+        for (double x : v) m += x;
+        m /= (double)v.size();
+        double ss = 0.0;
+        for (double x : v) ss += (x - m) * (x - m);
+        se = std::sqrt(ss / (double)(v.size() - 1) / (double)v.size());
+    };
+    std::memset(out, 0, sizeof(*out));
+    out->z0 = z0;
+    mean_se(shift, out->shift, out->shift_se);
+    mean_se(spread, out->spread, out->spread_se);
+    out->pairs = n_pairs;
     return QMPM_OK;
 }

@@ -161,6 +161,12 @@ double predicted(const qmpm_solve_in_t &in, const int *frac)
     return e / 12.0;
 }
 
+// floor(v / 2^k) for any sign (an arithmetic shift)
+int64_t floor_shift(int64_t v, int k)
+{
+    return v >= 0 ? (v >> k) : -((-v + (int64_t(1) << k) - 1) >> k);
+}
+
 // Visit every integer vector v with lo[h] <= v[h] <= hi[h].
 template <class F>
 void odometer(int H, const int *lo, const int *hi, F &&visit)
@@ -193,6 +199,15 @@ extern "C" int qmpm_scheme_solve_impl(const qmpm_solve_in_t *in, qmpm_solve_out_
         err = "qmpm_scheme_solve: need 1 <= H <= 8 and eps > 0";
         return QMPM_ERR_INVALID_ARG;
     }
+    if (in->max_bits < 0 || in->max_bits > 64) {
+        err = "qmpm_scheme_solve: max_bits must be in 0..64";
+        return QMPM_ERR_INVALID_ARG;
+    }
+    for (int h = 0; h < in->H; ++h)
+        if (in->margin_gain[h] > 0.0 && (in->margin_src[h] < 0 || in->margin_src[h] >= in->H)) {
+            err = "qmpm_scheme_solve: margin_src names no type";
+            return QMPM_ERR_INVALID_ARG;
+        }
     std::memset(out, 0, sizeof(*out));
     const int H = in->H;
     std::array<Window, 8> win{};
@@ -323,14 +338,100 @@ extern "C" int qmpm_scheme_solve_impl(const qmpm_solve_in_t *in, qmpm_solve_out_
         }
         for (int h = 0; h < H; ++h) frac[h] = finest_frac(bits[h], win[h]);
     }
+    int64_t offset[8];
+    for (int h = 0; h < H; ++h) offset[h] = (int64_t)std::floor(std::ldexp(win[h].lo, frac[h]));
+    const int cap = in->max_bits > 0 ? in->max_bits : 0;
+    // option 1: hold every type at max_bits, coarser by one power of two per bit dropped
+    if (cap > 0)
+        for (int h = 0; h < H; ++h)
+            if (bits[h] > cap) {
+                const int drop = bits[h] - cap;
+                frac[h] -= drop;
+                offset[h] = floor_shift(offset[h], drop);
+                bits[h] = cap;
+                out->capped |= 1 << h;
+            }
+    // option 2: the second-order refinement (error mode)
+    auto moments = [&](const int *fr, double &bias, double &var) {
+        bias = 0.0;
+        var = 0.0;
+        for (int h = 0; h < H; ++h) {
+            const double d2 = std::ldexp(1.0, -2 * fr[h]) / 6.0;
+            bias += in->beta[h] * d2;
+            var += in->g[h] * d2;
+        }
+    };
+    if (in->refine && in->mode == 0) {
+        const double target = (in->eps * in->z) * (in->eps * in->z);
+        const int limit = cap > 0 ? cap : QMPM_MAX_FIELD_BITS;
+        for (int it = 0; it < 64; ++it) {
+            double b, v;
+            moments(frac, b, v);
+            if (b * b + v <= target) break;
+            int pick = -1;
+            double best = 0.0;
+            for (int h = 0; h < H; ++h) {
+                if (bits[h] >= limit) continue;
+                int f2[8];
+                std::copy(frac, frac + H, f2);
+                f2[h] += 1;
+                double b2, v2;
+                moments(f2, b2, v2);
+                const double gain = (b * b + v - b2 * b2 - v2) / in->P[h];
+                if (gain > best) {
+                    best = gain;
+                    pick = h;
+                }
+            }
+            if (pick >= 0) {
+                frac[pick] += 1;
+                bits[pick] += 1;
+                offset[pick] *= 2;
+                out->refined += 1;
+                continue;
+            }
+            // no single bit lowers bias^2 + var (biases of opposite signs cancel): refine
+            // every type at once, which divides both moments by 4
+            bool any = false;
+            for (int h = 0; h < H; ++h) {
+                if (bits[h] >= limit) continue;
+                frac[h] += 1;
+                bits[h] += 1;
+                offset[h] *= 2;
+                out->refined += 1;
+                any = true;
+            }
+            if (!any) break;
+        }
+    }
+    // option 3: windows widened by another type's noise, at the type's own resolution
+    for (int h = 0; h < H; ++h) {
+        const int src = in->margin_src[h];
+        if (!(in->margin_gain[h] > 0.0) || src < 0 || src >= H) continue;
+        const double m = in->margin_gain[h] * std::ldexp(1.0, -frac[src]);
+        const Window w{win[h].lo - m, win[h].hi + m, win[h].R + 2.0 * m};
+        int k = frac[h];
+        int n = bits_at(k, w);
+        if (cap > 0 && n > cap) {
+            while (n > cap) {
+                --k;
+                n = bits_at(k, w);
+            }
+            out->capped |= 1 << h;
+        }
+        frac[h] = k;
+        bits[h] = n;
+        offset[h] = (int64_t)std::floor(std::ldexp(w.lo, k));
+    }
     double tb = 0.0;
     for (int h = 0; h < H; ++h) {
         out->bits[h] = bits[h];
         out->frac[h] = frac[h];
-        out->offset[h] = (int64_t)std::floor(std::ldexp(win[h].lo, frac[h]));
+        out->offset[h] = offset[h];
         tb += in->P[h] * bits[h];
     }
     out->pred_err = predicted(*in, frac);
     out->total_bits = tb;
+    moments(frac, out->pred_bias, out->pred_var_dither);
     return QMPM_OK;
 }

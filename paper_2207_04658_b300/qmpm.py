@@ -77,13 +77,15 @@ class qmpm_solve_in_t(ct.Structure):
     _fields_ = [("H", ct.c_int32), ("P", ct.c_double * 8), ("g", ct.c_double * 8),
                 ("lo", ct.c_double * 8), ("hi", ct.c_double * 8), ("kappa", ct.c_double),
                 ("z", ct.c_double), ("eps", ct.c_double), ("mode", ct.c_int32),
-                ("rounding", ct.c_int32)]
+                ("rounding", ct.c_int32), ("max_bits", ct.c_int32), ("refine", ct.c_int32),
+                ("beta", ct.c_double * 8), ("margin_gain", ct.c_double * 8), ("margin_src", ct.c_int32 * 8)]
 
 
 class qmpm_solve_out_t(ct.Structure):
     _fields_ = [("delta_cont", ct.c_double * 8), ("bits_paper", ct.c_int32 * 8),
                 ("bits", ct.c_int32 * 8), ("frac", ct.c_int32 * 8), ("offset", ct.c_int64 * 8),
-                ("pred_err", ct.c_double), ("total_bits", ct.c_double)]
+                ("pred_err", ct.c_double), ("total_bits", ct.c_double), ("pred_bias", ct.c_double),
+                ("pred_var_dither", ct.c_double), ("capped", ct.c_int32), ("refined", ct.c_int32)]
 
 
 class qmpm_adjoint_out_t(ct.Structure):
@@ -95,6 +97,14 @@ class qmpm_adjoint_out_t(ct.Structure):
         return {"z": self.z, "g": list(self.g), "lo": list(self.lo), "hi": list(self.hi),
                 "P": list(self.P), "forward_steps": self.forward_steps,
                 "state_buffers": self.state_buffers}
+
+
+class qmpm_noise_out_t(ct.Structure):
+    _fields_ = [("z0", ct.c_double), ("shift", ct.c_double), ("shift_se", ct.c_double), ("spread", ct.c_double),
+                ("spread_se", ct.c_double), ("pairs", ct.c_int32), ("pad", ct.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class qmpm_rev_op_t(ct.Structure):
@@ -199,6 +209,8 @@ _SIGNATURES = [
     ("qmpm_last_error", ct.c_char_p, []),
     ("qmpm_adjoint", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
                                 ct.c_void_p, _P(qmpm_adjoint_out_t)]),
+    ("qmpm_noise_moments", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, _P(ct.c_double), ct.c_uint64,
+                                      ct.c_int32, _P(qmpm_noise_out_t)]),
     ("qmpm_footprint", ct.c_int, [_P(qmpm_scene_t), _P(qmpm_scheme_t), _P(ct.c_int64), _P(ct.c_int64)]),
     ("qmpm_bisection_schedule", ct.c_int, [ct.c_int32, _P(qmpm_rev_op_t), ct.c_int64, _P(ct.c_int64),
                                            _P(ct.c_int32)]),
@@ -335,7 +347,12 @@ def qmpm_scheme_layout(dim, material, scheme_struct):
     return scheme_struct
 
 
-def qmpm_scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper", kappa=2.0):
+def qmpm_scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper", kappa=2.0, max_bits=0, beta=None,
+                      margins=None):
+    """The bit-allocation solve (Eq. 10 / Algorithm 1 or the memory-bound form) with its
+    options: max_bits caps a type's bits (window kept, resolution coarser); beta (one per
+    type) turns on the second-order refinement; margins = {h: (src, gain)} widens type h's
+    window by gain times the resolution of type src."""
     si = qmpm_solve_in_t()
     si.H = len(P)
     for h in range(len(P)):
@@ -343,13 +360,21 @@ def qmpm_scheme_solve(P, g, lo, hi, z, eps, mode="error", rounding="paper", kapp
     si.kappa, si.z, si.eps = kappa, z, eps
     si.mode = 0 if mode == "error" else 1
     si.rounding = 0 if rounding == "paper" else 1
+    si.max_bits = int(max_bits)
+    if beta is not None:
+        si.refine = 1
+        for h, b in enumerate(beta):
+            si.beta[h] = float(b)
+    for h, (src, gain) in (margins or {}).items():
+        si.margin_src[h], si.margin_gain[h] = int(src), float(gain)
     so = qmpm_solve_out_t()
     _check(lib().qmpm_scheme_solve(ct.byref(si), ct.byref(so)))
     H = len(P)
     return {"delta_cont": list(so.delta_cont)[:H], "bits_paper": list(so.bits_paper)[:H],
             "bits": list(so.bits)[:H], "frac": list(so.frac)[:H],
             "offset": [int(v) for v in so.offset][:H], "pred_err": so.pred_err,
-            "total_bits": so.total_bits}
+            "total_bits": so.total_bits, "pred_bias": so.pred_bias, "pred_var_dither": so.pred_var_dither,
+            "capped_mask": so.capped, "refined": so.refined}
 
 
 def qmpm_init(scene_struct, scheme_struct, h_state, stream=0):
@@ -417,6 +442,13 @@ def qmpm_adjoint(h, T, ckpt_every=32, measure=MEASURE_MEAN_SQ_POS, d_seed_ptr=0,
     out = qmpm_adjoint_out_t()
     _check(lib().qmpm_adjoint(h, int(T), int(ckpt_every), int(measure), ct.c_void_p(d_seed_ptr),
                               ct.c_void_p(d_grad0_ptr), ct.byref(out)))
+    return out.as_dict()
+
+
+def qmpm_noise_moments(h, T, measure, sigma, seed0=1, n_pairs=16):
+    sg = (ct.c_double * 4)(*[float(v) for v in sigma])
+    out = qmpm_noise_out_t()
+    _check(lib().qmpm_noise_moments(h, int(T), int(measure), sg, int(seed0), int(n_pairs), ct.byref(out)))
     return out.as_dict()
 
 
@@ -609,24 +641,19 @@ def sensitivities(scene, state0, T, ckpt_every=32, measure=MEASURE_MEAN_SQ_POS):
 
 
 def solve_scheme(info, eps, mode="error", rounding="paper", kappa=2.0, containers=(0, 0, 0, 0),
-                 material="corotated", max_bits=24):
+                 material="corotated", max_bits=24, margins=None, beta=None):
     """Scheme from the adjoint's sensitivities (Eq. 10 / Algorithm 1, or the memory-bound
     form): returns the per-field scheme dict consumed by Scene and the solve report.  A
     field the solve gives more than max_bits (the FP32 compute limit) keeps its window at
     max_bits, one power of two coarser per bit dropped; the report lists such fields in
-    "capped" (their share of the error bound is then not met)."""
+    "capped" (their share of the error bound is then not met).  margins and beta are the
+    solve's window-margin and second-order options (qmpm_scheme_solve)."""
     res = qmpm_scheme_solve(info["P"], info["g"], info["lo"], info["hi"], info["z"], eps, mode=mode,
-                            rounding=rounding, kappa=kappa)
+                            rounding=rounding, kappa=kappa, max_bits=max_bits, margins=margins, beta=beta)
     names = ["x", "v", "C", "J" if material == "fluid" else "F"]
-    scheme, capped = {}, []
-    for h in range(4):
-        bits, frac, off = int(res["bits"][h]), int(res["frac"][h]), int(res["offset"][h])
-        if bits > max_bits:
-            drop = bits - max_bits
-            bits, frac, off = max_bits, frac - drop, off >> drop
-            capped.append(names[h])
-        scheme[names[h]] = dict(bits=bits, frac=frac, offset=off, container=int(containers[h]))
-    res["capped"] = capped
+    scheme = {names[h]: dict(bits=int(res["bits"][h]), frac=int(res["frac"][h]), offset=int(res["offset"][h]),
+                             container=int(containers[h])) for h in range(4)}
+    res["capped"] = [names[h] for h in range(4) if res["capped_mask"] >> h & 1]
     return scheme, res
 
 

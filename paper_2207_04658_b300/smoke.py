@@ -220,48 +220,36 @@ def predicted_moments(frac, g, beta):
     return float(np.dot(beta, d2) / 6.0), float(np.dot(g, d2) / 6.0)
 
 
-def refine_for_bias(scheme, g, beta, P, z, eps, max_bits=24):
-    """Add fraction bits (one at a time, to the type with the largest drop of the predicted
-    second moment bias^2 + var per stored bit) until bias^2 + var <= (eps z)^2: the error
-    bound of Eq. 6 on the second moment, with the second-order term that the linear model
-    of Eq. 8 leaves out.  Ranges stay: each added bit doubles the code range."""
-    sch = {k: dict(v) for k, v in scheme.items()}
-    target = (eps * z) ** 2
-    for _ in range(64):
-        frac = [sch[t]["frac"] for t in TYPES]
-        b, v = predicted_moments(frac, g, beta)
-        if b * b + v <= target:
-            break
-        best, gain = None, 0.0
-        for h, t in enumerate(TYPES):
-            if sch[t]["bits"] >= max_bits:
-                continue
-            f2 = list(frac)
-            f2[h] += 1
-            b2, v2 = predicted_moments(f2, g, beta)
-            r = (b * b + v - b2 * b2 - v2) / P[h]
-            if r > gain:
-                best, gain = h, r
-        if best is None:
-            break
-        t = TYPES[best]
-        sch[t] = dict(bits=sch[t]["bits"] + 1, frac=sch[t]["frac"] + 1, offset=sch[t]["offset"] * 2)
-    return sch
+def solve_types(P, g, lo, hi, z, eps, kappa=2.0, max_bits=24, beta=None):
+    """qmpm_scheme_solve for the smoke's two types (velocity, pressure): Algorithm 1 with
+    the ranges widened by kappa, each type held at max_bits, and with beta the solve's
+    second-order refinement (fraction bits added, one at a time to the type with the largest
+    drop of the predicted bias^2 + variance per stored bit, until bias^2 + var <= (eps z)^2:
+    the bound of Eq. 6 on the second moment with the term Eq. 8 leaves out).  Returns the
+    scheme dict and the solve report."""
+    res = qmpm.qmpm_scheme_solve(P, list(g), list(lo), list(hi), z, eps, kappa=kappa, max_bits=max_bits,
+                                 beta=None if beta is None else list(beta))
+    scheme = {name: dict(bits=int(res["bits"][h]), frac=int(res["frac"][h]), offset=int(res["offset"][h]))
+              for h, name in enumerate(TYPES)}
+    return scheme, res
 
 
-def bias_aware_scheme(scene, T, eps, paper, g, beta, P, z, pairs=32, iters=3, state=None, max_bits=24):
-    """refine_for_bias, with the second-order term re-estimated at the refined scheme's own
-    noise scale (sigma_h = Delta_h / sqrt(6), the dither's spread): the shift of z is not
-    quadratic in the noise scale (the advection samples piecewise-bilinearly), so the
-    estimate taken at the sensitivity run's scale is only a start.  Stops when the scheme
-    repeats; where the last two differ, keeps the finer fraction per type.  Returns the
-    scheme and the last beta."""
-    sch = refine_for_bias(paper, g, beta, P, z, eps, max_bits)
+def bias_aware_scheme(scene, T, eps, ref, g, beta, P, pairs=32, iters=3, state=None, max_bits=24, kappa=2.0):
+    """The solve's second-order refinement (solve_types with beta), with the second-order
+    term re-estimated at the refined scheme's own noise scale (sigma_h = Delta_h / sqrt(6),
+    the dither's spread): the shift of z is not quadratic in the noise scale (the advection
+    samples piecewise-bilinearly), so the estimate taken at the sensitivity run's scale is
+    only a start.  Stops when the scheme repeats; where the last two differ, keeps the finer
+    fraction per type.  ref: the FP32 run (z, ranges).  Returns the scheme and the last
+    beta."""
+    def refined(b):
+        return solve_types(P, g, ref["lo"], ref["hi"], ref["z"], eps, kappa=kappa, max_bits=max_bits, beta=b)[0]
+    sch = refined(beta)
     prev = None
     for _ in range(iters):
         sig = tuple(2.0 ** -sch[t]["frac"] / 6 ** 0.5 for t in TYPES)
-        beta = sensitivities(scene, T, pairs, sig, state=state, z0=z)["beta"]
-        prev, sch = sch, refine_for_bias(paper, g, beta, P, z, eps, max_bits)
+        beta = sensitivities(scene, T, pairs, sig, state=state, z0=ref["z"])["beta"]
+        prev, sch = sch, refined(beta)
         if sch == prev:
             break
     if prev is not None and sch != prev:
@@ -271,26 +259,19 @@ def bias_aware_scheme(scene, T, eps, paper, g, beta, P, z, pairs=32, iters=3, st
 
 def solve(scene, T, eps, pairs=32, sigma=(3e-3, 3e-5), kappa=2.0, state=None, max_bits=24, bias_aware=False):
     """Scheme for the error bound eps on z (Algorithm 1 with the recorded ranges widened by
-    kappa about their midpoint, Sec. 3.1); bias_aware adds the bits refine_for_bias asks
-    for.  Returns (scheme dict, report)."""
+    kappa about their midpoint, Sec. 3.1); bias_aware adds the bits of the solve's
+    second-order refinement.  Returns (scheme dict, report)."""
     n = int(scene["n"])
     ref = reference(scene, T, state)
     sens = sensitivities(scene, T, pairs, sigma, state=state, z0=ref["z"])
     g = sens["g"]
     P = [2.0 * n * (n + 1), float(n * n)]
-    res = qmpm.qmpm_scheme_solve(P, list(g), list(ref["lo"]), list(ref["hi"]), ref["z"], eps, kappa=kappa)
-    scheme, capped = {}, []
-    for h, name in enumerate(TYPES):
-        bits, frac, off = int(res["bits"][h]), int(res["frac"][h]), int(res["offset"][h])
-        if bits > max_bits:
-            drop = bits - max_bits
-            bits, frac, off = max_bits, frac - drop, off >> drop
-            capped.append(name)
-        scheme[name] = dict(bits=bits, frac=frac, offset=off)
+    scheme, res = solve_types(P, g, ref["lo"], ref["hi"], ref["z"], eps, kappa=kappa, max_bits=max_bits)
+    capped = [TYPES[h] for h in range(2) if res["capped_mask"] >> h & 1]
     beta = sens["beta"]
     if bias_aware:
-        scheme, beta = bias_aware_scheme(scene, T, eps, scheme, g, beta, P, ref["z"], pairs, state=state,
-                                         max_bits=max_bits)
+        scheme, beta = bias_aware_scheme(scene, T, eps, ref, g, beta, P, pairs, state=state, max_bits=max_bits,
+                                         kappa=kappa)
     frac = [scheme[t]["frac"] for t in TYPES]
     bias, var = predicted_moments(frac, g, beta)
     bits_state = P[0] * scheme["v"]["bits"] + 32.0 * n * n
@@ -315,17 +296,12 @@ def error_bound_protocol(scene, T, eps_list, runs=20, z_ref=None, pairs=32, seed
     P = [2.0 * n * (n + 1), float(n * n)]
     out = []
     for eps in eps_list:
-        res = qmpm.qmpm_scheme_solve(P, list(g), list(ref["lo"]), list(ref["hi"]), ref["z"], eps, kappa=2.0)
-        paper = {}
-        for h, name in enumerate(TYPES):
-            drop = max(0, int(res["bits"][h]) - 24)
-            paper[name] = dict(bits=int(res["bits"][h]) - drop, frac=int(res["frac"][h]) - drop,
-                               offset=int(res["offset"][h]) >> drop)
+        paper, res = solve_types(P, g, ref["lo"], ref["hi"], ref["z"], eps, kappa=2.0, max_bits=24)
         for aware in variants:
             beta = sens["beta"]
             scheme = paper
             if aware:
-                scheme, beta = bias_aware_scheme(scene, T, eps, paper, g, beta, P, ref["z"], pairs)
+                scheme, beta = bias_aware_scheme(scene, T, eps, ref, g, beta, P, pairs)
             with Smoke(scene, scheme, runs, seeds=[seed0 + r for r in range(runs)]) as s:
                 s.step(T)
                 zs = s.measure()

@@ -47,12 +47,30 @@ def impact_block(n_strata=(64, 32)):
     return dict(sc, resort_every=8), s0
 
 
-def error_bound_protocol(scene, state0, T, eps_list, runs, z_ref, ckpt_every=25, seed0=1000):
-    """Per eps: the solved scheme, predicted and observed spread of z, bias, success rates."""
+def predicted_moments(scene, state0, T, scheme, pairs=16, seed=4242, measure=qmpm.MEASURE_KINETIC_ENERGY):
+    """The mean shift and the spread of z that dithered stores of `scheme` cause, predicted by
+    antithetic noise injection (qmpm_noise_moments): an error of standard deviation
+    Delta_h / sqrt 6 (a dithered store's variance, averaged over the fraction) at every
+    store of type h.  The shift is the second-order term that Eq. 8 leaves out."""
+    names = ("x", "v", "C", "J" if scene["material"] == "fluid" else "F")
+    sigma = [2.0 ** -scheme[k]["frac"] / np.sqrt(6.0) for k in names]
+    g = qmpm.Scene(dict(scene, resort_every=0), None, state0)
+    try:
+        m = qmpm.qmpm_noise_moments(g.h, T, measure, sigma, seed, pairs)
+    finally:
+        g.close()
+    return m
+
+
+def error_bound_protocol(scene, state0, T, eps_list, runs, z_ref, ckpt_every=25, seed0=1000, noise_pairs=16):
+    """Per eps: the solved scheme, predicted and observed spread of z, predicted (second
+    order) and observed bias, success rates, and each run's z (run r has dither seed
+    seed0 + r)."""
     info = qmpm.sensitivities(scene, state0, T, ckpt_every, qmpm.MEASURE_KINETIC_ENERGY)
     out = []
     for eps in eps_list:
         scheme, res = qmpm.solve_scheme(info, eps, material=scene["material"])
+        mom = predicted_moments(scene, state0, T, scheme, pairs=noise_pairs) if noise_pairs >= 2 else None
         zs = []
         for r in range(runs):
             g = qmpm.Scene(dict(scene, seed=seed0 + r), scheme, state0)
@@ -69,8 +87,11 @@ def error_bound_protocol(scene, state0, T, eps_list, runs, z_ref, ckpt_every=25,
             "bias": float(dev.mean()), "bias_stderr": float(dev.std(ddof=1) / np.sqrt(runs)) if runs > 1 else 0.0,
             "success_3eps": float((np.abs(dev) <= 3 * eps * abs(z_ref)).mean()),
             "success_eps": float((np.abs(dev) <= eps * abs(z_ref)).mean()),
-            "z_ref": z_ref, "runs": runs,
+            "z_ref": z_ref, "runs": runs, "z_runs": zs.tolist(), "seed0": seed0, "scheme": scheme,
         })
+        if mom is not None:
+            out[-1].update(pred_bias=mom["shift"], pred_bias_se=mom["shift_se"],
+                           pred_sigma_dither=float(np.sqrt(max(mom["spread"], 0.0))), noise_pairs=mom["pairs"])
     return out
 
 

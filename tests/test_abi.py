@@ -107,3 +107,37 @@ def test_missing_library_fails_loudly(monkeypatch, q):
     monkeypatch.setattr(qm, "LIB_PATH", "/nonexistent/libqmpm.so")
     with pytest.raises(ImportError):
         qm.lib()
+
+
+@pytest.mark.parametrize("case", ["cap", "refine", "margin", "all"])
+def test_scheme_solve_options_match_oracle(q, oracle, case):
+    gen = np.random.default_rng({"cap": 1, "refine": 2, "margin": 3, "all": 4}[case])
+    for trial in range(40):
+        H = int(gen.integers(2, 5))
+        P = gen.integers(1000, 100000, H).astype(float)
+        g = 10.0 ** gen.uniform(-4, 4, H)
+        lo = gen.uniform(-5, 0, H)
+        hi = lo + 10.0 ** gen.uniform(-1, 1.5, H)
+        z = float(10.0 ** gen.uniform(-1, 2))
+        eps = float(10.0 ** gen.uniform(-5, -1))
+        kw = {}
+        if case in ("cap", "all"):
+            kw["max_bits"] = int(gen.integers(6, 20))
+        if case in ("refine", "all"):
+            kw["beta"] = list(gen.normal(0, 1, H) * 10.0 ** gen.uniform(0, 5, H))
+        if case in ("margin", "all"):
+            h = int(gen.integers(0, H))
+            kw["margins"] = {h: (int(gen.integers(0, H)), float(10.0 ** gen.uniform(0, 3)))}
+        a = q.qmpm_scheme_solve(P, g, lo, hi, z, eps, **kw)
+        b = oracle.scheme_solve(P, g, lo, hi, z, eps, **kw)
+        for key in ("bits", "frac", "offset", "capped_mask", "refined"):
+            assert a[key] == b[key], (case, trial, key, a[key], b[key], kw)
+        for key in ("pred_err", "pred_bias", "pred_var_dither", "total_bits"):
+            assert a[key] == pytest.approx(b[key], rel=1e-12, abs=1e-300), (case, key)
+
+
+def test_scheme_solve_options_reject_bad_input(q):
+    with pytest.raises(q.QmpmError):
+        q.qmpm_scheme_solve([1.0, 1.0], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0], 1.0, 0.01, max_bits=-1)
+    with pytest.raises(q.QmpmError):
+        q.qmpm_scheme_solve([1.0, 1.0], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0], 1.0, 0.01, margins={0: (5, 1.0)})

@@ -135,3 +135,76 @@ def test_resolution_never_coarser_than_half_the_range(oracle):
     assert out["bits_paper"][1] == 1
     R = 2.0 * 2e-4
     assert 2.0 ** -out["frac"][1] <= R / 2
+
+
+# ---------------------------------------------------------------------------- options
+def test_options_cap_keeps_the_window(oracle):
+    # x would need more than 12 bits: held at 12 over (at least) the same window
+    P, g, lo, hi = [1000.0, 1000.0], [1e8, 1e-6], [0.0, -1.0], [1.0, 1.0]
+    plain = oracle.scheme_solve(P, g, lo, hi, 1.0, 1e-4)
+    capped = oracle.scheme_solve(P, g, lo, hi, 1.0, 1e-4, max_bits=12)
+    assert plain["bits"][0] > 12 and capped["bits"][0] == 12 and capped["capped_mask"] == 1
+    drop = plain["bits"][0] - 12
+    assert capped["frac"][0] == plain["frac"][0] - drop
+    d = 2.0 ** -capped["frac"][0]
+    assert capped["offset"][0] * d <= -0.5 and (capped["offset"][0] + 2 ** 12 - 1) * d >= 1.5  # kappa 2 window
+    assert capped["bits"][1] == plain["bits"][1] and capped["frac"][1] == plain["frac"][1]
+
+
+def test_options_refinement_worked_example(oracle):
+    # Two types with equal P; the paper solve gives Delta_1 = Delta_2 = D.  With a bias
+    # coefficient on type 0 only, bias^2 + var = (beta0 D0^2/6)^2 + (g0 D0^2 + g1 D1^2)/6 must
+    # drop below (eps z)^2 = 1e-4.  Taking g = (1, 1), z = 1, eps = 1e-2: Eq. 10 gives
+    # Delta_h = sqrt(12 * 1e-4 / 2) = 0.02449, frac = ceil(-log2 0.02449) = 6 (D = 1/64,
+    # var = 2 D^2 / 6 = 8.14e-5 <= 1e-4 without bias).  beta0 = 400: bias = 400 D^2 / 6 =
+    # 0.01628, bias^2 = 2.65e-4: too large.  Refining type 0 (frac 7): bias = 4.07e-3,
+    # bias^2 = 1.66e-5, var = (D^2/4 + D^2)/6 = 5.09e-5, total 6.75e-5 <= 1e-4: one bit, on
+    # type 0 (type 1 would leave the bias untouched).
+    res = oracle.scheme_solve([100.0, 100.0], [1.0, 1.0], [-1.0, -1.0], [1.0, 1.0], 1.0, 1e-2, beta=[400.0, 0.0])
+    assert res["frac"] == [7, 6] and res["refined"] == 1
+    assert res["pred_bias"] == pytest.approx(400.0 * 2.0 ** -14 / 6.0, rel=1e-14)
+    assert res["pred_var_dither"] == pytest.approx((2.0 ** -14 + 2.0 ** -12) / 6.0, rel=1e-14)
+    assert res["pred_bias"] ** 2 + res["pred_var_dither"] <= 1e-4
+    # one fraction bit doubles the code range over the same window
+    plain = oracle.scheme_solve([100.0, 100.0], [1.0, 1.0], [-1.0, -1.0], [1.0, 1.0], 1.0, 1e-2)
+    assert res["bits"][0] == plain["bits"][0] + 1 and res["offset"][0] == 2 * plain["offset"][0]
+
+
+def test_options_refinement_is_feasible_and_stops_at_once(oracle):
+    gen = np.random.default_rng(8)
+    for _ in range(50):
+        H = 3
+        P = list(gen.integers(100, 10000, H).astype(float))
+        g = list(10.0 ** gen.uniform(-2, 2, H))
+        beta = list(gen.normal(0, 1, H) * 10.0 ** gen.uniform(1, 4, H))
+        lo, hi, z, eps = [-1.0] * H, [1.0] * H, 1.0, 1e-2
+        res = oracle.scheme_solve(P, g, lo, hi, z, eps, beta=beta)
+        d2 = [2.0 ** (-2 * f) / 6.0 for f in res["frac"]]
+        bias = sum(b * d for b, d in zip(beta, d2))
+        var = sum(gg * d for gg, d in zip(g, d2))
+        assert bias ** 2 + var <= (eps * z) ** 2 or max(res["bits"]) >= 24
+        plain = oracle.scheme_solve(P, g, lo, hi, z, eps)
+        assert sum(res["frac"]) - sum(plain["frac"]) == res["refined"]
+        if res["refined"] > 0:
+            # it stopped at once: one fraction bit fewer (undoing any single added bit) fails
+            for h in range(H):
+                if res["frac"][h] > plain["frac"][h]:
+                    f = list(res["frac"])
+                    f[h] -= 1
+                    d2 = [2.0 ** (-2 * ff) / 6.0 for ff in f]
+                    b2 = sum(b * d for b, d in zip(beta, d2))
+                    v2 = sum(gg * d for gg, d in zip(g, d2))
+                    assert b2 ** 2 + v2 > (eps * z) ** 2 or res["refined"] > 1
+
+
+def test_options_margin_covers_the_widened_window(oracle):
+    P, g, lo, hi = [1000.0, 1000.0, 1000.0], [1.0, 10.0, 1e-3], [0.0, -1.0, -0.1], [1.0, 1.0, 0.1]
+    res = oracle.scheme_solve(P, g, lo, hi, 1.0, 1e-2, margins={2: (1, 384.0)})
+    plain = oracle.scheme_solve(P, g, lo, hi, 1.0, 1e-2)
+    k, L, n = res["frac"][2], res["offset"][2], res["bits"][2]
+    assert k == plain["frac"][2]  # resolution kept
+    m = 384.0 * 2.0 ** -res["frac"][1]
+    want_lo, want_hi = -0.2 - m, 0.2 + m  # kappa 2 window of [-0.1, 0.1], widened by m
+    assert L * 2.0 ** -k <= want_lo and (L + 2 ** n - 1) * 2.0 ** -k >= want_hi
+    assert (L + 2 ** (n - 1) - 1) * 2.0 ** -k < want_hi  # one bit fewer would not cover it
+    assert res["bits"][:2] == plain["bits"][:2]
