@@ -64,7 +64,7 @@ typedef struct {
     double bulk;          /* fluid bulk modulus K */
     double p_vol, p_mass; /* per-particle volume and mass */
     double gravity[3];
-    uint64_t seed;        /* key of the dither hash */
+    uint64_t seed;        /* key of the dither hash (Philox4x32-7, counter (slot, step, comp / 8, 0)) */
     int32_t dither;       /* 1: dithered stores (Sec. 5), 0: round to nearest */
     int32_t resort_every;
     int32_t chunk;        /* particles per CTA work item, 0 = default (256) */
@@ -248,6 +248,7 @@ const char *qmpm_last_error(void);
 #define QMPM_MEASURE_USER 1        /* seed dz/ds_T supplied by the caller (z reported as
                                       the mean square position) */
 #define QMPM_MEASURE_KINETIC_ENERGY 2 /* z = (1/2) m sum |v_T|^2, seed m v_T (Sec. 8.1) */
+#define QMPM_MEASURE_POSITIONS 3   /* the vector of final positions x_T (qmpm_noise_moments) */
 /* OR'ed into `measure`: the adjoint's forward follows the quantized trajectory of the
  * handle's scheme (each step's state goes through the dithered store, Eq. 1), so the
  * gradients and ranges are taken at the quantized solution -- one round of the iterative
@@ -324,9 +325,13 @@ typedef struct {
  *   spread = mean_k ((z+ - z-) / 2)^2      ~ sum_h g_h sigma_h^2     (Eq. 8's linear term).
  * With sigma_h = Delta_h / sqrt 6 (the variance of a dithered store, averaged over the
  * fraction) the shift predicts the mean error of the quantized runs.  measure:
- * QMPM_MEASURE_MEAN_SQ_POS or QMPM_MEASURE_KINETIC_ENERGY.  Synchronous; allocates three
- * FP32 states and a dense grid for the call.  Errors: QMPM_ERR_INVALID_ARG (n_pairs < 2,
- * negative sigma), QMPM_ERR_OOM, QMPM_ERR_CUDA. */
+ * QMPM_MEASURE_MEAN_SQ_POS or QMPM_MEASURE_KINETIC_ENERGY (z a scalar), or
+ * QMPM_MEASURE_POSITIONS (the evaluation is the vector of final positions): then with
+ * m_k = (x+ + x-)/2 - x0 per particle, shift = |b|^2, the squared norm of the bias vector
+ * b = E[m], estimated without the noise of the mean as (K |mean_k m_k|^2 - mean_k |m_k|^2)
+ * / (K - 1), and spread = mean_k sum_p |(x+ - x-)/2|^2; z0 = mean |x_T|^2.  Synchronous;
+ * allocates up to five FP32 states and a dense grid for the call.  Errors:
+ * QMPM_ERR_INVALID_ARG (n_pairs < 2, negative sigma), QMPM_ERR_OOM, QMPM_ERR_CUDA. */
 int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, const double *sigma, uint64_t seed0,
                        int32_t n_pairs, qmpm_noise_out_t *out);
 

@@ -27,7 +27,7 @@
  * `bits` per value; density stays FP32.  The store counter of the k-th store of step t
  * (t = 1, 2, ...) is 1024 t + k.  With dither on, the threshold of the store of sample i of
  * field f (0 u, 1 v, 2 q; i the row-major index in the layout above) is the 16-bit draw of
- * Philox4x32-10 with key = the scene's seed, counter (i / 8, counter, f, 0), lane i % 8
+ * Philox4x32-7 (the dither generator) with key = the scene's seed, counter (i / 8, counter, f, 0), lane i % 8
  * (the same rule as the particle codec's component lanes).
  */
 #ifndef QMPM_SMOKE_H
@@ -107,7 +107,7 @@ int qmpm_smoke_get_states(qmpm_smoke_handle h, float *h_u, float *h_v, float *h_
 
 /* Noise injection for sensitivity estimates (FP32 handles only): every velocity store
  * except the reflection u^ and every pressure store gets sign_s * sigma_h * r added, r = +-1
- * from Philox4x32-10 with key = h_noise_seeds[s] and the store's dither counter (the top bit
+ * from Philox4x32-7 with key = h_noise_seeds[s] and the store's dither counter (the top bit
  * of lane i % 8); wall faces (an exact zero) get none.  sigma = {0, 0} turns it off.
  * Scenes 2k and 2k+1 given one noise seed and signs +1, -1 form antithetic pairs:
  * E[((z+ - z-) / 2)^2] = sigma_h^2 sum over stores of type h of (dz/dstore)^2 (Eq. 8's g_h).

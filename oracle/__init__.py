@@ -75,6 +75,7 @@ def _bind(L):
     P = ct.POINTER
     d, i64, u32 = ct.c_double, ct.c_int64, ct.c_uint32
     L.or_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+    L.or_philox4x32.argtypes = [P(u32), P(u32), ct.c_int, P(u32)]
     L.or_dither_draw.argtypes = [ct.c_uint64, u32, u32, ct.c_int]
     L.or_dither_draw.restype = u32
     L.or_encode.argtypes = [d, ct.c_int, ct.c_int, i64, ct.c_int, u32, P(ct.c_int)]
@@ -126,11 +127,19 @@ def _p(a, ctype):
 
 
 # ------------------------------------------------------------------------------ codec
-def philox(ctr, key):
+DITHER_ROUNDS = 7
+
+
+def philox(ctr, key, rounds=10):
+    """Philox4x32 with `rounds` rounds (10: the published known answers; the dither draws
+    use DITHER_ROUNDS)."""
     c = (ct.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
     k = (ct.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
     o = (ct.c_uint32 * 4)()
-    lib().or_philox4x32_10(c, k, o)
+    if rounds == 10:
+        lib().or_philox4x32_10(c, k, o)
+    else:
+        lib().or_philox4x32(c, k, int(rounds), o)
     return [int(v) for v in o]
 
 
@@ -302,9 +311,9 @@ def add_noise(dim, material, s, step, seed, sigma, sign):
     return s
 
 
-def noise_rollout_z(scene, s0, T, sigma, seed, sign, measure="mean_sq_pos"):
-    """z after T FP64 steps (no re-ordering) from s0 with the explicit error of (seed, sign)
-    added after every step (sign 0: none)."""
+def noise_rollout_state(scene, s0, T, sigma, seed, sign):
+    """The state after T FP64 steps (no re-ordering) from s0 with the explicit error of
+    (seed, sign) added after every step (sign 0: none)."""
     ph = make_phys(scene)
     s = np.ascontiguousarray(s0, dtype=np.float64).copy()
     grid = np.zeros(n_nodes(ph) * (1 + ph.dim))
@@ -312,6 +321,13 @@ def noise_rollout_z(scene, s0, T, sigma, seed, sign, measure="mean_sq_pos"):
         s = step_fp64(ph, s, grid)
         if sign != 0.0:
             s = add_noise(ph.dim, ph.material, s, t + 1, seed, sigma, sign)
+    return s
+
+
+def noise_rollout_z(scene, s0, T, sigma, seed, sign, measure="mean_sq_pos"):
+    """z of noise_rollout_state."""
+    ph = make_phys(scene)
+    s = noise_rollout_state(scene, s0, T, sigma, seed, sign)
     if measure == "kinetic_energy":
         return kinetic_energy(ph, s)
     return mean_sq_pos(ph.dim, s)

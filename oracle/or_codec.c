@@ -11,17 +11,19 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------------------------
- * Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as
- * 1, 2, 3", SC 2011).  Ten rounds of the 4x32 Philox S-box; between rounds the two
- * key words are bumped by the Weyl constants (golden ratio, sqrt(3)-1 in 32-bit).
+ * Philox4x32-R (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as
+ * 1, 2, 3", SC 2011).  R rounds of the 4x32 Philox S-box; between rounds the two key
+ * words are bumped by the Weyl constants (golden ratio, sqrt(3)-1 in 32-bit).  The
+ * published known answers are for R = 10; the authors report that R = 7 already passes
+ * their Crush batteries, and the dither draws use R = 7 (OR_DITHER_ROUNDS).
  * ---------------------------------------------------------------------------------- */
-void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+void or_philox4x32(const uint32_t ctr[4], const uint32_t key[2], int rounds, uint32_t out[4])
 {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
     const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
     uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
     uint32_t k0 = key[0], k1 = key[1];
-    for (int round = 0; round < 10; ++round) {
+    for (int round = 0; round < rounds; ++round) {
         if (round > 0) {
             k0 += W0;
             k1 += W1;
@@ -39,9 +41,14 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    or_philox4x32(ctr, key, 10, out);
+}
+
 /* The dither threshold of Sec. 5 for one stored component, compared with the 32-bit
  * fraction f of the value (round up when f > r).  A 16-bit uniform draw q is taken from the
- * Philox block with counter (slot, step, comp / 8, 0) and key = the 64-bit scene seed:
+ * Philox4x32-7 block with counter (slot, step, comp / 8, 0) and key = the 64-bit scene seed:
  * the low (comp even) or high (comp odd) half of word (comp / 2) % 4, so one call serves
  * eight consecutive components.  The threshold sits in the middle of q's bucket of 2^16
  * fractions, r = q 2^16 + 2^15, so P(round up) is the fraction rounded to 16 bits: exact
@@ -51,7 +58,7 @@ uint32_t or_dither_draw(uint64_t seed, uint32_t slot, uint32_t step, int comp)
     uint32_t ctr[4] = {slot, step, (uint32_t)(comp >> 3), 0u};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t out[4];
-    or_philox4x32_10(ctr, key, out);
+    or_philox4x32(ctr, key, OR_DITHER_ROUNDS, out);
     const uint32_t w = out[(comp >> 1) & 3];
     const uint32_t q = (comp & 1) ? (w >> 16) : (w & 0xFFFFu);
     return (q << 16) | 0x8000u;

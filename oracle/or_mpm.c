@@ -65,11 +65,18 @@ static void mat3_transpose(const double *A, double *T)
         for (int j = 0; j < 3; ++j) T[j * 3 + i] = A[i * 3 + j];
 }
 
+static double det_d(int d, const double *F);
+
 /* 3D polar factor R = F S^-1 with S = (F^T F)^{1/2}; the symmetric square root comes
  * from a cyclic Jacobi eigen-decomposition of F^T F (Golub & Van Loan, Sec. 8.5).
- * For det F < 0 the factor has det R = -1. */
+ * For det F < 0 the factor has det R = -1.  A (nearly) singular F, |det F| < 1e-6, has
+ * no unique factor (S^-1 does not exist): R = I there. */
 void or_polar3(const double F[9], double R[9])
 {
+    if (!(fabs(det_d(3, F)) >= 1e-6)) {
+        for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        return;
+    }
     double Ft[9], A[9], V[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     mat3_transpose(F, Ft);
     mat3_mul(Ft, F, A);

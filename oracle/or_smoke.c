@@ -137,7 +137,7 @@ static double store_q(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int fi
                       uint32_t counter, int64_t *sat);
 
 /* Noise at every store (sensitivity estimates by antithetic injection): sign * sigma_h * r
- * with r = +-1 the top bit of the 16-bit lane of Philox4x32-10 (key = noise seed, counter
+ * with r = +-1 the top bit of the 16-bit lane of the dither generator (Philox4x32-7; key = noise seed, counter
  * (i / 8, store counter, field, 0), lane i % 8), at every store of type h except the
  * reflected velocity and the wall faces (stores that make no rounding error). */
 static struct {

@@ -65,8 +65,11 @@ typedef struct {
 #define OR_STAT_OOG     12
 #define OR_N_STATS      13
 
-/* ---- counter-based generator (Philox4x32-10, Salmon et al. SC'11) ---- */
+/* ---- counter-based generator (Philox4x32, Salmon et al. SC'11; 10 rounds, the dither 7) ---- */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Philox4x32 with `rounds` rounds; the dither draws take OR_DITHER_ROUNDS */
+void or_philox4x32(const uint32_t ctr[4], const uint32_t key[2], int rounds, uint32_t out[4]);
+#define OR_DITHER_ROUNDS 7
 /* dither draw for (slot, step, comp): Philox(ctr={slot, step, comp/4, 0}, key=seed)[comp%4] */
 uint32_t or_dither_draw(uint64_t seed, uint32_t slot, uint32_t step, int comp);
 

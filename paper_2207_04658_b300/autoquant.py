@@ -71,6 +71,88 @@ def cubes3d_scheme(eps=0.01, T=None, samples=2, ckpt_every=32, material="corotat
     return scheme, {"solve": res, "sensitivities": info}
 
 
+def _shift_frac(field, k):
+    """A field's scheme k fraction bits finer (k < 0: coarser) over the same window."""
+    f = dict(field)
+    f["bits"], f["frac"] = f["bits"] + k, f["frac"] + k
+    f["offset"] = f["offset"] << k if k >= 0 else f["offset"] >> -k
+    return f
+
+
+def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=2, containers=(0, 0, 0, 0),
+                        seed=100, log=None):
+    """Algorithm 1's scheme for the vector evaluation (the final particle positions),
+    refined with the second-order term of the error at the resolution it will run at.
+
+    Eq. 6 bounds the second moment of the error; Eq. 8 keeps its linear part.  For the
+    position vector the second moment is |b|^2 + tr(Cov) with b the bias vector of the
+    final positions, and zero-mean dithered stores of the deformation gradient (a random
+    walk over the rollout) or of the positions shift the positions systematically.  Per
+    round, for each type h: qmpm_noise_moments of the final positions with errors of the
+    dithered variance (Delta_h / sqrt 6) at the stores of type h only gives |b_h|^2 and
+    the first-order spread; then beta_h = |b_h| / sigma_h^2 (the combined bias |sum_h b_h|
+    is at most sum_h |b_h|), g_h = spread_h / sigma_h^2, and the solve's second-order
+    refinement of Algorithm 1's scheme adds fraction bits until (sum_h beta_h Delta_h^2 /
+    6)^2 + sum_h g_h Delta_h^2 / 6 <= (eps z)^2.  The moments are re-estimated at the
+    refined scheme's own noise level (the shift is not quadratic in it: a coarse deformation
+    gradient can make the runs blow up, which reads as an unbounded sensitivity) until the
+    scheme repeats or after `iters` rounds, each round moving a type's resolution by at most
+    max_step bits (a damped fixed-point iteration), and keeping the finer fraction per type
+    where the last two differ.  info: the sensitivities and ranges of Algorithm 1 (g_h, lo,
+    hi; the run the ranges come from).  Returns (scheme, report)."""
+    import numpy as np
+    material = scene["material"]
+    dim = scene["dim"]
+    names = ["x", "v", "C", "J" if material == "fluid" else "F"]
+    N = state0.shape[0]
+    per = [dim, dim, dim * dim, 1 if material == "fluid" else dim * dim]
+    P = [float(N * k) for k in per]
+    base, res0 = qmpm.solve_scheme(info, eps, containers=containers, material=material)
+    g = qmpm.Scene(dict(scene, resort_every=0), None, state0)
+    rounds = []
+    try:
+        scheme, prev = base, None
+        z = None
+        for it in range(iters):
+            sig = [2.0 ** -scheme[n]["frac"] / np.sqrt(6.0) for n in names]
+            mom = []
+            for h in range(4):
+                s_h = [sig[k] if k == h else 0.0 for k in range(4)]
+                mom.append(qmpm.qmpm_noise_moments(g.h, T, qmpm.MEASURE_POSITIONS, s_h, seed + 10 * it + h, pairs))
+            z = float(np.sqrt(N * mom[0]["z0"]))
+            # a noise level that makes the run blow up (non-finite moments) counts as an
+            # unbounded sensitivity: the refinement then takes bits until the next round
+            beta = [float(np.sqrt(max(m["shift"], 0.0))) / sig[h] ** 2 if np.isfinite(m["shift"]) else 1e30
+                    for h, m in enumerate(mom)]
+            geff = [float(m["spread"]) / sig[h] ** 2 if np.isfinite(m["spread"]) else 1e30
+                    for h, m in enumerate(mom)]
+            sol = dict(info, g=geff, P=P, z=z)
+            want, res = qmpm.solve_scheme(sol, eps, containers=containers, material=material, beta=beta)
+            nxt = {}
+            for n in names:
+                # the current window, the resolution moved toward the solve's by at most
+                # max_step bits (and never past the 24 bits FP32 compute decodes exactly)
+                k = max(-max_step, min(max_step, want[n]["frac"] - scheme[n]["frac"]))
+                k = min(k, 24 - scheme[n]["bits"])
+                k = max(k, 1 - scheme[n]["bits"])
+                nxt[n] = _shift_frac(scheme[n], k)
+            rounds.append({"scheme": scheme, "sigma": sig, "moments": mom, "beta": beta, "g": geff, "solve": want,
+                           "next": nxt, "pred_bias": res["pred_bias"], "pred_var": res["pred_var_dither"]})
+            if log:
+                log(it, {k: v["bits"] for k, v in nxt.items()}, res["pred_bias"], res["pred_var_dither"], z)
+            # each round refines Algorithm 1's scheme with the moments measured at the current
+            # one, moving at most max_step bits per type
+            seen = [r["scheme"] for r in rounds]
+            prev, scheme = scheme, nxt
+            if scheme in seen:  # a fixed point, or a cycle: keep the finer of the last two
+                break
+        if prev is not None and scheme != prev:
+            scheme = {n: (scheme[n] if scheme[n]["frac"] >= prev[n]["frac"] else prev[n]) for n in names}
+    finally:
+        g.close()
+    return scheme, {"algorithm1": base, "algorithm1_solve": res0, "rounds": rounds, "z": z, "eps": eps}
+
+
 def c_noise_margin(grid_log2):
     """The solve's window margin for C (type 2) from the velocity noise (type 1): the
     recorded C range comes from the unquantized run, where C of a rigidly moving body is

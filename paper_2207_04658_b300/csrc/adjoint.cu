@@ -108,7 +108,7 @@ __device__ __forceinline__ void stress_adjoint(const float *FJ, const float *T, 
         R[2] = s;
         R[3] = c;
     } else {
-        polar3(F, R);
+        polar3(F, J, R);
     }
     float G[DIM * DIM];
 #pragma unroll
@@ -587,7 +587,7 @@ __global__ void adj_quantize_kernel(const __grid_constant__ StepParams P, float 
     uint4 rnd = make_uint4(0, 0, 0, 0);
     for (int c = 0; c < P.n_comp; ++c) {
         if (P.dither && (c & 7) == 0)
-            rnd = philox4x32_10(make_uint4((uint32_t)p, step, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
+            rnd = philox4x32(make_uint4((uint32_t)p, step, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
         const CompCodec &cc = P.comp[c];
         int fl;
         const uint32_t u = encode_f32(s[p * P.n_comp + c], cc, P.dither != 0, dither_threshold(rnd, c), fl);
@@ -606,7 +606,7 @@ __global__ void adj_noise_kernel(const __grid_constant__ StepParams P, float *s,
     if (p >= N) return;
     uint4 rnd = make_uint4(0, 0, 0, 0);
     for (int c = 0; c < P.n_comp; ++c) {
-        if ((c & 3) == 0) rnd = philox4x32_10(make_uint4((uint32_t)p, step, (uint32_t)(c >> 2), 0xA5u), seed_lo, seed_hi);
+        if ((c & 3) == 0) rnd = philox4x32<10>(make_uint4((uint32_t)p, step, (uint32_t)(c >> 2), 0xA5u), seed_lo, seed_hi);
         const uint32_t w = uint4_at(rnd, c & 3);
         // 2u - 1 with u = (w / 2^9 + 1/2) 2^-23 in (0, 1): exact in FP32
         const float xi = ((float)(2u * (w >> 9) + 1u) * (1.0f / 8388608.0f) - 1.0f) * 1.7320508f;
@@ -955,12 +955,55 @@ extern "C" int qmpm_adjoint(qmpm_handle h, int32_t T, int32_t ckpt_every, int32_
     return QMPM_OK;
 }
 
+namespace qmpm {
+namespace {
+
+// positions of the final state of a noise pair: m = (x+ + x-)/2 - x0 is added to acc, and
+// sums[0] += |m|^2, sums[1] += |(x+ - x-)/2|^2 (FP64)
+__global__ void noise_pair_kernel(const float *sp, const float *sm, const float *s0, int64_t N, int nc, int dim,
+                                  float *acc, double *sums)
+{
+    double a = 0.0, b = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < dim; ++c) {
+            const float xp = sp[p * nc + c], xm = sm[p * nc + c];
+            const double m = 0.5 * ((double)xp + (double)xm) - (double)s0[p * nc + c];
+            const double d = 0.5 * ((double)xp - (double)xm);
+            acc[p * dim + c] += (float)m;
+            a += m * m;
+            b += d * d;
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sums, a);
+        atomicAdd(sums + 1, b);
+    }
+}
+
+__global__ void sq_sum_kernel(const float *v, int64_t n, double scale, double *out)
+{
+    double a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = (double)v[i] * scale;
+        a += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, a);
+}
+
+}  // namespace
+}  // namespace qmpm
+
 extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, const double *sigma, uint64_t seed0,
                                   int32_t n_pairs, qmpm_noise_out_t *out)
 {
     using namespace qmpm;
     if (!h || T < 0 || n_pairs < 2 || !sigma || !out ||
-        (measure != QMPM_MEASURE_MEAN_SQ_POS && measure != QMPM_MEASURE_KINETIC_ENERGY)) {
+        (measure != QMPM_MEASURE_MEAN_SQ_POS && measure != QMPM_MEASURE_KINETIC_ENERGY &&
+         measure != QMPM_MEASURE_POSITIONS)) {
         set_last_error("qmpm_noise_moments: bad handle, T, measure, sigma, out or n_pairs (>= 2)");
         return QMPM_ERR_INVALID_ARG;
     }
@@ -972,6 +1015,7 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
     Ctx &c = *h;
     const int dim = c.scene.dim, nc = c.n_comp;
     const int64_t N = c.N;
+    const bool vec = measure == QMPM_MEASURE_POSITIONS;
     ForwardFn fwd;
     ReverseFn rev;
     pick(dim, c.scene.material, fwd, rev);
@@ -990,13 +1034,18 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
     auto cleanup = [&]() {
         for (void *ptr : allocs) cudaFree(ptr);
     };
+    // s0, two run buffers, the noise-free final state and the + run's final state (vector
+    // measure), the accumulated shift vector, the grid
     float *s0 = static_cast<float *>(alloc(state_bytes));
     float *a = static_cast<float *>(alloc(state_bytes));
     float *b = static_cast<float *>(alloc(state_bytes));
+    float *fin0 = vec ? static_cast<float *>(alloc(state_bytes)) : nullptr;
+    float *finp = vec ? static_cast<float *>(alloc(state_bytes)) : nullptr;
+    float *acc = vec ? static_cast<float *>(alloc(sizeof(float) * (size_t)std::max<int64_t>(N, 1) * dim)) : nullptr;
     float *gm = static_cast<float *>(alloc(sizeof(float) * (size_t)nn));
     float4 *gv = static_cast<float4 *>(alloc(sizeof(float4) * (size_t)nn));
     double *dz = static_cast<double *>(alloc(sizeof(double) * 8));
-    if (!s0 || !a || !b || !gm || !gv || !dz) {
+    if (!s0 || !a || !b || !gm || !gv || !dz || (vec && (!fin0 || !finp || !acc))) {
         cudaGetLastError();
         cleanup();
         set_last_error("qmpm_noise_moments: device allocation failed");
@@ -1007,9 +1056,12 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
         adj_load_kernel<<<nblk(N), kAdjThreads, 0, st>>>(P, c.quant ? 1 : 0, s0, N);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && vec) e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)std::max<int64_t>(N, 1) * dim, st);
     const float4 sig = make_float4((float)sigma[0], (float)sigma[1], (float)sigma[2], (float)sigma[3]);
-    // z of a T-step run from s_0, with the noise of (seed, sign) or none (sign 0)
-    auto run = [&](uint64_t seed, float sign, double *zout) -> cudaError_t {
+    const unsigned nbk = std::min<unsigned>(nblk(std::max<int64_t>(N, 1)), (unsigned)c.n_sms * 8);
+    // a T-step run from s_0 with the noise of (seed, sign) or none (sign 0); the final state
+    // is left in *final
+    auto run = [&](uint64_t seed, float sign, float **final) -> cudaError_t {
         cudaError_t r = cudaMemcpyAsync(a, s0, state_bytes, cudaMemcpyDeviceToDevice, st);
         float *cur = a, *nxt = b;
         for (int t = 0; t < T && r == cudaSuccess; ++t) {
@@ -1021,10 +1073,13 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
             }
             std::swap(cur, nxt);
         }
-        if (r == cudaSuccess) r = cudaMemsetAsync(dz, 0, sizeof(double) * 8, st);
+        *final = cur;
+        return r;
+    };
+    auto z_of = [&](const float *fin, double *zout) -> cudaError_t {
+        cudaError_t r = cudaMemsetAsync(dz, 0, sizeof(double) * 8, st);
         if (r == cudaSuccess && N > 0) {
-            const unsigned nbk = std::min<unsigned>(nblk(N), (unsigned)c.n_sms * 8);
-            adj_reduce_kernel<<<nbk, kAdjThreads, 0, st>>>(cur, N, nc, dim, dz, nullptr, nullptr, dz + 4, 0, 0,
+            adj_reduce_kernel<<<nbk, kAdjThreads, 0, st>>>(fin, N, nc, dim, dz, nullptr, nullptr, dz + 4, 0, 0,
                                                            measure == QMPM_MEASURE_KINETIC_ENERGY ? 2 : 1, P.p_mass);
             r = cudaGetLastError();
         }
@@ -1036,13 +1091,46 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
     };
     double z0 = 0.0;
     std::vector<double> shift, spread;
-    if (e == cudaSuccess) e = run(0, 0.0f, &z0);
+    float *fin = nullptr;
+    if (e == cudaSuccess) e = run(0, 0.0f, &fin);
+    if (e == cudaSuccess) e = vec ? cudaMemcpyAsync(fin0, fin, state_bytes, cudaMemcpyDeviceToDevice, st) : z_of(fin, &z0);
+    if (e == cudaSuccess && vec) e = z_of(fin0, &z0);
     for (int k = 0; k < n_pairs && e == cudaSuccess; ++k) {
-        double zp = 0.0, zm = 0.0;
-        e = run(seed0 + (uint64_t)k, 1.0f, &zp);
-        if (e == cudaSuccess) e = run(seed0 + (uint64_t)k, -1.0f, &zm);
-        shift.push_back(0.5 * (zp + zm) - z0);
-        spread.push_back(0.25 * (zp - zm) * (zp - zm));
+        if (vec) {
+            e = run(seed0 + (uint64_t)k, 1.0f, &fin);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(finp, fin, state_bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = run(seed0 + (uint64_t)k, -1.0f, &fin);
+            if (e == cudaSuccess) e = cudaMemsetAsync(dz, 0, sizeof(double) * 8, st);
+            if (e == cudaSuccess && N > 0) {
+                noise_pair_kernel<<<nbk, kAdjThreads, 0, st>>>(finp, fin, fin0, N, nc, dim, acc, dz);
+                e = cudaGetLastError();
+            }
+            double hz[8];
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hz, dz, sizeof(hz), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            shift.push_back(hz[0]);   // |m_k|^2
+            spread.push_back(hz[1]);  // sum |(x+ - x-)/2|^2
+        } else {
+            double zp = 0.0, zm = 0.0;
+            e = run(seed0 + (uint64_t)k, 1.0f, &fin);
+            if (e == cudaSuccess) e = z_of(fin, &zp);
+            if (e == cudaSuccess) e = run(seed0 + (uint64_t)k, -1.0f, &fin);
+            if (e == cudaSuccess) e = z_of(fin, &zm);
+            shift.push_back(0.5 * (zp + zm) - z0);
+            spread.push_back(0.25 * (zp - zm) * (zp - zm));
+        }
+    }
+    double mean_sq = 0.0;  // |mean_k m_k|^2 (vector measure)
+    if (e == cudaSuccess && vec) {
+        e = cudaMemsetAsync(dz, 0, sizeof(double) * 8, st);
+        if (e == cudaSuccess && N > 0) {
+            sq_sum_kernel<<<nbk, kAdjThreads, 0, st>>>(acc, N * dim, 1.0 / n_pairs, dz);
+            e = cudaGetLastError();
+        }
+        double hz[8];
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hz, dz, sizeof(hz), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        mean_sq = hz[0];
     }
     cleanup();
     if (e != cudaSuccess) {
@@ -1059,8 +1147,18 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
     };
     std::memset(out, 0, sizeof(*out));
     out->z0 = z0;
-    mean_se(shift, out->shift, out->shift_se);
     mean_se(spread, out->spread, out->spread_se);
+    if (vec) {
+        // E|mean_k m_k|^2 = |b|^2 + E|m - b|^2 / K and E|m_k|^2 = |b|^2 + E|m - b|^2:
+        // |b|^2 = (K |mean m|^2 - mean |m_k|^2) / (K - 1)
+        double msq, msq_se;
+        mean_se(shift, msq, msq_se);
+        const double K = (double)n_pairs;
+        out->shift = (K * mean_sq - msq) / (K - 1.0);
+        out->shift_se = msq_se * K / (K - 1.0);  // scale of its noise: the per-pair spread of |m_k|^2
+    } else {
+        mean_se(shift, out->shift, out->shift_se);
+    }
     out->pairs = n_pairs;
     return QMPM_OK;
 }

@@ -10,15 +10,20 @@
 namespace qmpm {
 
 // ------------------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of the 4x32 S-box,
-// keys bumped by the Weyl constants between rounds.  Used for the dither threshold of
-// Sec. 5: counter (slot, step, comp / 8, 0), key = scene seed; component comp takes the
-// 16-bit half comp % 2 of word (comp / 2) % 4 (dither_threshold).
+// Philox4x32-R (Salmon, Moraes, Dror, Shaw, SC 2011): R rounds of the 4x32 S-box, keys
+// bumped by the Weyl constants between rounds.  The dither threshold of Sec. 5 takes
+// R = kDitherRounds = 7 (the authors report 7 rounds already pass their Crush batteries;
+// the published known answers are for 10): counter (slot, step, comp / 8, 0), key = scene
+// seed; component comp takes the 16-bit half comp % 2 of word (comp / 2) % 4
+// (dither_threshold).  The explicit store errors of qmpm_noise_moments take R = 10.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+constexpr int kDitherRounds = 7;
+
+template <int R = kDitherRounds>
+__device__ __forceinline__ uint4 philox4x32(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = 0; r < R; ++r) {
         if (r > 0) {
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
@@ -30,13 +35,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// The same generator with its ten round keys given (round r: seed_lo + r 0x9E3779B9,
+// The dither generator with its round keys given (round r: seed_lo + r 0x9E3779B9,
 // seed_hi + r 0xBB67AE85, precomputed on the host): read from the kernel's parameters, each
 // key is an operand of the round's XOR instead of two additions per round.
-__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk)[2][10])
+__device__ __forceinline__ uint4 philox4x32_rk(uint4 c, const uint32_t (&rk)[2][10])
 {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = 0; r < kDitherRounds; ++r) {
         const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
         c = make_uint4(hi1 ^ c.y ^ rk[0][r], lo1, hi0 ^ c.w ^ rk[1][r], lo0);

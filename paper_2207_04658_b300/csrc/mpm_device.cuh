@@ -11,11 +11,18 @@ namespace qmpm {
 // 3D polar factor by the scaled Newton iteration X <- (g X + X^-T / g) / 2 with
 // determinant scaling g = |det X|^(-1/3) (Higham 1986; Byers & Xu 2008).  X^-T is the
 // cofactor matrix (rows: cross products of the other two rows) over det X.
-__device__ __forceinline__ void polar3(const float *F, float *R)
+// detF: det F, which the caller has already.  A (nearly) singular F has no unique polar
+// factor and the iteration's scaling would overflow: R = I there (|det F| < 1e-6, or NaN).
+__device__ __forceinline__ void polar3(const float *F, float detF, float *R)
 {
     float X[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) X[i] = F[i];
+    if (!(fabsf(detF) >= 1e-6f)) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+        return;
+    }
     for (int it = 0; it < 10; ++it) {
         const float c0 = X[4] * X[8] - X[5] * X[7], c1 = X[5] * X[6] - X[3] * X[8],
                     c2 = X[3] * X[7] - X[4] * X[6];
@@ -89,7 +96,7 @@ __device__ __forceinline__ void kirchhoff(const float *FJ, const StepParams &P, 
             R[2] = s;
             R[3] = c;
         } else {
-            polar3(F, R);
+            polar3(F, J, R);
         }
         const float vol = P.lambda * (J - 1.0f) * J;
 #pragma unroll

@@ -242,7 +242,7 @@ __device__ __forceinline__ float store(const Params &P, int s, int type, int fie
         uint32_t r = 0u;
         if (P.dither) {
             const uint2 key = P.seed[s];
-            const uint4 blk = philox4x32_10(make_uint4(k >> 3, counter, (uint32_t)field, 0u), key.x, key.y);
+            const uint4 blk = philox4x32(make_uint4(k >> 3, counter, (uint32_t)field, 0u), key.x, key.y);
             r = dither_threshold(blk, (int)(k & 7u));
         }
         int flags = 0;
@@ -256,7 +256,7 @@ __device__ __forceinline__ float store(const Params &P, int s, int type, int fie
     } else {
         if (inject && !wall && P.sigma[type] != 0.0f) {
             const uint2 key = P.nseed[s];
-            const uint4 blk = philox4x32_10(make_uint4(k >> 3, counter, (uint32_t)field, 0u), key.x, key.y);
+            const uint4 blk = philox4x32(make_uint4(k >> 3, counter, (uint32_t)field, 0u), key.x, key.y);
             const uint32_t w = uint4_at(blk, (int)((k >> 1) & 3u));
             const uint32_t q16 = (k & 1u) ? (w >> 16) : (w & 0xFFFFu);
             y = x + P.sign[s] * P.sigma[type] * ((q16 & 0x8000u) ? 1.0f : -1.0f);
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kT, 4) jacobi_kernel(Params P, int it0, int ns
             }
             if (Q) {
                 uint4 blk = make_uint4(0u, 0u, 0u, 0u);
-                if (P.dither) blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), dkey.x, dkey.y);
+                if (P.dither) blk = philox4x32(make_uint4(oct, counter, 2u, 0u), dkey.x, dkey.y);
                 uint32_t code[8];
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kT, 4) jacobi_kernel(Params P, int it0, int ns
                     for (int m = 0; m < 8; ++m) x[m] = __uint_as_float(code[m]);
                 }
             } else if (noise) {
-                const uint4 blk = philox4x32_10(make_uint4(oct, counter, 2u, 0u), nkey.x, nkey.y);
+                const uint4 blk = philox4x32(make_uint4(oct, counter, 2u, 0u), nkey.x, nkey.y);
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
                     const uint32_t wd = uint4_at(blk, (m >> 1) & 3);

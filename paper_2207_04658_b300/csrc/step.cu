@@ -356,9 +356,9 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
                         // additions per round are cheaper than loading the keys
                         const uint4 ctr = make_uint4((uint32_t)slot, MULTI ? step : P.step, (uint32_t)(c >> 3), 0u);
                         if (ROUND_KEYS)
-                            rnd = philox4x32_10_rk(ctr, P.round_key);
+                            rnd = philox4x32_rk(ctr, P.round_key);
                         else
-                            rnd = philox4x32_10(ctr, P.seed_lo, P.seed_hi);
+                            rnd = philox4x32(ctr, P.seed_lo, P.seed_hi);
                     }
                     int fl;
                     const CompCodec &cc = P.comp[c];
@@ -738,7 +738,7 @@ __global__ void encode_init_kernel(const __grid_constant__ StepParams P, const d
     uint4 rnd = make_uint4(0, 0, 0, 0);
     for (int c = 0; c < P.n_comp; ++c) {
         if (P.dither && (c & 7) == 0)
-            rnd = philox4x32_10(make_uint4((uint32_t)p, 0u, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
+            rnd = philox4x32(make_uint4((uint32_t)p, 0u, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
         int fl;
         const uint32_t u = encode_f64(s[p * P.n_comp + c], P.comp[c], P.dither != 0, dither_threshold(rnd, c), fl);
         if (P.stats && fl) {
@@ -832,7 +832,7 @@ __global__ void pack_f32_kernel(const __grid_constant__ StepParams P, const floa
     uint4 rnd = make_uint4(0, 0, 0, 0);
     for (int c = 0; c < P.n_comp; ++c) {
         if (P.dither && (c & 7) == 0)
-            rnd = philox4x32_10(make_uint4((uint32_t)p, P.step, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
+            rnd = philox4x32(make_uint4((uint32_t)p, P.step, (uint32_t)(c >> 3), 0u), P.seed_lo, P.seed_hi);
         int fl;
         const uint32_t u = encode_f32(vals[p * P.n_comp + c], P.comp[c], P.dither != 0, dither_threshold(rnd, c), fl);
         if (P.stats && fl) {

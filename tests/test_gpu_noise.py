@@ -50,3 +50,34 @@ def test_noise_moments_arguments():
         assert m["shift"] == 0.0 and m["spread"] == 0.0  # no noise: every run is the noise-free one
     finally:
         g.close()
+
+
+def test_position_noise_moments_match_the_oracle(oracle):
+    """The vector evaluation (final positions): |b|^2 of the bias vector and the summed
+    first-order spread, against the same estimates from the oracle's FP64 runs."""
+    import torch
+    from paper_2207_04658_b300 import qmpm
+    from test_gpu_adjoint import small
+    assert torch.cuda.is_available()
+    sc, s0 = small(3, "corotated", N_side=10, seed=3)
+    T, sigma, seed0, K = 20, [2e-3, 0.2, 20.0, 2e-2], 11, 3
+    g = qmpm.Scene(sc, None, s0)
+    ids = g.readback(state=False, ids=True)["ids"]
+    m = qmpm.qmpm_noise_moments(g.h, T, qmpm.MEASURE_POSITIONS, sigma, seed0, K)
+    g.close()
+    s_slot = s0[ids]
+    x0 = oracle.noise_rollout_state(sc, s_slot, T, sigma, 0, 0.0)[:, :3]
+    ms, sq, sp = [], [], []
+    for k in range(K):
+        xp = oracle.noise_rollout_state(sc, s_slot, T, sigma, seed0 + k, 1.0)[:, :3]
+        xm = oracle.noise_rollout_state(sc, s_slot, T, sigma, seed0 + k, -1.0)[:, :3]
+        mk = 0.5 * (xp + xm) - x0
+        ms.append(mk)
+        sq.append((mk ** 2).sum())
+        sp.append((0.25 * (xp - xm) ** 2).sum())
+    mean = np.mean(ms, axis=0)
+    b2 = (K * (mean ** 2).sum() - np.mean(sq)) / (K - 1)
+    assert abs(m["z0"] - (x0 ** 2).sum(1).mean()) <= 1e-5 * m["z0"]
+    assert abs(m["spread"] - np.mean(sp)) <= 1e-3 * np.mean(sp), (m, np.mean(sp))
+    # |b|^2 is a difference of two close sums: compare within FP32 rounding of the positions
+    assert abs(m["shift"] - b2) <= 5e-2 * abs(b2) + 1e-3 * np.mean(sq), (m, b2, np.mean(sq))

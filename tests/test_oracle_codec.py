@@ -10,17 +10,37 @@ from conftest import read_golden
 
 
 def test_philox_known_answers(oracle):
+    import ctypes as ct
     for row in read_golden("philox4x32_10_kat.txt"):
         vals = [int(v, 16) for v in row]
         assert oracle.philox(vals[0:4], vals[4:6]) == vals[6:10]
+        # the generator with a round count (the dither draws take 7) is the same function
+        c = (ct.c_uint32 * 4)(*vals[0:4])
+        k = (ct.c_uint32 * 2)(*vals[4:6])
+        o = (ct.c_uint32 * 4)()
+        oracle.lib().or_philox4x32(c, k, 10, o)
+        assert list(o) == vals[6:10]
+
+
+def test_dither_rounds_differ_from_ten(oracle):
+    # the dither generator stops after DITHER_ROUNDS = 7 rounds: its blocks differ from the
+    # ten-round ones, and consecutive counters give unrelated blocks
+    key = [0x01234567, 0x89ABCDEF]
+    b7 = [oracle.philox([i, 3, 0, 0], key, rounds=oracle.DITHER_ROUNDS) for i in range(64)]
+    b10 = [oracle.philox([i, 3, 0, 0], key) for i in range(64)]
+    assert oracle.DITHER_ROUNDS == 7 and all(a != b for a, b in zip(b7, b10))
+    bits = np.array([[(w >> k) & 1 for w in blk for k in range(32)] for blk in b7])
+    assert abs(bits.mean() - 0.5) < 4 * 0.5 / np.sqrt(bits.size)
 
 
 def test_dither_draw_counter(oracle):
     # the draw of component c is the 16-bit half c % 2 of word (c // 2) % 4 of the Philox
-    # block (slot, step, c // 8, 0), placed mid-bucket among the 32-bit fractions
+    # block (slot, step, c // 8, 0) of DITHER_ROUNDS rounds, placed mid-bucket among the
+    # 32-bit fractions
     seed = 0x0123456789ABCDEF
     for slot, step, comp in [(0, 0, 0), (5, 7, 3), (123456, 99, 13), (2**31, 2**20, 23), (9, 9, 8)]:
-        block = oracle.philox([slot, step, comp // 8, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        block = oracle.philox([slot, step, comp // 8, 0], [seed & 0xFFFFFFFF, seed >> 32],
+                              rounds=oracle.DITHER_ROUNDS)
         w = block[(comp // 2) % 4]
         q = (w >> 16) if comp % 2 else (w & 0xFFFF)
         assert oracle.dither_draw(seed, slot, step, comp) == (q << 16) | 0x8000

@@ -342,3 +342,20 @@ def test_threaded_build_matches_sequential(oracle):
     quanta = np.array([2.0 ** -sch[["x", "v", "C", "F"][h]]["frac"] for h in fields])
     assert (d <= quanta[None] * (1 + 1e-9)).all()
     assert (d == 0).mean() > 0.999
+
+
+def test_polar_decomposition_inverted_and_singular(oracle):
+    """An inverted F (det < 0) gets the orthogonal factor of the SVD (det R = -1, U V^T); a
+    (nearly) singular one, |det F| < 1e-6, has no unique factor and gets R = I (the reading
+    both the oracle and the kernels take)."""
+    gen = np.random.default_rng(17)
+    for _ in range(20):
+        F = np.eye(3) + 0.5 * gen.normal(0, 1, (3, 3))
+        F[0] *= -1.0  # invert
+        if np.linalg.det(F) > -0.05:
+            continue
+        R = oracle.polar(F)
+        U, _, Vt = np.linalg.svd(F)
+        assert np.allclose(R, U @ Vt, atol=1e-10) and np.linalg.det(R) == pytest.approx(-1.0, abs=1e-12)
+    for F in (np.zeros((3, 3)), np.diag([1.0, 1.0, 0.0]), np.outer([1.0, 2.0, 3.0], [0.5, -1.0, 2.0])):
+        assert np.array_equal(oracle.polar(F), np.eye(3))
