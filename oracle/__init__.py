@@ -592,6 +592,9 @@ def _bind_smoke(L):
     L.or_smoke_follow_first.argtypes = [P(ct.c_int64), P(d), P(d)]
     L.or_smoke_noise.argtypes = [ct.c_int, d, d, ct.c_uint64, d]
     L.or_smoke_record.argtypes = [P(ct.c_uint32), ct.c_int64]
+    L.or_smoke_record_values.argtypes = [P(ct.c_uint32), P(d), ct.c_int64]
+    L.or_smoke_stage.argtypes = [P(Smoke), P(SmokeScheme), ct.c_int, ct.c_int, ct.c_uint32] + [P(d)] * 11
+    L.or_smoke_stage.restype = ct.c_int
     L.or_smoke_recorded.restype = ct.c_int64
 
 
@@ -702,6 +705,45 @@ class smoke_follow:
                       "dist": fd.value} if self.report[2] else None
         L.or_smoke_follow(None, 0, 0.0, 0.0)
         return False
+
+
+SMOKE_STAGES = {"advect1": 0, "jacobi": 1, "gradsub2": 2, "advect4": 3, "gradsub5": 4}
+
+
+def smoke_stage(scene, scheme, stage, step, arg=0, a=None, b=None, q=None, div=None):
+    """One stage of the quantized smoke step from given inputs (or_smoke_stage): a, b are
+    (u [n][n+1], v [n+1][n]) pairs, q and div [n][n].  Returns the codes every store of the
+    stage wrote (in order), the values they were offered (FP64) and the stage's outputs."""
+    L = _smoke_lib()
+    sm, sch = make_smoke(scene), make_smoke_scheme(scheme)
+    n = sm.n
+
+    def arr(x, shape):
+        return None if x is None else np.ascontiguousarray(x, dtype=np.float64).reshape(shape)
+
+    au, av = (arr(a[0], (n, n + 1)), arr(a[1], (n + 1, n))) if a is not None else (None, None)
+    bu, bv = (arr(b[0], (n, n + 1)), arr(b[1], (n + 1, n))) if b is not None else (None, None)
+    qq, dv = arr(q, (n, n)), arr(div, (n, n))
+    out = {k: np.zeros(sh) for k, sh in (("u", (n, n + 1)), ("v", (n + 1, n)), ("u2", (n, n + 1)), ("v2", (n + 1, n)),
+                                           ("q", (n, n)))}
+    cap = 4 * (n + 1) * n + n * n
+    codes = np.zeros(cap, dtype=np.uint32)
+    xs = np.zeros(cap)
+    L.or_smoke_record_values(_p(codes, ct.c_uint32), _p(xs, ct.c_double), cap)
+
+    def ptr(x):
+        return None if x is None else _p(x, ct.c_double)
+
+    try:
+        rc = L.or_smoke_stage(ct.byref(sm), ct.byref(sch), SMOKE_STAGES[stage], int(arg), int(step), ptr(au), ptr(av),
+                              ptr(bu), ptr(bv), ptr(qq), ptr(dv), ptr(out["u"]), ptr(out["v"]), ptr(out["u2"]),
+                              ptr(out["v2"]), ptr(out["q"]))
+        m = int(L.or_smoke_recorded())
+    finally:
+        L.or_smoke_record(None, 0)
+    if rc != 0:
+        raise ValueError(f"oracle smoke stage failed ({rc})")
+    return {"codes": codes[:m], "x": xs[:m], **out}
 
 
 def smoke_store_events(n, jacobi, T):

@@ -197,14 +197,22 @@ void or_smoke_follow(const uint32_t *codes, int64_t n, double tau_v, double tau_
 
 static struct {
     uint32_t *buf;
+    double *xs;   /* optional: the value each store was offered */
     int64_t n, pos;
 } g_record;
 
 void or_smoke_record(uint32_t *buf, int64_t n)
 {
     g_record.buf = buf;
+    g_record.xs = NULL;
     g_record.n = n;
     g_record.pos = 0;
+}
+
+void or_smoke_record_values(uint32_t *buf, double *xs, int64_t n)
+{
+    or_smoke_record(buf, n);
+    g_record.xs = xs;
 }
 
 int64_t or_smoke_recorded(void) { return g_record.pos; }
@@ -237,7 +245,10 @@ static double store_q(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int fi
     uint32_t q = or_encode(x, bits, frac, offset, sm->dither, r, &flags);
     if ((flags & OR_FLAG_SAT) && sat) *sat += 1;
     if (g_record.buf) {
-        if (g_record.pos < g_record.n) g_record.buf[g_record.pos] = q;
+        if (g_record.pos < g_record.n) {
+            g_record.buf[g_record.pos] = q;
+            if (g_record.xs) g_record.xs[g_record.pos] = x;
+        }
         g_record.pos += 1;
     }
     if (g_follow.codes) {
@@ -280,34 +291,51 @@ static void store_velocity(const or_smoke_t *sm, const or_smoke_scheme_t *sch, d
     for (int k = 0; k < n * (n + 1); ++k) v[k] = store(sm, sch, 1, v[k], (uint32_t)k, counter, sat);
 }
 
+/* one Jacobi sweep of lap(q) = div from the iterate q into q2, each value stored */
+static void jacobi_sweep(const or_smoke_t *sm, const or_smoke_scheme_t *sch, const double *q, double *q2,
+                         const double *div, uint32_t counter, int64_t *sat)
+{
+    const int n = sm->n;
+    const double h2 = 1.0 / ((double)n * n);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            int cnt = 0;
+            if (i > 0) { acc += q[j * n + i - 1]; ++cnt; }
+            if (i < n - 1) { acc += q[j * n + i + 1]; ++cnt; }
+            if (j > 0) { acc += q[(j - 1) * n + i]; ++cnt; }
+            if (j < n - 1) { acc += q[(j + 1) * n + i]; ++cnt; }
+            q2[j * n + i] = store(sm, sch, 2, (acc - h2 * div[j * n + i]) / cnt, (uint32_t)(j * n + i), counter, sat);
+        }
+}
+
+/* w -= grad q on the interior faces, then the walls */
+static void grad_subtract(const or_smoke_t *sm, double *u, double *v, const double *q)
+{
+    const int n = sm->n;
+    const double inv_h = (double)n;
+    for (int j = 0; j < n; ++j)
+        for (int i = 1; i < n; ++i) u[j * (n + 1) + i] -= (q[j * n + i] - q[j * n + i - 1]) * inv_h;
+    for (int j = 1; j < n; ++j)
+        for (int i = 0; i < n; ++i) v[j * n + i] -= (q[j * n + i] - q[(j - 1) * n + i]) * inv_h;
+    walls(n, u, v);
+}
+
 static void project(const or_smoke_t *sm, const or_smoke_scheme_t *sch, double *u, double *v, double *q,
                     double *q2, double *div, uint32_t *counter, int64_t *sat)
 {
     const int n = sm->n;
-    const double inv_h = (double)n, h2 = 1.0 / ((double)n * n);
+    const double inv_h = (double)n;
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i)
             div[j * n + i] = (u[j * (n + 1) + i + 1] - u[j * (n + 1) + i] + v[(j + 1) * n + i] - v[j * n + i]) * inv_h;
     memset(q, 0, sizeof(double) * (size_t)n * n);
     for (int it = 0; it < sm->jacobi; ++it) {
         *counter += 1;
-        for (int j = 0; j < n; ++j)
-            for (int i = 0; i < n; ++i) {
-                double acc = 0.0;
-                int cnt = 0;
-                if (i > 0) { acc += q[j * n + i - 1]; ++cnt; }
-                if (i < n - 1) { acc += q[j * n + i + 1]; ++cnt; }
-                if (j > 0) { acc += q[(j - 1) * n + i]; ++cnt; }
-                if (j < n - 1) { acc += q[(j + 1) * n + i]; ++cnt; }
-                q2[j * n + i] = store(sm, sch, 2, (acc - h2 * div[j * n + i]) / cnt, (uint32_t)(j * n + i), *counter, sat);
-            }
+        jacobi_sweep(sm, sch, q, q2, div, *counter, sat);
         memcpy(q, q2, sizeof(double) * (size_t)n * n);
     }
-    for (int j = 0; j < n; ++j)
-        for (int i = 1; i < n; ++i) u[j * (n + 1) + i] -= (q[j * n + i] - q[j * n + i - 1]) * inv_h;
-    for (int j = 1; j < n; ++j)
-        for (int i = 0; i < n; ++i) v[j * n + i] -= (q[j * n + i] - q[(j - 1) * n + i]) * inv_h;
-    walls(n, u, v);
+    grad_subtract(sm, u, v, q);
 }
 
 int64_t or_smoke_step(const or_smoke_t *sm, const or_smoke_scheme_t *sch, uint32_t step, double *u, double *v,
@@ -374,4 +402,64 @@ double or_smoke_measure(const or_smoke_t *sm, const double *d)
     double acc = 0.0;
     for (int k = 0; k < sm->n * sm->n; ++k) acc += d[k] * d[k];
     return acc;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Single stages of the step, for a stage-by-stage comparison with kernels that compute
+ * them from the same stored inputs (no value of the kernel enters here).  Step index
+ * `step` (1-based: the store counter is 1024 step + k).  Velocity pairs in the MAC layout
+ * of this file; arrays not used by a stage may be NULL.
+ *   OR_SMOKE_ADVECT1  out = store_1(A(a; (a_u, a_v), dt/2)), a_v = v after the forces
+ *   OR_SMOKE_JACOBI   out_q = store_(1 + it)(sweep it of the first projection from the
+ *                     iterate q (zeros when it = 1) with the divergence div), it = arg
+ *   OR_SMOKE_GRADSUB2 out = store_(J+2)(a - grad q), out2 = store_(J+3)(2 out - a)
+ *   OR_SMOKE_ADVECT4  out = store_(J+4)(A(a; (b_u, b_v), dt/2))
+ *   OR_SMOKE_GRADSUB5 out = store_(2J+5)(a - grad q)
+ * ---------------------------------------------------------------------------------- */
+int or_smoke_stage(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int stage, int arg, uint32_t step,
+                   const double *a_u, const double *a_v, const double *b_u, const double *b_v, const double *q,
+                   const double *div, double *out_u, double *out_v, double *out2_u, double *out2_v, double *out_q)
+{
+    const int n = sm->n, J = sm->jacobi;
+    const size_t nu = (size_t)(n + 1) * n, nv = (size_t)n * (n + 1), nc = (size_t)n * n;
+    const uint32_t base = 1024u * step;
+    int64_t sat = 0;
+    switch (stage) {
+    case OR_SMOKE_ADVECT1:
+    case OR_SMOKE_ADVECT4: {
+        const double *wu = stage == OR_SMOKE_ADVECT1 ? a_u : b_u, *wv = stage == OR_SMOKE_ADVECT1 ? a_v : b_v;
+        advect(sm, 0, a_u, wu, wv, 0.5 * sm->dt, out_u);
+        advect(sm, 1, a_v, wu, wv, 0.5 * sm->dt, out_v);
+        walls(n, out_u, out_v);
+        store_velocity(sm, sch, out_u, out_v, base + (stage == OR_SMOKE_ADVECT1 ? 1u : (uint32_t)J + 4u), &sat);
+        return 0;
+    }
+    case OR_SMOKE_JACOBI: {
+        if (arg < 1 || arg > J) return -1;
+        double *zero = NULL;
+        if (arg == 1) {
+            zero = calloc(nc, sizeof(double));
+            if (!zero) return -2;
+        }
+        jacobi_sweep(sm, sch, arg == 1 ? zero : q, out_q, div, base + 1u + (uint32_t)arg, &sat);
+        free(zero);
+        return 0;
+    }
+    case OR_SMOKE_GRADSUB2:
+    case OR_SMOKE_GRADSUB5: {
+        memcpy(out_u, a_u, sizeof(double) * nu);
+        memcpy(out_v, a_v, sizeof(double) * nv);
+        grad_subtract(sm, out_u, out_v, q);
+        store_velocity(sm, sch, out_u, out_v, base + (stage == OR_SMOKE_GRADSUB2 ? (uint32_t)J + 2u : 2u * J + 5u),
+                       &sat);
+        if (stage == OR_SMOKE_GRADSUB2) {
+            for (size_t k = 0; k < nu; ++k) out2_u[k] = 2.0 * out_u[k] - a_u[k];
+            for (size_t k = 0; k < nv; ++k) out2_v[k] = 2.0 * out_v[k] - a_v[k];
+            store_velocity(sm, sch, out2_u, out2_v, base + (uint32_t)J + 3u, &sat);
+        }
+        return 0;
+    }
+    default:
+        return -1;
+    }
 }

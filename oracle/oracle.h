@@ -203,6 +203,15 @@ typedef struct {       /* type 0: velocity (u and v), type 1: pressure q */
 int64_t or_smoke_step(const or_smoke_t *sm, const or_smoke_scheme_t *sch, uint32_t step, double *u, double *v,
                       double *d, double *q);
 double or_smoke_measure(const or_smoke_t *sm, const double *d);
+/* one stage of the step from given stored inputs (see or_smoke.c) */
+#define OR_SMOKE_ADVECT1 0
+#define OR_SMOKE_JACOBI 1
+#define OR_SMOKE_GRADSUB2 2
+#define OR_SMOKE_ADVECT4 3
+#define OR_SMOKE_GRADSUB5 4
+int or_smoke_stage(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int stage, int arg, uint32_t step,
+                   const double *a_u, const double *a_v, const double *b_u, const double *b_v, const double *q,
+                   const double *div, double *out_u, double *out_v, double *out2_u, double *out2_v, double *out_q);
 /* inject delta at the store (field 0 u, 1 v, 2 q; sample index; store counter) while active */
 void or_smoke_inject(int active, int field, uint32_t idx, uint32_t counter, double delta);
 /* +-sigma_h noise at every store of type h but the reflection and the wall faces (signs
@@ -212,6 +221,8 @@ void or_smoke_noise(int active, double sigma_v, double sigma_p, uint64_t seed, d
 void or_smoke_follow(const uint32_t *codes, int64_t n, double tau_v, double tau_p);
 /* record the oracle's own code of every store in order (buf NULL: off) */
 void or_smoke_record(uint32_t *buf, int64_t n);
+/* the same, also recording the value each store was offered (FP64, before the codec) */
+void or_smoke_record_values(uint32_t *buf, double *xs, int64_t n);
 int64_t or_smoke_recorded(void);
 /* the first violation: {store position, oracle code, kernel code}, the FP64 value there and
  * the distance of its fraction from the threshold in quanta */
