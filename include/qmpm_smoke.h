@@ -147,6 +147,35 @@ int qmpm_smoke_info(qmpm_smoke_handle h, qmpm_smoke_info_t *out);
  * QMPM_ERR_CUDA. */
 int qmpm_smoke_profile(qmpm_smoke_handle h, double *h_step_ms, double *h_jacobi_ms, int64_t *h_jacobi_launches);
 
+/* One stage of a quantized step, run by its own kernel launch on scene 0 from inputs the
+ * caller gives (the stage-by-stage parity check of the advection-reflection step, Sec. 8.1:
+ * every stage's stores compared with the FP64 oracle's from identical stored inputs).
+ * Inputs in the layouts of qmpm_smoke_set_state (u: n rows of n + 1 faces, v: n + 1 rows
+ * of n faces, cells n x n; FP32, host); stored inputs are encoded with nearest rounding, so values on
+ * the type's lattice are stored exactly.  step >= 1 is the step index of the stores (store
+ * counter 1024 step + k, as in qmpm_smoke_step).
+ *   QMPM_SMOKE_ADVECT1   a = (u, v after the forces; v stays FP32): out = store 1 of
+ *                        A(a; a, dt/2)
+ *   QMPM_SMOKE_JACOBI    sweep `arg` (1..jacobi) of the first projection from the stored
+ *                        iterate q (unused for arg 1) and the FP32 divergence div: store 1 + arg
+ *   QMPM_SMOKE_GRADSUB2  a = u~ (stored), q: out = store J + 2 of a - grad q, then store
+ *                        J + 3 of the reflection 2 out - a
+ *   QMPM_SMOKE_ADVECT4   a = u^ (stored), b = u' (stored): out = store J + 4 of A(a; b, dt/2)
+ *   QMPM_SMOKE_GRADSUB5  a = u~2 (stored), q: out = store 2 J + 5 of a - grad q
+ * h_codes (host) receives the stage's codes in store order: the u codes (k = row (n+1) +
+ * column) then the v codes (k = row n + column), or the n^2 pressure codes; GRADSUB2 writes
+ * both of its stores, 4 n (n+1) codes.  The call overwrites the scene's stored fields and
+ * leaves its step count as it was.  Synchronous.  Errors: QMPM_ERR_INVALID_ARG (FP32
+ * handle, unknown stage, missing input), QMPM_ERR_OOM, QMPM_ERR_CUDA. */
+#define QMPM_SMOKE_ADVECT1 0
+#define QMPM_SMOKE_JACOBI 1
+#define QMPM_SMOKE_GRADSUB2 2
+#define QMPM_SMOKE_ADVECT4 3
+#define QMPM_SMOKE_GRADSUB5 4
+int qmpm_smoke_stage(qmpm_smoke_handle h, int32_t stage, int32_t arg, uint32_t step, const float *h_a_u,
+                     const float *h_a_v, const float *h_b_u, const float *h_b_v, const float *h_q,
+                     const float *h_div, uint32_t *h_codes);
+
 /* Free everything the handle holds (synchronises its stream).  NULL is a no-op. */
 int qmpm_smoke_destroy(qmpm_smoke_handle h);
 

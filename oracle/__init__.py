@@ -587,9 +587,6 @@ def _bind_smoke(L):
     L.or_smoke_measure.argtypes = [P(Smoke), P(d)]
     L.or_smoke_measure.restype = d
     L.or_smoke_inject.argtypes = [ct.c_int, ct.c_int, ct.c_uint32, ct.c_uint32, d]
-    L.or_smoke_follow.argtypes = [P(ct.c_uint32), ct.c_int64, d, d]
-    L.or_smoke_follow_report.argtypes = [P(ct.c_int64), P(d)]
-    L.or_smoke_follow_first.argtypes = [P(ct.c_int64), P(d), P(d)]
     L.or_smoke_noise.argtypes = [ct.c_int, d, d, ct.c_uint64, d]
     L.or_smoke_record.argtypes = [P(ct.c_uint32), ct.c_int64]
     L.or_smoke_record_values.argtypes = [P(ct.c_uint32), P(d), ct.c_int64]
@@ -676,34 +673,6 @@ class smoke_noise:
 
     def __exit__(self, *exc):
         _smoke_lib().or_smoke_noise(0, 0.0, 0.0, 0, 0.0)
-        return False
-
-
-class smoke_follow:
-    """Context: the quantized smoke oracle follows the kernel's stored codes (every store in
-    order, uint32) at near-ties within tau quanta; .report = (stores, adopted, violations,
-    largest adopted distance in quanta)."""
-
-    def __init__(self, codes, tau_v, tau_p):
-        self.codes = np.ascontiguousarray(codes, dtype=np.uint32)
-        self.tau = (float(tau_v), float(tau_p))
-        self.report = None
-
-    def __enter__(self):
-        _smoke_lib().or_smoke_follow(_p(self.codes, ct.c_uint32), self.codes.size, *self.tau)
-        return self
-
-    def __exit__(self, *exc):
-        L = _smoke_lib()
-        out = (ct.c_int64 * 3)()
-        md = ct.c_double()
-        L.or_smoke_follow_report(out, ct.byref(md))
-        self.report = (int(out[0]), int(out[1]), int(out[2]), float(md.value))
-        fx, fd = ct.c_double(), ct.c_double()
-        L.or_smoke_follow_first(out, ct.byref(fx), ct.byref(fd))
-        self.first = {"pos": int(out[0]), "oracle": int(out[1]), "kernel": int(out[2]), "x": fx.value,
-                      "dist": fd.value} if self.report[2] else None
-        L.or_smoke_follow(None, 0, 0.0, 0.0)
         return False
 
 

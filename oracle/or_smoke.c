@@ -37,12 +37,9 @@
  * component 8 f + i % 8: one Philox block (counter (i / 8, c, f, 0)) serves eight
  * consecutive samples of a field.
  *
- * Follow mode (parity with a kernel that computes in FP32): a kernel's stored codes can
- * differ from these only where the FP64 value's fraction lies within rounding error of the
- * dither threshold.  Given the kernel's codes of every store in order, the oracle accepts a
- * code that differs by one from its own where the fraction is within tau quanta of the
- * threshold, continues from the kernel's code there (so both runs take the same rounding
- * decision), and counts every other difference as a violation.
+ * Single stages (or_smoke_stage) run one stage from given stored inputs, so that kernels
+ * can be compared with it stage by stage; record mode returns every store's code and the
+ * value it was offered.
  */
 #include "oracle.h"
 
@@ -179,23 +176,6 @@ static double store(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int fiel
 }
 
 static struct {
-    const uint32_t *codes;
-    int64_t n, pos, adopted, violations;
-    double tau[2], max_dist;
-    int64_t first[3];   /* first violation: store position, oracle code, kernel code */
-    double first_x, first_dist;
-} g_follow;
-
-void or_smoke_follow(const uint32_t *codes, int64_t n, double tau_v, double tau_p)
-{
-    memset(&g_follow, 0, sizeof(g_follow));
-    g_follow.codes = codes;
-    g_follow.n = n;
-    g_follow.tau[0] = tau_v;
-    g_follow.tau[1] = tau_p;
-}
-
-static struct {
     uint32_t *buf;
     double *xs;   /* optional: the value each store was offered */
     int64_t n, pos;
@@ -217,23 +197,6 @@ void or_smoke_record_values(uint32_t *buf, double *xs, int64_t n)
 
 int64_t or_smoke_recorded(void) { return g_record.pos; }
 
-void or_smoke_follow_first(int64_t out[3], double *x, double *dist)
-{
-    out[0] = g_follow.first[0];
-    out[1] = g_follow.first[1];
-    out[2] = g_follow.first[2];
-    *x = g_follow.first_x;
-    *dist = g_follow.first_dist;
-}
-
-void or_smoke_follow_report(int64_t out[3], double *max_dist)
-{
-    out[0] = g_follow.pos;
-    out[1] = g_follow.adopted;
-    out[2] = g_follow.violations;
-    *max_dist = g_follow.max_dist;
-}
-
 static double store_q(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int field, double x, uint32_t idx,
                       uint32_t counter, int64_t *sat)
 {
@@ -250,35 +213,6 @@ static double store_q(const or_smoke_t *sm, const or_smoke_scheme_t *sch, int fi
             if (g_record.xs) g_record.xs[g_record.pos] = x;
         }
         g_record.pos += 1;
-    }
-    if (g_follow.codes) {
-        if (g_follow.pos >= g_follow.n) {
-            g_follow.violations += 1;
-        } else {
-            const uint32_t k = g_follow.codes[g_follow.pos];
-            if (k != q) {
-                /* distance of the fraction from the rounding threshold, in quanta */
-                const double t = ldexp(x, frac), y = t - floor(t);
-                const double thr = sm->dither ? (double)r * 0x1p-32 : 0.5;
-                const double dist = fabs(y - thr);
-                const int64_t dk = (int64_t)k - (int64_t)q;
-                if ((dk == 1 || dk == -1) && dist <= (field == 2 ? g_follow.tau[1] : g_follow.tau[0])) {
-                    g_follow.adopted += 1;
-                    if (dist > g_follow.max_dist) g_follow.max_dist = dist;
-                } else {
-                    if (g_follow.violations == 0) {
-                        g_follow.first[0] = g_follow.pos;
-                        g_follow.first[1] = q;
-                        g_follow.first[2] = k;
-                        g_follow.first_x = x;
-                        g_follow.first_dist = dist;
-                    }
-                    g_follow.violations += 1;
-                }
-                q = k;
-            }
-        }
-        g_follow.pos += 1;
     }
     return or_decode(q, frac, offset);
 }

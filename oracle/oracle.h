@@ -217,18 +217,11 @@ void or_smoke_inject(int active, int field, uint32_t idx, uint32_t counter, doub
 /* +-sigma_h noise at every store of type h but the reflection and the wall faces (signs
  * from Philox with key seed), times sign; active 0 turns it off */
 void or_smoke_noise(int active, double sigma_v, double sigma_p, uint64_t seed, double sign);
-/* follow a kernel's codes of every store in order (codes NULL: off); tau in quanta */
-void or_smoke_follow(const uint32_t *codes, int64_t n, double tau_v, double tau_p);
 /* record the oracle's own code of every store in order (buf NULL: off) */
 void or_smoke_record(uint32_t *buf, int64_t n);
 /* the same, also recording the value each store was offered (FP64, before the codec) */
 void or_smoke_record_values(uint32_t *buf, double *xs, int64_t n);
 int64_t or_smoke_recorded(void);
-/* the first violation: {store position, oracle code, kernel code}, the FP64 value there and
- * the distance of its fraction from the threshold in quanta */
-void or_smoke_follow_first(int64_t out[3], double *x, double *dist);
-/* out = {stores seen, codes adopted at near-ties, violations}; largest adopted distance */
-void or_smoke_follow_report(int64_t out[3], double *max_dist);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,8 @@ Eq. 10 (or its memory-bound form) for the bit widths, and apply the scheme to th
 high-resolution run.  Forward and backward passes run in the library's FP32 adjoint;
 the solve is the library's host solver.
 """
+import os
+
 from . import qmpm, scenes
 
 
@@ -214,3 +216,93 @@ def iterate_scheme(scene, state0, T, eps, measure=qmpm.MEASURE_KINETIC_ENERGY, m
             break
         seen.append(scheme)
     return scheme, history
+
+
+def cubes3d_second_order_scheme(eps=0.01, cube_cells=40, grid_log2=8, T=None, pairs=2, iters=6, log=None):
+    """The cubes' scheme at relative error eps on the final positions, Algorithm 1 plus the
+    second-order refinement: the sensitivities g_h come from the same 16 cubes at half
+    resolution (the scaling procedure of Sec. 8.3), the ranges from the FP32 run at the
+    resolution the scheme runs at (so C's window holds its full-resolution values), and
+    second_order_scheme refines the scheme there.  Returns (scheme, report)."""
+    sc_lo, s0_lo = scenes.cubes3d_scene(cube_cells=cube_cells // 2, grid_log2=grid_log2 - 1)
+    sc, s0 = scenes.cubes3d_scene(cube_cells=cube_cells, grid_log2=grid_log2)
+    steps = T if T is not None else sc["steps"]
+    info_lo = position_sensitivities(sc_lo, s0_lo, steps)
+    rng_hi = qmpm.sensitivities(sc, s0, steps)  # the forward records the ranges
+    info = dict(info_lo, lo=rng_hi["lo"], hi=rng_hi["hi"])
+    scheme, rep = second_order_scheme(sc, s0, steps, eps, info, pairs=pairs, iters=iters,
+                                      containers=(64, 0, 0, 0), log=log)
+    rep["sensitivities"] = {k: info_lo[k] for k in ("g", "z", "P")}
+    rep["ranges"] = {"lo": list(rng_hi["lo"]), "hi": list(rng_hi["hi"])}
+    return scheme, rep
+
+
+SCHEME_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "schemes")
+
+
+def cached_scheme_path(name, eps):
+    return os.path.join(SCHEME_DIR, f"{name}_eps{eps:g}.json")
+
+
+def load_cubes3d_scheme(eps=0.01):
+    """The cubes' second-order scheme as written by `python -m paper_2207_04658_b300.autoquant
+    cubes3d --eps EPS` (it takes several minutes to compute), with the hash of the scene it
+    was computed for; None when absent or computed for another scene."""
+    import json
+    path = cached_scheme_path("cubes3d", eps)
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    sc, s0 = scenes.cubes3d_scene()
+    if d.get("scene_hash") != scene_hash(sc, s0):
+        return None
+    return d
+
+
+def scene_hash(sc, s0):
+    import hashlib
+    import json
+    import numpy as np
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(s0, dtype=np.float64).tobytes())
+    h.update(json.dumps({k: sc[k] for k in sorted(sc) if k not in ("resort_every",)}, sort_keys=True,
+                        default=str).encode())
+    return h.hexdigest()
+
+
+def _summary(rep):
+    rounds = []
+    for r in rep["rounds"]:
+        rounds.append({"scheme": r["scheme"], "beta": r["beta"], "g": r["g"], "pred_bias": r["pred_bias"],
+                       "pred_var": r["pred_var"],
+                       "moments": [{k: m[k] for k in ("shift", "spread", "z0")} for m in r["moments"]]})
+    return {"algorithm1": rep["algorithm1"], "rounds": rounds, "z": rep["z"], "eps": rep["eps"],
+            "sensitivities": rep["sensitivities"], "ranges": rep["ranges"]}
+
+
+def main():
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description="solve and cache a workload's second-order scheme")
+    ap.add_argument("workload", choices=["cubes3d"])
+    ap.add_argument("--eps", type=float, default=0.01)
+    args = ap.parse_args()
+    t0 = time.time()
+    scheme, rep = cubes3d_second_order_scheme(args.eps, log=lambda *a: print(f"[{time.time() - t0:6.0f}s]", *a,
+                                                                               flush=True))
+    sc, s0 = scenes.cubes3d_scene()
+    out = {"what": "3D fixed-corotated cubes (8,192,000 particles, 256^3): Algorithm 1 from half-resolution "
+                   "sensitivities, refined with the second-order term at full resolution",
+           "eps": args.eps, "scheme": scheme, "scene_hash": scene_hash(sc, s0), "report": _summary(rep),
+           "seconds": time.time() - t0}
+    os.makedirs(SCHEME_DIR, exist_ok=True)
+    path = cached_scheme_path(args.workload, args.eps)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1, default=float)
+    print(path, {k: (v["bits"], v["frac"]) for k, v in scheme.items()})
+
+
+if __name__ == "__main__":
+    main()

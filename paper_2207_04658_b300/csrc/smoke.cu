@@ -693,6 +693,45 @@ __global__ void __launch_bounds__(kT) readback_kernel(Params P, int s0, float *u
     }
 }
 
+// Stage inputs of scene 0 (qmpm_smoke_stage): a velocity pair in the oracle layout into
+// the stored fields fu, fv (nearest rounding: values on the type's lattice are stored as
+// they are), or n^2 cell values into the stored pressure field f.
+__global__ void __launch_bounds__(kT) set_pair_kernel(Params P, Fld fu, Fld fv, const float *u, const float *v)
+{
+    const int n = P.n;
+    const int64_t nu = (int64_t)n * P.su, nv = (int64_t)(n + 1) * n;
+    const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (t - (threadIdx.x & 31) >= nu + nv) return;
+    uint32_t *out;
+    int64_t pidx;
+    float x = 0.0f;
+    bool valid = true;
+    if (t < nu) {
+        const int i = (int)((uint32_t)t % (uint32_t)P.su), j = (int)((uint32_t)t / (uint32_t)P.su);
+        valid = i <= n;
+        if (valid) x = u[(int64_t)j * (n + 1) + i];
+        out = fu.p;
+        pidx = t;
+    } else {
+        pidx = t - nu;
+        x = v[pidx];
+        out = fv.p;
+    }
+    int flags = 0;
+    uint32_t code = encode_f32(x, P.cc[0], false, 0u, flags);
+    if (!valid) code = 0u;
+    put_codes(out, pidx, code, P.bits[0]);
+}
+
+__global__ void __launch_bounds__(kT) set_cells_kernel(Params P, Fld f, const float *x)
+{
+    const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;  // n^2 is a multiple of 32
+    if (t - (threadIdx.x & 31) >= (int64_t)P.n * P.n) return;
+    int flags = 0;
+    const uint32_t code = encode_f32(x[t], P.cc[1], false, 0u, flags);
+    put_codes(f.p, t, code, P.bits[1]);
+}
+
 }  // namespace smoke
 }  // namespace qmpm
 
@@ -1270,3 +1309,102 @@ int qmpm_smoke_destroy(qmpm_smoke_handle h)
 }
 
 }  // extern "C"
+
+int qmpm_smoke_stage(qmpm_smoke_handle h, int32_t stage, int32_t arg, uint32_t step, const float *h_a_u,
+                     const float *h_a_v, const float *h_b_u, const float *h_b_v, const float *h_q,
+                     const float *h_div, uint32_t *h_codes)
+{
+    if (!h || !h->quant || stage < QMPM_SMOKE_ADVECT1 || stage > QMPM_SMOKE_GRADSUB5 || step < 1 || !h_codes)
+        return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_stage: needs a quantized handle, a stage, step >= 1 and h_codes");
+    Params P = h->p;
+    const int n = P.n, J = P.J;
+    const bool need_a = true, need_b = stage == QMPM_SMOKE_ADVECT4;
+    const bool need_q = stage == QMPM_SMOKE_GRADSUB2 || stage == QMPM_SMOKE_GRADSUB5 ||
+                        (stage == QMPM_SMOKE_JACOBI && arg > 1);
+    const bool need_div = stage == QMPM_SMOKE_JACOBI;
+    if (stage == QMPM_SMOKE_JACOBI && (arg < 1 || arg > J))
+        return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_stage: the sweep index must be in 1..jacobi");
+    if ((stage != QMPM_SMOKE_JACOBI && (!h_a_u || !h_a_v)) || (need_b && (!h_b_u || !h_b_v)) || (need_q && !h_q) ||
+        (need_div && !h_div))
+        return fail(QMPM_ERR_INVALID_ARG, "qmpm_smoke_stage: an input of the stage is NULL");
+    const int64_t nu = (int64_t)n * (n + 1), nc = (int64_t)n * n;
+    const int64_t V = 2 * nu;  // velocity codes of one store
+    const int64_t n_codes = stage == QMPM_SMOKE_JACOBI ? nc : stage == QMPM_SMOKE_GRADSUB2 ? 2 * V : V;
+    std::vector<void *> tmp;
+    auto dal = [&](size_t bytes) -> void * {
+        void *ptr = nullptr;
+        if (cudaMalloc(&ptr, bytes) != cudaSuccess) return nullptr;
+        tmp.push_back(ptr);
+        return ptr;
+    };
+    auto cleanup = [&]() {
+        for (void *ptr : tmp) cudaFree(ptr);
+    };
+    float *d_au = (float *)dal(sizeof(float) * nu), *d_av = (float *)dal(sizeof(float) * nu);
+    float *d_bu = (float *)dal(sizeof(float) * nu), *d_bv = (float *)dal(sizeof(float) * nu);
+    float *d_q = (float *)dal(sizeof(float) * nc);
+    uint32_t *d_tr = (uint32_t *)dal(sizeof(uint32_t) * (size_t)n_codes);
+    if (!d_au || !d_av || !d_bu || !d_bv || !d_q || !d_tr) {
+        cudaGetLastError();
+        cleanup();
+        return fail(QMPM_ERR_OOM, "qmpm_smoke_stage: device allocation failed");
+    }
+    cudaStream_t st = h->st;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](float *d, const float *hsrc, int64_t cnt) {
+        if (e == cudaSuccess && hsrc) e = cudaMemcpyAsync(d, hsrc, sizeof(float) * cnt, cudaMemcpyHostToDevice, st);
+    };
+    up(d_au, h_a_u, nu);
+    up(d_av, h_a_v, nu);
+    up(d_bu, h_b_u, nu);
+    up(d_bv, h_b_v, nu);
+    up(d_q, h_q, nc);
+    const uint32_t done = step - 1u;  // the kernels store with step index = steps done + 1
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.ctr, &done, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_tr, 0, sizeof(uint32_t) * (size_t)n_codes, st);
+    const int64_t nfaces = (int64_t)n * P.su + nu;
+    const unsigned gf = (unsigned)((nfaces + kT - 1) / kT), gc = (unsigned)((nc + kT - 1) / kT);
+    if (e == cudaSuccess) {
+        switch (stage) {
+        case QMPM_SMOKE_ADVECT1:
+            // u stored; v after the forces is FP32 (vf)
+            set_pair_kernel<<<gf, kT, 0, st>>>(P, P.u, P.v, d_au, d_av);
+            e = cudaMemcpyAsync(P.vf, d_av, sizeof(float) * nu, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) advect_vel_kernel<true, 1><<<gf, kT, 0, st>>>(P, d_tr);
+            break;
+        case QMPM_SMOKE_JACOBI: {
+            if (need_q) set_cells_kernel<<<gc, kT, 0, st>>>(P, P.q[0], d_q);
+            e = cudaMemcpyAsync(P.div, h_div, sizeof(float) * nc, cudaMemcpyHostToDevice, st);
+            const dim3 gj((unsigned)(((n + kTX - 1) / kTX) * (n / kTY)), 1);
+            if (e == cudaSuccess) jacobi_kernel<true><<<gj, kT, kJacobiSmem, st>>>(P, arg, 1, 1u, 0, d_tr);
+            break;
+        }
+        case QMPM_SMOKE_GRADSUB2:
+        case QMPM_SMOKE_GRADSUB5:
+            P.qfin = 0;
+            set_cells_kernel<<<gc, kT, 0, st>>>(P, P.q[0], d_q);
+            if (stage == QMPM_SMOKE_GRADSUB2) {
+                set_pair_kernel<<<gf, kT, 0, st>>>(P, P.ut, P.vt, d_au, d_av);
+                gradsub_kernel<true, 2><<<gf, kT, 0, st>>>(P, d_tr, d_tr + V);
+            } else {
+                set_pair_kernel<<<gf, kT, 0, st>>>(P, P.u, P.v, d_au, d_av);
+                gradsub_kernel<true, 5><<<gf, kT, 0, st>>>(P, d_tr, nullptr);
+            }
+            break;
+        case QMPM_SMOKE_ADVECT4:
+            set_pair_kernel<<<gf, kT, 0, st>>>(P, P.ut, P.vt, d_au, d_av);
+            set_pair_kernel<<<gf, kT, 0, st>>>(P, P.up, P.vp, d_bu, d_bv);
+            advect_vel_kernel<true, 4><<<gf, kT, 0, st>>>(P, d_tr);
+            break;
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_codes, d_tr, sizeof(uint32_t) * (size_t)n_codes, cudaMemcpyDeviceToHost, st);
+    const uint32_t back = (uint32_t)h->steps;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.ctr, &back, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail("qmpm_smoke_stage", e);
+    return QMPM_OK;
+}

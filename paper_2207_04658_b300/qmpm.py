@@ -257,6 +257,8 @@ _SIGNATURES += [
     ("qmpm_smoke_ranges", ct.c_int, [ct.c_void_p, _P(ct.c_float), _P(ct.c_float), _P(ct.c_int64)]),
     ("qmpm_smoke_info", ct.c_int, [ct.c_void_p, _P(qmpm_smoke_info_t)]),
     ("qmpm_smoke_profile", ct.c_int, [ct.c_void_p, _P(ct.c_double), _P(ct.c_double), _P(ct.c_int64)]),
+    ("qmpm_smoke_stage", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_uint32] + [_P(ct.c_float)] * 6
+     + [_P(ct.c_uint32)]),
     ("qmpm_smoke_destroy", ct.c_int, [ct.c_void_p]),
 ]
 OPTIONAL_SIGNATURES = [

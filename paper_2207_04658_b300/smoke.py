@@ -130,6 +130,24 @@ class Smoke:
         _check(lib().qmpm_smoke_measure(self.h, _dptr(z, ct.c_double)))
         return z
 
+    STAGES = {"advect1": 0, "jacobi": 1, "gradsub2": 2, "advect4": 3, "gradsub5": 4}
+
+    def stage(self, stage, step, arg=0, a=None, b=None, q=None, div=None):
+        """One stage of a quantized step on scene 0 from given inputs (qmpm_smoke_stage):
+        a, b are (u, v) pairs, q and div cell arrays.  Returns the codes of the stage's
+        stores in order.  Overwrites the scene's stored fields."""
+        n = self.n
+        nu = n * (n + 1)
+        m = {"jacobi": n * n, "gradsub2": 4 * nu}.get(stage, 2 * nu)
+        out = np.zeros(m, dtype=np.uint32)
+        au, av = (_f32(a[0], (n, n + 1)), _f32(a[1], (n + 1, n))) if a is not None else (None, None)
+        bu, bv = (_f32(b[0], (n, n + 1)), _f32(b[1], (n + 1, n))) if b is not None else (None, None)
+        qq, dv = _f32(q, (n, n)), _f32(div, (n, n))
+        p = lambda x: _dptr(x, ct.c_float) if x is not None else None  # noqa: E731
+        _check(lib().qmpm_smoke_stage(self.h, self.STAGES[stage], int(arg), int(step), p(au), p(av), p(bu), p(bv),
+                                      p(qq), p(dv), _dptr(out, ct.c_uint32)))
+        return out
+
     def readback(self, scene=0):
         n = self.n
         out = {"u": np.zeros((n, n + 1), np.float32), "v": np.zeros((n + 1, n), np.float32),

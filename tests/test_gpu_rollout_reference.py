@@ -6,13 +6,19 @@ The evaluation function is the vector of final positions (relative error bound e
 positions: RMS position error <= eps x RMS position) with z = mean |x|^2 reported beside it.
 Bars: the FP32 run of the library's kernels matches the FP64 oracle to 1e-3 relative in z
 and RMS position (both integrate the same explicit scheme; FP32 rounding in a stiff,
-colliding scene grows to that size over 1000 steps); the quantized run with the scheme that
-Algorithm 1 solves at eps = 0.01 keeps the position measurement z within eps of the FP64
-run, and the RMS position error within the paper's success band (Sec. 8.1: 3 eps) on the
-half-resolution scene the sensitivities come from.  Applied unchanged at full resolution
-(the scaling procedure of Sec. 8.3) the RMS position error measures 3.1 eps (one B300
-run), so the full-resolution bar is 4 eps.  Positions are compared on the stored sample
-of particles (every k-th particle by initial index)."""
+colliding scene grows to that size over 1000 steps).  The quantized runs keep z within eps
+of the FP64 run and the RMS position error within the paper's success band (Sec. 8.1:
+3 eps), for two dither seeds:
+  * Algorithm 1 alone, from the half-resolution sensitivities, on the half-resolution scene
+    (its linear error model holds there within a factor of about 3);
+  * the second-order scheme (Algorithm 1 refined with the bias and spread that noise
+    injection measures at the resolution the scheme runs at) at both resolutions: the one
+    committed for the full-resolution benchmark, and one solved here for the
+    half-resolution scene.  Algorithm 1 alone reaches 2.6 eps at full resolution, where the
+    dithered deformation gradient's random walk shifts the positions systematically; its
+    saturations are counted and must be zero for the second-order schemes.
+Positions are compared on the stored sample of particles (every k-th particle by initial
+index)."""
 import json
 import os
 
@@ -92,17 +98,40 @@ def solved():
     return scheme, rep
 
 
-@pytest.mark.parametrize("half", [True, False])
-def test_solved_scheme_rollout_within_the_error_bound(q, solved, half):
-    ref = load(f"cubes3d_fp64_{'n128' if half else 'n256'}_T1000.json")
-    sc, s0 = scene_of(half)
+def test_algorithm1_scheme_rollout_within_the_error_bound(q, solved):
+    ref = load("cubes3d_fp64_n128_T1000.json")
+    sc, s0 = scene_of(True)
     check_fixture(ref, sc, s0)
     scheme, rep = solved
     eps = 0.01
-    st, stats = rollout(q, sc, s0, scheme, ref["steps"])
-    assert np.isfinite(st).all()
-    dz, dx = compare(st, ref)
     # the predicted error (Eq. 8) of the solved scheme is within the bound by construction
     assert rep["solve"]["pred_err"] <= (eps * rep["sensitivities"]["z"]) ** 2
-    assert dz <= eps, dz
-    assert dx <= (3 if half else 4) * eps, dx
+    for seed in (None, 777):
+        st, stats = rollout(q, dict(sc, seed=seed) if seed else sc, s0, scheme, ref["steps"])
+        assert np.isfinite(st).all()
+        dz, dx = compare(st, ref)
+        assert dz <= eps and dx <= 3 * eps, (seed, dz, dx)
+
+
+@pytest.fixture(scope="module")
+def second_order():
+    from paper_2207_04658_b300 import autoquant
+    full = autoquant.load_cubes3d_scheme(0.01)
+    full = full["scheme"] if full is not None else autoquant.cubes3d_second_order_scheme(0.01)[0]
+    half, rep = autoquant.cubes3d_second_order_scheme(0.01, cube_cells=20, grid_log2=7)
+    return {False: full, True: half}
+
+
+@pytest.mark.parametrize("half", [True, False])
+def test_second_order_scheme_rollout_within_the_error_bound(q, second_order, half):
+    ref = load(f"cubes3d_fp64_{'n128' if half else 'n256'}_T1000.json")
+    sc, s0 = scene_of(half)
+    check_fixture(ref, sc, s0)
+    scheme = second_order[half]
+    eps = 0.01
+    for seed in (None, 777):
+        st, stats = rollout(q, dict(sc, seed=seed) if seed else sc, s0, scheme, ref["steps"])
+        assert np.isfinite(st).all()
+        dz, dx = compare(st, ref)
+        assert dz <= eps and dx <= 3 * eps, (half, seed, dz, dx, scheme)
+        assert stats["saturations"] == [0, 0, 0, 0], stats["saturations"]

@@ -14,8 +14,8 @@ mathematics fixes, CPU only:
   - the store-event enumeration and injection hook: central differences over every
     store, combined with the dither's rounding variance Delta^2 / 6 (Sec. 5), predict the
     variance of z over dither seeds (Eq. 8's linear error propagation);
-  - follow mode: codes taken from the oracle itself are all accepted, a code moved by one
-    far from a tie is a violation;
+  - single stages: the step's stores up to the second advection, rebuilt from or_smoke_stage's
+    stages, equal or_smoke_step's codes;
   - antithetic noise injection estimates the FD sensitivities g_h, and the mean shift of
     z under dithered stores equals that under noise of the same variance."""
 import numpy as np
@@ -230,42 +230,6 @@ def test_predicted_variance_matches_dither_runs(oracle):
     assert 0.75 < obs / parts.sum() < 1.2, (obs, parts)
 
 
-def test_follow_accepts_own_codes_and_rejects_far_changes(oracle):
-    sc, T = plume(n=8, jacobi=4, T=2)
-    sch = {"v": dict(bits=16, frac=10, offset=-(1 << 15)), "p": dict(bits=16, frac=14, offset=-(1 << 15))}
-    ev = oracle.smoke_store_events(8, 4, T)
-    codes = oracle.smoke_codes(sc, sch, T)
-    assert codes.size == len(ev)
-    ref = oracle.SmokeRollout(sc, sch)
-    ref.step(T)
-    mine = oracle.SmokeRollout(sc, sch)
-    with oracle.smoke_follow(codes, 0.0, 0.0) as f:
-        mine.step(T)
-    assert f.report == (len(ev), 0, 0, 0.0)
-    assert np.array_equal(mine.u, ref.u) and np.array_equal(mine.d, ref.d)
-    # a code moved by one is adopted only within tau of its threshold: with tau = 0 it is
-    # a violation, and the run continues from it
-    bad = codes.copy()
-    k = len(bad) // 3
-    bad[k] += 1
-    other = oracle.SmokeRollout(sc, sch)
-    with oracle.smoke_follow(bad, 0.0, 0.0) as f:
-        other.step(T)
-    assert f.report[1] == 0 and f.report[2] >= 1
-    # with tau = 1 quantum every one-code difference is within reach and adopted
-    other = oracle.SmokeRollout(sc, sch)
-    with oracle.smoke_follow(bad, 1.0, 1.0) as f:
-        other.step(T)
-    assert f.report[1] >= 1 and f.report[2] == 0
-    # a code moved by two is never a near-tie
-    bad2 = codes.copy()
-    bad2[k] += 2
-    other = oracle.SmokeRollout(sc, sch)
-    with oracle.smoke_follow(bad2, 1.0, 1.0) as f:
-        other.step(T)
-    assert f.report[2] >= 1
-
-
 def test_antithetic_noise_estimates_the_sensitivities(oracle):
     """Over random +-sigma_h injections at every store of type h, E[((z+ - z-) / 2)^2] is
     sigma_h^2 g_h (the FD sum over the same stores): the estimator the kernels use for
@@ -322,3 +286,47 @@ def test_dither_bias_has_the_sign_and_size_of_equal_variance_noise(oracle):
     assert zq.mean() < -5 * se_q and zn.mean() < -5 * se_n, (zq.mean(), zn.mean(), se_q, se_n)
     assert 0.5 < zq.mean() / zn.mean() < 2.0, (zq.mean(), zn.mean())
     assert 0.6 < zq.std() / zn.std() < 1.25
+
+
+def test_stages_rebuild_the_step(oracle):
+    """Advection, the first projection's sweeps, the gradient subtraction with the
+    reflection and the second advection, each from or_smoke_stage with the previous stage's
+    stored output, give exactly the codes or_smoke_step stores (no source, no buoyancy: the
+    forces change nothing)."""
+    import ctypes as ct
+    n, J, step = 32, 6, 2
+    sc = dict(n=n, jacobi=J, dt=0.01, buoyancy=0.0, v_in=0.0, src=(1.0, 1.0, -1.0, -1.0), seed=5)
+    sch = {"v": dict(bits=16, frac=12, offset=-(1 << 15)), "p": dict(bits=16, frac=18, offset=-(1 << 15))}
+    gen = np.random.default_rng(4)
+    u = np.round(gen.normal(0, 0.3, (n, n + 1)) * 4096) / 4096
+    v = np.round(gen.normal(0, 0.3, (n + 1, n)) * 4096) / 4096
+    u[:, 0] = u[:, -1] = 0.0
+    v[0, :] = v[-1, :] = 0.0
+    # the whole step, recording every store
+    total = 5 * 2 * n * (n + 1) + 2 * J * n * n
+    rec = np.zeros(total, dtype=np.uint32)
+    L = oracle.lib()
+    L.or_smoke_record(rec.ctypes.data_as(ct.POINTER(ct.c_uint32)), total)
+    try:
+        o = oracle.SmokeRollout(sc, sch, u, v, np.zeros((n, n)))
+        o.t = step - 1
+        o.step(1)
+    finally:
+        L.or_smoke_record(None, 0)
+    # the same from single stages
+    parts = []
+    r = oracle.smoke_stage(sc, sch, "advect1", step, a=(u, v))
+    parts.append(r["codes"])
+    ut, vt = r["u"], r["v"]
+    div = (ut[:, 1:] - ut[:, :-1] + vt[1:, :] - vt[:-1, :]) * n
+    q = np.zeros((n, n))
+    for it in range(1, J + 1):
+        r = oracle.smoke_stage(sc, sch, "jacobi", step, arg=it, q=q, div=div)
+        parts.append(r["codes"])
+        q = r["q"]
+    r = oracle.smoke_stage(sc, sch, "gradsub2", step, a=(ut, vt), q=q)
+    parts.append(r["codes"])
+    r = oracle.smoke_stage(sc, sch, "advect4", step, a=(r["u2"], r["v2"]), b=(r["u"], r["v"]))
+    parts.append(r["codes"])
+    built = np.concatenate(parts)
+    assert np.array_equal(built, rec[:built.size])
