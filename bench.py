@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
-    ap.add_argument("--serving-duration", type=float, default=10.0,
+    ap.add_argument("--serving-duration", type=float, default=60.0,
                     help="seconds of Poisson arrivals in the serving run (0: skip it)")
     ap.add_argument("--fixed-scheme", action="store_true",
                     help="hand-written scheme instead of the solved one (quick runs)")
@@ -94,10 +94,13 @@ def workload(name, scale=1.0, seed_offset=0, scheme=None):
         # of the interval (8 ... 128, 2^27 particles) left the step kernel within 0.2 % while
         # the amortised sort (11.5 ms a pass) fell from 1.43 to 0.18 ms per step
         sc, s0 = scenes.dambreak3d_scene(column_cells=cells, seed=3 + seed_offset, resort_every=64)
-        sch = scenes.fixed_scheme_3d("fluid", C=(16, -2048.0, 2048.0))
+        sch = scheme if scheme is not None else scenes.fixed_scheme_3d("fluid", C=(16, -2048.0, 2048.0))
         desc = {"workload": "3D weakly compressible dam break", "particles": int(s0.shape[0]),
                 "grid": "512^3", "dt": sc["dt"], "bulk": sc["bulk"], "ppc": 8,
-                "resort_every": sc["resort_every"]}
+                "resort_every": sc["resort_every"],
+                "scheme": {k: [f["bits"], f["frac"]] for k, f in sch.items()},
+                "scheme_source": ("Algorithm 1, eps 0.01 on final positions, sensitivities of the column at "
+                                  "quarter resolution" if scheme is not None else "fixed")}
     else:
         sc, s0 = scenes.block2d_scene(seed=1 + seed_offset)
         sch = scenes.block2d_scheme()
@@ -269,24 +272,118 @@ def alu_roofline(kernel, avg_ms, winst, tinst, peaks, **extra):
     return out
 
 
+class _DevArray:
+    """A raw device buffer seen by torch without a copy (__cuda_array_interface__)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2}
+
+
+def device_positions(qmpm, torch, g):
+    """Positions of a resident scene as a device tensor [N, dim] in initial particle order,
+    decoded on the device (the packed words through qmpm_unpack_f32, FP32 words as they
+    are); nothing crosses the host link."""
+    w, ld, ids = qmpm.qmpm_state_device(g.h)
+    N, nc, dim = g.N, g.n_comp, g.dim
+    idx = torch.as_tensor(_DevArray(ids, N, "<i8"), device="cuda")
+    if g.quantized:
+        vals = torch.empty((N, nc), dtype=torch.float32, device="cuda")
+        qmpm.qmpm_unpack_f32(dim, qmpm.MATERIALS[g.material], g._scheme_struct, w, N, ld, vals.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+        pos = vals[:, :dim]
+    else:
+        planes = torch.as_tensor(_DevArray(w, nc * ld, "<f4"), device="cuda").view(nc, ld)
+        pos = planes[:dim, :N].t()
+    out = torch.empty((N, dim), dtype=torch.float32, device="cuda")
+    out[idx] = pos
+    torch.cuda.synchronize()
+    return out
+
+
+def dambreak_variants(qmpm, torch, args, dc, peaks):
+    """The dam break as the scaling experiment states it (Sec. 8.3): Algorithm 1's schemes at
+    relative error bounds 0.1 and 0.01 on the final positions (sensitivities and ranges of the
+    column at quarter resolution), each with dithered and with round-to-nearest stores, timed
+    like the headline and run for the scene's full step count against the FP32 run of the
+    same kernels (z and RMS position error, compared on the device).  Returns the variants
+    and the scheme of the headline (eps 0.01, dithered)."""
+    from paper_2207_04658_b300 import autoquant
+    schemes, info = autoquant.dambreak3d_schemes((0.1, 0.01))
+    sc, s0, _, desc = workload("dambreak3d", args.scale, seed_offset=dc.rank)
+    T = int(sc["steps"])
+    g32 = qmpm.Scene(sc, None, s0)
+    g32.step(T)
+    x32 = device_positions(qmpm, torch, g32)
+    z32 = float((x32.double() ** 2).sum(1).mean())
+    rms = float(torch.sqrt((x32.double() ** 2).sum(1).mean()))
+    g32.close()
+    out = []
+    for eps in (0.1, 0.01):
+        scheme, res = schemes[eps]
+        for dither in (True, False):
+            s = dict(sc, dither=dither)
+            k = max(8, min(args.steps, 64))
+            g, ms, prof, st = time_scene(qmpm, torch, s, s0, scheme, k, args.warmup, dc)
+            W = g.n_words
+            g.close()
+            gq = qmpm.Scene(s, scheme, s0, stats=True)
+            gq.step(T)
+            xq = device_positions(qmpm, torch, gq)
+            sat = gq.readback(state=False, ids=False)["stats"]["saturations"]
+            gq.close()
+            d = (xq.double() - x32.double())
+            err = float(torch.sqrt((d ** 2).sum(1).mean())) / rms
+            zq = float((xq.double() ** 2).sum(1).mean())
+            del xq, d
+            out.append({"eps": eps, "dither": dither, "bits": res["bits"], "frac": res["frac"],
+                        "words_per_particle": W, "bytes_per_particle": 4 * W,
+                        "value": dc.world * s0.shape[0] * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k,
+                        "timed_steps": k,
+                        "step_kernel_ms": round(prof["step_ms"] / max(1, prof["step_launches"]), 4),
+                        "accuracy": {"steps": T, "z_rel_err": abs(zq - z32) / abs(z32), "rms_pos_err_rel": err,
+                                     "saturations": sat, "within_eps": err <= eps, "within_3eps": err <= 3 * eps,
+                                     "reference": "FP32 run of the same kernels (an FP64 oracle run of 2^27 "
+                                                  "particles is out of reach on the host; the reduced case is "
+                                                  "checked against the FP64 oracle in tests/test_gpu_dambreak.py)"}})
+            torch.cuda.empty_cache()
+    return out, schemes[0.01][0], info
+
+
 def accuracy(qmpm, sc, s0, sch):
     """Full rollouts (the scene's step count) of the quantized and the FP32 state from the
     same initial state: relative error of z = mean |x|^2 and RMS per-particle position
-    error over RMS position (the bound the scheme was solved for)."""
+    error over RMS position (the bound the scheme was solved for), compared on the device."""
+    import torch
     steps = int(sc.get("steps", 1000))
     out = {}
     for name, scheme in (("quant", sch), ("fp32", None)):
         g = qmpm.Scene(sc, scheme, s0, stats=True)
         g.step(steps)
-        out[name] = (g.measure(), g.state_by_id(), g.readback(state=False, ids=False)["stats"])
+        out[name] = (device_positions(qmpm, torch, g).double(), g.readback(state=False, ids=False)["stats"])
         g.close()
-    zq, zf = out["quant"][0], out["fp32"][0]
-    d = out["quant"][1][:, :sc["dim"]] - out["fp32"][1][:, :sc["dim"]]
-    rms_err = float(np.sqrt((d ** 2).sum(1).mean()))
-    rms_pos = float(np.sqrt((out["fp32"][1][:, :sc["dim"]] ** 2).sum(1).mean()))
+    xq, xf = out["quant"][0], out["fp32"][0]
+    zq, zf = float((xq ** 2).sum(1).mean()), float((xf ** 2).sum(1).mean())
+    rms_err = float(torch.sqrt(((xq - xf) ** 2).sum(1).mean()))
+    rms_pos = float(torch.sqrt((xf ** 2).sum(1).mean()))
     return {"steps": steps, "z_quant": zq, "z_fp32": zf, "z_rel_err": abs(zq - zf) / abs(zf),
-            "rms_pos_err_rel": rms_err / rms_pos, "saturations": out["quant"][2]["saturations"],
-            "reference": "FP32 run of the same kernels (the FP64 oracle is too slow at this size)"}
+            "rms_pos_err_rel": rms_err / rms_pos, "saturations": out["quant"][1]["saturations"],
+            "reference": "FP32 run of the same kernels (the FP64 oracle comparison at this size is in "
+                         "tests/test_gpu_rollout_reference.py)"}
+
+
+def latency_spread(lat, windows=3, resamples=1000, seed=7):
+    """Run-to-run spread of the latency percentiles: p50 and p99 of consecutive windows of
+    the arrivals (each its own run), and a bootstrap 90 % interval of each over requests."""
+    if len(lat) < 10:
+        return None
+    gen = np.random.default_rng(seed)
+    boot = np.percentile(gen.choice(lat, (resamples, len(lat))), [50, 99], axis=1)
+    parts = np.array_split(lat, windows)
+    return {"windows": [{"p50_ms": round(float(np.percentile(w, 50)), 2),
+                         "p99_ms": round(float(np.percentile(w, 99)), 2), "requests": int(len(w))} for w in parts],
+            "bootstrap90_p50_ms": [round(float(v), 2) for v in np.percentile(boot[0], [5, 95])],
+            "bootstrap90_p99_ms": [round(float(v), 2) for v in np.percentile(boot[1], [5, 95])]}
 
 
 def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
@@ -302,16 +399,21 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
     reqs = scenes.serving_requests(rate=rate, duration=duration, seed=5)
     if dc is not None and dc.world > 1:
         reqs = shard(reqs, dc.rank, dc.world)  # replicas: each GPU serves every world-th request
-    # the scenes are drawn before the clock starts (in parallel; numpy releases the GIL), and
-    # submitted without a copy at their arrival times
+    # the scenes are drawn ahead of their arrival times by a pool of threads (numpy releases
+    # the GIL) with a bounded lookahead, and submitted without a copy at their arrival times;
+    # finished requests are polled as they come, which releases their borrowed states
+    import collections
     import concurrent.futures as cf
 
     def draw(r):
         return scenes.serving_scene(r["dim"], r["material"], r["n"], r["grid_log2"], r["seed"])
 
+    lookahead = 48
+    ex = cf.ThreadPoolExecutor(8)
+    pending = collections.deque(ex.submit(draw, r) for r in reqs[:lookahead])
     t_gen = time.perf_counter()
-    with cf.ThreadPoolExecutor(8) as ex:
-        drawn = list(ex.map(draw, reqs))
+    for f in list(pending)[:16]:  # a head start before the clock starts
+        f.result()
     t_gen = time.perf_counter() - t_gen
     eng = qmpm.Engine(budget_bytes=int(budget_gb * 2 ** 30), resort_every=8, max_active=max_active)
     eng.start()
@@ -319,7 +421,11 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
     lateness = []
     submitted = 0
     particle_steps = 0
-    for r, (sc, s0) in zip(reqs, drawn):
+    recs = []
+    for i, r in enumerate(reqs):
+        sc, s0 = pending.popleft().result()
+        if i + lookahead < len(reqs):
+            pending.append(ex.submit(draw, reqs[i + lookahead]))
         wait = r["t"] - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
@@ -327,8 +433,11 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
         eng.submit(sc, schemes[(r["dim"], r["material"], r["grid_log2"], r["eps"])], s0, sc["steps"], borrow=True)
         submitted += 1
         particle_steps += s0.shape[0] * sc["steps"]
+        if i % 16 == 15:
+            recs += eng.poll(max_n=256)
+    ex.shutdown()
     eng.stop(drain=True)
-    recs = eng.poll(max_n=max(1, submitted))
+    recs += eng.poll(max_n=max(1, submitted))
     st = eng.stats()
     eng.close()
     done = [r for r in recs if r["status"] == qmpm.REQ_DONE]
@@ -347,6 +456,8 @@ def serving(qmpm, duration, rate=20.0, budget_gb=120.0, max_active=64, dc=None):
             "arrival_rate_per_s": rate, "duration_s": duration,
             "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
             "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None,
+            "p99_requests_above": int(np.sum(lat > np.percentile(lat, 99))) if len(lat) else None,
+            "spread": latency_spread(lat),
             "mean_ms": round(float(lat.mean()), 2) if len(lat) else None,
             "particle_steps_per_s": st["particle_steps"] / span if done else None, "unit": UNIT,
             "particle_steps": st["particle_steps"], "offered_particle_steps": particle_steps,
@@ -636,6 +747,13 @@ def run_ours(args):
                           "method": "Algorithm 1 alone",
                           "sensitivity_run": "16 cubes at half resolution (1,024,000 particles, 128^3), "
                                              "1000 steps, 2 Gaussian seeds on x_T"}
+    variants = None
+    if args.workload == "dambreak3d" and not args.fixed_scheme:
+        variants, scheme, dinfo = dambreak_variants(qmpm, torch, args, dc, peaks)
+        solve_info = {"method": "Algorithm 1 (the scaling procedure of Sec. 8.3)", "eps": 0.01,
+                      "sensitivity_run": "column of 64^3 cells on a 128^3 grid (2,097,152 particles), 500 steps, "
+                                         "2 Gaussian seeds on x_T",
+                      "bits": {k: v["bits"] for k, v in scheme.items()}}
     if args.save_scheme and scheme is not None and dc.rank == 0:
         with open(args.save_scheme, "w") as f:
             json.dump({"scheme": scheme, "solve": solve_info}, f)
@@ -715,7 +833,9 @@ def run_ours(args):
         g32.close()
     if solve_info is not None:
         line["scheme_solve"] = solve_info
-    if not args.no_accuracy and dc.rank == 0:
+    if variants is not None:
+        line["variants"] = variants
+    if not args.no_accuracy and dc.rank == 0 and variants is None:
         line["accuracy"] = accuracy(qmpm, sc, s0, sch)
     if args.serving_duration > 0:
         line["serving"] = serving(qmpm, args.serving_duration, dc=dc)

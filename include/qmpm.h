@@ -249,6 +249,8 @@ const char *qmpm_last_error(void);
                                       the mean square position) */
 #define QMPM_MEASURE_KINETIC_ENERGY 2 /* z = (1/2) m sum |v_T|^2, seed m v_T (Sec. 8.1) */
 #define QMPM_MEASURE_POSITIONS 3   /* the vector of final positions x_T (qmpm_noise_moments) */
+#define QMPM_NOISE_MATCHED 0x200   /* qmpm_noise_moments: sigma[h] is Delta_h and each store gets its
+                                      dithered store's variance Delta_h^2 Y (1 - Y) */
 /* OR'ed into `measure`: the adjoint's forward follows the quantized trajectory of the
  * handle's scheme (each step's state goes through the dithered store, Eq. 1), so the
  * gradients and ranges are taken at the quantized solution -- one round of the iterative
@@ -324,7 +326,10 @@ typedef struct {
  *   shift  = mean_k ((z+ + z-) / 2 - z0)   ~ sum_h beta_h sigma_h^2  (second order),
  *   spread = mean_k ((z+ - z-) / 2)^2      ~ sum_h g_h sigma_h^2     (Eq. 8's linear term).
  * With sigma_h = Delta_h / sqrt 6 (the variance of a dithered store, averaged over the
- * fraction) the shift predicts the mean error of the quantized runs.  measure:
+ * fraction) the shift estimates the mean error of the quantized runs; with measure |
+ * QMPM_NOISE_MATCHED and sigma_h = Delta_h (a power of two) each store gets the variance
+ * its dithered store has, Delta_h^2 Y (1 - Y) with Y the fraction of x / Delta_h (a value
+ * on the lattice is stored without error), which the second-order term depends on.  measure:
  * QMPM_MEASURE_MEAN_SQ_POS or QMPM_MEASURE_KINETIC_ENERGY (z a scalar), or
  * QMPM_MEASURE_POSITIONS (the evaluation is the vector of final positions): then with
  * m_k = (x+ + x-)/2 - x0 per particle, shift = |b|^2, the squared norm of the bias vector

@@ -99,6 +99,7 @@ def _bind(L):
     L.or_step_fp64.argtypes = [P(Phys), i64, P(d), P(d)]
     L.or_step_fp64.restype = i64
     L.or_add_noise.argtypes = [ct.c_int, ct.c_int, i64, P(d), u32, ct.c_uint64, P(d), d]
+    L.or_add_noise_matched.argtypes = [ct.c_int, ct.c_int, i64, P(d), u32, ct.c_uint64, P(d), d, ct.c_int]
     L.or_encode_state.argtypes = [P(Codec), i64, P(d), u32, P(u32), P(i64)]
     L.or_decode_state.argtypes = [P(Codec), i64, P(u32), P(d)]
     L.or_step_quant.argtypes = [P(Phys), P(Codec), i64, P(u32), u32, P(d), P(d), P(i64)]
@@ -294,7 +295,7 @@ def step_fp64(ph, s, grid=None):
     return s
 
 
-def add_noise(dim, material, s, step, seed, sigma, sign):
+def add_noise(dim, material, s, step, seed, sigma, sign, matched=False):
     """s + sign * sigma[field] * xi at every component (the explicit store error of the
     noise-injection estimate; xi uniform with unit variance from the Philox counter
     (particle, step, comp / 4, 0xA5)).  Returns a new array."""
@@ -305,13 +306,12 @@ def add_noise(dim, material, s, step, seed, sigma, sign):
     sg = np.ascontiguousarray(sigma, dtype=np.float64)
     if sg.shape != (4,):
         raise ValueError("sigma holds one value per field")
-    lib().or_add_noise(int(dim), MATERIALS[material] if isinstance(material, str) else int(material), s.shape[0],
-                       _p(s, ct.c_double), int(step), int(seed) & 0xFFFFFFFFFFFFFFFF, _p(sg, ct.c_double),
-                       float(sign))
+    lib().or_add_noise_matched(int(dim), mat, s.shape[0], _p(s, ct.c_double), int(step),
+                               int(seed) & 0xFFFFFFFFFFFFFFFF, _p(sg, ct.c_double), float(sign), int(bool(matched)))
     return s
 
 
-def noise_rollout_state(scene, s0, T, sigma, seed, sign):
+def noise_rollout_state(scene, s0, T, sigma, seed, sign, matched=False):
     """The state after T FP64 steps (no re-ordering) from s0 with the explicit error of
     (seed, sign) added after every step (sign 0: none)."""
     ph = make_phys(scene)
@@ -320,14 +320,14 @@ def noise_rollout_state(scene, s0, T, sigma, seed, sign):
     for t in range(T):
         s = step_fp64(ph, s, grid)
         if sign != 0.0:
-            s = add_noise(ph.dim, ph.material, s, t + 1, seed, sigma, sign)
+            s = add_noise(ph.dim, ph.material, s, t + 1, seed, sigma, sign, matched)
     return s
 
 
-def noise_rollout_z(scene, s0, T, sigma, seed, sign, measure="mean_sq_pos"):
+def noise_rollout_z(scene, s0, T, sigma, seed, sign, measure="mean_sq_pos", matched=False):
     """z of noise_rollout_state."""
     ph = make_phys(scene)
-    s = noise_rollout_state(scene, s0, T, sigma, seed, sign)
+    s = noise_rollout_state(scene, s0, T, sigma, seed, sign, matched)
     if measure == "kinetic_energy":
         return kinetic_energy(ph, s)
     return mean_sq_pos(ph.dim, s)

@@ -319,6 +319,14 @@ int64_t or_step_fp64(const or_phys_t *ph, int64_t N, double *s, double *grid_scr
 void or_add_noise(int dim, int material, int64_t N, double *s, uint32_t step, uint64_t seed,
                   const double sigma[4], double sign)
 {
+    or_add_noise_matched(dim, material, N, s, step, seed, sigma, sign, 0);
+}
+
+/* matched: sigma[h] is the resolution Delta_h and a store of value x gets the dithered
+ * store's own variance, sigma = Delta_h sqrt(Y (1 - Y)), Y the fraction of x / Delta_h. */
+void or_add_noise_matched(int dim, int material, int64_t N, double *s, uint32_t step, uint64_t seed,
+                          const double sigma[4], double sign, int matched)
+{
     const int nc = or_n_comp(dim, material);
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int64_t p = 0; p < N; ++p) {
@@ -331,7 +339,13 @@ void or_add_noise(int dim, int material, int64_t N, double *s, uint32_t step, ui
             const double k = (double)(blk[c % 4] >> 9);
             const double u = (k + 0.5) / 8388608.0;
             const double xi = (2.0 * u - 1.0) * sqrt(3.0);
-            s[p * nc + c] += sign * sigma[or_comp_field(dim, material, c)] * xi;
+            double sg = sigma[or_comp_field(dim, material, c)];
+            if (matched && sg > 0.0) {
+                const double t = s[p * nc + c] / sg;
+                const double Y = t - floor(t);
+                sg *= sqrt(Y * (1.0 - Y));
+            }
+            s[p * nc + c] += sign * sg * xi;
         }
     }
 }

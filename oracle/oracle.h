@@ -107,6 +107,9 @@ int64_t or_step_fp64(const or_phys_t *ph, int64_t N, double *s, double *grid_scr
  * c / 4, 0xA5), key seed). */
 void or_add_noise(int dim, int material, int64_t N, double *s, uint32_t step, uint64_t seed,
                   const double sigma[4], double sign);
+/* the same; matched != 0: sigma[h] = Delta_h, each store's variance Delta_h^2 Y (1 - Y) */
+void or_add_noise_matched(int dim, int material, int64_t N, double *s, uint32_t step, uint64_t seed,
+                          const double sigma[4], double sign, int matched);
 
 /* ---- quantized state ---- */
 void or_encode_state(const or_codec_t *cd, int64_t N, const double *s, uint32_t step,

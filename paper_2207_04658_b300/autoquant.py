@@ -90,8 +90,9 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=
     position vector the second moment is |b|^2 + tr(Cov) with b the bias vector of the
     final positions, and zero-mean dithered stores of the deformation gradient (a random
     walk over the rollout) or of the positions shift the positions systematically.  Per
-    round, for each type h: qmpm_noise_moments of the final positions with errors of the
-    dithered variance (Delta_h / sqrt 6) at the stores of type h only gives |b_h|^2 and
+    round, for each type h: qmpm_noise_moments of the final positions with errors matched to
+    the dithered stores (variance Delta_h^2 Y (1 - Y) at fraction Y, whose average over
+    the fraction is sigma_h^2 = Delta_h^2 / 6) at the stores of type h only gives |b_h|^2 and
     the first-order spread; then beta_h = |b_h| / sigma_h^2 (the combined bias |sum_h b_h|
     is at most sum_h |b_h|), g_h = spread_h / sigma_h^2, and the solve's second-order
     refinement of Algorithm 1's scheme adds fraction bits until (sum_h beta_h Delta_h^2 /
@@ -116,11 +117,16 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=
         scheme, prev = base, None
         z = None
         for it in range(iters):
-            sig = [2.0 ** -scheme[n]["frac"] / np.sqrt(6.0) for n in names]
+            # errors matched to the dithered stores (variance Delta_h^2 Y (1 - Y) at fraction
+            # Y); sigma_h^2 = Delta_h^2 / 6 is its average over the fraction, the scale the
+            # solve's moments take
+            deltas = [2.0 ** -scheme[n]["frac"] for n in names]
+            sig = [d / np.sqrt(6.0) for d in deltas]
             mom = []
             for h in range(4):
-                s_h = [sig[k] if k == h else 0.0 for k in range(4)]
-                mom.append(qmpm.qmpm_noise_moments(g.h, T, qmpm.MEASURE_POSITIONS, s_h, seed + 10 * it + h, pairs))
+                d_h = [deltas[k] if k == h else 0.0 for k in range(4)]
+                mom.append(qmpm.qmpm_noise_moments(g.h, T, qmpm.MEASURE_POSITIONS | qmpm.NOISE_MATCHED, d_h,
+                                                   seed + 10 * it + h, pairs))
             z = float(np.sqrt(N * mom[0]["z0"]))
             # a noise level that makes the run blow up (non-finite moments) counts as an
             # unbounded sensitivity: the refinement then takes bits until the next round
@@ -306,3 +312,24 @@ def main():
 
 if __name__ == "__main__":
     main()
+
+
+def dambreak3d_schemes(eps_list=(0.1, 0.01), cells=256, grid_log2=9, factor=4, T=None, samples=2):
+    """Schemes of Algorithm 1 for the 3D dam break at the given relative error bounds on the
+    final particle positions (the scaling procedure of Sec. 8.3): the sensitivities and
+    ranges of the column at 1/factor resolution (cells / factor cells on a grid factor times
+    coarser, same dt and step count), the affine field C's window scaled by the resolution
+    ratio (C is a velocity gradient: it grows like 1 / dx), bit pack.  Returns
+    {eps: (scheme, solve report)} and the sensitivity report."""
+    k = factor.bit_length() - 1
+    sc_lo, s0_lo = scenes.dambreak3d_scene(column_cells=cells // factor, grid_log2=grid_log2 - k)
+    steps = T if T is not None else sc_lo["steps"]
+    info = position_sensitivities(sc_lo, s0_lo, steps, samples=samples)
+    lo, hi = list(info["lo"]), list(info["hi"])
+    mid, half = 0.5 * (lo[2] + hi[2]), 0.5 * (hi[2] - lo[2]) * factor
+    lo[2], hi[2] = mid - half, mid + half
+    info_hi = dict(info, lo=lo, hi=hi)
+    out = {}
+    for eps in eps_list:
+        out[eps] = qmpm.solve_scheme(info_hi, eps, material="fluid")
+    return out, info

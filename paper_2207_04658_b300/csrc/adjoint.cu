@@ -599,8 +599,11 @@ __global__ void adj_quantize_kernel(const __grid_constant__ StepParams P, float 
 // particle p gets sign * sigma[field(c)] * xi with xi uniform on [-sqrt 3, sqrt 3) (unit
 // variance), drawn from Philox4x32-10 with counter (p, step, c / 4, 0xA5) and key `seed`:
 // word c % 4 of the block gives u = (floor(w / 2^9) + 1/2) 2^-23 and xi = (2u - 1) sqrt 3.
+// matched: sig holds the resolution Delta_h of each type, and the store of value x gets the
+// dithered store's own variance there, sigma = Delta_h sqrt(Y (1 - Y)) with Y the fraction
+// of x / Delta_h (a dithered store errs by -Y Delta or (1 - Y) Delta, zero mean).
 __global__ void adj_noise_kernel(const __grid_constant__ StepParams P, float *s, int64_t N, uint32_t step,
-                                 uint32_t seed_lo, uint32_t seed_hi, float4 sig, float sign)
+                                 uint32_t seed_lo, uint32_t seed_hi, float4 sig, float sign, int matched)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
@@ -611,8 +614,14 @@ __global__ void adj_noise_kernel(const __grid_constant__ StepParams P, float *s,
         // 2u - 1 with u = (w / 2^9 + 1/2) 2^-23 in (0, 1): exact in FP32
         const float xi = ((float)(2u * (w >> 9) + 1u) * (1.0f / 8388608.0f) - 1.0f) * 1.7320508f;
         const int h = P.comp[c].field;
-        const float sg = h == 0 ? sig.x : h == 1 ? sig.y : h == 2 ? sig.z : sig.w;
-        s[p * P.n_comp + c] += sign * sg * xi;
+        float sg = h == 0 ? sig.x : h == 1 ? sig.y : h == 2 ? sig.z : sig.w;
+        const float x = s[p * P.n_comp + c];
+        if (matched && sg > 0.0f) {
+            const float t = x / sg;  // sg a power of two: exact
+            const float Y = t - floorf(t);
+            sg *= sqrtf(Y * (1.0f - Y));
+        }
+        s[p * P.n_comp + c] = x + sign * sg * xi;
     }
 }
 
@@ -1001,6 +1010,8 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
                                   int32_t n_pairs, qmpm_noise_out_t *out)
 {
     using namespace qmpm;
+    const int matched = (measure & QMPM_NOISE_MATCHED) ? 1 : 0;
+    measure &= ~QMPM_NOISE_MATCHED;
     if (!h || T < 0 || n_pairs < 2 || !sigma || !out ||
         (measure != QMPM_MEASURE_MEAN_SQ_POS && measure != QMPM_MEASURE_KINETIC_ENERGY &&
          measure != QMPM_MEASURE_POSITIONS)) {
@@ -1008,8 +1019,8 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
         return QMPM_ERR_INVALID_ARG;
     }
     for (int q = 0; q < 4; ++q)
-        if (!(sigma[q] >= 0.0)) {
-            set_last_error("qmpm_noise_moments: sigma must be >= 0");
+        if (!(sigma[q] >= 0.0) || (matched && sigma[q] > 0.0 && std::exp2(std::round(std::log2(sigma[q]))) != sigma[q])) {
+            set_last_error("qmpm_noise_moments: sigma must be >= 0 (and powers of two, the resolutions, when matched)");
             return QMPM_ERR_INVALID_ARG;
         }
     Ctx &c = *h;
@@ -1068,7 +1079,7 @@ extern "C" int qmpm_noise_moments(qmpm_handle h, int32_t T, int32_t measure, con
             r = fwd(P, cur, nxt, N, gm, gv, nn, st);
             if (r == cudaSuccess && sign != 0.0f && N > 0) {
                 adj_noise_kernel<<<nblk(N), kAdjThreads, 0, st>>>(P, nxt, N, (uint32_t)(t + 1), (uint32_t)seed,
-                                                                 (uint32_t)(seed >> 32), sig, sign);
+                                                                 (uint32_t)(seed >> 32), sig, sign, matched);
                 r = cudaGetLastError();
             }
             std::swap(cur, nxt);

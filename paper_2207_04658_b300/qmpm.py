@@ -118,6 +118,7 @@ OP_ADVANCE, OP_REVERSE = 0, 1
 
 
 MEASURE_MEAN_SQ_POS, MEASURE_USER, MEASURE_KINETIC_ENERGY, MEASURE_POSITIONS = 0, 1, 2, 3
+NOISE_MATCHED = 0x200
 BATCH_GRAPHS = 1
 SUBMIT_KEEP_STATE, SUBMIT_BORROW = 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3

@@ -49,14 +49,14 @@ def impact_block(n_strata=(64, 32)):
 
 def predicted_moments(scene, state0, T, scheme, pairs=16, seed=4242, measure=qmpm.MEASURE_KINETIC_ENERGY):
     """The mean shift and the spread of z that dithered stores of `scheme` cause, predicted by
-    antithetic noise injection (qmpm_noise_moments): an error of standard deviation
-    Delta_h / sqrt 6 (a dithered store's variance, averaged over the fraction) at every
-    store of type h.  The shift is the second-order term that Eq. 8 leaves out."""
+    antithetic noise injection (qmpm_noise_moments, matched): at every store of type h an
+    error with the dithered store's own variance there, Delta_h^2 Y (1 - Y) for a value at
+    fraction Y of its lattice.  The shift is the second-order term that Eq. 8 leaves out."""
     names = ("x", "v", "C", "J" if scene["material"] == "fluid" else "F")
-    sigma = [2.0 ** -scheme[k]["frac"] / np.sqrt(6.0) for k in names]
+    deltas = [2.0 ** -scheme[k]["frac"] for k in names]
     g = qmpm.Scene(dict(scene, resort_every=0), None, state0)
     try:
-        m = qmpm.qmpm_noise_moments(g.h, T, measure, sigma, seed, pairs)
+        m = qmpm.qmpm_noise_moments(g.h, T, measure | qmpm.NOISE_MATCHED, deltas, seed, pairs)
     finally:
         g.close()
     return m

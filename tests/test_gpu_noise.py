@@ -9,24 +9,28 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dim,material", [(2, "neohookean"), (3, "corotated"), (2, "fluid")])
-def test_noise_moments_match_the_oracle(oracle, dim, material):
+@pytest.mark.parametrize("dim,material,matched", [(2, "neohookean", False), (3, "corotated", False),
+                                                  (2, "fluid", False), (3, "corotated", True)])
+def test_noise_moments_match_the_oracle(oracle, dim, material, matched):
     import torch
     from paper_2207_04658_b300 import qmpm
     from test_gpu_adjoint import small
     assert torch.cuda.is_available()
     sc, s0 = small(dim, material, N_side=10, seed=3)
-    T, sigma, seed0, pairs = 20, [2e-3, 0.2, 20.0, 2e-2], 11, 3
+    T, seed0, pairs = 20, 11, 3
+    # matched: the resolutions (powers of two), each store's error of its dithered variance
+    sigma = [2.0 ** -8, 0.5, 64.0, 2.0 ** -5] if matched else [2e-3, 0.2, 20.0, 2e-2]
     g = qmpm.Scene(sc, None, s0)
     ids = g.readback(state=False, ids=True)["ids"]
-    m = qmpm.qmpm_noise_moments(g.h, T, qmpm.MEASURE_MEAN_SQ_POS, sigma, seed0, pairs)
+    m = qmpm.qmpm_noise_moments(g.h, T, qmpm.MEASURE_MEAN_SQ_POS | (qmpm.NOISE_MATCHED if matched else 0), sigma,
+                                seed0, pairs)
     g.close()
     s_slot = s0[ids]  # particle p of the device runs is slot p
     z0 = oracle.noise_rollout_z(sc, s_slot, T, sigma, 0, 0.0)
     sh, sp = [], []
     for k in range(pairs):
-        zp = oracle.noise_rollout_z(sc, s_slot, T, sigma, seed0 + k, 1.0)
-        zm = oracle.noise_rollout_z(sc, s_slot, T, sigma, seed0 + k, -1.0)
+        zp = oracle.noise_rollout_z(sc, s_slot, T, sigma, seed0 + k, 1.0, matched=matched)
+        zm = oracle.noise_rollout_z(sc, s_slot, T, sigma, seed0 + k, -1.0, matched=matched)
         sh.append(0.5 * (zp + zm) - z0)
         sp.append(0.25 * (zp - zm) ** 2)
     assert m["pairs"] == pairs

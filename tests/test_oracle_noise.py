@@ -43,3 +43,20 @@ def test_noise_free_rollout_is_the_fp64_rollout(oracle):
     z = oracle.noise_rollout_z(sc, s0, 5, [1.0] * 4, 3, 0.0)
     states = oracle.rollout_fp64(oracle.make_phys(sc), s0, 5)
     assert z == oracle.mean_sq_pos(2, states[-1])
+
+
+def test_matched_noise_has_the_dithered_variance(oracle):
+    """Matched errors: a value on the lattice gets none, a value at fraction Y gets
+    Delta sqrt(Y (1 - Y)) times the unit draw (the dithered store's standard deviation)."""
+    delta = 2.0 ** -4
+    n = 20_000
+    Y = np.random.default_rng(2).uniform(0, 1, n)
+    s0 = np.zeros((n, 9))
+    s0[:, 8] = (7 + Y) * delta  # J of a 2D fluid, fraction Y
+    s0[:, 0] = 3 * delta        # x on the lattice
+    unit = oracle.add_noise(2, "fluid", np.zeros((n, 9)), 2, 11, [1.0] * 4, 1.0)
+    m = oracle.add_noise(2, "fluid", s0, 2, 11, [delta] * 4, 1.0, matched=True)
+    assert np.array_equal(m[:, 0], s0[:, 0])
+    assert np.allclose(m[:, 8] - s0[:, 8], delta * np.sqrt(Y * (1 - Y)) * unit[:, 8], rtol=1e-9, atol=1e-15)
+    # averaged over uniform fractions the variance is Delta^2 / 6, as for uniform errors of sd Delta / sqrt 6
+    assert abs(((m[:, 8] - s0[:, 8]) ** 2).mean() / delta ** 2 - 1 / 6) < 0.01
