@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--scheme-json", default=None,
                     help="load a scheme saved by --save-scheme instead of solving it again")
     ap.add_argument("--save-scheme", default=None, help="write the solved scheme to this file")
+    ap.add_argument("--fp32-state", action="store_true",
+                    help="time the FP32 state as the headline (the comparator's step kernel, for profiling)")
     ap.add_argument("--resolve-scheme", action="store_true",
                     help="solve the cubes' second-order scheme in this run instead of loading the cached one")
     ap.add_argument("--algorithm1-scheme", action="store_true",
@@ -738,7 +740,14 @@ def run_ours(args):
                           "source": ("cached: python -m paper_2207_04658_b300.autoquant cubes3d --eps 0.01"
                                      if cached is not None else "solved in this run"),
                           "method": "Algorithm 1 (sensitivities of the 16 cubes at half resolution), refined "
-                                    "with the second-order term (noise injection at full resolution)"}
+                                    "with the second-order term (noise injection at full resolution), the last "
+                                    "word's free bits spent on wider windows, accepted by quantized rollouts "
+                                    "against the FP32 rollout at full resolution"}
+            acc = rep.get("acceptance") or []
+            if acc:
+                solve_info["acceptance"] = {"rounds": len(acc), "rel_err": acc[-1]["rel_err"],
+                                            "saturations": acc[-1]["saturations"],
+                                            "dither_seeds": acc[-1].get("seeds")}
         else:
             scheme, rep = solved_cubes_scheme(0.01)
             solve_info = {"bits": rep["solve"]["bits"], "frac": rep["solve"]["frac"],
@@ -758,6 +767,9 @@ def run_ours(args):
         with open(args.save_scheme, "w") as f:
             json.dump({"scheme": scheme, "solve": solve_info}, f)
     sc, s0, sch, desc = workload(args.workload, args.scale, seed_offset=dc.rank, scheme=scheme)
+    if args.fp32_state:  # the comparator alone (profiling the FP32 step kernel)
+        sch = None
+        desc = dict(desc, scheme=None, scheme_source="FP32 state")
     N = s0.shape[0]
     clocks = ClockSampler(dc.local)
     clocks.start()

@@ -81,8 +81,71 @@ def _shift_frac(field, k):
     return f
 
 
-def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=2, containers=(0, 0, 0, 0),
-                        seed=100, log=None):
+def _rewindow(field, lo, hi):
+    """A field's scheme at its own resolution over the window [lo, hi] (the bits and offset
+    the solve gives a window: offset floor(lo 2^frac), enough bits for ceil(hi 2^frac))."""
+    import math
+    f = dict(field)
+    k = f["frac"]
+    L = math.floor(math.ldexp(lo, k))
+    need = math.ceil(math.ldexp(hi, k)) - L + 1
+    n = 1
+    while n < 64 and 2 ** n < need:
+        n += 1
+    f["bits"], f["offset"] = n, int(L)
+    return f
+
+
+def _margin_windows(scheme, names, info, margins, kappa=2.0, grow_only=False):
+    """The windows of the types in margins = {h: (src, gain)} widened by gain Delta_src on
+    each side, Delta_src the resolution of type src in this scheme (the solve's window
+    option, here applied after every change of resolution); grow_only keeps the union with
+    the type's current window."""
+    out = dict(scheme)
+    for h, (src, gain) in (margins or {}).items():
+        f = scheme[names[h]]
+        mid = 0.5 * (info["lo"][h] + info["hi"][h])
+        half = 0.5 * kappa * (info["hi"][h] - info["lo"][h])
+        m = gain * 2.0 ** -scheme[names[src]]["frac"]
+        lo, hi = mid - half - m, mid + half + m
+        if grow_only:
+            q = 2.0 ** -f["frac"]
+            lo, hi = min(lo, f["offset"] * q), max(hi, (f["offset"] + (1 << f["bits"]) - 1) * q)
+        out[names[h]] = _rewindow(f, lo, hi)
+    return out
+
+
+def _widened(field):
+    """A field's scheme with its window doubled about its middle at the same resolution."""
+    f = dict(field)
+    f["offset"] -= 1 << (f["bits"] - 1)
+    f["bits"] += 1
+    return f
+
+
+def fill_word_slack(scheme, dim, material, types=("v", "C", "F", "J")):
+    """Spend the unused bits of the last packed word on wider windows: each of the given
+    types in turn gets its window doubled (one more bit, same resolution) while the packed
+    layout keeps its number of words, until none fits.  A dithered run's values spread
+    past the full-precision run's ranges (the noise of the stores feeds back through the
+    grid), and this headroom costs no memory traffic."""
+    words = qmpm.make_scheme_struct(scheme, dim, material).n_words
+    out = dict(scheme)
+    grew = True
+    while grew:
+        grew = False
+        for n in types:
+            if n not in out or out[n]["bits"] >= 24:
+                continue
+            trial = dict(out, **{n: _widened(out[n])})
+            if qmpm.make_scheme_struct(trial, dim, material).n_words == words:
+                out = trial
+                grew = True
+    return out
+
+
+def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=8, max_step=2, containers=(0, 0, 0, 0),
+                        seed=100, margins=None, accept_seeds=(None, 777, 1001, 1002), accept_rounds=6, log=None):
     """Algorithm 1's scheme for the vector evaluation (the final particle positions),
     refined with the second-order term of the error at the resolution it will run at.
 
@@ -97,12 +160,16 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=
     is at most sum_h |b_h|), g_h = spread_h / sigma_h^2, and the solve's second-order
     refinement of Algorithm 1's scheme adds fraction bits until (sum_h beta_h Delta_h^2 /
     6)^2 + sum_h g_h Delta_h^2 / 6 <= (eps z)^2.  The moments are re-estimated at the
-    refined scheme's own noise level (the shift is not quadratic in it: a coarse deformation
-    gradient can make the runs blow up, which reads as an unbounded sensitivity) until the
-    scheme repeats or after `iters` rounds, each round moving a type's resolution by at most
+    refined scheme's own noise level (the shift is not quadratic in it; a resolution at which
+    a field's runs blow up becomes a lower bound for that field) until the scheme repeats
+    or after `iters` rounds, each round moving a type's resolution by at most
     max_step bits (a damped fixed-point iteration), and keeping the finer fraction per type
-    where the last two differ.  info: the sensitivities and ranges of Algorithm 1 (g_h, lo,
-    hi; the run the ranges come from).  Returns (scheme, report)."""
+    where the last two differ.  margins (the solve's window option, {h: (src, gain)}) are
+    re-applied at every resolution.  The last packed word's free bits then widen the windows
+    (fill_word_slack), and _accept checks the scheme with quantized rollouts against the FP32
+    rollout at this resolution, refining it where they miss the bound or saturate.  info:
+    the sensitivities and ranges of Algorithm 1 (g_h, lo, hi; the run the ranges come from).
+    Returns (scheme, report)."""
     import numpy as np
     material = scene["material"]
     dim = scene["dim"]
@@ -110,9 +177,14 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=
     N = state0.shape[0]
     per = [dim, dim, dim * dim, 1 if material == "fluid" else dim * dim]
     P = [float(N * k) for k in per]
-    base, res0 = qmpm.solve_scheme(info, eps, containers=containers, material=material)
+    base, res0 = qmpm.solve_scheme(info, eps, containers=containers, material=material, margins=margins)
     g = qmpm.Scene(dict(scene, resort_every=0), None, state0)
     rounds = []
+    # a noise level at which a field's runs blow up (non-finite moments) bounds that field's
+    # resolution from below (floor) until the end; the field's last finite coefficients
+    # stand in for the missing ones
+    floor = {n: -(10 ** 9) for n in names}
+    last_beta, last_g = [1e30] * 4, [1e30] * 4
     try:
         scheme, prev = base, None
         z = None
@@ -127,25 +199,33 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=
                 d_h = [deltas[k] if k == h else 0.0 for k in range(4)]
                 mom.append(qmpm.qmpm_noise_moments(g.h, T, qmpm.MEASURE_POSITIONS | qmpm.NOISE_MATCHED, d_h,
                                                    seed + 10 * it + h, pairs))
-            z = float(np.sqrt(N * mom[0]["z0"]))
-            # a noise level that makes the run blow up (non-finite moments) counts as an
-            # unbounded sensitivity: the refinement then takes bits until the next round
-            beta = [float(np.sqrt(max(m["shift"], 0.0))) / sig[h] ** 2 if np.isfinite(m["shift"]) else 1e30
-                    for h, m in enumerate(mom)]
-            geff = [float(m["spread"]) / sig[h] ** 2 if np.isfinite(m["spread"]) else 1e30
-                    for h, m in enumerate(mom)]
+            z = float(np.sqrt(N * mom[0]["z0"])) if np.isfinite(mom[0]["z0"]) else z
+            beta, geff = [], []
+            for h, m in enumerate(mom):
+                if np.isfinite(m["shift"]) and np.isfinite(m["spread"]):
+                    last_beta[h] = float(np.sqrt(max(m["shift"], 0.0))) / sig[h] ** 2
+                    last_g[h] = float(m["spread"]) / sig[h] ** 2
+                else:
+                    floor[names[h]] = max(floor[names[h]], scheme[names[h]]["frac"] + 1)
+                beta.append(last_beta[h])
+                geff.append(last_g[h])
             sol = dict(info, g=geff, P=P, z=z)
-            want, res = qmpm.solve_scheme(sol, eps, containers=containers, material=material, beta=beta)
+            want, res = qmpm.solve_scheme(sol, eps, containers=containers, material=material, beta=beta,
+                                          margins=margins)
             nxt = {}
             for n in names:
-                # the current window, the resolution moved toward the solve's by at most
-                # max_step bits (and never past the 24 bits FP32 compute decodes exactly)
-                k = max(-max_step, min(max_step, want[n]["frac"] - scheme[n]["frac"]))
+                # the current window, the resolution moved toward the solve's (not below the
+                # field's floor) by at most max_step bits, and never past the 24 bits FP32
+                # compute decodes exactly
+                target = max(want[n]["frac"], floor[n])
+                k = max(-max_step, min(max_step, target - scheme[n]["frac"]))
                 k = min(k, 24 - scheme[n]["bits"])
                 k = max(k, 1 - scheme[n]["bits"])
                 nxt[n] = _shift_frac(scheme[n], k)
+            nxt = _margin_windows(nxt, names, info, margins)
             rounds.append({"scheme": scheme, "sigma": sig, "moments": mom, "beta": beta, "g": geff, "solve": want,
-                           "next": nxt, "pred_bias": res["pred_bias"], "pred_var": res["pred_var_dither"]})
+                           "next": nxt, "pred_bias": res["pred_bias"], "pred_var": res["pred_var_dither"],
+                           "floor": dict(floor)})
             if log:
                 log(it, {k: v["bits"] for k, v in nxt.items()}, res["pred_bias"], res["pred_var_dither"], z)
             # each round refines Algorithm 1's scheme with the moments measured at the current
@@ -156,9 +236,69 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=6, max_step=
                 break
         if prev is not None and scheme != prev:
             scheme = {n: (scheme[n] if scheme[n]["frac"] >= prev[n]["frac"] else prev[n]) for n in names}
+            scheme = _margin_windows(scheme, names, info, margins)
     finally:
         g.close()
-    return scheme, {"algorithm1": base, "algorithm1_solve": res0, "rounds": rounds, "z": z, "eps": eps}
+    last = rounds[-1] if rounds else None
+    scheme = fill_word_slack(scheme, dim, material)
+    scheme, accepted = _accept(scene, state0, T, eps, z, scheme, names, last, info, margins, accept_seeds,
+                               accept_rounds, log)
+    return scheme, {"algorithm1": base, "algorithm1_solve": res0, "rounds": rounds, "z": z, "eps": eps,
+                    "acceptance": accepted}
+
+
+def _accept(scene, state0, T, eps, z, scheme, names, last, info, margins, seeds, max_rounds, log):
+    """The acceptance check of a solved scheme at the resolution it runs at: the quantized
+    rollouts (one per dither seed in seeds) against the FP32 rollout of the same scene.
+    The scheme is accepted when the mean over the seeds of the summed squared error of
+    the final positions is within (eps z)^2 (Eq. 6 for the position vector) and no store
+    saturated.  Otherwise a type that saturated gets its window doubled about its middle,
+    and while the error is above the bound the type with the largest share of the
+    predicted second moment (beta_h sigma_h^2 sum_k beta_k sigma_k^2 + g_h sigma_h^2, the
+    coefficients of the last round) gets one more fraction bit; at most max_rounds times.
+    Returns (scheme, history)."""
+    import numpy as np
+    dim = scene["dim"]
+    history = []
+    if not seeds or max_rounds <= 0 or z is None:
+        return scheme, history
+    ref = qmpm.Scene(dict(scene), None, state0)
+    ref.step(T)
+    x32 = ref.state_by_id()[:, :dim]
+    ref.close()
+    for r in range(max_rounds + 1):
+        err2, sat = [], np.zeros(4, dtype=np.int64)
+        for sd in seeds:
+            q = qmpm.Scene(dict(scene, seed=sd) if sd is not None else dict(scene), scheme, state0, stats=True)
+            q.step(T)
+            x = q.state_by_id()[:, :dim]
+            sat += np.asarray(q.readback(state=False, ids=False)["stats"]["saturations"][:4], dtype=np.int64)
+            q.close()
+            err2.append(float(((x - x32) ** 2).sum()) if np.isfinite(x).all() else float("inf"))
+        rel = float(np.sqrt(np.mean(err2))) / z
+        history.append({"scheme": scheme, "rel_err": rel, "saturations": sat.tolist(),
+                        "seeds": [sd for sd in seeds]})
+        if log:
+            log("accept", {n: scheme[n]["bits"] for n in names}, rel, sat.tolist())
+        if rel <= eps and not sat.any():
+            break
+        if r == max_rounds:
+            break
+        nxt = dict(scheme)
+        for h, n in enumerate(names):
+            if sat[h] > 0:
+                nxt[n] = _widened(nxt[n])
+        if rel > eps:
+            sig2 = [2.0 ** (-2 * scheme[n]["frac"]) / 6.0 for n in names]
+            beta = last["beta"] if last else [0.0] * 4
+            gg = last["g"] if last else [1.0] * 4
+            B = sum(b * s2 for b, s2 in zip(beta, sig2))
+            share = [beta[h] * sig2[h] * B + gg[h] * sig2[h] if scheme[names[h]]["bits"] < 24 else -1.0
+                     for h in range(4)]
+            h = int(np.argmax(share))
+            nxt[names[h]] = _shift_frac(nxt[names[h]], 1)
+        scheme = _margin_windows(nxt, names, info, margins, grow_only=True)
+    return scheme, history
 
 
 def c_noise_margin(grid_log2):
@@ -224,7 +364,7 @@ def iterate_scheme(scene, state0, T, eps, measure=qmpm.MEASURE_KINETIC_ENERGY, m
     return scheme, history
 
 
-def cubes3d_second_order_scheme(eps=0.01, cube_cells=40, grid_log2=8, T=None, pairs=2, iters=6, log=None):
+def cubes3d_second_order_scheme(eps=0.01, cube_cells=40, grid_log2=8, T=None, pairs=2, iters=8, log=None):
     """The cubes' scheme at relative error eps on the final positions, Algorithm 1 plus the
     second-order refinement: the sensitivities g_h come from the same 16 cubes at half
     resolution (the scaling procedure of Sec. 8.3), the ranges from the FP32 run at the
@@ -237,7 +377,7 @@ def cubes3d_second_order_scheme(eps=0.01, cube_cells=40, grid_log2=8, T=None, pa
     rng_hi = qmpm.sensitivities(sc, s0, steps)  # the forward records the ranges
     info = dict(info_lo, lo=rng_hi["lo"], hi=rng_hi["hi"])
     scheme, rep = second_order_scheme(sc, s0, steps, eps, info, pairs=pairs, iters=iters,
-                                      containers=(64, 0, 0, 0), log=log)
+                                      containers=(64, 0, 0, 0), margins=c_noise_margin(grid_log2), log=log)
     rep["sensitivities"] = {k: info_lo[k] for k in ("g", "z", "P")}
     rep["ranges"] = {"lo": list(rng_hi["lo"]), "hi": list(rng_hi["hi"])}
     return scheme, rep
@@ -281,10 +421,11 @@ def _summary(rep):
     rounds = []
     for r in rep["rounds"]:
         rounds.append({"scheme": r["scheme"], "beta": r["beta"], "g": r["g"], "pred_bias": r["pred_bias"],
-                       "pred_var": r["pred_var"],
+                       "pred_var": r["pred_var"], "floor": r["floor"],
                        "moments": [{k: m[k] for k in ("shift", "spread", "z0")} for m in r["moments"]]})
     return {"algorithm1": rep["algorithm1"], "rounds": rounds, "z": rep["z"], "eps": rep["eps"],
-            "sensitivities": rep["sensitivities"], "ranges": rep["ranges"]}
+            "sensitivities": rep["sensitivities"], "ranges": rep["ranges"],
+            "acceptance": rep.get("acceptance", [])}
 
 
 def main():
@@ -300,7 +441,8 @@ def main():
                                                                                flush=True))
     sc, s0 = scenes.cubes3d_scene()
     out = {"what": "3D fixed-corotated cubes (8,192,000 particles, 256^3): Algorithm 1 from half-resolution "
-                   "sensitivities, refined with the second-order term at full resolution",
+                   "sensitivities, refined with the second-order term at full resolution and accepted by FP32-referenced "
+                   "rollouts there",
            "eps": args.eps, "scheme": scheme, "scene_hash": scene_hash(sc, s0), "report": _summary(rep),
            "seconds": time.time() - t0}
     os.makedirs(SCHEME_DIR, exist_ok=True)
@@ -309,9 +451,6 @@ def main():
         json.dump(out, f, indent=1, default=float)
     print(path, {k: (v["bits"], v["frac"]) for k, v in scheme.items()})
 
-
-if __name__ == "__main__":
-    main()
 
 
 def dambreak3d_schemes(eps_list=(0.1, 0.01), cells=256, grid_log2=9, factor=4, T=None, samples=2):
@@ -333,3 +472,7 @@ def dambreak3d_schemes(eps_list=(0.1, 0.01), cells=256, grid_log2=9, factor=4, T
     for eps in eps_list:
         out[eps] = qmpm.solve_scheme(info_hi, eps, material="fluid")
     return out, info
+
+
+if __name__ == "__main__":
+    main()

@@ -35,7 +35,9 @@ def test_noise_moments_match_the_oracle(oracle, dim, material, matched):
         sp.append(0.25 * (zp - zm) ** 2)
     assert m["pairs"] == pairs
     assert abs(m["z0"] - z0) <= 1e-5 * abs(z0), (m, z0)
-    assert abs(m["spread"] - np.mean(sp)) <= 1e-3 * np.mean(sp), (m, np.mean(sp))
+    # matched errors scale with each value's fraction on its lattice, which FP32 and FP64
+    # runs see a few units apart: 5e-3 for the spread there, 1e-3 otherwise
+    assert abs(m["spread"] - np.mean(sp)) <= (5e-3 if matched else 1e-3) * np.mean(sp), (m, np.mean(sp))
     assert abs(m["shift"] - np.mean(sh)) <= 2e-2 * abs(np.mean(sh)) + 5e-6 * abs(z0), (m, np.mean(sh))
 
 

@@ -279,12 +279,20 @@ def compare_stage(oracle, sc, scheme, stage, step, kernel_codes, ref, tau):
     return codes.size, diff.size
 
 
+def window(field):
+    d = 2.0 ** -field["frac"]
+    return field["offset"] * d, (field["offset"] + 2 ** field["bits"] - 1) * d
+
+
 def stage_inputs(gen, sc, scheme, stage):
+    """Seeded stage inputs inside the scheme's windows (a stored input outside would
+    saturate on one side only)."""
     n = sc["n"]
     fv, fp = scheme["v"]["frac"], scheme["p"]["frac"]
-    a = vel_pair(gen, n, fv)
-    b = vel_pair(gen, n, fv)
-    q = lattice(gen, (n, n), fp, 0.01)
+    (vlo, vhi), (qlo, qhi) = window(scheme["v"]), window(scheme["p"])
+    a = tuple(np.clip(x, vlo, vhi) for x in vel_pair(gen, n, fv))
+    b = tuple(np.clip(x, vlo, vhi) for x in vel_pair(gen, n, fv))
+    q = np.clip(lattice(gen, (n, n), fp, 0.01), qlo, qhi)
     div = f32(gen, (n, n), 5.0)
     if stage == "advect1":
         # the advecting v is the FP32 velocity after the forces, off the lattice

@@ -108,3 +108,50 @@ def test_scheme_cap_keeps_the_window(q):
     lo = scheme["x"]["offset"] * d
     hi = (scheme["x"]["offset"] + 2 ** 24 - 1) * d
     assert lo <= -0.5 and hi >= 1.5  # the kappa = 2 window of [0, 1]
+
+
+def test_margin_windows_match_the_solve(q):
+    """The second-order iteration re-derives a margin type's window after every change of
+    resolution; at the solve's own resolutions it gives the solve's window option."""
+    from paper_2207_04658_b300 import autoquant
+    info = {"P": [300.0, 300.0, 900.0, 900.0], "g": [1e6, 1e2, 1e-4, 1e3],
+            "lo": [0.1, -11.7, -3044.5, -2.06], "hi": [0.9, 14.1, 3871.5, 2.07], "z": 1.0}
+    names = ["x", "v", "C", "F"]
+    margins = {2: (1, 6.0 * 256)}
+    for eps in (1e-2, 1e-3, 1e-4):
+        plain, _ = q.solve_scheme(info, eps, material="corotated")
+        wide, _ = q.solve_scheme(info, eps, material="corotated", margins=margins)
+        assert wide["C"]["frac"] == plain["C"]["frac"]
+        got = autoquant._margin_windows(plain, names, info, margins)
+        assert got["C"] == wide["C"] and got["x"] == plain["x"]
+        # grow_only keeps a wider current window, and the new one holds the old
+        big = dict(wide, C=dict(wide["C"], bits=wide["C"]["bits"] + 1,
+                                offset=wide["C"]["offset"] - (1 << (wide["C"]["bits"] - 1))))
+        kept = autoquant._margin_windows(big, names, info, margins, grow_only=True)
+        assert kept["C"] == big["C"]
+        finer = autoquant._shift_frac(wide["C"], 1)
+        grown = autoquant._margin_windows(dict(wide, C=finer), names, info, margins, grow_only=True)
+        d = 2.0 ** -finer["frac"]
+        assert grown["C"]["offset"] * d <= finer["offset"] * d
+        assert (grown["C"]["offset"] + 2 ** grown["C"]["bits"] - 1) * d >= (finer["offset"] + 2 ** finer["bits"] - 1) * d
+
+
+def test_fill_word_slack_keeps_words_and_resolution(q):
+    from paper_2207_04658_b300 import autoquant
+    sch = {"x": {"bits": 16, "frac": 15, "offset": -9688, "container": 64},
+           "v": {"bits": 4, "frac": -2, "offset": -7, "container": 0},
+           "C": {"bits": 4, "frac": -11, "offset": -7, "container": 0},
+           "F": {"bits": 11, "frac": 7, "offset": -536, "container": 0}}
+    words = q.make_scheme_struct(sch, 3, "corotated").n_words
+    got = autoquant.fill_word_slack(sch, 3, "corotated")
+    assert q.make_scheme_struct(got, 3, "corotated").n_words == words
+    assert got["x"] == sch["x"]
+    for n in "vCF":
+        a, b = sch[n], got[n]
+        assert a["frac"] == b["frac"] and b["bits"] >= a["bits"]
+        assert b["offset"] <= a["offset"] and b["offset"] + 2 ** b["bits"] >= a["offset"] + 2 ** a["bits"]
+        # no type can take one more window bit without another word
+        wider = dict(got, **{n: autoquant._widened(got[n])})
+        assert q.make_scheme_struct(wider, 3, "corotated").n_words > words
+    # 3 v components and 9 of C take the 13 free bits of the last word: one bit each
+    assert (got["v"]["bits"], got["C"]["bits"], got["F"]["bits"]) == (5, 5, 11)
