@@ -188,21 +188,31 @@ def time_scene(qmpm, torch, sc, s0, sch, steps, warmup, dist_ctx):
     return g, ms, prof, st
 
 
-def e2e_scene(qmpm, torch, g, steps, warmup):
-    """End to end through qmpm_step_host: every step copies the packed state from pinned
-    host memory, steps it and copies it back."""
+def e2e_scene(qmpm, torch, g, steps, warmup, chunks=8):
+    """End to end through the host, every step: the packed state copied in from pinned host
+    memory, the grid cleared and the P2G redone from it, the step, and the state copied back.
+    Timed twice: through qmpm_step_host_stream (copies in `chunks` particle ranges, the
+    download of a step's result overlapping the next step's upload), the headline, and
+    through one qmpm_step_host call per step (the copies one after the other).  Returns
+    (seconds pipelined, seconds one call per step, bytes each way per step)."""
     r = g.readback(state=False, words=True, ids=False)
     words = r["words"]
-    hin = torch.from_numpy(words.copy()).pin_memory()
+    hw = torch.from_numpy(words.copy()).pin_memory()
+    qmpm.qmpm_step_host_stream(g.h, max(3, warmup), hw.data_ptr(), chunks)
+    t = time.perf_counter()
+    qmpm.qmpm_step_host_stream(g.h, steps, hw.data_ptr(), chunks)
+    el_stream = time.perf_counter() - t
+    hin = torch.from_numpy(hw.numpy().copy()).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
-    for _ in range(max(1, warmup)):
+    for _ in range(max(3, warmup)):
         qmpm.qmpm_step_host(g.h, 1, hin.data_ptr(), hout.data_ptr())
+        hin, hout = hout, hin
     t = time.perf_counter()
     for _ in range(steps):
         qmpm.qmpm_step_host(g.h, 1, hin.data_ptr(), hout.data_ptr())
         hin, hout = hout, hin
     el = time.perf_counter() - t
-    return el, int(words.nbytes)
+    return el_stream, el, int(words.nbytes)
 
 
 L2_BYTES = 126 * 2 ** 20  # B300 L2
@@ -817,11 +827,14 @@ def run_ours(args):
             "stats": {"active_blocks": st["active_blocks"], "out_of_tile": st["out_of_tile"]}}
     if not args.no_e2e:
         k = max(3, min(args.steps // 4, 50))
-        el, nbytes = e2e_scene(qmpm, torch, g, k, 1)
-        el = dc.max(torch, el)
+        el, el_serial, nbytes = e2e_scene(qmpm, torch, g, k, 3)
+        el, el_serial = dc.max(torch, el), dc.max(torch, el_serial)
         line["e2e"] = {"value": dc.world * N * k / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes,
-                       "path": "qmpm_step_host: pinned host words -> device, P2G, step, -> host"}
+                       "path": "qmpm_step_host_stream: pinned host words -> device, P2G, step, -> host, every "
+                               "step, copies in 8 particle ranges (download of one overlapping upload of the next)",
+                       "one_call_per_step": {"value": dc.world * N * k / el_serial, "unit": UNIT,
+                                             "path": "qmpm_step_host, copies one after the other"}}
     g.close()
     if not args.no_fp32:
         g32, ms32, prof32, st32 = time_scene(qmpm, torch, sc, s0, None, args.steps, args.warmup, dc)
@@ -836,10 +849,11 @@ def run_ours(args):
         if not args.no_e2e:
             # the same end-to-end path on FP32 state: four times the bytes over the host link
             k = max(3, min(args.steps // 4, 50))
-            el32, nb32 = e2e_scene(qmpm, torch, g32, k, 1)
-            el32 = dc.max(torch, el32)
+            el32, el32_serial, nb32 = e2e_scene(qmpm, torch, g32, k, 3)
+            el32, el32_serial = dc.max(torch, el32), dc.max(torch, el32_serial)
             line["fp32"]["e2e"] = {"value": dc.world * N * k / el32, "unit": UNIT,
-                                   "h2d_bytes_per_step": nb32, "d2h_bytes_per_step": nb32}
+                                   "h2d_bytes_per_step": nb32, "d2h_bytes_per_step": nb32,
+                                   "one_call_per_step": dc.world * N * k / el32_serial}
             if "e2e" in line:
                 line["e2e"]["quantized_over_fp32"] = round(line["e2e"]["value"] / line["fp32"]["e2e"]["value"], 3)
         g32.close()

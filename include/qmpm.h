@@ -228,6 +228,19 @@ int qmpm_measure(qmpm_handle h, double *z);
 int qmpm_step_host(qmpm_handle h, int32_t nsteps, const uint32_t *h_words_in,
                    uint32_t *h_words_out);
 
+/* End-to-end rollout through host memory, pipelined: nsteps steps, each of which takes
+ * its input state from h_words (pinned host, plane layout as qmpm_step_host, ld =
+ * n_particles) and writes its result back into h_words.  Every step uploads the words,
+ * clears the grid and redoes the P2G of the uploaded state (as qmpm_step_host), steps, and
+ * downloads the result.  The copies are split into `chunks` particle ranges: downloads run
+ * on a second stream owned by the handle, and the next step's upload of range j waits only
+ * for the download of range j, so the two directions of the host link overlap.  On return
+ * (the handle's stream and the copy stream synchronised) h_words holds the state after
+ * nsteps steps.  chunks in [0, 64]; 0 picks 8.
+ * Errors: QMPM_ERR_INVALID_ARG (bad handle, nsteps < 0, chunks out of range, NULL
+ * h_words with work to do), QMPM_ERR_CUDA. */
+int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int32_t chunks);
+
 /* Collect the device times recorded since the last reset (synchronises the stream).
  * reset != 0 clears the totals afterwards.  Kernel launches are counted whether or not
  * QMPM_FLAG_PROFILE is set. */

@@ -458,7 +458,9 @@ def dambreak3d_schemes(eps_list=(0.1, 0.01), cells=256, grid_log2=9, factor=4, T
     final particle positions (the scaling procedure of Sec. 8.3): the sensitivities and
     ranges of the column at 1/factor resolution (cells / factor cells on a grid factor times
     coarser, same dt and step count), the affine field C's window scaled by the resolution
-    ratio (C is a velocity gradient: it grows like 1 / dx), bit pack.  Returns
+    ratio (C is a velocity gradient: it grows like 1 / dx), bit pack, the last word's free
+    bits spent on wider windows of v, C and J (fill_word_slack: the dithered J wanders
+    past the range of the full-precision run).  Returns
     {eps: (scheme, solve report)} and the sensitivity report."""
     k = factor.bit_length() - 1
     sc_lo, s0_lo = scenes.dambreak3d_scene(column_cells=cells // factor, grid_log2=grid_log2 - k)
@@ -470,7 +472,8 @@ def dambreak3d_schemes(eps_list=(0.1, 0.01), cells=256, grid_log2=9, factor=4, T
     info_hi = dict(info, lo=lo, hi=hi)
     out = {}
     for eps in eps_list:
-        out[eps] = qmpm.solve_scheme(info_hi, eps, material="fluid")
+        scheme, res = qmpm.solve_scheme(info_hi, eps, material="fluid")
+        out[eps] = (fill_word_slack(scheme, 3, "fluid"), res)
     return out, info
 
 

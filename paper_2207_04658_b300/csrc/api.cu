@@ -72,6 +72,13 @@ void release(qmpm_ctx *c)
         for (auto e : c->prof->pool) cudaEventDestroy(e);
         delete c->prof;
     }
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    for (int j = 0; j < qmpm::kMaxCopyChunks; ++j)
+        if (c->copy_ev[j]) cudaEventDestroy(c->copy_ev[j]);
+    if (c->step_ev) cudaEventDestroy(c->step_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -518,6 +525,59 @@ int qmpm_step_host(qmpm_handle h, int32_t nsteps, const uint32_t *h_words_in, ui
     }
     e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_host");
+    return QMPM_OK;
+}
+
+int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int32_t chunks)
+{
+    if (!h || nsteps < 0 || chunks < 0 || chunks > qmpm::kMaxCopyChunks)
+        return fail(QMPM_ERR_INVALID_ARG, "qmpm_step_host_stream: bad handle, nsteps or chunks");
+    Ctx &c = *h;
+    if (c.N == 0 || nsteps == 0) return QMPM_OK;
+    if (!h_words) return fail(QMPM_ERR_INVALID_ARG, "qmpm_step_host_stream: no host buffer");
+    if (chunks == 0) chunks = 8;
+    cudaError_t e = cudaSuccess;
+    if (!c.copy_stream) e = cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c.step_ev) e = cudaEventCreateWithFlags(&c.step_ev, cudaEventDisableTiming);
+    for (int j = 0; j < chunks && e == cudaSuccess; ++j)
+        if (!c.copy_ev[j]) e = cudaEventCreateWithFlags(&c.copy_ev[j], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "qmpm_step_host_stream: copy stream");
+    const int64_t per = (c.N + chunks - 1) / chunks;
+    const size_t hp = sizeof(uint32_t) * (size_t)c.N, dp = sizeof(uint32_t) * (size_t)c.ld;
+    for (int s = 0; s < nsteps; ++s) {
+        // the input: range j after the previous step's download of range j (the same host
+        // words), so that it overlaps the download of the ranges after it
+        for (int j = 0; j < chunks; ++j) {
+            const int64_t p0 = (int64_t)j * per, n = std::min<int64_t>(per, c.N - p0);
+            if (n <= 0) break;
+            if (s > 0) e = cudaStreamWaitEvent(c.stream, c.copy_ev[j], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(c.words[c.cur] + p0, dp, h_words + p0, hp, sizeof(uint32_t) * (size_t)n,
+                                      (size_t)c.W, cudaMemcpyHostToDevice, c.stream);
+            if (e != cudaSuccess) return cuda_fail(e, "qmpm_step_host_stream: upload");
+        }
+        // the grid of the device's previous state is stale: clear it and redo the P2G
+        qmpm::batch_invalidate(c.batch);
+        int rc = do_clear(c, c.gcur);
+        if (rc != QMPM_OK) return rc;
+        c.primed = false;
+        rc = qmpm_step(h, 1);
+        if (rc != QMPM_OK) return rc;
+        // the result, range by range on the copy stream
+        e = cudaEventRecord(c.step_ev, c.stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c.copy_stream, c.step_ev, 0);
+        for (int j = 0; j < chunks && e == cudaSuccess; ++j) {
+            const int64_t p0 = (int64_t)j * per, n = std::min<int64_t>(per, c.N - p0);
+            if (n <= 0) break;
+            e = cudaMemcpy2DAsync(h_words + p0, hp, c.words[c.cur] + p0, dp, sizeof(uint32_t) * (size_t)n,
+                                  (size_t)c.W, cudaMemcpyDeviceToHost, c.copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c.copy_ev[j], c.copy_stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "qmpm_step_host_stream: download");
+    }
+    e = cudaStreamSynchronize(c.copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "qmpm_step_host_stream");
     return QMPM_OK;
 }
 

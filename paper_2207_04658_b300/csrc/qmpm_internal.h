@@ -95,6 +95,9 @@ struct Profile {
     int64_t n[4] = {0, 0, 0, 0};
 };
 
+// particle ranges of qmpm_step_host_stream's pipelined copies
+constexpr int kMaxCopyChunks = 64;
+
 struct Ctx {
     qmpm_scene_t scene;
     qmpm_scheme_t scheme;
@@ -136,6 +139,11 @@ struct Ctx {
     int64_t launches;           // kernel launches since the last profile reset
 
     qmpm_batch *batch;          // the batch the scene steps in, or null
+
+    // qmpm_step_host_stream: the download stream and its events, created on first use
+    cudaStream_t copy_stream;
+    cudaEvent_t copy_ev[kMaxCopyChunks];
+    cudaEvent_t step_ev;
 
     unsigned long long *d_stats; // 16 counters, then the step kernels' tile queue (2 x u32)
     double *d_z;

@@ -203,6 +203,7 @@ _SIGNATURES = [
                                  _P(qmpm_stats_t)]),
     ("qmpm_measure", ct.c_int, [ct.c_void_p, _P(ct.c_double)]),
     ("qmpm_step_host", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
+    ("qmpm_step_host_stream", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
     ("qmpm_profile", ct.c_int, [ct.c_void_p, _P(qmpm_profile_t), ct.c_int32]),
     ("qmpm_state_device", ct.c_int, [ct.c_void_p, _P(ct.c_void_p), _P(ct.c_int64),
                                      _P(ct.c_void_p)]),
@@ -410,6 +411,10 @@ def qmpm_measure(h):
 def qmpm_step_host(h, nsteps, h_words_in_ptr, h_words_out_ptr):
     _check(lib().qmpm_step_host(h, int(nsteps), ct.c_void_p(h_words_in_ptr),
                                 ct.c_void_p(h_words_out_ptr)))
+
+
+def qmpm_step_host_stream(h, nsteps, h_words_ptr, chunks=0):
+    _check(lib().qmpm_step_host_stream(h, int(nsteps), ct.c_void_p(h_words_ptr), int(chunks)))
 
 
 def qmpm_profile(h, reset=True):

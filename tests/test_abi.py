@@ -141,3 +141,11 @@ def test_scheme_solve_options_reject_bad_input(q):
         q.qmpm_scheme_solve([1.0, 1.0], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0], 1.0, 0.01, max_bits=-1)
     with pytest.raises(q.QmpmError):
         q.qmpm_scheme_solve([1.0, 1.0], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0], 1.0, 0.01, margins={0: (5, 1.0)})
+
+
+def test_step_host_stream_rejects_bad_arguments(q):
+    # argument checks come before any CUDA call: no device needed
+    for args in ((None, 1, 0, 0), (None, -1, 0, 0), (None, 1, 0, 65)):
+        with pytest.raises(q.QmpmError) as ei:
+            q.qmpm_step_host_stream(*args)
+        assert ei.value.code == -1

@@ -248,6 +248,38 @@ def test_step_host_round_trip(q, oracle):
     assert np.array_equal(hout.numpy(), b.readback(state=False, words=True, ids=False)["words"])
 
 
+@pytest.mark.parametrize("chunks", [1, 3, 64])
+def test_step_host_stream_matches_step_by_step_host_calls(q, oracle, chunks):
+    # the pipelined end-to-end rollout (copies in particle ranges on two streams) gives the
+    # state of one qmpm_step_host call per step, and leaves the final state in the host words
+    import torch
+    name, sc, s0, sch = SCENES[1]
+    a = q.Scene(sc, sch, s0)
+    b = q.Scene(sc, sch, s0)
+    w = a.readback(state=False, words=True, ids=False)["words"]
+    hin = torch.from_numpy(w.copy()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    steps = 5
+    for _ in range(steps):
+        q.qmpm_step_host(a.h, 1, hin.data_ptr(), hout.data_ptr())
+        hin, hout = hout, hin
+    hb = torch.from_numpy(w.copy()).pin_memory()
+    q.qmpm_step_host_stream(b.h, steps, hb.data_ptr(), chunks)
+    sa = a.readback(state=True, ids=False)["state"]
+    rb = b.readback(state=True, words=True, ids=False)
+    d = np.abs(sa - rb["state"]) / quanta(oracle, sc, sch)[None]
+    assert d.max() <= 2
+    assert np.array_equal(hb.numpy(), rb["words"])
+    # nothing to do, and bad arguments
+    q.qmpm_step_host_stream(b.h, 0, 0, chunks)
+    for bad in ((b.h, -1, hb.data_ptr(), 1), (b.h, 1, hb.data_ptr(), 65), (b.h, 1, 0, 1)):
+        with pytest.raises(q.QmpmError) as ei:
+            q.qmpm_step_host_stream(*bad)
+        assert ei.value.code == -1
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("dim,grid_log2", [(2, 11), (3, 10)])
 def test_largest_grids_free_fall(q, dim, grid_log2):
     # the largest grids the ABI accepts (2048^2, 1024^3: 35 GB of 3D grid buffers): a small
