@@ -188,11 +188,12 @@ def time_scene(qmpm, torch, sc, s0, sch, steps, warmup, dist_ctx):
     return g, ms, prof, st
 
 
-def e2e_scene(qmpm, torch, g, steps, warmup, chunks=8):
+def e2e_scene(qmpm, torch, g, steps, warmup, chunks=0):
     """End to end through the host, every step: the packed state copied in from pinned host
     memory, the grid cleared and the P2G redone from it, the step, and the state copied back.
-    Timed twice: through qmpm_step_host_stream (copies in `chunks` particle ranges, the
-    download of a step's result overlapping the next step's upload), the headline, and
+    Timed twice: through qmpm_step_host_stream (copies in `chunks` particle ranges, 0: the
+    library's choice, one per 16 MiB of state up to 8; the download of a step's result
+    overlapping the next step's upload), the headline, and
     through one qmpm_step_host call per step (the copies one after the other).  Returns
     (seconds pipelined, seconds one call per step, bytes each way per step)."""
     r = g.readback(state=False, words=True, ids=False)
@@ -348,7 +349,9 @@ def dambreak_variants(qmpm, torch, args, dc, peaks):
             err = float(torch.sqrt((d ** 2).sum(1).mean())) / rms
             zq = float((xq.double() ** 2).sum(1).mean())
             del xq, d
-            out.append({"eps": eps, "dither": dither, "bits": res["bits"], "frac": res["frac"],
+            names = ("x", "v", "C", "J")
+            out.append({"eps": eps, "dither": dither, "bits": [scheme[n]["bits"] for n in names],
+                        "frac": [scheme[n]["frac"] for n in names], "solved_bits": res["bits"],
                         "words_per_particle": W, "bytes_per_particle": 4 * W,
                         "value": dc.world * s0.shape[0] * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k,
                         "timed_steps": k,
@@ -518,28 +521,36 @@ def _oracle_slice(job):
 def cpu_baseline(name, scheme=None, sample_steps=2):
     """The oracle (single-threaded FP64 C, as it stands) on bounded samples of the same
     workload and scheme.  Single core: the first cube (or a slice of the column) on the full
-    grid, `sample_steps` quantized steps.  Aggregate: one oracle process per host core (capped
+    grid, `sample_steps` quantized steps (more for small scenes).  Aggregate: one oracle process per host core (capped
     by the memory each needs: the full FP64 grid plus its slice), each stepping a disjoint
     slice of the whole scene; value = the particle-steps of all processes over the slowest
-    one's time."""
+    one's time.  The unquantized FP64 oracle step on the single-core sample is reported
+    beside it."""
     import multiprocessing as mp
     import oracle
     sc, s0, sch, desc = workload(name, scheme=scheme)
     n = {"cubes3d": 512_000, "dambreak3d": 256_000}.get(name, s0.shape[0])
     what = {"cubes3d": "first cube of 16", "dambreak3d": "first particles of the column"}.get(name, "whole scene")
+    # small scenes take more steps, so that every sample is ~1e6 particle-steps or more
+    steps1 = max(sample_steps, min(100, int(2e6 // n)))
     ro = oracle.QuantRollout(sc, sch, s0[:n])
     t = time.perf_counter()
-    ro.step(sample_steps)
+    ro.step(steps1)
     el = time.perf_counter() - t
-    one = n * sample_steps / el
+    one = n * steps1 / el
+    rf = oracle.Fp64Rollout(sc, s0[:n])
+    t = time.perf_counter()
+    rf.step(steps1)
+    one_fp64 = n * steps1 / (time.perf_counter() - t)
+    del rf
     host = host_cpu()
     grid_bytes = oracle.n_nodes(ro.ph) * (1 + ro.ph.dim) * 8
     del ro
     per_proc = 2 * grid_bytes + 3 * 8 * s0.shape[1] * (s0.shape[0] // max(1, host["cores"]))
     P = max(1, min(host["cores"], 256, int(0.6 * host["mem_available_gb"] * 2 ** 30 // max(1, per_proc))))
     out = {"value": one, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{what} ({n} particles) on the full grid, {sample_steps} steps, the bench's scheme",
-           "host": host, "single_core": one}
+           "sample": f"{what} ({n} particles) on the full grid, {steps1} steps, the bench's scheme",
+           "host": host, "single_core": one, "single_core_fp64_unquantized": one_fp64}
     N = s0.shape[0]
     if P > 1:
         with tempfile.TemporaryDirectory() as td:
@@ -547,13 +558,15 @@ def cpu_baseline(name, scheme=None, sample_steps=2):
             np.save(path, s0)
             del s0
             bounds = [N * i // P for i in range(P + 1)]
-            jobs = [(sc, sch, path, bounds[i], bounds[i + 1], 1) for i in range(P)]
+            steps_p = max(1, min(100, int(2e6 // max(1, N // P))))
+            jobs = [(sc, sch, path, bounds[i], bounds[i + 1], steps_p) for i in range(P)]
             with mp.get_context("spawn").Pool(P) as pool:
                 res = pool.map(_oracle_slice, jobs, chunksize=1)
         work = sum(r[0] for r in res)
         out.update(value=work / max(r[1] for r in res), cores=P,
                    sample=f"{P} oracle processes (one per core, memory permitting), each a disjoint "
-                          f"1/{P} of the whole {N}-particle scene on the full grid for one quantized step, "
+                          f"1/{P} of the whole {N}-particle scene on the full grid for {steps_p} quantized "
+                          f"step{'s' if steps_p > 1 else ''}, "
                           "the bench's scheme; value = all particle-steps over the slowest process's time")
     return out
 
@@ -767,7 +780,7 @@ def run_ours(args):
                           "sensitivity_run": "16 cubes at half resolution (1,024,000 particles, 128^3), "
                                              "1000 steps, 2 Gaussian seeds on x_T"}
     variants = None
-    if args.workload == "dambreak3d" and not args.fixed_scheme:
+    if args.workload == "dambreak3d" and not args.fixed_scheme and not args.scheme_json:
         variants, scheme, dinfo = dambreak_variants(qmpm, torch, args, dc, peaks)
         solve_info = {"method": "Algorithm 1 (the scaling procedure of Sec. 8.3)", "eps": 0.01,
                       "sensitivity_run": "column of 64^3 cells on a 128^3 grid (2,097,152 particles), 500 steps, "
@@ -832,7 +845,7 @@ def run_ours(args):
         line["e2e"] = {"value": dc.world * N * k / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes,
                        "path": "qmpm_step_host_stream: pinned host words -> device, P2G, step, -> host, every "
-                               "step, copies in 8 particle ranges (download of one overlapping upload of the next)",
+                               "step, copies in up to 8 particle ranges (download of one overlapping upload of the next)",
                        "one_call_per_step": {"value": dc.world * N * k / el_serial, "unit": UNIT,
                                              "path": "qmpm_step_host, copies one after the other"}}
     g.close()

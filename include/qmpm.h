@@ -236,7 +236,8 @@ int qmpm_step_host(qmpm_handle h, int32_t nsteps, const uint32_t *h_words_in,
  * on a second stream owned by the handle, and the next step's upload of range j waits only
  * for the download of range j, so the two directions of the host link overlap.  On return
  * (the handle's stream and the copy stream synchronised) h_words holds the state after
- * nsteps steps.  chunks in [0, 64]; 0 picks 8.
+ * nsteps steps.  chunks in [0, 64]; 0 picks one range per 16 MiB of packed state, between
+ * 1 and 8.
  * Errors: QMPM_ERR_INVALID_ARG (bad handle, nsteps < 0, chunks out of range, NULL
  * h_words with work to do), QMPM_ERR_CUDA. */
 int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int32_t chunks);

@@ -535,7 +535,11 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
     Ctx &c = *h;
     if (c.N == 0 || nsteps == 0) return QMPM_OK;
     if (!h_words) return fail(QMPM_ERR_INVALID_ARG, "qmpm_step_host_stream: no host buffer");
-    if (chunks == 0) chunks = 8;
+    if (chunks == 0) {
+        // ranges of at least 16 MiB (a small state goes in one copy each way), at most 8
+        const int64_t bytes = (int64_t)sizeof(uint32_t) * c.N * c.W;
+        chunks = (int)std::max<int64_t>(1, std::min<int64_t>(8, bytes >> 24));
+    }
     cudaError_t e = cudaSuccess;
     if (!c.copy_stream) e = cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !c.step_ev) e = cudaEventCreateWithFlags(&c.step_ev, cudaEventDisableTiming);
