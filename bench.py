@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--scheme-json", default=None,
                     help="load a scheme saved by --save-scheme instead of solving it again")
     ap.add_argument("--save-scheme", default=None, help="write the solved scheme to this file")
+    ap.add_argument("--generic-kernel", action="store_true",
+                    help="step with the library's step kernel instead of the one compiled for the scheme")
     ap.add_argument("--fp32-state", action="store_true",
                     help="time the FP32 state as the headline (the comparator's step kernel, for profiling)")
     ap.add_argument("--resolve-scheme", action="store_true",
@@ -165,9 +167,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ our arm
-def time_scene(qmpm, torch, sc, s0, sch, steps, warmup, dist_ctx):
+def time_scene(qmpm, torch, sc, s0, sch, steps, warmup, dist_ctx, specialize=False):
+    """K steps of one scene timed with CUDA events on its stream after `warmup` steps;
+    specialize: step with the kernel compiled for the scheme at init (outside the timing)."""
     stream = torch.cuda.current_stream()
-    g = qmpm.Scene(sc, sch, s0, stream=stream.cuda_stream, profile=True)
+    g = qmpm.Scene(sc, sch, s0, stream=stream.cuda_stream, profile=True, specialize=specialize and sch is not None)
     for _ in range(warmup):
         g.step(1)
     torch.cuda.synchronize()
@@ -217,7 +221,7 @@ def e2e_scene(qmpm, torch, g, steps, warmup, chunks=0):
 
 
 L2_BYTES = 126 * 2 ** 20  # B300 L2
-STEP_SOURCES = ("step.cu", "device_common.cuh", "mpm_device.cuh", "qmpm_internal.h")
+STEP_SOURCES = ("step.cu", "step_kernels.cuh", "jit.cpp", "device_common.cuh", "mpm_device.cuh", "qmpm_internal.h")
 SMOKE_SOURCES = ("smoke.cu", "device_common.cuh", "qmpm_internal.h")
 
 
@@ -337,7 +341,8 @@ def dambreak_variants(qmpm, torch, args, dc, peaks):
         for dither in (True, False):
             s = dict(sc, dither=dither)
             k = max(8, min(args.steps, 64))
-            g, ms, prof, st = time_scene(qmpm, torch, s, s0, scheme, k, args.warmup, dc)
+            g, ms, prof, st = time_scene(qmpm, torch, s, s0, scheme, k, args.warmup, dc,
+                                         specialize=not args.generic_kernel)
             W = g.n_words
             g.close()
             gq = qmpm.Scene(s, scheme, s0, stats=True)
@@ -796,8 +801,10 @@ def run_ours(args):
     N = s0.shape[0]
     clocks = ClockSampler(dc.local)
     clocks.start()
-    g, ms, prof, st = time_scene(qmpm, torch, sc, s0, sch, args.steps, args.warmup, dc)
+    spec = sch is not None and not args.generic_kernel
+    g, ms, prof, st = time_scene(qmpm, torch, sc, s0, sch, args.steps, args.warmup, dc, specialize=spec)
     clk = clocks.stop()
+    kinfo = qmpm.qmpm_step_kernel_info(g.h)
     ms_max = dc.max(torch, ms)
     W = g.n_words
     from paper_2207_04658_b300.replicas import job_throughput
@@ -837,6 +844,11 @@ def run_ours(args):
                            bytes_per_particle_quantized=4 * W, bytes_per_particle_fp32=4 * g.n_comp,
                            compression=round(g.n_comp / W, 3), parallelism=f"replicas{dc.world}"),
             "roofline": roofline, "breakdown": breakdown, "clocks": clk,
+            "step_kernel": {"specialized_to_the_scheme": kinfo["specialized"],
+                            "compile_seconds": round(kinfo["compile_seconds"], 3),
+                            "how": ("the library's step kernel source compiled at qmpm_init (NVRTC, sm_103a) with "
+                                    "the scheme's codec table as constants, outside the timed region"
+                                    if kinfo["specialized"] else "the step kernel compiled with the library")},
             "stats": {"active_blocks": st["active_blocks"], "out_of_tile": st["out_of_tile"]}}
     if not args.no_e2e:
         k = max(3, min(args.steps // 4, 50))
@@ -849,6 +861,14 @@ def run_ours(args):
                        "one_call_per_step": {"value": dc.world * N * k / el_serial, "unit": UNIT,
                                              "path": "qmpm_step_host, copies one after the other"}}
     g.close()
+    if kinfo["specialized"]:
+        # the same steps with the library's step kernel, for comparison
+        gg, msg, profg, _ = time_scene(qmpm, torch, sc, s0, sch, args.steps, args.warmup, dc)
+        gg.close()
+        msg = dc.max(torch, msg)
+        line["step_kernel"]["library_kernel"] = {
+            "value": dc.world * N * args.steps / (msg / 1e3), "unit": UNIT, "ms_per_step": msg / args.steps,
+            "step_kernel_ms": round(profg["step_ms"] / max(1, profg["step_launches"]), 4)}
     if not args.no_fp32:
         g32, ms32, prof32, st32 = time_scene(qmpm, torch, sc, s0, None, args.steps, args.warmup, dc)
         ms32 = dc.max(torch, ms32)

@@ -21,7 +21,17 @@
 #ifndef QMPM_H
 #define QMPM_H
 
+#ifdef __CUDACC_RTC__
+/* compiled at run time (the scheme-specialised step kernel): no C library headers */
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+#else
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -45,6 +55,8 @@ enum { QMPM_FIELD_X = 0, QMPM_FIELD_V = 1, QMPM_FIELD_C = 2, QMPM_FIELD_F = 3 };
 #define QMPM_FLAG_STATS 1  /* count saturations and round-ups/-downs per field */
 #define QMPM_FLAG_STRICT 2 /* qmpm_readback fails with QMPM_ERR_OVERFLOW after a saturation */
 #define QMPM_FLAG_PROFILE 4 /* record CUDA events around each launch group (qmpm_profile) */
+#define QMPM_FLAG_SPECIALIZE 8 /* quantized state: step with a kernel compiled at qmpm_init for
+                                  this scheme (see qmpm_specialize_compile); FP32 state ignores it */
 
 /* Scene: one MLS-MPM simulation (the simulator quantized in Sec. 8.1).
  * Grid: n = 2^grid_log2 nodes per axis (n >= 16), dx = 1/n; sticky walls zero the grid
@@ -241,6 +253,31 @@ int qmpm_step_host(qmpm_handle h, int32_t nsteps, const uint32_t *h_words_in,
  * Errors: QMPM_ERR_INVALID_ARG (bad handle, nsteps < 0, chunks out of range, NULL
  * h_words with work to do), QMPM_ERR_CUDA. */
 int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int32_t chunks);
+
+/* The scheme-specialised step kernel (Sec. 3.1 Eq. 3 codec, Sec. 7 bit pack).  The step
+ * kernel compiled with the library reads each component's codec (word, shift, straddle,
+ * scale, offset) from its parameters; with QMPM_FLAG_SPECIALIZE, qmpm_init compiles the same
+ * kernel source once more at run time (NVRTC, sm_103a) with the scene's codec table as
+ * compile-time constants, and qmpm_step launches that kernel for the G2P -> store -> P2G
+ * step (the priming P2G, batches and the adjoint keep the library's kernels).  The results
+ * are those of the library's kernel: the arithmetic is the same.  Compiled kernels are
+ * kept for the life of the process, one per (dim, material, statistics flag, codec table);
+ * a first compile takes about a second.  The kernel sources are read from the csrc/
+ * directory beside the library file.
+ *
+ * qmpm_specialize_compile compiles (or finds) the kernel of a scheme without a device, for
+ * warming the cache and for checking that the runtime compiler works: *seconds receives
+ * the compile time of the first build, *cubin_bytes the size of the code (either may be
+ * NULL).  stats != 0 takes the variant with saturation counters.
+ * Errors: QMPM_ERR_INVALID_ARG (scheme NULL or not quantized), QMPM_ERR_SCHEME (layout),
+ * QMPM_ERR_CUDA (the runtime compiler failed: its log is in qmpm_last_error()). */
+int qmpm_specialize_compile(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, int32_t stats,
+                            double *seconds, int64_t *cubin_bytes);
+
+/* Which step kernel the handle launches: *specialized = 1 for the scheme-specialised one
+ * (QMPM_FLAG_SPECIALIZE), else 0; *compile_seconds = its compile time (0 if none).  Either
+ * pointer may be NULL.  Errors: QMPM_ERR_INVALID_ARG (bad handle). */
+int qmpm_step_kernel_info(qmpm_handle h, int32_t *specialized, double *compile_seconds);
 
 /* Collect the device times recorded since the last reset (synchronises the stream).
  * reset != 0 clears the totals afterwards.  Kernel launches are counted whether or not

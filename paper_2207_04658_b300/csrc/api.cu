@@ -328,6 +328,14 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
         if (ae == cudaErrorMemoryAllocation) return fail(QMPM_ERR_OOM, "device allocation failed");
         return cuda_fail(ae, "device allocation");
     }
+    if ((scene->flags & QMPM_FLAG_SPECIALIZE) && c->quant) {
+        std::string err;
+        rc = qmpm::specialize_step_kernel(*c, err);
+        if (rc != QMPM_OK) {
+            release(c);
+            return fail(rc, err);
+        }
+    }
     c->n_chunks = c->key_chunks + c->n_blocks;
     c->n_tiles = c->tile_idx + c->n_blocks;
     c->prof = new (std::nothrow) qmpm::Profile();
@@ -582,6 +590,30 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
     e = cudaStreamSynchronize(c.copy_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return cuda_fail(e, "qmpm_step_host_stream");
+    return QMPM_OK;
+}
+
+int qmpm_specialize_compile(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, int32_t stats,
+                            double *seconds, int64_t *cubin_bytes)
+{
+    if (!scheme || !scheme->quantized) return fail(QMPM_ERR_INVALID_ARG, "qmpm_specialize_compile: no quantized scheme");
+    qmpm_scheme_t s = *scheme;
+    std::string err;
+    int rc = qmpm::layout(dim, material, &s, err);
+    if (rc != QMPM_OK) return fail(rc, err);
+    qmpm::CompCodec cc[qmpm::kMaxComp];
+    qmpm::build_codec(s, dim, material, cc);
+    rc = qmpm::specialize_compile_only(dim, material, stats != 0, s.n_words, cc, qmpm::n_comp(dim, material), seconds,
+                                       cubin_bytes, err);
+    if (rc != QMPM_OK) return fail(rc, err);
+    return QMPM_OK;
+}
+
+int qmpm_step_kernel_info(qmpm_handle h, int32_t *specialized, double *compile_seconds)
+{
+    if (!h) return fail(QMPM_ERR_INVALID_ARG, "bad handle");
+    if (specialized) *specialized = h->spec_kernel ? 1 : 0;
+    if (compile_seconds) *compile_seconds = h->spec_kernel ? h->spec_seconds : 0.0;
     return QMPM_OK;
 }
 

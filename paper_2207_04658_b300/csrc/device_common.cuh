@@ -2,8 +2,10 @@
 // codec and the padded block layout of the grid.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 #include "qmpm_internal.h"
 

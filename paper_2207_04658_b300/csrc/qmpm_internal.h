@@ -1,11 +1,13 @@
 // qmpm_internal.h -- internal types of libqmpm shared by its translation units.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
+#endif
 
 #include "../../include/qmpm.h"
 
@@ -69,6 +71,13 @@ struct StepParams {
     const uint32_t *step_ctr;   // multi-scene launches: steps done so far (the store uses + 1)
     uint32_t *work;             // [0] next tile to take, [1] CTAs finished; both 0 between launches
 };
+
+}  // namespace qmpm
+
+// Everything below is host-side (or host-visible) only; a step kernel compiled at run time
+// for one scheme sees the types above.
+#ifndef __CUDACC_RTC__
+namespace qmpm {
 
 // Grid buffer of one member of a multi-scene clear.
 struct ClearItem {
@@ -140,6 +149,13 @@ struct Ctx {
 
     qmpm_batch *batch;          // the batch the scene steps in, or null
 
+    // QMPM_FLAG_SPECIALIZE: the step kernel compiled for this scheme (a cudaKernel_t), its
+    // NVRTC compile time, and the launch shape cached for its shared-memory size
+    void *spec_kernel;
+    double spec_seconds;
+    size_t spec_smem;
+    int spec_per_sm;
+
     // qmpm_step_host_stream: the download stream and its events, created on first use
     cudaStream_t copy_stream;
     cudaEvent_t copy_ev[kMaxCopyChunks];
@@ -209,6 +225,13 @@ cudaError_t launch_step_ctr(int dim, int material, bool quant, bool stats, const
                             int n_sms, cudaStream_t s);
 cudaError_t launch_advance(uint32_t *d_ctr, int n, cudaStream_t s);
 
+// jit.cpp: the step kernel specialised to the handle's scheme (sets spec_kernel; compiled on
+// first use and kept for the process), the compile alone (no device), and its launch
+int specialize_step_kernel(Ctx &c, std::string &err);
+int specialize_compile_only(int dim, int material, bool stats, int W, const CompCodec *cc, int nc,
+                            double *seconds, int64_t *cubin_bytes, std::string &err);
+cudaError_t launch_specialized(Ctx &c, const StepParams &p);
+
 // batch.cu: a member's host-side state changed outside the batch (its tables are stale)
 void batch_invalidate(qmpm_batch *b);
 
@@ -223,3 +246,5 @@ void destroy_nosync(qmpm_ctx *c);
 // The opaque handle type of the C ABI is the context itself.
 struct qmpm_ctx : public qmpm::Ctx {
 };
+
+#endif  // __CUDACC_RTC__

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libqmpm.so")
 
 MAX_COMP = 24
 MATERIALS = {"neohookean": 0, "corotated": 1, "fluid": 2}
-FLAG_STATS, FLAG_STRICT, FLAG_PROFILE = 1, 2, 4
+FLAG_STATS, FLAG_STRICT, FLAG_PROFILE, FLAG_SPECIALIZE = 1, 2, 4, 8
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "SCHEME", -4: "CUDA", -5: "TIMEOUT",
           -6: "OVERFLOW", -7: "QUEUE_FULL"}
 ERR_INVALID_ARG, ERR_OOM, ERR_SCHEME, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_QUEUE_FULL = -1, -2, -3, -4, -5, -6, -7
@@ -204,6 +204,9 @@ _SIGNATURES = [
     ("qmpm_measure", ct.c_int, [ct.c_void_p, _P(ct.c_double)]),
     ("qmpm_step_host", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     ("qmpm_step_host_stream", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
+    ("qmpm_specialize_compile", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32,
+                                           ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
+    ("qmpm_step_kernel_info", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double)]),
     ("qmpm_profile", ct.c_int, [ct.c_void_p, _P(qmpm_profile_t), ct.c_int32]),
     ("qmpm_state_device", ct.c_int, [ct.c_void_p, _P(ct.c_void_p), _P(ct.c_int64),
                                      _P(ct.c_void_p)]),
@@ -417,6 +420,22 @@ def qmpm_step_host_stream(h, nsteps, h_words_ptr, chunks=0):
     _check(lib().qmpm_step_host_stream(h, int(nsteps), ct.c_void_p(h_words_ptr), int(chunks)))
 
 
+def qmpm_specialize_compile(dim, material, scheme, stats=False):
+    """Compile (or find) the step kernel specialised to this scheme; no device needed.
+    Returns (seconds of the first compile, cubin bytes)."""
+    sch = make_scheme_struct(scheme)
+    sec, nb = ct.c_double(), ct.c_int64()
+    _check(lib().qmpm_specialize_compile(int(dim), MATERIALS[material], ct.byref(sch), int(bool(stats)),
+                                         ct.byref(sec), ct.byref(nb)))
+    return sec.value, nb.value
+
+
+def qmpm_step_kernel_info(h):
+    on, sec = ct.c_int32(), ct.c_double()
+    _check(lib().qmpm_step_kernel_info(h, ct.byref(on), ct.byref(sec)))
+    return {"specialized": bool(on.value), "compile_seconds": sec.value}
+
+
 def qmpm_profile(h, reset=True):
     p = qmpm_profile_t()
     _check(lib().qmpm_profile(h, ct.byref(p), int(reset)))
@@ -512,7 +531,7 @@ def qmpm_autotune(scene_struct, scheme_struct, h_state, trial_steps=32, use_cach
 class Scene:
     """One simulation resident on the device (a qmpm handle)."""
 
-    def __init__(self, scene, scheme, state0, stream=0, stats=False, strict=False, profile=False):
+    def __init__(self, scene, scheme, state0, stream=0, stats=False, strict=False, profile=False, specialize=False):
         self.scene = dict(scene)
         self.dim = scene["dim"]
         self.material = scene["material"]
@@ -521,7 +540,7 @@ class Scene:
         self.n_comp = _scenes.n_comp(self.dim, self.material)
         assert state0.shape[1] == self.n_comp
         flags = ((FLAG_STATS if stats else 0) | (FLAG_STRICT if strict else 0)
-                 | (FLAG_PROFILE if profile else 0))
+                 | (FLAG_PROFILE if profile else 0) | (FLAG_SPECIALIZE if specialize else 0))
         self._scene_struct = make_scene_struct(scene, self.N, flags)
         self._scheme_struct = make_scheme_struct(scheme, self.dim, self.material)
         self.quantized = scheme is not None

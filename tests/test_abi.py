@@ -149,3 +149,27 @@ def test_step_host_stream_rejects_bad_arguments(q):
         with pytest.raises(q.QmpmError) as ei:
             q.qmpm_step_host_stream(*args)
         assert ei.value.code == -1
+
+
+def test_specialized_step_kernel_compiles_without_a_device(q):
+    # the runtime compiler builds the scheme-specialised step kernel from the csrc/ sources
+    # beside the library, for 2D/3D and every material, with and without statistics
+    from paper_2207_04658_b300 import scenes
+    cases = [(2, "neohookean", scenes.block2d_scheme()),
+             (3, "corotated", scenes.fixed_scheme_3d("corotated")),
+             (3, "fluid", scenes.fixed_scheme_3d("fluid", C=(16, -2048.0, 2048.0)))]
+    for dim, material, scheme in cases:
+        for stats in (False, True):
+            sec, nbytes = q.qmpm_specialize_compile(dim, material, scheme, stats)
+            assert nbytes > 10000 and sec >= 0.0
+    # a second request returns the cached build
+    first = q.qmpm_specialize_compile(3, "fluid", cases[2][2], False)
+    assert q.qmpm_specialize_compile(3, "fluid", cases[2][2], False) == first
+
+
+def test_specialize_compile_rejects_bad_input(q):
+    with pytest.raises(q.QmpmError) as ei:
+        q.qmpm_specialize_compile(3, "corotated", None)
+    assert ei.value.code == -1
+    with pytest.raises(q.QmpmError):
+        q.qmpm_step_kernel_info(None)

@@ -58,10 +58,12 @@ def test_init_encode_and_sort_bit_exact(q, oracle, case):
     g.close()
 
 
+@pytest.mark.parametrize("spec", [False, True], ids=["library", "specialized"])
 @pytest.mark.parametrize("case", range(len(SCENES)), ids=IDS)
-def test_one_quantized_step_within_two_quanta(q, oracle, case):
+def test_one_quantized_step_within_two_quanta(q, oracle, case, spec):
     name, sc, s0, sch = SCENES[case]
-    g = q.Scene(sc, sch, s0, stats=True)
+    g = q.Scene(sc, sch, s0, stats=True, specialize=spec)
+    assert q.qmpm_step_kernel_info(g.h)["specialized"] == spec
     o = oracle.QuantRollout(sc, sch, s0)
     g.step(1)
     o.step(1)
@@ -73,6 +75,32 @@ def test_one_quantized_step_within_two_quanta(q, oracle, case):
     assert (d == 0).mean() > 0.95
     assert sum(r["stats"]["saturations"]) == 0
     g.close()
+
+
+@pytest.mark.parametrize("case", range(len(SCENES)), ids=IDS)
+def test_specialized_step_matches_the_library_kernel(q, oracle, case):
+    # the kernel compiled for the scheme does the library kernel's arithmetic.  The grid a
+    # step starts from is summed by FP32 atomics from the overlapping tiles, in an order
+    # that varies from run to run, so two runs of either kernel may store a code one quantum
+    # apart where a value sits at a rounding threshold; all else is equal
+    name, sc, s0, sch = SCENES[case]
+    a = q.Scene(sc, sch, s0)
+    b = q.Scene(sc, sch, s0, specialize=True)
+    info = q.qmpm_step_kernel_info(b.h)
+    assert info["specialized"] and not q.qmpm_step_kernel_info(a.h)["specialized"]
+    assert info["compile_seconds"] >= 0.0
+    a.step(1)
+    b.step(1)
+    ra = a.readback(state=True, words=True, ids=True)
+    rb = b.readback(state=True, words=True, ids=True)
+    assert np.array_equal(ra["ids"], rb["ids"])
+    d = np.abs(ra["state"] - rb["state"]) / quanta(oracle, sc, sch)[None]
+    assert d.max() <= 1.0 + 1e-9 and (d > 0).mean() <= 1e-3, (d.max(), (d > 0).mean())
+    # FP32 state ignores the flag
+    c = q.Scene(sc, None, s0, specialize=True)
+    assert not q.qmpm_step_kernel_info(c.h)["specialized"]
+    for g in (a, b, c):
+        g.close()
 
 
 @pytest.mark.parametrize("case", range(len(SCENES)), ids=IDS)
@@ -113,11 +141,12 @@ def test_fp32_step_matches_fp64(q, oracle, case):
     g.close()
 
 
+@pytest.mark.parametrize("spec", [False, True], ids=["library", "specialized"])
 @pytest.mark.parametrize("case", [0, 1, 3], ids=[IDS[0], IDS[1], IDS[3]])
-def test_quantized_rollout_tracks_oracle(q, oracle, case):
+def test_quantized_rollout_tracks_oracle(q, oracle, case, spec):
     name, sc, s0, sch = SCENES[case]
     steps = 40
-    g = q.Scene(sc, sch, s0, stats=True)
+    g = q.Scene(sc, sch, s0, stats=True, specialize=spec)
     o = oracle.QuantRollout(sc, sch, s0)
     g.step(steps)
     o.step(steps)
