@@ -261,18 +261,21 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
  * compile-time constants, and qmpm_step launches that kernel for the G2P -> store -> P2G
  * step (the priming P2G, batches and the adjoint keep the library's kernels).  The results
  * are those of the library's kernel: the arithmetic is the same.  Compiled kernels are
- * kept for the life of the process, one per (dim, material, statistics flag, codec table);
+ * kept for the life of the process, one per (dim, material, statistics and dither flags,
+ * codec table);
  * a first compile takes about a second.  The kernel sources are read from the csrc/
  * directory beside the library file.
  *
  * qmpm_specialize_compile compiles (or finds) the kernel of a scheme without a device, for
  * warming the cache and for checking that the runtime compiler works: *seconds receives
  * the compile time of the first build, *cubin_bytes the size of the code (either may be
- * NULL).  stats != 0 takes the variant with saturation counters.
+ * NULL).  stats != 0 takes the variant with saturation counters, dither != 0 the one with
+ * dithered stores (the scene's dither flag is a compile-time constant of the kernel, as are
+ * the record's word count and the codec table).
  * Errors: QMPM_ERR_INVALID_ARG (scheme NULL or not quantized), QMPM_ERR_SCHEME (layout),
  * QMPM_ERR_CUDA (the runtime compiler failed: its log is in qmpm_last_error()). */
 int qmpm_specialize_compile(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, int32_t stats,
-                            double *seconds, int64_t *cubin_bytes);
+                            int32_t dither, double *seconds, int64_t *cubin_bytes);
 
 /* Which step kernel the handle launches: *specialized = 1 for the scheme-specialised one
  * (QMPM_FLAG_SPECIALIZE), else 0; *compile_seconds = its compile time (0 if none).  Either

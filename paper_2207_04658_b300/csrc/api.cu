@@ -594,7 +594,7 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
 }
 
 int qmpm_specialize_compile(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, int32_t stats,
-                            double *seconds, int64_t *cubin_bytes)
+                            int32_t dither, double *seconds, int64_t *cubin_bytes)
 {
     if (!scheme || !scheme->quantized) return fail(QMPM_ERR_INVALID_ARG, "qmpm_specialize_compile: no quantized scheme");
     qmpm_scheme_t s = *scheme;
@@ -603,8 +603,8 @@ int qmpm_specialize_compile(int32_t dim, int32_t material, const qmpm_scheme_t *
     if (rc != QMPM_OK) return fail(rc, err);
     qmpm::CompCodec cc[qmpm::kMaxComp];
     qmpm::build_codec(s, dim, material, cc);
-    rc = qmpm::specialize_compile_only(dim, material, stats != 0, s.n_words, cc, qmpm::n_comp(dim, material), seconds,
-                                       cubin_bytes, err);
+    rc = qmpm::specialize_compile_only(dim, material, stats != 0, dither != 0, s.n_words, cc, qmpm::n_comp(dim, material),
+                                       seconds, cubin_bytes, err);
     if (rc != QMPM_OK) return fail(rc, err);
     return QMPM_OK;
 }

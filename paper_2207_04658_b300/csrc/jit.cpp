@@ -1,11 +1,12 @@
 // jit.cpp -- the step kernel specialised to one scheme.  step_kernels.cuh is compiled at run
 // time by NVRTC with the scene's codec table (Sec. 3.1 Eq. 3, Sec. 7 bit pack) as
-// compile-time constants (QMPM_SPECIALIZED_CODEC), loaded as a CUDA library and launched by
+// compile-time constants (QMPM_SPECIALIZED_CODEC), with the record's word count and the
+// dither flag, loaded as a CUDA library and launched by
 // launch_g2p2g in place of the kernel compiled with the library.  The arithmetic is the
 // same; what changes is that a component's word index, shift and straddle are immediates,
 // so the decode reads fixed shared-memory offsets and the encode assembles the record words
 // in registers.  Compiled cubins are kept for the life of the process, one per generated
-// source (that is, per dimension, material, statistics flag and codec table).
+// source (that is, per dimension, material, statistics and dither flags and codec table).
 #include <dlfcn.h>
 #include <nvrtc.h>
 
@@ -57,7 +58,7 @@ std::string kernel_name(int dim, int material, bool stats)
            (stats ? "true" : "false") + ", true>";
 }
 
-std::string kernel_source(int dim, int material, int W, const CompCodec *cc, int nc)
+std::string kernel_source(int dim, int material, int W, bool dither, const CompCodec *cc, int nc)
 {
     std::string s;
     s += "#define QMPM_SPECIALIZED_CODEC 1\n";
@@ -65,6 +66,7 @@ std::string kernel_source(int dim, int material, int W, const CompCodec *cc, int
     s += "namespace qmpm {\n";
     s += "constexpr int kSpecDim = " + std::to_string(dim) + ", kSpecMat = " + std::to_string(material) +
          ", kSpecWords = " + std::to_string(W) + ";\n";
+    s += std::string("constexpr bool kSpecDither = ") + (dither ? "true" : "false") + ";\n";
     s += "__device__ constexpr CompCodec kSpecCodec[" + std::to_string(nc) + "] = {\n";
     for (int c = 0; c < nc; ++c) {
         const CompCodec &k = cc[c];
@@ -129,9 +131,10 @@ int compile(const std::string &src, const std::string &name, Compiled &out, std:
 }
 
 // The cache entry of this codec, compiled on first use.  g_mu held.
-int entry(int dim, int material, bool stats, int W, const CompCodec *cc, int nc, Compiled *&out, std::string &err)
+int entry(int dim, int material, bool stats, int W, bool dither, const CompCodec *cc, int nc, Compiled *&out,
+          std::string &err)
 {
-    const std::string src = kernel_source(dim, material, W, cc, nc);
+    const std::string src = kernel_source(dim, material, W, dither, cc, nc);
     const std::string name = kernel_name(dim, material, stats);
     const std::string key = name + "\n" + src;
     auto it = g_cache.find(key);
@@ -152,7 +155,7 @@ int specialize_step_kernel(Ctx &c, std::string &err)
     const bool stats = (c.scene.flags & QMPM_FLAG_STATS) != 0;
     std::lock_guard<std::mutex> lk(g_mu);
     Compiled *e = nullptr;
-    int rc = entry(c.scene.dim, c.scene.material, stats, c.W, c.cc, c.n_comp, e, err);
+    int rc = entry(c.scene.dim, c.scene.material, stats, c.W, c.scene.dither != 0, c.cc, c.n_comp, e, err);
     if (rc != QMPM_OK) return rc;
     if (!e->kern) {
         cudaError_t r = cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
@@ -173,12 +176,12 @@ int specialize_step_kernel(Ctx &c, std::string &err)
     return QMPM_OK;
 }
 
-int specialize_compile_only(int dim, int material, bool stats, int W, const CompCodec *cc, int nc,
+int specialize_compile_only(int dim, int material, bool stats, bool dither, int W, const CompCodec *cc, int nc,
                             double *seconds, int64_t *cubin_bytes, std::string &err)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     Compiled *e = nullptr;
-    const int rc = entry(dim, material, stats, W, cc, nc, e, err);
+    const int rc = entry(dim, material, stats, W, dither, cc, nc, e, err);
     if (rc != QMPM_OK) return rc;
     if (seconds) *seconds = e->seconds;
     if (cubin_bytes) *cubin_bytes = (int64_t)e->cubin.size();

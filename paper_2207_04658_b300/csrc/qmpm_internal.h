@@ -228,7 +228,7 @@ cudaError_t launch_advance(uint32_t *d_ctr, int n, cudaStream_t s);
 // jit.cpp: the step kernel specialised to the handle's scheme (sets spec_kernel; compiled on
 // first use and kept for the process), the compile alone (no device), and its launch
 int specialize_step_kernel(Ctx &c, std::string &err);
-int specialize_compile_only(int dim, int material, bool stats, int W, const CompCodec *cc, int nc,
+int specialize_compile_only(int dim, int material, bool stats, bool dither, int W, const CompCodec *cc, int nc,
                             double *seconds, int64_t *cubin_bytes, std::string &err);
 cudaError_t launch_specialized(Ctx &c, const StepParams &p);
 

@@ -21,11 +21,32 @@ namespace qmpm {
 // are known, and the encode assembles the record words in registers.
 #ifndef QMPM_SPECIALIZED_CODEC
 constexpr int kSpecDim = 0, kSpecMat = -1, kSpecWords = 1;
+constexpr bool kSpecDither = false;
 __device__ constexpr CompCodec kSpecCodec[1] = {};
 #endif
 
 template <int DIM, int MAT, bool QUANT>
 constexpr bool specialized_codec() { return QUANT && DIM == kSpecDim && MAT == kSpecMat; }
+
+// The record's word count and whether the stores are dithered: compile-time constants in
+// the specialised kernel (its loops over the words unroll), the parameters otherwise.
+template <int DIM, int MAT, bool QUANT>
+__device__ __forceinline__ int words_of(const StepParams &P)
+{
+    if constexpr (specialized_codec<DIM, MAT, QUANT>())
+        return kSpecWords;
+    else
+        return P.n_words;
+}
+
+template <int DIM, int MAT, bool QUANT>
+__device__ __forceinline__ bool dithered(const StepParams &P)
+{
+    if constexpr (specialized_codec<DIM, MAT, QUANT>())
+        return kSpecDither;
+    else
+        return P.dither != 0;
+}
 
 template <int DIM, int MAT, bool QUANT>
 __device__ __forceinline__ const CompCodec &codec_of(const StepParams &P, int c)
@@ -267,7 +288,8 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
     const Chunk ch = P.chunks[ci0 + jc];
     // 2. coalesced load of the chunk's records into shared memory (column per slot)
     if (tid < (int)ch.count)
-        for (int j = 0; j < P.n_words; ++j) sw[j * kThreads + mycol] = P.words[j * P.ld + ch.start + tid];
+        for (int j = 0; j < words_of<DIM, MAT, QUANT>(P); ++j)
+            sw[j * kThreads + mycol] = P.words[j * P.ld + ch.start + tid];
     __syncthreads();
 
     const int pj = chunk_particle(tid, (int)ch.count);
@@ -366,7 +388,7 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
                 uint4 rnd = make_uint4(0, 0, 0, 0);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    if (P.dither && (c & 7) == 0) {
+                    if (dithered<DIM, MAT, QUANT>(P) && (c & 7) == 0) {
                         const uint4 ctr = make_uint4((uint32_t)slot, MULTI ? step : P.step, (uint32_t)(c >> 3), 0u);
                         if (ROUND_KEYS)
                             rnd = philox4x32_rk(ctr, P.round_key);
@@ -375,7 +397,7 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
                     }
                     int fl;
                     const CompCodec &cc = codec_of<DIM, MAT, QUANT>(P, c);
-                    const uint32_t u = encode_f32(val[c], cc, P.dither != 0, dither_threshold(rnd, c), fl);
+                    const uint32_t u = encode_f32(val[c], cc, dithered<DIM, MAT, QUANT>(P), dither_threshold(rnd, c), fl);
                     ow[cc.word] |= u << cc.shift;
                     if (cc.straddle) ow[cc.word + 1] |= __funnelshift_l(u, 0u, cc.shift);
                     val[c] = decode_u(u, cc);  // the stored (quantized) value
@@ -561,7 +583,8 @@ __device__ __forceinline__ void run_chunk(const StepParams &P, const uint32_t ci
 
     // 6. coalesced store of the new records
     if (DO_G2P && tid < (int)ch.count)
-        for (int j = 0; j < P.n_words; ++j) __stcs(P.words + j * P.ld + ch.start + tid, sw[j * kThreads + mycol]);
+        for (int j = 0; j < words_of<DIM, MAT, QUANT>(P); ++j)
+            __stcs(P.words + j * P.ld + ch.start + tid, sw[j * kThreads + mycol]);
     if (jc + 1 < n_tile_chunks) __syncthreads();  // the next chunk reuses the record columns
     }  // chunks of the tile
 

@@ -204,7 +204,7 @@ _SIGNATURES = [
     ("qmpm_measure", ct.c_int, [ct.c_void_p, _P(ct.c_double)]),
     ("qmpm_step_host", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     ("qmpm_step_host_stream", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
-    ("qmpm_specialize_compile", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32,
+    ("qmpm_specialize_compile", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_int32,
                                            ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
     ("qmpm_step_kernel_info", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double)]),
     ("qmpm_profile", ct.c_int, [ct.c_void_p, _P(qmpm_profile_t), ct.c_int32]),
@@ -420,13 +420,13 @@ def qmpm_step_host_stream(h, nsteps, h_words_ptr, chunks=0):
     _check(lib().qmpm_step_host_stream(h, int(nsteps), ct.c_void_p(h_words_ptr), int(chunks)))
 
 
-def qmpm_specialize_compile(dim, material, scheme, stats=False):
+def qmpm_specialize_compile(dim, material, scheme, stats=False, dither=True):
     """Compile (or find) the step kernel specialised to this scheme; no device needed.
     Returns (seconds of the first compile, cubin bytes)."""
     sch = make_scheme_struct(scheme)
     sec, nb = ct.c_double(), ct.c_int64()
     _check(lib().qmpm_specialize_compile(int(dim), MATERIALS[material], ct.byref(sch), int(bool(stats)),
-                                         ct.byref(sec), ct.byref(nb)))
+                                         int(bool(dither)), ct.byref(sec), ct.byref(nb)))
     return sec.value, nb.value
 
 

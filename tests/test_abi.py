@@ -159,8 +159,8 @@ def test_specialized_step_kernel_compiles_without_a_device(q):
              (3, "corotated", scenes.fixed_scheme_3d("corotated")),
              (3, "fluid", scenes.fixed_scheme_3d("fluid", C=(16, -2048.0, 2048.0)))]
     for dim, material, scheme in cases:
-        for stats in (False, True):
-            sec, nbytes = q.qmpm_specialize_compile(dim, material, scheme, stats)
+        for stats, dither in ((False, True), (True, True), (False, False)):
+            sec, nbytes = q.qmpm_specialize_compile(dim, material, scheme, stats, dither)
             assert nbytes > 10000 and sec >= 0.0
     # a second request returns the cached build
     first = q.qmpm_specialize_compile(3, "fluid", cases[2][2], False)

@@ -77,14 +77,16 @@ def test_one_quantized_step_within_two_quanta(q, oracle, case, spec):
     g.close()
 
 
+@pytest.mark.parametrize("dither", [True, False], ids=["dithered", "nearest"])
 @pytest.mark.parametrize("case", range(len(SCENES)), ids=IDS)
-def test_specialized_step_matches_the_library_kernel(q, oracle, case):
+def test_specialized_step_matches_the_library_kernel(q, oracle, case, dither):
     # the kernel compiled for the scheme does the library kernel's arithmetic.  The grid a
     # step starts from is summed by FP32 atomics from the overlapping tiles, in an order
     # that varies from run to run, and the two compilations may contract a multiply-add
     # differently; either moves a value by an FP32 rounding, so a code can land one quantum
     # apart where the value sits at a rounding threshold; nearly all are equal
     name, sc, s0, sch = SCENES[case]
+    sc = dict(sc, dither=dither)
     a = q.Scene(sc, sch, s0)
     b = q.Scene(sc, sch, s0, specialize=True)
     info = q.qmpm_step_kernel_info(b.h)
