@@ -345,7 +345,7 @@ def dambreak_variants(qmpm, torch, args, dc, peaks):
                                          specialize=not args.generic_kernel)
             W = g.n_words
             g.close()
-            gq = qmpm.Scene(s, scheme, s0, stats=True)
+            gq = qmpm.Scene(s, scheme, s0, stats=True, specialize=not args.generic_kernel)
             gq.step(T)
             xq = device_positions(qmpm, torch, gq)
             sat = gq.readback(state=False, ids=False)["stats"]["saturations"]
@@ -370,15 +370,16 @@ def dambreak_variants(qmpm, torch, args, dc, peaks):
     return out, schemes[0.01][0], info
 
 
-def accuracy(qmpm, sc, s0, sch):
+def accuracy(qmpm, sc, s0, sch, specialize=False):
     """Full rollouts (the scene's step count) of the quantized and the FP32 state from the
     same initial state: relative error of z = mean |x|^2 and RMS per-particle position
-    error over RMS position (the bound the scheme was solved for), compared on the device."""
+    error over RMS position (the bound the scheme was solved for), compared on the device.
+    specialize: the quantized run steps with the kernel compiled for the scheme, as timed."""
     import torch
     steps = int(sc.get("steps", 1000))
     out = {}
     for name, scheme in (("quant", sch), ("fp32", None)):
-        g = qmpm.Scene(sc, scheme, s0, stats=True)
+        g = qmpm.Scene(sc, scheme, s0, stats=True, specialize=specialize and scheme is not None)
         g.step(steps)
         out[name] = (device_positions(qmpm, torch, g).double(), g.readback(state=False, ids=False)["stats"])
         g.close()
@@ -895,7 +896,7 @@ def run_ours(args):
     if variants is not None:
         line["variants"] = variants
     if not args.no_accuracy and dc.rank == 0 and variants is None:
-        line["accuracy"] = accuracy(qmpm, sc, s0, sch)
+        line["accuracy"] = accuracy(qmpm, sc, s0, sch, specialize=spec)
     if args.serving_duration > 0:
         line["serving"] = serving(qmpm, args.serving_duration, dc=dc)
     if not args.no_smoke:
