@@ -55,8 +55,8 @@ enum { QMPM_FIELD_X = 0, QMPM_FIELD_V = 1, QMPM_FIELD_C = 2, QMPM_FIELD_F = 3 };
 #define QMPM_FLAG_STATS 1  /* count saturations and round-ups/-downs per field */
 #define QMPM_FLAG_STRICT 2 /* qmpm_readback fails with QMPM_ERR_OVERFLOW after a saturation */
 #define QMPM_FLAG_PROFILE 4 /* record CUDA events around each launch group (qmpm_profile) */
-#define QMPM_FLAG_SPECIALIZE 8 /* quantized state: step with a kernel compiled at qmpm_init for
-                                  this scheme (see qmpm_specialize_compile); FP32 state ignores it */
+#define QMPM_FLAG_SPECIALIZE 8 /* step with a kernel compiled at qmpm_init for this scheme (FP32
+                                  state: for its word count; see qmpm_specialize_compile) */
 
 /* Scene: one MLS-MPM simulation (the simulator quantized in Sec. 8.1).
  * Grid: n = 2^grid_log2 nodes per axis (n >= 16), dx = 1/n; sticky walls zero the grid
@@ -258,12 +258,12 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
  * kernel compiled with the library reads each component's codec (word, shift, straddle,
  * scale, offset) from its parameters; with QMPM_FLAG_SPECIALIZE, qmpm_init compiles the same
  * kernel source once more at run time (NVRTC, sm_103a) with the scene's codec table as
- * compile-time constants, and qmpm_step launches that kernel for the G2P -> store -> P2G
- * step (the priming P2G, batches and the adjoint keep the library's kernels).  The results
- * are those of the library's kernel: the arithmetic is the same.  Compiled kernels are
- * kept for the life of the process, one per (dim, material, statistics and dither flags,
- * codec table);
- * a first compile takes about a second.  The kernel sources are read from the csrc/
+ * compile-time constants (FP32 state: its word count), and qmpm_step launches that kernel
+ * for the G2P -> store -> P2G step (the priming P2G, batches and the adjoint keep the
+ * library's kernels).  The results are those of the library's kernel: the arithmetic is
+ * the same.  Compiled kernels are kept for the life of the process, one per (dim,
+ * material, state, statistics and dither flags, codec table); a first compile takes about
+ * a second.  The kernel sources are read from the csrc/
  * directory beside the library file.
  *
  * qmpm_specialize_compile compiles (or finds) the kernel of a scheme without a device, for
@@ -272,7 +272,9 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
  * NULL).  stats != 0 takes the variant with saturation counters, dither != 0 the one with
  * dithered stores (the scene's dither flag is a compile-time constant of the kernel, as are
  * the record's word count and the codec table).
- * Errors: QMPM_ERR_INVALID_ARG (scheme NULL or not quantized), QMPM_ERR_SCHEME (layout),
+ * scheme NULL (or not quantized) compiles the FP32-state kernel, whose record word count is
+ * the constant.
+ * Errors: QMPM_ERR_INVALID_ARG (bad dim or material), QMPM_ERR_SCHEME (layout),
  * QMPM_ERR_CUDA (the runtime compiler failed: its log is in qmpm_last_error()). */
 int qmpm_specialize_compile(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, int32_t stats,
                             int32_t dither, double *seconds, int64_t *cubin_bytes);

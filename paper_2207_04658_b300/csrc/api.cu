@@ -328,7 +328,7 @@ int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const doub
         if (ae == cudaErrorMemoryAllocation) return fail(QMPM_ERR_OOM, "device allocation failed");
         return cuda_fail(ae, "device allocation");
     }
-    if ((scene->flags & QMPM_FLAG_SPECIALIZE) && c->quant) {
+    if (scene->flags & QMPM_FLAG_SPECIALIZE) {
         std::string err;
         rc = qmpm::specialize_step_kernel(*c, err);
         if (rc != QMPM_OK) {
@@ -596,15 +596,21 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
 int qmpm_specialize_compile(int32_t dim, int32_t material, const qmpm_scheme_t *scheme, int32_t stats,
                             int32_t dither, double *seconds, int64_t *cubin_bytes)
 {
-    if (!scheme || !scheme->quantized) return fail(QMPM_ERR_INVALID_ARG, "qmpm_specialize_compile: no quantized scheme");
-    qmpm_scheme_t s = *scheme;
+    if ((dim != 2 && dim != 3) || material < 0 || material > 2)
+        return fail(QMPM_ERR_INVALID_ARG, "qmpm_specialize_compile: bad dim or material");
+    qmpm_scheme_t s;
+    if (scheme && scheme->quantized) {
+        s = *scheme;
+    } else {
+        std::memset(&s, 0, sizeof(s));  // FP32 state
+    }
     std::string err;
     int rc = qmpm::layout(dim, material, &s, err);
     if (rc != QMPM_OK) return fail(rc, err);
     qmpm::CompCodec cc[qmpm::kMaxComp];
     qmpm::build_codec(s, dim, material, cc);
-    rc = qmpm::specialize_compile_only(dim, material, stats != 0, dither != 0, s.n_words, cc, qmpm::n_comp(dim, material),
-                                       seconds, cubin_bytes, err);
+    rc = qmpm::specialize_compile_only(dim, material, stats != 0, dither != 0, s.n_words, s.quantized ? cc : nullptr,
+                                       qmpm::n_comp(dim, material), seconds, cubin_bytes, err);
     if (rc != QMPM_OK) return fail(rc, err);
     return QMPM_OK;
 }

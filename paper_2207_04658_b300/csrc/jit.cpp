@@ -1,7 +1,7 @@
 // jit.cpp -- the step kernel specialised to one scheme.  step_kernels.cuh is compiled at run
 // time by NVRTC with the scene's codec table (Sec. 3.1 Eq. 3, Sec. 7 bit pack) as
 // compile-time constants (QMPM_SPECIALIZED_CODEC), with the record's word count and the
-// dither flag, loaded as a CUDA library and launched by
+// dither flag (FP32 state: the word count alone), loaded as a CUDA library and launched by
 // launch_g2p2g in place of the kernel compiled with the library.  The arithmetic is the
 // same; what changes is that a component's word index, shift and straddle are immediates,
 // so the decode reads fixed shared-memory offsets and the encode assembles the record words
@@ -52,12 +52,13 @@ std::string hex_float(float v)
     return b;
 }
 
-std::string kernel_name(int dim, int material, bool stats)
+std::string kernel_name(int dim, int material, bool quant, bool stats)
 {
-    return "qmpm::step_kernel<" + std::to_string(dim) + ", " + std::to_string(material) + ", true, " +
-           (stats ? "true" : "false") + ", true>";
+    return "qmpm::step_kernel<" + std::to_string(dim) + ", " + std::to_string(material) + ", " +
+           (quant ? "true" : "false") + ", " + (stats ? "true" : "false") + ", true>";
 }
 
+// cc == nullptr: FP32 state (the word count and the dither flag only)
 std::string kernel_source(int dim, int material, int W, bool dither, const CompCodec *cc, int nc)
 {
     std::string s;
@@ -66,7 +67,13 @@ std::string kernel_source(int dim, int material, int W, bool dither, const CompC
     s += "namespace qmpm {\n";
     s += "constexpr int kSpecDim = " + std::to_string(dim) + ", kSpecMat = " + std::to_string(material) +
          ", kSpecWords = " + std::to_string(W) + ";\n";
-    s += std::string("constexpr bool kSpecDither = ") + (dither ? "true" : "false") + ";\n";
+    s += std::string("constexpr bool kSpecQuant = ") + (cc ? "true" : "false") + ", kSpecDither = " +
+         (dither ? "true" : "false") + ";\n";
+    if (!cc) {
+        s += "__device__ constexpr CompCodec kSpecCodec[1] = {};\n}  // namespace qmpm\n";
+        s += "#include \"step_kernels.cuh\"\n";
+        return s;
+    }
     s += "__device__ constexpr CompCodec kSpecCodec[" + std::to_string(nc) + "] = {\n";
     for (int c = 0; c < nc; ++c) {
         const CompCodec &k = cc[c];
@@ -135,7 +142,7 @@ int entry(int dim, int material, bool stats, int W, bool dither, const CompCodec
           std::string &err)
 {
     const std::string src = kernel_source(dim, material, W, dither, cc, nc);
-    const std::string name = kernel_name(dim, material, stats);
+    const std::string name = kernel_name(dim, material, cc != nullptr, stats);
     const std::string key = name + "\n" + src;
     auto it = g_cache.find(key);
     if (it == g_cache.end()) {
@@ -155,7 +162,8 @@ int specialize_step_kernel(Ctx &c, std::string &err)
     const bool stats = (c.scene.flags & QMPM_FLAG_STATS) != 0;
     std::lock_guard<std::mutex> lk(g_mu);
     Compiled *e = nullptr;
-    int rc = entry(c.scene.dim, c.scene.material, stats, c.W, c.scene.dither != 0, c.cc, c.n_comp, e, err);
+    int rc = entry(c.scene.dim, c.scene.material, stats, c.W, c.scene.dither != 0, c.quant ? c.cc : nullptr,
+                   c.n_comp, e, err);
     if (rc != QMPM_OK) return rc;
     if (!e->kern) {
         cudaError_t r = cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);

@@ -15,25 +15,31 @@ namespace qmpm {
 // from their parameters (P.comp, in the constant bank): a component's word index, shift
 // and straddle are run-time values, so each component loads both of its words, computes
 // their addresses and ORs itself into the record with a shared-memory atomic.  A kernel
-// compiled at run time for one scheme (QMPM_SPECIALIZED_CODEC, jit.cpp) defines kSpecDim,
-// kSpecMat, kSpecWords and the table kSpecCodec before including this header; there the
-// decode reads fixed offsets (components that share a word share its load), the straddles
-// are known, and the encode assembles the record words in registers.
+// compiled at run time for one scene class (QMPM_SPECIALIZED_CODEC, jit.cpp) defines
+// kSpecDim, kSpecMat, kSpecQuant, kSpecWords, kSpecDither and, for quantized state, the
+// table kSpecCodec before including this header; there the decode reads fixed offsets
+// (components that share a word share its load), the straddles are known, the encode
+// assembles the record words in registers, and the loops over the record's words unroll.
 #ifndef QMPM_SPECIALIZED_CODEC
 constexpr int kSpecDim = 0, kSpecMat = -1, kSpecWords = 1;
-constexpr bool kSpecDither = false;
+constexpr bool kSpecQuant = false, kSpecDither = false;
 __device__ constexpr CompCodec kSpecCodec[1] = {};
 #endif
 
+// this instantiation is the one the run-time compilation specialises
 template <int DIM, int MAT, bool QUANT>
-constexpr bool specialized_codec() { return QUANT && DIM == kSpecDim && MAT == kSpecMat; }
+constexpr bool specialized() { return DIM == kSpecDim && MAT == kSpecMat && QUANT == kSpecQuant; }
+
+// ... and its state is quantized: the codec table is a set of constants
+template <int DIM, int MAT, bool QUANT>
+constexpr bool specialized_codec() { return QUANT && specialized<DIM, MAT, QUANT>(); }
 
 // The record's word count and whether the stores are dithered: compile-time constants in
 // the specialised kernel (its loops over the words unroll), the parameters otherwise.
 template <int DIM, int MAT, bool QUANT>
 __device__ __forceinline__ int words_of(const StepParams &P)
 {
-    if constexpr (specialized_codec<DIM, MAT, QUANT>())
+    if constexpr (specialized<DIM, MAT, QUANT>())
         return kSpecWords;
     else
         return P.n_words;
@@ -42,7 +48,7 @@ __device__ __forceinline__ int words_of(const StepParams &P)
 template <int DIM, int MAT, bool QUANT>
 __device__ __forceinline__ bool dithered(const StepParams &P)
 {
-    if constexpr (specialized_codec<DIM, MAT, QUANT>())
+    if constexpr (specialized<DIM, MAT, QUANT>())
         return kSpecDither;
     else
         return P.dither != 0;

@@ -423,7 +423,7 @@ def qmpm_step_host_stream(h, nsteps, h_words_ptr, chunks=0):
 def qmpm_specialize_compile(dim, material, scheme, stats=False, dither=True):
     """Compile (or find) the step kernel specialised to this scheme; no device needed.
     Returns (seconds of the first compile, cubin bytes)."""
-    sch = make_scheme_struct(scheme)
+    sch = make_scheme_struct(scheme)  # None: FP32 state
     sec, nb = ct.c_double(), ct.c_int64()
     _check(lib().qmpm_specialize_compile(int(dim), MATERIALS[material], ct.byref(sch), int(bool(stats)),
                                          int(bool(dither)), ct.byref(sec), ct.byref(nb)))

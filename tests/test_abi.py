@@ -168,8 +168,11 @@ def test_specialized_step_kernel_compiles_without_a_device(q):
 
 
 def test_specialize_compile_rejects_bad_input(q):
+    # FP32 state (no scheme) compiles the kernel with its word count as the constant
+    sec, nbytes = q.qmpm_specialize_compile(3, "corotated", None)
+    assert nbytes > 10000
     with pytest.raises(q.QmpmError) as ei:
-        q.qmpm_specialize_compile(3, "corotated", None)
+        q.qmpm_specialize_compile(4, "corotated", None)
     assert ei.value.code == -1
     with pytest.raises(q.QmpmError):
         q.qmpm_step_kernel_info(None)

@@ -99,10 +99,23 @@ def test_specialized_step_matches_the_library_kernel(q, oracle, case, dither):
     assert np.array_equal(ra["ids"], rb["ids"])
     d = np.abs(ra["state"] - rb["state"]) / quanta(oracle, sc, sch)[None]
     assert d.max() <= 1.0 + 1e-9 and (d > 0).mean() <= 1e-2, (d.max(), (d > 0).mean())
-    # FP32 state ignores the flag
+    # FP32 state: the kernel compiled with its word count as a constant gives the library
+    # kernel's state but for FP32 roundings of the grid sums
     c = q.Scene(sc, None, s0, specialize=True)
-    assert not q.qmpm_step_kernel_info(c.h)["specialized"]
-    for g in (a, b, c):
+    e = q.Scene(sc, None, s0)
+    assert q.qmpm_step_kernel_info(c.h)["specialized"] and not q.qmpm_step_kernel_info(e.h)["specialized"]
+    c.step(1)
+    e.step(1)
+    sc_, se = c.readback(state=True, ids=True), e.readback(state=True, ids=True)
+    assert np.array_equal(sc_["ids"], se["ids"])
+    # scale: each field's largest magnitude (x, v, C, F or J), so that the near-zero
+    # off-diagonal F of a rigid body is held to the rounding of F itself
+    d = sc["dim"]
+    bounds = [0, d, 2 * d, 2 * d + d * d, se["state"].shape[1]]
+    scale = np.concatenate([np.full(bounds[h + 1] - bounds[h], np.abs(se["state"][:, bounds[h]:bounds[h + 1]]).max())
+                            for h in range(4)])[None]
+    assert (np.abs(sc_["state"] - se["state"]) <= 1e-5 * (np.abs(se["state"]) + scale)).all()
+    for g in (a, b, c, e):
         g.close()
 
 
