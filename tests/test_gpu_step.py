@@ -108,12 +108,16 @@ def test_specialized_step_matches_the_library_kernel(q, oracle, case, dither):
     e.step(1)
     sc_, se = c.readback(state=True, ids=True), e.readback(state=True, ids=True)
     assert np.array_equal(sc_["ids"], se["ids"])
-    # scale: each field's largest magnitude (x, v, C, F or J), so that the near-zero
-    # off-diagonal F of a rigid body is held to the rounding of F itself
+    # scale: each field's natural magnitude (x: 1; v: its largest speed; C, a velocity
+    # gradient: n times that; F or J: its largest entry), so that the near-zero C and
+    # off-diagonal F of a nearly rigid body are held to the rounding of the fields
+    # they come from
     d = sc["dim"]
-    bounds = [0, d, 2 * d, 2 * d + d * d, se["state"].shape[1]]
-    scale = np.concatenate([np.full(bounds[h + 1] - bounds[h], np.abs(se["state"][:, bounds[h]:bounds[h + 1]]).max())
-                            for h in range(4)])[None]
+    st = se["state"]
+    vmax = np.abs(st[:, d:2 * d]).max() + 1e-3
+    widths = [d, d, d * d, st.shape[1] - 2 * d - d * d]
+    field = [1.0, vmax, (1 << sc["grid_log2"]) * vmax, np.abs(st[:, 2 * d + d * d:]).max()]
+    scale = np.concatenate([np.full(w, f) for w, f in zip(widths, field)])[None]
     assert (np.abs(sc_["state"] - se["state"]) <= 1e-5 * (np.abs(se["state"]) + scale)).all()
     for g in (a, b, c, e):
         g.close()
