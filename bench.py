@@ -936,7 +936,16 @@ def run_reference(args):
         print(json.dumps(line), flush=True)
         return
     import oracle
-    sc, s0, sch, desc = workload(args.workload, args.scale)
+    scheme = None
+    if args.workload == "cubes3d" and not args.fixed_scheme:
+        # our arm's scheme: the cached second-order scheme (solving it needs a device)
+        from paper_2207_04658_b300 import autoquant
+        cached = autoquant.load_cubes3d_scheme(0.01)
+        scheme = cached["scheme"] if cached is not None else None
+    sc, s0, sch, desc = workload(args.workload, args.scale, scheme=scheme)
+    if scheme is not None:
+        desc = dict(desc, scheme_source="cached: python -m paper_2207_04658_b300.autoquant cubes3d --eps 0.01 "
+                                        "(the scheme the GPU arm times)")
     n = {"cubes3d": 64_000, "dambreak3d": 64_000}.get(args.workload, s0.shape[0])
     sample = f"first {n} particles of the scene on its full grid, one quantized oracle step per step"
     ro = oracle.QuantRollout(sc, sch, s0[:n])
