@@ -81,10 +81,11 @@ def workload(name, scale=1.0, seed_offset=0, scheme=None):
     from paper_2207_04658_b300 import scenes
     if name == "cubes3d":
         n_cubes = max(1, int(round(16 * scale)))
-        # re-sort every 16 steps: the best period with margin over a 480-step run of this
-        # workload (ms per step, sort included: 1.152 at 12, 1.140 at 16, 1.134 at 20, 1.130
-        # at 24, 1.176 at 32, where particles start to leave their tiles)
-        sc, s0 = scenes.cubes3d_scene(n_cubes=n_cubes, seed=2 + seed_offset, resort_every=16)
+        # re-sort every 20 steps: the best period with margin over a 480-step run of this
+        # workload with the scheme-specialised step kernel (ms per step, sort included:
+        # 0.944 at 12, 0.933 at 16, 0.927 at 20, 0.922 at 24, 0.942 at 32, 1.247 at 48, where
+        # particles have left their tiles)
+        sc, s0 = scenes.cubes3d_scene(n_cubes=n_cubes, seed=2 + seed_offset, resort_every=20)
         sch = scheme if scheme is not None else scenes.fixed_scheme_3d("corotated")
         desc = {"workload": "3D fixed-corotated elastic cubes", "particles": int(s0.shape[0]),
                 "cubes": n_cubes, "grid": "256^3", "dt": sc["dt"], "E": sc["E"], "nu": sc["nu"],
