@@ -155,3 +155,51 @@ def test_fill_word_slack_keeps_words_and_resolution(q):
         assert q.make_scheme_struct(wider, 3, "corotated").n_words > words
     # 3 v components and 9 of C take the 13 free bits of the last word: one bit each
     assert (got["v"]["bits"], got["C"]["bits"], got["F"]["bits"]) == (5, 5, 11)
+
+
+def test_acceptance_loop_refines_until_the_bound_holds(monkeypatch):
+    # the acceptance check of the second-order scheme against a fake scene: the quantized
+    # run's position error scales with the velocity resolution, and C saturates while its
+    # window is narrower than 6 bits; the loop adds velocity fraction bits (the type with
+    # the largest predicted share) and widens C until both hold
+    import numpy as np
+    from paper_2207_04658_b300 import autoquant
+
+    class FakeScene:
+        def __init__(self, scene, scheme, state0, stats=False):
+            self.scheme, self.s0, self.seed = scheme, np.asarray(state0, float), scene.get("seed")
+
+        def step(self, n=1):
+            pass
+
+        def state_by_id(self):
+            if self.scheme is None:
+                return self.s0.copy()
+            err = 2.0 ** -self.scheme["v"]["frac"]
+            return self.s0 + err
+
+        def readback(self, state=False, ids=False):
+            sat = [0, 0, 5 if self.scheme["C"]["bits"] < 6 else 0, 0]
+            return {"stats": {"saturations": sat}}
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(autoquant.qmpm, "Scene", FakeScene)
+    names = ["x", "v", "C", "F"]
+    s0 = np.zeros((10, 24))
+    f = lambda bits, frac, off: {"bits": bits, "frac": frac, "offset": off, "container": 0}
+    scheme = {"x": f(16, 15, 0), "v": f(4, 2, -8), "C": f(4, -8, -8), "F": f(11, 7, -536)}
+    last = {"beta": [0.0] * 4, "g": [0.0, 1.0, 0.0, 0.0]}
+    out, hist = autoquant._accept({"dim": 3}, s0, 10, 0.5, 1.0, scheme, names, last, {}, None,
+                                  (None, 7), 6, None)
+    # error: sqrt(30) 2^-frac_v relative to z = 1: 1.37 at frac 2, 0.68 at 3, 0.34 at 4
+    assert [round(h["rel_err"], 2) for h in hist] == [1.37, 0.68, 0.34]
+    assert hist[0]["saturations"] == [0, 0, 10, 0] and hist[-1]["saturations"] == [0, 0, 0, 0]
+    assert out["v"]["frac"] == 4 and out["v"]["bits"] == 6 and out["v"]["offset"] == -32
+    assert out["C"]["frac"] == -8 and out["C"]["bits"] == 6 and out["C"]["offset"] == -8 - 8 - 16
+    assert out["x"] == scheme["x"] and out["F"] == scheme["F"]
+    # a bound that is already met returns the scheme after one check
+    out2, hist2 = autoquant._accept({"dim": 3}, s0, 10, 5.0, 1.0, dict(scheme, C=f(6, -8, -8)), names, last,
+                                    {}, None, (None,), 6, None)
+    assert len(hist2) == 1 and out2["v"] == scheme["v"]
