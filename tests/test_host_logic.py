@@ -203,3 +203,55 @@ def test_acceptance_loop_refines_until_the_bound_holds(monkeypatch):
     out2, hist2 = autoquant._accept({"dim": 3}, s0, 10, 5.0, 1.0, dict(scheme, C=f(6, -8, -8)), names, last,
                                     {}, None, (None,), 6, None)
     assert len(hist2) == 1 and out2["v"] == scheme["v"]
+
+
+def test_second_order_iteration_damps_floors_and_stops(monkeypatch, q):
+    # the second-order refinement against fake noise moments (no device): per field h,
+    # shift = (beta_h sigma_h^2)^2 and spread = g_h sigma_h^2, except that the velocity's
+    # runs blow up (non-finite moments) while its resolution is coarser than 2^-7.  Checks:
+    # every round moves a field by at most max_step bits; after the blow-up the velocity is
+    # held at or above its floor; the result meets the refined bound of the coefficients
+    import numpy as np
+    from paper_2207_04658_b300 import autoquant
+
+    class FakeScene:
+        def __init__(self, scene, scheme, state0, stats=False):
+            self.h = 1
+
+        def close(self):
+            pass
+
+    N = 1000
+    beta = [2e3, 5.0, 1e-9, 50.0]
+    g = [4e3, 20.0, 1e-10, 3e2]
+
+    def fake_moments(h, T, measure, sigma, seed0=1, n_pairs=16):
+        k = [i for i, s in enumerate(sigma) if s > 0][0]
+        s2 = sigma[k] ** 2 / 6.0
+        if k == 1 and sigma[k] > 2.0 ** -7:
+            return {"z0": 1.0 / N, "shift": float("nan"), "spread": float("nan")}
+        return {"z0": 1.0 / N, "shift": (beta[k] * s2) ** 2, "spread": g[k] * s2}
+
+    monkeypatch.setattr(autoquant.qmpm, "Scene", FakeScene)
+    monkeypatch.setattr(autoquant.qmpm, "qmpm_noise_moments", fake_moments)
+    info = {"P": [3.0 * N, 3.0 * N, 9.0 * N, 9.0 * N], "g": [1e3, 10.0, 1e-10, 1e2],
+            "lo": [0.1, -2.0, -50.0, -1.5], "hi": [0.9, 2.0, 50.0, 1.5], "z": 1.0}
+    scene = {"dim": 3, "material": "corotated"}
+    eps = 0.05
+    scheme, rep = autoquant.second_order_scheme(scene, np.zeros((N, 24)), 10, eps, info, iters=8, max_step=2,
+                                                accept_seeds=())
+    names = ["x", "v", "C", "F"]
+    rounds = rep["rounds"]
+    assert 1 <= len(rounds) <= 8
+    for r in rounds:
+        for n in names:
+            assert abs(r["next"][n]["frac"] - r["scheme"][n]["frac"]) <= 2
+    # the velocity blew up in the first round (Algorithm 1 left it at 2^-6) and is floored
+    # one bit finer for the rest of the iteration
+    assert rounds[0]["scheme"]["v"]["frac"] == 6 and rounds[0]["floor"]["v"] == 7
+    assert scheme["v"]["frac"] >= rounds[-1]["floor"]["v"]
+    # the result meets the second-order bound of the true coefficients (z^2 = N z0 = 1)
+    s2 = [2.0 ** (-2 * scheme[n]["frac"]) / 6.0 for n in names]
+    bias = sum(b * s for b, s in zip(beta, s2))
+    var = sum(gg * s for gg, s in zip(g, s2))
+    assert bias ** 2 + var <= eps ** 2 * 1.0001
