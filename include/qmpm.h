@@ -263,7 +263,8 @@ int qmpm_step_host_stream(qmpm_handle h, int32_t nsteps, uint32_t *h_words, int3
  * library's kernels).  The results are those of the library's kernel: the arithmetic is
  * the same.  Compiled kernels are kept for the life of the process, one per (dim,
  * material, state, statistics and dither flags, codec table); a first compile takes about
- * a second.  The kernel sources are read from the csrc/
+ * a second.  The loaded kernels do not survive a device reset (cudaDeviceReset): a process
+ * that resets the device must not ask for specialised kernels afterwards.  The kernel sources are read from the csrc/
  * directory beside the library file.
  *
  * qmpm_specialize_compile compiles (or finds) the kernel of a scheme without a device, for
