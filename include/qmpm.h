@@ -199,6 +199,36 @@ typedef struct {
  * scheme in the search window). */
 int qmpm_scheme_solve(const qmpm_solve_in_t *in, qmpm_solve_out_t *out);
 
+/* Edits of one type h (0 x, 1 v, 2 C, 3 F or J) of a quantized scheme, in place; the other
+ * types are kept.  They serve the second-order refinement of a solved scheme and its
+ * acceptance check (Sec. 4): a type's fixed point is its resolution 2^-frac and its window
+ * [offset 2^-frac, (offset + 2^bits - 1) 2^-frac] (Sec. 3.1).  Each fails without touching
+ * the scheme when the edited type would leave 1..24 bits or |offset| < 2^24
+ * (QMPM_ERR_SCHEME), or on a NULL or unquantized scheme or h out of 0..3
+ * (QMPM_ERR_INVALID_ARG).
+ *
+ * qmpm_scheme_shift: k fraction bits finer (k < 0: coarser) over the same window: bits and
+ *   frac + k, offset 2^k (rounded down).
+ * qmpm_scheme_widen: the window doubled about its middle at the same resolution: bits + 1,
+ *   offset - 2^(bits - 1).
+ * qmpm_scheme_window: the window set, at the type's resolution, to qmpm_scheme_solve's
+ *   window of the recorded range [lo, hi] (kappa times its width about its middle), widened
+ *   by gain 2^-frac[src] on each side (src < 0: no margin; the solve's window-margin
+ *   option); grow != 0 keeps the union with the current window.  offset = floor(lo'
+ *   2^frac), and the fewest bits that reach ceil(hi' 2^frac).  Also QMPM_ERR_INVALID_ARG
+ *   unless lo <= hi, kappa > 0, gain >= 0.
+ * qmpm_scheme_fill_words: the free bits of the last packed word (Sec. 7 bit pack) spent on
+ *   wider windows: each type in type_mask (bit h) in turn has its window doubled while the
+ *   layout for (dim, material) keeps its word count and the type stays within 24 bits,
+ *   until none fits; *widened (may be NULL) receives the number of doublings.  Layout
+ *   errors as qmpm_scheme_layout. */
+int qmpm_scheme_shift(qmpm_scheme_t *scheme, int32_t h, int32_t k);
+int qmpm_scheme_widen(qmpm_scheme_t *scheme, int32_t h);
+int qmpm_scheme_window(qmpm_scheme_t *scheme, int32_t h, double lo, double hi, double kappa, int32_t src,
+                       double gain, int32_t grow);
+int qmpm_scheme_fill_words(int32_t dim, int32_t material, qmpm_scheme_t *scheme, int32_t type_mask,
+                           int32_t *widened);
+
 /* ---- simulation --------------------------------------------------------------- */
 
 /* Create a scene on the current CUDA device.  h_state: the initial state (host, see the

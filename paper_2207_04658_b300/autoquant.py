@@ -73,75 +73,24 @@ def cubes3d_scheme(eps=0.01, T=None, samples=2, ckpt_every=32, material="corotat
     return scheme, {"solve": res, "sensitivities": info}
 
 
-def _shift_frac(field, k):
-    """A field's scheme k fraction bits finer (k < 0: coarser) over the same window."""
-    f = dict(field)
-    f["bits"], f["frac"] = f["bits"] + k, f["frac"] + k
-    f["offset"] = f["offset"] << k if k >= 0 else f["offset"] >> -k
-    return f
-
-
-def _rewindow(field, lo, hi):
-    """A field's scheme at its own resolution over the window [lo, hi] (the bits and offset
-    the solve gives a window: offset floor(lo 2^frac), enough bits for ceil(hi 2^frac))."""
-    import math
-    f = dict(field)
-    k = f["frac"]
-    L = math.floor(math.ldexp(lo, k))
-    need = math.ceil(math.ldexp(hi, k)) - L + 1
-    n = 1
-    while n < 64 and 2 ** n < need:
-        n += 1
-    f["bits"], f["offset"] = n, int(L)
-    return f
-
-
-def _margin_windows(scheme, names, info, margins, kappa=2.0, grow_only=False):
-    """The windows of the types in margins = {h: (src, gain)} widened by gain Delta_src on
-    each side, Delta_src the resolution of type src in this scheme (the solve's window
+def _margin_windows(scheme, material, info, margins, kappa=2.0, grow_only=False):
+    """The windows of the types in margins = {h: (src, gain)} re-derived at their current
+    resolution by qmpm_scheme_window: the solve's window of the recorded range [lo_h,
+    hi_h] widened by gain times the resolution of type src (the solve's window-margin
     option, here applied after every change of resolution); grow_only keeps the union with
     the type's current window."""
-    out = dict(scheme)
     for h, (src, gain) in (margins or {}).items():
-        f = scheme[names[h]]
-        mid = 0.5 * (info["lo"][h] + info["hi"][h])
-        half = 0.5 * kappa * (info["hi"][h] - info["lo"][h])
-        m = gain * 2.0 ** -scheme[names[src]]["frac"]
-        lo, hi = mid - half - m, mid + half + m
-        if grow_only:
-            q = 2.0 ** -f["frac"]
-            lo, hi = min(lo, f["offset"] * q), max(hi, (f["offset"] + (1 << f["bits"]) - 1) * q)
-        out[names[h]] = _rewindow(f, lo, hi)
-    return out
-
-
-def _widened(field):
-    """A field's scheme with its window doubled about its middle at the same resolution."""
-    f = dict(field)
-    f["offset"] -= 1 << (f["bits"] - 1)
-    f["bits"] += 1
-    return f
+        scheme = qmpm.scheme_window(scheme, material, h, info["lo"][h], info["hi"][h], kappa, src, gain, grow_only)
+    return scheme
 
 
 def fill_word_slack(scheme, dim, material, types=("v", "C", "F", "J")):
-    """Spend the unused bits of the last packed word on wider windows: each of the given
-    types in turn gets its window doubled (one more bit, same resolution) while the packed
-    layout keeps its number of words, until none fits.  A dithered run's values spread
-    past the full-precision run's ranges (the noise of the stores feeds back through the
-    grid), and this headroom costs no memory traffic."""
-    words = qmpm.make_scheme_struct(scheme, dim, material).n_words
-    out = dict(scheme)
-    grew = True
-    while grew:
-        grew = False
-        for n in types:
-            if n not in out or out[n]["bits"] >= 24:
-                continue
-            trial = dict(out, **{n: _widened(out[n])})
-            if qmpm.make_scheme_struct(trial, dim, material).n_words == words:
-                out = trial
-                grew = True
-    return out
+    """Spend the unused bits of the last packed word on wider windows
+    (qmpm_scheme_fill_words): each of the given types in turn gets its window doubled (one
+    more bit, same resolution) while the packed layout keeps its number of words, until none
+    fits.  A dithered run's values spread past the full-precision run's ranges (the noise of
+    the stores feeds back through the grid), and this headroom costs no memory traffic."""
+    return qmpm.scheme_fill_words(scheme, dim, material, types)[0]
 
 
 def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=8, max_step=2, containers=(0, 0, 0, 0),
@@ -212,7 +161,7 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=8, max_step=
             sol = dict(info, g=geff, P=P, z=z)
             want, res = qmpm.solve_scheme(sol, eps, containers=containers, material=material, beta=beta,
                                           margins=margins)
-            nxt = {}
+            nxt = dict(scheme)
             for n in names:
                 # the current window, the resolution moved toward the solve's (not below the
                 # field's floor) by at most max_step bits, and never past the 24 bits FP32
@@ -221,8 +170,8 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=8, max_step=
                 k = max(-max_step, min(max_step, target - scheme[n]["frac"]))
                 k = min(k, 24 - scheme[n]["bits"])
                 k = max(k, 1 - scheme[n]["bits"])
-                nxt[n] = _shift_frac(scheme[n], k)
-            nxt = _margin_windows(nxt, names, info, margins)
+                nxt = qmpm.scheme_shift(nxt, material, n, k)
+            nxt = _margin_windows(nxt, material, info, margins)
             rounds.append({"scheme": scheme, "sigma": sig, "moments": mom, "beta": beta, "g": geff, "solve": want,
                            "next": nxt, "pred_bias": res["pred_bias"], "pred_var": res["pred_var_dither"],
                            "floor": dict(floor)})
@@ -236,7 +185,7 @@ def second_order_scheme(scene, state0, T, eps, info, pairs=2, iters=8, max_step=
                 break
         if prev is not None and scheme != prev:
             scheme = {n: (scheme[n] if scheme[n]["frac"] >= prev[n]["frac"] else prev[n]) for n in names}
-            scheme = _margin_windows(scheme, names, info, margins)
+            scheme = _margin_windows(scheme, material, info, margins)
     finally:
         g.close()
     last = rounds[-1] if rounds else None
@@ -259,6 +208,7 @@ def _accept(scene, state0, T, eps, z, scheme, names, last, info, margins, seeds,
     Returns (scheme, history)."""
     import numpy as np
     dim = scene["dim"]
+    material = scene["material"]
     history = []
     if not seeds or max_rounds <= 0 or z is None:
         return scheme, history
@@ -287,7 +237,7 @@ def _accept(scene, state0, T, eps, z, scheme, names, last, info, margins, seeds,
         nxt = dict(scheme)
         for h, n in enumerate(names):
             if sat[h] > 0:
-                nxt[n] = _widened(nxt[n])
+                nxt = qmpm.scheme_widen(nxt, material, n)
         if rel > eps:
             sig2 = [2.0 ** (-2 * scheme[n]["frac"]) / 6.0 for n in names]
             beta = last["beta"] if last else [0.0] * 4
@@ -296,8 +246,8 @@ def _accept(scene, state0, T, eps, z, scheme, names, last, info, margins, seeds,
             share = [beta[h] * sig2[h] * B + gg[h] * sig2[h] if scheme[names[h]]["bits"] < 24 else -1.0
                      for h in range(4)]
             h = int(np.argmax(share))
-            nxt[names[h]] = _shift_frac(nxt[names[h]], 1)
-        scheme = _margin_windows(nxt, names, info, margins, grow_only=True)
+            nxt = qmpm.scheme_shift(nxt, material, names[h], 1)
+        scheme = _margin_windows(nxt, material, info, margins, grow_only=True)
     return scheme, history
 
 

@@ -11,6 +11,12 @@
 #include "qmpm_internal.h"
 
 extern "C" int qmpm_scheme_solve_impl(const qmpm_solve_in_t *in, qmpm_solve_out_t *out, std::string &err);
+extern "C" int qmpm_scheme_shift_impl(qmpm_scheme_t *s, int32_t h, int32_t k, std::string &err);
+extern "C" int qmpm_scheme_widen_impl(qmpm_scheme_t *s, int32_t h, std::string &err);
+extern "C" int qmpm_scheme_window_impl(qmpm_scheme_t *s, int32_t h, double lo, double hi, double kappa,
+                                       int32_t src, double gain, int32_t grow, std::string &err);
+extern "C" int qmpm_scheme_fill_words_impl(int32_t dim, int32_t material, qmpm_scheme_t *s, int32_t type_mask,
+                                           int32_t *widened, std::string &err);
 
 namespace {
 
@@ -271,6 +277,36 @@ int qmpm_scheme_solve(const qmpm_solve_in_t *in, qmpm_solve_out_t *out)
     const int rc = qmpm_scheme_solve_impl(in, out, err);
     if (rc != QMPM_OK) return fail(rc, err);
     return QMPM_OK;
+}
+
+int qmpm_scheme_shift(qmpm_scheme_t *scheme, int32_t h, int32_t k)
+{
+    std::string err;
+    const int rc = qmpm_scheme_shift_impl(scheme, h, k, err);
+    return rc == QMPM_OK ? QMPM_OK : fail(rc, err);
+}
+
+int qmpm_scheme_widen(qmpm_scheme_t *scheme, int32_t h)
+{
+    std::string err;
+    const int rc = qmpm_scheme_widen_impl(scheme, h, err);
+    return rc == QMPM_OK ? QMPM_OK : fail(rc, err);
+}
+
+int qmpm_scheme_window(qmpm_scheme_t *scheme, int32_t h, double lo, double hi, double kappa, int32_t src,
+                       double gain, int32_t grow)
+{
+    std::string err;
+    const int rc = qmpm_scheme_window_impl(scheme, h, lo, hi, kappa, src, gain, grow, err);
+    return rc == QMPM_OK ? QMPM_OK : fail(rc, err);
+}
+
+int qmpm_scheme_fill_words(int32_t dim, int32_t material, qmpm_scheme_t *scheme, int32_t type_mask,
+                           int32_t *widened)
+{
+    std::string err;
+    const int rc = qmpm_scheme_fill_words_impl(dim, material, scheme, type_mask, widened, err);
+    return rc == QMPM_OK ? QMPM_OK : fail(rc, err);
 }
 
 int qmpm_init(const qmpm_scene_t *scene, const qmpm_scheme_t *scheme, const double *h_state, void *stream,

@@ -435,3 +435,120 @@ extern "C" int qmpm_scheme_solve_impl(const qmpm_solve_in_t *in, qmpm_solve_out_
     moments(frac, out->pred_bias, out->pred_var_dither);
     return QMPM_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// Edits of one type of a scheme (the second-order refinement and its acceptance check).
+// A type's fixed point is its resolution 2^-frac and its window [offset 2^-frac,
+// (offset + 2^bits - 1) 2^-frac] (Sec. 3.1); each edit keeps the other types.
+// ---------------------------------------------------------------------------------
+namespace {
+
+int edit_check(const qmpm_scheme_t *s, int h, const char *what, std::string &err)
+{
+    if (!s || !s->quantized) {
+        err = std::string(what) + ": no quantized scheme";
+        return QMPM_ERR_INVALID_ARG;
+    }
+    if (h < 0 || h > 3) {
+        err = std::string(what) + ": type index out of 0..3";
+        return QMPM_ERR_INVALID_ARG;
+    }
+    return QMPM_OK;
+}
+
+int field_check(const qmpm_field_t &f, const char *what, std::string &err)
+{
+    if (f.bits < 1 || f.bits > 24 || f.offset <= -(int64_t(1) << 24) || f.offset >= (int64_t(1) << 24)) {
+        err = std::string(what) + ": the edited type leaves 1..24 bits or |offset| < 2^24";
+        return QMPM_ERR_SCHEME;
+    }
+    return QMPM_OK;
+}
+
+}  // namespace
+
+extern "C" int qmpm_scheme_shift_impl(qmpm_scheme_t *s, int32_t h, int32_t k, std::string &err)
+{
+    int rc = edit_check(s, h, "qmpm_scheme_shift", err);
+    if (rc != QMPM_OK) return rc;
+    qmpm_field_t f = s->field[h];
+    f.bits += k;
+    f.frac += k;
+    f.offset = k >= 0 ? f.offset * (int64_t(1) << std::min(k, 40)) : qmpm::floor_shift(f.offset, -k);
+    rc = field_check(f, "qmpm_scheme_shift", err);
+    if (rc != QMPM_OK) return rc;
+    s->field[h] = f;
+    return QMPM_OK;
+}
+
+extern "C" int qmpm_scheme_widen_impl(qmpm_scheme_t *s, int32_t h, std::string &err)
+{
+    int rc = edit_check(s, h, "qmpm_scheme_widen", err);
+    if (rc != QMPM_OK) return rc;
+    qmpm_field_t f = s->field[h];
+    f.offset -= int64_t(1) << (f.bits - 1);
+    f.bits += 1;
+    rc = field_check(f, "qmpm_scheme_widen", err);
+    if (rc != QMPM_OK) return rc;
+    s->field[h] = f;
+    return QMPM_OK;
+}
+
+extern "C" int qmpm_scheme_window_impl(qmpm_scheme_t *s, int32_t h, double lo, double hi, double kappa,
+                                       int32_t src, double gain, int32_t grow, std::string &err)
+{
+    int rc = edit_check(s, h, "qmpm_scheme_window", err);
+    if (rc != QMPM_OK) return rc;
+    if (!(lo <= hi) || !(kappa > 0.0) || !(gain >= 0.0) || src > 3) {
+        err = "qmpm_scheme_window: need lo <= hi, kappa > 0, gain >= 0, src < 4";
+        return QMPM_ERR_INVALID_ARG;
+    }
+    qmpm_field_t f = s->field[h];
+    // the solve's window of the recorded range, widened by the margin (its option 3)
+    const double mid = 0.5 * (lo + hi);
+    double R = kappa * (hi - lo);
+    if (!(R > 0.0)) R = std::ldexp(1.0, -30);
+    const double m = src >= 0 ? gain * std::ldexp(1.0, -s->field[src].frac) : 0.0;
+    qmpm::Window w{mid - 0.5 * R - m, mid + 0.5 * R + m, R + 2.0 * m};
+    if (grow) {
+        w.lo = std::min(w.lo, std::ldexp((double)f.offset, -f.frac));
+        w.hi = std::max(w.hi, std::ldexp((double)(f.offset + (int64_t(1) << f.bits) - 1), -f.frac));
+        w.R = w.hi - w.lo;
+    }
+    f.offset = (int64_t)std::floor(std::ldexp(w.lo, f.frac));
+    f.bits = qmpm::bits_at(f.frac, w);
+    rc = field_check(f, "qmpm_scheme_window", err);
+    if (rc != QMPM_OK) return rc;
+    s->field[h] = f;
+    return QMPM_OK;
+}
+
+extern "C" int qmpm_scheme_fill_words_impl(int32_t dim, int32_t material, qmpm_scheme_t *s, int32_t type_mask,
+                                           int32_t *widened, std::string &err)
+{
+    if (!s || !s->quantized) {
+        err = "qmpm_scheme_fill_words: no quantized scheme";
+        return QMPM_ERR_INVALID_ARG;
+    }
+    qmpm_scheme_t cur = *s;
+    int rc = qmpm::layout(dim, material, &cur, err);
+    if (rc != QMPM_OK) return rc;
+    const int32_t words = cur.n_words;
+    int n = 0;
+    for (bool grew = true; grew;) {
+        grew = false;
+        for (int h = 0; h < 4; ++h) {
+            if (!(type_mask >> h & 1) || cur.field[h].bits >= 24) continue;
+            qmpm_scheme_t trial = cur;
+            std::string e2;
+            if (qmpm_scheme_widen_impl(&trial, h, e2) != QMPM_OK) continue;
+            if (qmpm::layout(dim, material, &trial, e2) != QMPM_OK || trial.n_words != words) continue;
+            cur = trial;
+            grew = true;
+            ++n;
+        }
+    }
+    *s = cur;
+    if (widened) *widened = n;
+    return QMPM_OK;
+}

@@ -204,6 +204,12 @@ _SIGNATURES = [
     ("qmpm_measure", ct.c_int, [ct.c_void_p, _P(ct.c_double)]),
     ("qmpm_step_host", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     ("qmpm_step_host_stream", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
+    ("qmpm_scheme_shift", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32]),
+    ("qmpm_scheme_widen", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("qmpm_scheme_window", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_double, ct.c_double, ct.c_double,
+                                      ct.c_int32, ct.c_double, ct.c_int32]),
+    ("qmpm_scheme_fill_words", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32,
+                                          ct.POINTER(ct.c_int32)]),
     ("qmpm_specialize_compile", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_int32,
                                            ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
     ("qmpm_step_kernel_info", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double)]),
@@ -665,6 +671,57 @@ def sensitivities(scene, state0, T, ckpt_every=32, measure=MEASURE_MEAN_SQ_POS):
     info = qmpm_adjoint(g.h, T, ckpt_every, measure)
     g.close()
     return info
+
+
+def _type_names(material):
+    return ["x", "v", "C", "J" if material == "fluid" else "F"]
+
+
+def _scheme_dict(st, scheme, material):
+    names = _type_names(material)
+    return {names[h]: dict(bits=int(st.field[h].bits), frac=int(st.field[h].frac), offset=int(st.field[h].offset),
+                           container=int(scheme[names[h]].get("container", 0))) for h in range(4)}
+
+
+def _type_index(material, t):
+    return t if isinstance(t, int) else _type_names(material).index(t)
+
+
+def scheme_shift(scheme, material, t, k):
+    """Type t (name or index) k fraction bits finer (k < 0: coarser) over the same window
+    (qmpm_scheme_shift); returns the new scheme dict."""
+    st = make_scheme_struct(scheme)
+    _check(lib().qmpm_scheme_shift(ct.byref(st), _type_index(material, t), int(k)))
+    return _scheme_dict(st, scheme, material)
+
+
+def scheme_widen(scheme, material, t):
+    """Type t's window doubled about its middle at the same resolution (qmpm_scheme_widen)."""
+    st = make_scheme_struct(scheme)
+    _check(lib().qmpm_scheme_widen(ct.byref(st), _type_index(material, t)))
+    return _scheme_dict(st, scheme, material)
+
+
+def scheme_window(scheme, material, t, lo, hi, kappa=2.0, src=-1, gain=0.0, grow=False):
+    """Type t's window from the recorded range [lo, hi] as qmpm_scheme_solve makes it, widened
+    by gain x the resolution of type src (qmpm_scheme_window); grow keeps the union."""
+    st = make_scheme_struct(scheme)
+    _check(lib().qmpm_scheme_window(ct.byref(st), _type_index(material, t), float(lo), float(hi), float(kappa),
+                                    _type_index(material, src) if src != -1 else -1, float(gain), int(bool(grow))))
+    return _scheme_dict(st, scheme, material)
+
+
+def scheme_fill_words(scheme, dim, material, types):
+    """The last packed word's free bits spent on wider windows of the given types
+    (qmpm_scheme_fill_words); returns (scheme dict, number of doublings)."""
+    st = make_scheme_struct(scheme)
+    mask = 0
+    for t in types:
+        if t in _type_names(material) or isinstance(t, int):
+            mask |= 1 << _type_index(material, t)
+    n = ct.c_int32()
+    _check(lib().qmpm_scheme_fill_words(int(dim), MATERIALS[material], ct.byref(st), mask, ct.byref(n)))
+    return _scheme_dict(st, scheme, material), n.value
 
 
 def solve_scheme(info, eps, mode="error", rounding="paper", kappa=2.0, containers=(0, 0, 0, 0),

@@ -122,15 +122,15 @@ def test_margin_windows_match_the_solve(q):
         plain, _ = q.solve_scheme(info, eps, material="corotated")
         wide, _ = q.solve_scheme(info, eps, material="corotated", margins=margins)
         assert wide["C"]["frac"] == plain["C"]["frac"]
-        got = autoquant._margin_windows(plain, names, info, margins)
+        got = autoquant._margin_windows(plain, "corotated", info, margins)
         assert got["C"] == wide["C"] and got["x"] == plain["x"]
         # grow_only keeps a wider current window, and the new one holds the old
         big = dict(wide, C=dict(wide["C"], bits=wide["C"]["bits"] + 1,
                                 offset=wide["C"]["offset"] - (1 << (wide["C"]["bits"] - 1))))
-        kept = autoquant._margin_windows(big, names, info, margins, grow_only=True)
+        kept = autoquant._margin_windows(big, "corotated", info, margins, grow_only=True)
         assert kept["C"] == big["C"]
-        finer = autoquant._shift_frac(wide["C"], 1)
-        grown = autoquant._margin_windows(dict(wide, C=finer), names, info, margins, grow_only=True)
+        finer = q.scheme_shift(wide, "corotated", "C", 1)["C"]
+        grown = autoquant._margin_windows(dict(wide, C=finer), "corotated", info, margins, grow_only=True)
         d = 2.0 ** -finer["frac"]
         assert grown["C"]["offset"] * d <= finer["offset"] * d
         assert (grown["C"]["offset"] + 2 ** grown["C"]["bits"] - 1) * d >= (finer["offset"] + 2 ** finer["bits"] - 1) * d
@@ -151,7 +151,7 @@ def test_fill_word_slack_keeps_words_and_resolution(q):
         assert a["frac"] == b["frac"] and b["bits"] >= a["bits"]
         assert b["offset"] <= a["offset"] and b["offset"] + 2 ** b["bits"] >= a["offset"] + 2 ** a["bits"]
         # no type can take one more window bit without another word
-        wider = dict(got, **{n: autoquant._widened(got[n])})
+        wider = q.scheme_widen(got, "corotated", n)
         assert q.make_scheme_struct(wider, 3, "corotated").n_words > words
     # 3 v components and 9 of C take the 13 free bits of the last word: one bit each
     assert (got["v"]["bits"], got["C"]["bits"], got["F"]["bits"]) == (5, 5, 11)
@@ -191,7 +191,7 @@ def test_acceptance_loop_refines_until_the_bound_holds(monkeypatch):
     f = lambda bits, frac, off: {"bits": bits, "frac": frac, "offset": off, "container": 0}
     scheme = {"x": f(16, 15, 0), "v": f(4, 2, -8), "C": f(4, -8, -8), "F": f(11, 7, -536)}
     last = {"beta": [0.0] * 4, "g": [0.0, 1.0, 0.0, 0.0]}
-    out, hist = autoquant._accept({"dim": 3}, s0, 10, 0.5, 1.0, scheme, names, last, {}, None,
+    out, hist = autoquant._accept({"dim": 3, "material": "corotated"}, s0, 10, 0.5, 1.0, scheme, names, last, {}, None,
                                   (None, 7), 6, None)
     # error: sqrt(30) 2^-frac_v relative to z = 1: 1.37 at frac 2, 0.68 at 3, 0.34 at 4
     assert [round(h["rel_err"], 2) for h in hist] == [1.37, 0.68, 0.34]
@@ -200,7 +200,7 @@ def test_acceptance_loop_refines_until_the_bound_holds(monkeypatch):
     assert out["C"]["frac"] == -8 and out["C"]["bits"] == 6 and out["C"]["offset"] == -8 - 8 - 16
     assert out["x"] == scheme["x"] and out["F"] == scheme["F"]
     # a bound that is already met returns the scheme after one check
-    out2, hist2 = autoquant._accept({"dim": 3}, s0, 10, 5.0, 1.0, dict(scheme, C=f(6, -8, -8)), names, last,
+    out2, hist2 = autoquant._accept({"dim": 3, "material": "corotated"}, s0, 10, 5.0, 1.0, dict(scheme, C=f(6, -8, -8)), names, last,
                                     {}, None, (None,), 6, None)
     assert len(hist2) == 1 and out2["v"] == scheme["v"]
 
@@ -255,3 +255,27 @@ def test_second_order_iteration_damps_floors_and_stops(monkeypatch, q):
     bias = sum(b * s for b, s in zip(beta, s2))
     var = sum(gg * s for gg, s in zip(g, s2))
     assert bias ** 2 + var <= eps ** 2 * 1.0001
+
+
+def test_scheme_edits_through_the_abi(q):
+    # the edits of one type of a scheme (qmpm_scheme_shift / widen / window / fill_words):
+    # exact integer results, the other types kept, and the refusals
+    f = lambda b, fr, o, c=0: {"bits": b, "frac": fr, "offset": o, "container": c}
+    sch = {"x": f(16, 15, -9688, 64), "v": f(4, -2, -7), "C": f(4, -11, -7), "F": f(11, 7, -536)}
+    s2 = q.scheme_shift(sch, "corotated", "v", 2)
+    assert s2["v"] == f(6, 0, -28) and {k: s2[k] for k in "xCF"} == {k: sch[k] for k in "xCF"}
+    assert q.scheme_shift(sch, "corotated", "v", -1)["v"] == f(3, -3, -4)  # floor(-7 / 2)
+    assert q.scheme_widen(sch, "corotated", "C")["C"] == f(5, -11, -15)
+    # the window of the solve for [-2, 2] (kappa 2: [-4, 4]) at resolution 2^-frac = 4
+    assert q.scheme_window(sch, "corotated", "v", -2.0, 2.0)["v"] == f(2, -2, -1)
+    # a margin of 3 resolutions of v (Delta_v = 4) on each side: [-16, 16]
+    assert q.scheme_window(sch, "corotated", "v", -2.0, 2.0, 2.0, "v", 3.0)["v"] == f(4, -2, -4)
+    filled, n = q.scheme_fill_words(sch, 3, "corotated", ("v", "C", "F"))
+    assert n == 2 and filled["x"] == sch["x"]
+    assert q.scheme_fill_words(sch, 3, "corotated", ())[1] == 0
+    with pytest.raises(q.QmpmError) as ei:
+        q.scheme_shift(sch, "corotated", "F", 14)  # 25 bits
+    assert ei.value.code == -3
+    with pytest.raises(q.QmpmError) as ei:
+        q.scheme_window(sch, "corotated", "v", 2.0, -2.0)
+    assert ei.value.code == -1
