@@ -111,13 +111,12 @@ def _rollouts(scene, state0, T, scheme, runs, seed0, dither=True, stats=False):
     return np.asarray(zs), ups, dns
 
 
-def shift_bits(field, k):
-    """A field's scheme with k fewer bits (k < 0: more) over the same window: the resolution
-    doubles per bit taken."""
-    f = dict(field)
-    f["bits"], f["frac"] = f["bits"] - k, f["frac"] - k
-    f["offset"] = f["offset"] >> k if k >= 0 else f["offset"] << -k
-    return f
+def shift_bits(scheme, material, names, k):
+    """The scheme with k fewer bits (k < 0: more) for each type in names, each over its same
+    window (qmpm_scheme_shift by -k): the resolution doubles per bit taken."""
+    for n in names:
+        scheme = qmpm.scheme_shift(scheme, material, n, -k)
+    return scheme
 
 
 def optimality_check(scene, state0, T, z_ref, eps=0.01, runs=20, takes=(1, 2, 3), move_runs=10, seed=7,
@@ -137,16 +136,16 @@ def optimality_check(scene, state0, T, z_ref, eps=0.01, runs=20, takes=(1, 2, 3)
                 "z_mean": float(zs.mean()), "z_std": float(zs.std(ddof=1)) if n > 1 else 0.0,
                 "obs_rms": float(np.sqrt(np.mean(dev ** 2)))}
 
+    mat = scene["material"]
     out = {"eps": eps, "fields": names, "base": trial(base, runs), "reduce_all": {}, "reduce_half": {}, "move": {}}
     for k in takes:
-        out["reduce_all"][k] = trial({f: shift_bits(base[f], k) if base[f]["bits"] > k else base[f] for f in names}, runs)
+        out["reduce_all"][k] = trial(shift_bits(base, mat, [f for f in names if base[f]["bits"] > k], k), runs)
         half = set(gen.choice(names, size=len(names) // 2, replace=False).tolist())
-        red = {f: shift_bits(base[f], k) if f in half and base[f]["bits"] > k else base[f] for f in names}
+        red = shift_bits(base, mat, [f for f in names if f in half and base[f]["bits"] > k], k)
         out["reduce_half"][k] = dict(trial(red, runs), fields_reduced=sorted(half))
     pairs = [(names[0], names[1]), (names[1], names[0]), (names[2], names[3]), (names[3], names[2])]
     for a, b in pairs:
-        moved = dict(base)
-        moved[a], moved[b] = shift_bits(base[a], 1), shift_bits(base[b], -1)
+        moved = shift_bits(shift_bits(base, mat, [a], 1), mat, [b], -1)
         out["move"][f"{a}->{b}"] = trial(moved, move_runs)
     return out
 
